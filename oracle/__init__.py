@@ -1,0 +1,17 @@
+"""FP64 CPU oracle (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` import this package. The CUDA library never calls it.
+"""
+from .oracle import (  # noqa: F401
+    build,
+    verify,
+    eval_point,
+    forward,
+    pair_coverage,
+    ss_covered_fraction,
+    space_size,
+    digits,
+    mask_words,
+    TAU,
+)
