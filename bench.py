@@ -1,0 +1,305 @@
+"""Benchmark: verified perturbation points per second on the 784-512-512-10 ReLU
+workload (s = 6 pixels, k = 7, 15^6 = 11,390,625 points per query).
+
+One step = one full verification of a query (prologue, screen over every point,
+rechecks, FP64 pass, coverage and verdict). `value` is measured with the query
+already in device memory (vbmc_verify_query_device, CUDA events on the
+launching stream); `e2e` through vbmc_verify_query with host buffers plus the
+device-to-host copies of the verdict bitmap and coverage masks.
+
+Multi-GPU: each rank verifies its own query of the same net (independent
+problems, no collective on the data path): weak scaling.
+
+--impl reference times the FP64 CPU oracle (the slow reference program) on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "mlp784x512x512_relu_s6k7"
+METRIC = "verified perturbation points/sec"
+UNIT = "points/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default=os.environ.get("VBMC_BENCH_PRECISION", "bf16"))
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def rank_query(w, rank):
+    cfg = w["cfg"]
+    if rank == 0:
+        return w["query"]
+    return synth.make_query(cfg["seed"], rank, cfg["dims"][0], cfg["s"], cfg["k"])
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def oracle_rate(net, q, seconds):
+    """Oracle points/s on a contiguous sample of the workload (all host cores)."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    n = oracle.space_size(len(q["pixels"]), q["k"])
+    probe = min(n, 64 * cores)
+    t0 = time.perf_counter()
+    oracle.verify(net, q, lo=0, hi=probe, bitmap=False)
+    dt = time.perf_counter() - t0
+    m = int(min(n, max(probe, probe * seconds / max(dt, 1e-6))))
+    lo = (n - m) // 2
+    t0 = time.perf_counter()
+    oracle.verify(net, q, lo=lo, hi=lo + m, bitmap=False)
+    dt = time.perf_counter() - t0
+    return m / dt, cores, f"points [{lo}, {lo + m}) of query 0 ({m} of {n}), coverage on"
+
+
+# ------------------------------------------------------------------- clocks
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self, device_index=0):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9 or not parts[0].isdigit() or int(parts[0]) != device_index:
+                continue
+            rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------ roofline inputs
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+def screen_flops_per_point(dims, s):
+    """Algorithmic FLOPs of the screen per point: 2 * sum_{l>=2} H_{l-1} H_l
+    (dense layers) + s * H_1 table adds (incremental layer 1)."""
+    dense = sum(dims[l - 1] * dims[l] for l in range(2, len(dims)))
+    return 2 * dense + s * dims[1]
+
+
+def launches_per_step(precision, L):
+    pro = 1 + L + 1 + 1  # init, L base layers, tables, finish
+    if precision == "fp64":
+        return pro + 1
+    if precision == "fp32":
+        return pro + 2  # screen, FP64 pass
+    return pro + 4  # tensor screen, tensor 3x pass, FP32 pass, FP64 pass
+
+
+# -------------------------------------------------------------------- main
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    w = synth.workload(a.workload)
+    net_d, cfg = w["net"], w["cfg"]
+    q = rank_query(w, rank)
+    s, k = len(q["pixels"]), q["k"]
+    n_pts = (2 * k + 1) ** s
+
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        rate, cores, sample = oracle_rate(net_d, q, a.cpu_seconds * max(1, a.steps) / 10.0)
+        line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT,
+                "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+                "ms_per_step": 1000.0 * n_pts / rate, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": a.workload, "dims": cfg["dims"], "s": s, "k": k,
+                           "points_per_query": n_pts, "parallelism": "host threads"},
+                "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample,
+                                 "value": rate, "unit": UNIT},
+                "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl")
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    else:
+        torch.cuda.set_device(0)
+    import paper_1907_12933_gb300 as vb
+    from paper_1907_12933_gb300 import build
+    build.build()
+
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream()
+    vnet = vb.Net(net_d)
+    res = vb.Result(vnet, max_points=n_pts, max_s=s, max_k=k, ties_cap=1 << 16,
+                    queue_cap=n_pts)
+    d_img = torch.tensor(q["image"], dtype=torch.uint8, device=dev)
+    d_pix = torch.tensor(q["pixels"], dtype=torch.int32, device=dev)
+    flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # ---- device-resident steps (value)
+    for _ in range(a.warmup):
+        vb.verify_query_device(vnet, res, d_img, d_pix, k, precision=a.precision)
+        vb.result_summary(res)
+    clocks = Clocks()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(a.steps)]
+    screen_ms, sums = [], []
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    for i in range(a.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        vb.verify_query_device(vnet, res, d_img, d_pix, k, precision=a.precision)
+        ev[i][1].record(stream)
+        sm = vb.result_summary(res)
+        screen_ms.append(sm["ms_screen"])
+        sums.append(sm)
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - t_wall
+    ck = clocks.stop(torch.cuda.current_device())
+    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    ms = sum(step_ms) / len(step_ms)
+    t_local = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms_max = float(t_local.item())
+    value = world * n_pts / (ms_max / 1000.0)
+
+    # ---- end-to-end through the host API (copies inside the timed region)
+    fw, sw = vnet.mask_words()
+    e2e_ms = []
+    for i in range(max(1, min(a.steps, 5))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        vb.verify_query(vnet, res, q["image"], q["pixels"], k, precision=a.precision)
+        vb.get_verdict_bitmap(res, n_pts)
+        vb.get_coverage(res)
+        e2e_ms.append(1000.0 * (time.perf_counter() - t0))
+    e2e_local = torch.tensor([statistics.median(e2e_ms)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(e2e_local, op=dist.ReduceOp.MAX)
+    e2e_value = world * n_pts / (float(e2e_local.item()) / 1000.0)
+
+    if rank == 0:
+        last = sums[-1]
+        pk, pk_kind = peaks()
+        L = len(cfg["dims"]) - 1
+        scr_ms = statistics.median(screen_ms)
+        flops = screen_flops_per_point(cfg["dims"], s) * n_pts
+        if a.precision in ("bf16", "fp16", "fp8"):
+            peak = pk.get("bf16_tflops", 1900.0)
+            if a.precision == "fp8":
+                peak *= 2.0
+            roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
+                    "peak_kind": pk_kind + (" bf16 x2 (fp8 nominal ratio)" if a.precision == "fp8" else " bf16 burst")}
+        else:
+            mhz = pk.get("sm_max_mhz", 2070.0)
+            peak = 152 * 128 * 2 * mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 FLOP x clock
+            roof = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
+                    "peak_kind": "derived: 152 SM x 128 FP32 lanes x 2 FLOP x sm_max_mhz"}
+        achieved = flops / (scr_ms / 1000.0) / 1e12
+        roof.update({"achieved": achieved, "frac": achieved / peak, "traffic": None,
+                     "kernel": "screen pass (first pass over every point)",
+                     "flops_per_launch": flops, "launch_ms": scr_ms})
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "fp16": "f16",
+                          "fp8": "e4m3"}[a.precision],
+                "data": "synthetic",
+                "config": {"workload": a.workload, "dims": cfg["dims"], "act": cfg["act"],
+                           "s": s, "k": k, "points_per_query": n_pts, "precision": a.precision,
+                           "queries": "one per rank (rank r: query r of the workload seed)",
+                           "l2": "flushed between timed steps (256 MB write)",
+                           "parallelism": f"dp{world}" if world > 1 else "single GPU"},
+                "e2e": {"value": e2e_value, "unit": UNIT,
+                        "h2d_bytes_per_step": int(cfg["dims"][0] + 4 * s),
+                        "d2h_bytes_per_step": int(4 * ((n_pts + 31) // 32) + 8 * fw + 8 * sw + 128)},
+                "gpu_launches": a.steps * launches_per_step(a.precision, L),
+                "roofline": roof,
+                "verdict": {"verdict": last["verdict"], "n_adversarial": last["n_adversarial"],
+                            "first_witness": last["first_witness"], "n_ties": last["n_ties"],
+                            "n_recheck": last["n_recheck"], "ms_prologue": last["ms_prologue"],
+                            "ms_screen": last["ms_screen"], "ms_recheck": last["ms_recheck"]},
+                "wall_s": wall}
+        if ck:
+            line["clocks"] = ck
+        if world == 1 and not a.no_cpu_baseline:
+            rate, cores, sample = oracle_rate(net_d, q, a.cpu_seconds)
+            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                    "sample": sample}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/*
+ * vbmc.h -- C ABI of the GB300 verifier for MLPs over a discretised input
+ * perturbation box (arXiv 1907.12933, "Incremental Bounded Model Checking of
+ * Artificial Neural Networks in CUDA").
+ *
+ * The paper checks two things about a network given by its weights and
+ * biases (Sec. III-C, checkNN; Sec. III-B, covering methods):
+ *   - safety: every image in a region around a given image keeps the class
+ *     of that image (Eq. 9 restricts the region, Eq. 10 states the property;
+ *     a violation yields a counterexample image);
+ *   - coverage: which neurons change sign (sign(u) = 1 iff u >= 0, sc) and
+ *     which neuron pairs are SS-covered (Sec. III-B), and the covered
+ *     fraction of Eq. 3.
+ * This library decides both exactly over a finite region that replaces the
+ * Euclidean ball of Eq. 9: s chosen pixels, each moved by an integer number
+ * of grey levels in [-k, k] and clipped to [0, 255]. Point index t in
+ * [0, R^s), R = 2k+1, is read as s base-R digits with the first listed pixel
+ * most significant; digit d is the step d - k.
+ *
+ * Network semantics: activation potential u = sum_j w_j i_j + b (Eq. 1);
+ * hidden layers apply sigmoid (Eq. 2), ReLU or identity; the output layer is
+ * linear and the class is its argmax (lowest index on exact ties). A point
+ * is adversarial iff its class differs from the class D of the unperturbed
+ * image. Margin m = y_D - max_{i != D} y_i. Results agree with an FP64
+ * evaluation of every point: a point with |m| < 1e-9 is a tie (listed, not
+ * counted); a neuron evaluation with |u| < 1e-9 is a sign tie (its
+ * contributions go to the tie masks).
+ *
+ * Conventions for every call:
+ *   - Return value: VBMC_OK or a negative vbmc_status; no call aborts the
+ *     process. vbmc_last_error() gives a message for the calling thread.
+ *   - Ownership: the caller owns every input and may free it when the call
+ *     returns. Handles (vbmc_net, vbmc_result) are owned by the library
+ *     until the matching *_free. get_* calls copy into caller buffers.
+ *   - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
+ *     All device work of a call is ordered on it.
+ *   - Memory: device memory is allocated only by vbmc_net_create and
+ *     vbmc_result_create; verify calls allocate nothing.
+ *   - Errors found on the device (an invalid pixel list passed by device
+ *     pointer, a full recheck queue) are latched in the result and returned
+ *     by the next call that reads it.
+ */
+#ifndef VBMC_H
+#define VBMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VBMC_MAX_LAYERS 8   /* weight layers                     */
+#define VBMC_MAX_S 16       /* perturbed pixels per query        */
+#define VBMC_MAX_K 127      /* steps per pixel (R = 2k+1 <= 255) */
+#define VBMC_MAX_WIDTH 1024 /* neurons per layer                 */
+#define VBMC_NO_WITNESS UINT64_MAX
+
+typedef enum {
+    VBMC_OK = 0,
+    VBMC_ERR_ARG = -1,         /* invalid argument or buffer too small    */
+    VBMC_ERR_OOM = -2,         /* device allocation or queue capacity     */
+    VBMC_ERR_CUDA = -3,        /* CUDA runtime error                      */
+    VBMC_ERR_TIMEOUT = -4,     /* time budget exhausted                   */
+    VBMC_ERR_UNSUPPORTED = -5, /* shape or precision not supported        */
+    VBMC_ERR_STATE = -6,       /* handle used in the wrong state          */
+    VBMC_ERR_DEVICE = -7       /* error reported by a device-side check   */
+} vbmc_status;
+
+typedef enum { VBMC_ACT_IDENTITY = 0, VBMC_ACT_SIGMOID = 1, VBMC_ACT_RELU = 2 } vbmc_act;
+
+/* Precision of the first pass over all points. Every pass except FP64
+ * screens with a proven error bound; points it cannot decide are re-run in
+ * a tighter precision and finally in FP64, so the results do not depend on
+ * this choice. */
+typedef enum {
+    VBMC_PREC_FP64 = 0, /* every point in FP64 on CUDA cores              */
+    VBMC_PREC_FP32 = 1, /* FP32 screen on CUDA cores (the plain GPU path) */
+    VBMC_PREC_BF16 = 2, /* BF16 tcgen05 screen for layers 2..L            */
+    VBMC_PREC_FP16 = 3, /* FP16 tcgen05 screen for layers 2..L            */
+    VBMC_PREC_FP8 = 4   /* E4M3 tcgen05 screen, per-channel scales        */
+} vbmc_precision;
+
+typedef enum {
+    VBMC_SAFE = 0,      /* no adversarial point, no tie                */
+    VBMC_UNSAFE = 1,    /* at least one adversarial point              */
+    VBMC_TIES_ONLY = 2, /* no adversarial point, some |m| < 1e-9 ties  */
+    VBMC_PARTIAL = 3    /* the checked range is not the whole space    */
+} vbmc_verdict;
+
+/* Network: L weight layers, sizes H_0..H_L. W[l] is row-major
+ * H_{l+1} x H_l (row i = weights of neuron i of layer l+1), b[l] has H_{l+1}
+ * entries; host pointers, copied by vbmc_net_create. */
+typedef struct {
+    int32_t n_layers;
+    const int32_t *dims;
+    const float *const *W;
+    const float *const *b;
+    int32_t hidden_act; /* vbmc_act */
+} vbmc_mlp_desc;
+
+/* Query: base image (H_0 grey levels), s distinct pixel indices in digit
+ * order, step bound k, and the index range [lo, hi) to check (hi = 0: the
+ * whole space). Host pointers. */
+typedef struct {
+    const uint8_t *image;
+    int32_t s;
+    const int32_t *pixels;
+    int32_t k;
+    uint64_t lo, hi;
+} vbmc_query;
+
+typedef struct {
+    int32_t precision;  /* vbmc_precision                                  */
+    int32_t coverage;   /* nonzero: compute sign-change and SS masks       */
+    int32_t bitmap;     /* nonzero: record the per-point verdict bitmap    */
+    int32_t reserved;
+} vbmc_options;
+
+/* Capacities fixed when a result handle is created. */
+typedef struct {
+    uint64_t max_points; /* verdict bitmap bits (0: no bitmap)             */
+    int32_t max_s;       /* <= VBMC_MAX_S                                  */
+    int32_t max_k;       /* <= VBMC_MAX_K                                  */
+    uint32_t ties_cap;   /* tie indices kept (all are counted)             */
+    uint64_t queue_cap;  /* points that may wait for a tighter recheck     */
+} vbmc_caps;
+
+typedef struct {
+    int32_t verdict;           /* vbmc_verdict                            */
+    int32_t D;                 /* class of the unperturbed image          */
+    double base_margin;        /* FP64 margin of the unperturbed image    */
+    uint64_t n_points;         /* points checked                          */
+    uint64_t n_adversarial;    /* adversarial points (ties excluded)      */
+    uint64_t first_witness;    /* smallest adversarial index, or NO_WITNESS */
+    uint64_t n_ties;           /* points with |m| < 1e-9                  */
+    uint64_t n_recheck[3];     /* points re-run: tensor 3x, FP32, FP64    */
+    double ms_device;          /* device time of the last verify call     */
+    double ms_prologue;        /* of which: FP64 base pass and tables     */
+    double ms_screen;          /* of which: first pass over every point   */
+    double ms_recheck;         /* of which: all later passes              */
+} vbmc_summary;
+
+typedef struct vbmc_net vbmc_net;
+typedef struct vbmc_result vbmc_result;
+
+/* Copy a network, given only by its weights and biases as in checkNN's
+ * first input (Sec. III-C), to the device. Computes the weight norms the
+ * screens' error bounds use. Allocates device memory; not for the timed path. */
+vbmc_status vbmc_net_create(const vbmc_mlp_desc *desc, vbmc_net **out);
+vbmc_status vbmc_net_free(vbmc_net *net);
+
+/* Allocate a reusable result workspace for queries on `net` within `caps`. */
+vbmc_status vbmc_result_create(const vbmc_net *net, const vbmc_caps *caps, vbmc_result **out);
+vbmc_status vbmc_result_free(vbmc_result *res);
+
+/* checkNN over the box (Sec. III-C): enumerate [lo, hi), decide the safety
+ * property of Eq. 10 for every point, collect the sign-change and SS-Cover
+ * masks (Sec. III-B). Host inputs; blocks until the result is final. */
+vbmc_status vbmc_verify_query(vbmc_net *net, const vbmc_query *query, const vbmc_options *opt,
+                              vbmc_result *res, void *stream);
+
+/* Same, with the image (H_0 bytes) and pixel list (s int32) already in
+ * device memory. Asynchronous: enqueues the work on `stream` and returns;
+ * the result stays on the device until a get_* call or vbmc_result_summary
+ * reads it. Invalid pixel lists are detected on the device. */
+vbmc_status vbmc_verify_query_device(vbmc_net *net, const uint8_t *d_image, int32_t s,
+                                     const int32_t *d_pixels, int32_t k, uint64_t lo, uint64_t hi,
+                                     const vbmc_options *opt, vbmc_result *res, void *stream);
+
+/* Many queries against one net in one pass: every query's points go to one
+ * persistent launch per pass. results[i] receives query i. */
+vbmc_status vbmc_verify_batch(vbmc_net *net, const vbmc_query *queries, int32_t nq,
+                              const vbmc_options *opt, vbmc_result *const *results, void *stream);
+
+/* Waits for the result's last call and returns its summary. */
+vbmc_status vbmc_result_summary(vbmc_result *res, vbmc_summary *out);
+
+/* First (lexicographically smallest) counterexample of Eq. 10: its index,
+ * its s steps in [-k, k], the perturbed image (H_0 bytes) and its FP64
+ * margin. Any output pointer may be NULL. With no witness, *index =
+ * VBMC_NO_WITNESS and the other outputs are left untouched. */
+vbmc_status vbmc_get_witness(vbmc_result *res, uint64_t *index, int32_t *steps, uint8_t *image,
+                             double *margin_fp64);
+
+/* Coverage masks (Sec. III-B). flip: one bit per non-input neuron, layers
+ * 1..L back to back (bit n of word n/32). ss: one block per adjacent layer
+ * pair (l, l+1), l = 1..L-1, bit j*H_{l+1} + i for pair (j in l, i in l+1).
+ * *_tie: bits whose decision involved a sign tie. covered_fraction: Eq. 3,
+ * neurons in at least one SS-covered pair over all non-input neurons. Any
+ * pointer may be NULL; a non-NULL buffer shorter than needed is an error. */
+vbmc_status vbmc_get_coverage(vbmc_result *res, uint32_t *flip, size_t flip_words,
+                              uint32_t *flip_tie, uint32_t *ss, size_t ss_words, uint32_t *ss_tie,
+                              double *covered_fraction);
+
+/* Word counts of the coverage masks for a net. */
+vbmc_status vbmc_mask_words(const vbmc_net *net, size_t *flip_words, size_t *ss_words);
+
+/* Verdict bitmap: bit t set iff point t is adversarial (ties clear). */
+vbmc_status vbmc_get_verdict_bitmap(vbmc_result *res, uint32_t *words, size_t n_words);
+
+/* Tie indices (ascending) and their total count. */
+vbmc_status vbmc_get_ties(vbmc_result *res, uint64_t *idx, size_t cap, uint64_t *n_ties);
+
+/* Message for the last failing call of this thread. */
+const char *vbmc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VBMC_H */

@@ -1,0 +1,281 @@
+"""Python binding of libvbmc (include/vbmc.h): argument marshalling only.
+
+Every step of the verification runs in the CUDA library. PyTorch supplies the
+CUDA stream (and, for the device-resident entry point, device memory). There
+is no CPU fallback: importing this package without the built library, or
+calling it without a CUDA device, raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvbmc.so")
+
+PRECISIONS = {"fp64": 0, "fp32": 1, "bf16": 2, "fp16": 3, "fp8": 4}
+ACTS = {"identity": 0, "sigmoid": 1, "relu": 2}
+VERDICTS = {0: "SAFE", 1: "UNSAFE", 2: "TIES_ONLY", 3: "PARTIAL"}
+NO_WITNESS = 2**64 - 1
+MAX_S, MAX_K = 16, 127
+
+
+class VbmcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"vbmc status {status}: {msg}")
+        self.status = status
+
+
+class _MlpDesc(C.Structure):
+    _fields_ = [("n_layers", C.c_int32), ("dims", C.POINTER(C.c_int32)),
+                ("W", C.POINTER(C.POINTER(C.c_float))), ("b", C.POINTER(C.POINTER(C.c_float))),
+                ("hidden_act", C.c_int32)]
+
+
+class _Query(C.Structure):
+    _fields_ = [("image", C.POINTER(C.c_uint8)), ("s", C.c_int32),
+                ("pixels", C.POINTER(C.c_int32)), ("k", C.c_int32), ("lo", C.c_uint64),
+                ("hi", C.c_uint64)]
+
+
+class _Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("coverage", C.c_int32), ("bitmap", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class _Caps(C.Structure):
+    _fields_ = [("max_points", C.c_uint64), ("max_s", C.c_int32), ("max_k", C.c_int32),
+                ("ties_cap", C.c_uint32), ("queue_cap", C.c_uint64)]
+
+
+class _Summary(C.Structure):
+    _fields_ = [("verdict", C.c_int32), ("D", C.c_int32), ("base_margin", C.c_double),
+                ("n_points", C.c_uint64), ("n_adversarial", C.c_uint64),
+                ("first_witness", C.c_uint64), ("n_ties", C.c_uint64),
+                ("n_recheck", C.c_uint64 * 3), ("ms_device", C.c_double),
+                ("ms_prologue", C.c_double), ("ms_screen", C.c_double),
+                ("ms_recheck", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() "
+                              "(no CPU fallback exists)")
+        L = C.CDLL(LIB_PATH)
+        vp, st = C.c_void_p, C.c_int
+        sig = {
+            "vbmc_net_create": [C.POINTER(_MlpDesc), C.POINTER(vp)],
+            "vbmc_net_free": [vp],
+            "vbmc_result_create": [vp, C.POINTER(_Caps), C.POINTER(vp)],
+            "vbmc_result_free": [vp],
+            "vbmc_verify_query": [vp, C.POINTER(_Query), C.POINTER(_Options), vp, vp],
+            "vbmc_verify_query_device": [vp, vp, C.c_int32, vp, C.c_int32, C.c_uint64,
+                                         C.c_uint64, C.POINTER(_Options), vp, vp],
+            "vbmc_verify_batch": [vp, C.POINTER(_Query), C.c_int32, C.POINTER(_Options),
+                                  C.POINTER(vp), vp],
+            "vbmc_result_summary": [vp, C.POINTER(_Summary)],
+            "vbmc_get_witness": [vp, C.POINTER(C.c_uint64), C.POINTER(C.c_int32),
+                                 C.POINTER(C.c_uint8), C.POINTER(C.c_double)],
+            "vbmc_get_coverage": [vp, C.POINTER(C.c_uint32), C.c_size_t, C.POINTER(C.c_uint32),
+                                  C.POINTER(C.c_uint32), C.c_size_t, C.POINTER(C.c_uint32),
+                                  C.POINTER(C.c_double)],
+            "vbmc_mask_words": [vp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)],
+            "vbmc_get_verdict_bitmap": [vp, C.POINTER(C.c_uint32), C.c_size_t],
+            "vbmc_get_ties": [vp, C.POINTER(C.c_uint64), C.c_size_t, C.POINTER(C.c_uint64)],
+        }
+        for name, args in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = st
+        L.vbmc_last_error.restype = C.c_char_p
+        L.vbmc_last_error.argtypes = []
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise VbmcError(rc, lib().vbmc_last_error().decode())
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+def current_stream() -> int:
+    """cudaStream_t of torch's current stream (0 when torch has no CUDA)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # noqa: BLE001 - no torch: legacy default stream
+        pass
+    return 0
+
+
+class Net:
+    """vbmc_net_create / vbmc_net_free. `net` has dims, W (list of (H_out, H_in)
+    float32), b, act ('sigmoid' | 'relu' | 'identity')."""
+
+    def __init__(self, net: dict):
+        self.dims = [int(d) for d in net["dims"]]
+        W = [np.ascontiguousarray(w, dtype=np.float32) for w in net["W"]]
+        b = [np.ascontiguousarray(x, dtype=np.float32) for x in net["b"]]
+        L = len(W)
+        dims = np.ascontiguousarray(self.dims, dtype=np.int32)
+        Wp = (C.POINTER(C.c_float) * L)(*[_ptr(w, C.c_float) for w in W])
+        bp = (C.POINTER(C.c_float) * L)(*[_ptr(x, C.c_float) for x in b])
+        act = net["act"] if isinstance(net["act"], int) else ACTS[net["act"]]
+        desc = _MlpDesc(L, _ptr(dims, C.c_int32), Wp, bp, act)
+        h = C.c_void_p()
+        _check(lib().vbmc_net_create(C.byref(desc), C.byref(h)))
+        self.h = h
+
+    def mask_words(self) -> tuple[int, int]:
+        fw, sw = C.c_size_t(), C.c_size_t()
+        _check(lib().vbmc_mask_words(self.h, C.byref(fw), C.byref(sw)))
+        return fw.value, sw.value
+
+    def free(self):
+        if getattr(self, "h", None):
+            lib().vbmc_net_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+class Result:
+    """vbmc_result_create / vbmc_result_free: a reusable workspace."""
+
+    def __init__(self, net: Net, max_points: int = 0, max_s: int = MAX_S, max_k: int = 32,
+                 ties_cap: int = 1 << 16, queue_cap: int = 1 << 22):
+        caps = _Caps(max_points, max_s, max_k, ties_cap, queue_cap)
+        h = C.c_void_p()
+        _check(lib().vbmc_result_create(net.h, C.byref(caps), C.byref(h)))
+        self.h = h
+        self.net = net
+
+    def free(self):
+        if getattr(self, "h", None):
+            lib().vbmc_result_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+def _options(precision, coverage, bitmap):
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    return _Options(p, int(bool(coverage)), int(bool(bitmap)), 0)
+
+
+def _summary_dict(s: _Summary) -> dict:
+    return {"verdict": VERDICTS.get(s.verdict, s.verdict), "D": s.D, "base_margin": s.base_margin,
+            "n_points": s.n_points, "n_adversarial": s.n_adversarial,
+            "first_witness": None if s.first_witness == NO_WITNESS else int(s.first_witness),
+            "n_ties": s.n_ties, "n_recheck": list(s.n_recheck), "ms_device": s.ms_device,
+            "ms_prologue": s.ms_prologue, "ms_screen": s.ms_screen, "ms_recheck": s.ms_recheck}
+
+
+def verify_query(net: Net, res: Result, image, pixels, k: int, lo: int = 0, hi: int = 0,
+                 precision="fp32", coverage: bool = True, bitmap: bool = True,
+                 stream: int | None = None) -> dict:
+    """vbmc_verify_query: host inputs, blocks until the result is final."""
+    img = np.ascontiguousarray(image, dtype=np.uint8)
+    pix = np.ascontiguousarray(pixels, dtype=np.int32)
+    q = _Query(_ptr(img, C.c_uint8), len(pix), _ptr(pix, C.c_int32), int(k), int(lo), int(hi))
+    opt = _options(precision, coverage, bitmap)
+    st = current_stream() if stream is None else stream
+    _check(lib().vbmc_verify_query(net.h, C.byref(q), C.byref(opt), res.h, C.c_void_p(st)))
+    return result_summary(res)
+
+
+def verify_query_device(net: Net, res: Result, d_image, d_pixels, k: int, lo: int = 0,
+                        hi: int = 0, precision="fp32", coverage: bool = True, bitmap: bool = True,
+                        stream: int | None = None) -> None:
+    """vbmc_verify_query_device: image (uint8) and pixels (int32) are CUDA tensors;
+    enqueues on `stream` (default: torch's current stream) and returns."""
+    opt = _options(precision, coverage, bitmap)
+    st = current_stream() if stream is None else stream
+    _check(lib().vbmc_verify_query_device(net.h, C.c_void_p(d_image.data_ptr()),
+                                          int(d_pixels.numel()), C.c_void_p(d_pixels.data_ptr()),
+                                          int(k), int(lo), int(hi), C.byref(opt), res.h,
+                                          C.c_void_p(st)))
+
+
+def verify_batch(net: Net, results: list, queries: list, precision="fp32",
+                 coverage: bool = True, bitmap: bool = False,
+                 stream: int | None = None) -> list:
+    """vbmc_verify_batch: queries are dicts with image, pixels, k (and optional lo, hi)."""
+    keep = []
+    qs = (_Query * len(queries))()
+    for i, qd in enumerate(queries):
+        img = np.ascontiguousarray(qd["image"], dtype=np.uint8)
+        pix = np.ascontiguousarray(qd["pixels"], dtype=np.int32)
+        keep += [img, pix]
+        qs[i] = _Query(_ptr(img, C.c_uint8), len(pix), _ptr(pix, C.c_int32), int(qd["k"]),
+                       int(qd.get("lo", 0)), int(qd.get("hi", 0)))
+    hs = (C.c_void_p * len(results))(*[r.h for r in results])
+    opt = _options(precision, coverage, bitmap)
+    st = current_stream() if stream is None else stream
+    _check(lib().vbmc_verify_batch(net.h, qs, len(queries), C.byref(opt), hs, C.c_void_p(st)))
+    return [result_summary(r) for r in results]
+
+
+def result_summary(res: Result) -> dict:
+    s = _Summary()
+    _check(lib().vbmc_result_summary(res.h, C.byref(s)))
+    return _summary_dict(s)
+
+
+def get_witness(res: Result, s: int, h0: int) -> dict | None:
+    """vbmc_get_witness: first adversarial index, its steps, image and FP64 margin."""
+    idx = C.c_uint64()
+    steps = np.zeros(max(1, s), dtype=np.int32)
+    img = np.zeros(h0, dtype=np.uint8)
+    m = C.c_double()
+    _check(lib().vbmc_get_witness(res.h, C.byref(idx), _ptr(steps, C.c_int32),
+                                  _ptr(img, C.c_uint8), C.byref(m)))
+    if idx.value == NO_WITNESS:
+        return None
+    return {"index": int(idx.value), "steps": steps[:s], "image": img, "margin": m.value}
+
+
+def get_coverage(res: Result) -> dict:
+    """vbmc_get_coverage: sign-change and SS masks (uint32 words) and Eq. 3's fraction."""
+    fw, sw = res.net.mask_words()
+    f, ft = np.zeros(fw, np.uint32), np.zeros(fw, np.uint32)
+    s, stt = np.zeros(sw, np.uint32), np.zeros(sw, np.uint32)
+    frac = C.c_double()
+    _check(lib().vbmc_get_coverage(res.h, _ptr(f, C.c_uint32), fw, _ptr(ft, C.c_uint32),
+                                   _ptr(s, C.c_uint32), sw, _ptr(stt, C.c_uint32),
+                                   C.byref(frac)))
+    return {"flip": f, "flip_tie": ft, "ss": s, "ss_tie": stt, "covered_fraction": frac.value}
+
+
+def get_verdict_bitmap(res: Result, n_points: int) -> np.ndarray:
+    w = np.zeros(max(1, (n_points + 31) // 32), np.uint32)
+    _check(lib().vbmc_get_verdict_bitmap(res.h, _ptr(w, C.c_uint32), len(w)))
+    return w
+
+
+def get_ties(res: Result, cap: int = 1 << 16) -> np.ndarray:
+    n = C.c_uint64()
+    out = np.zeros(max(1, cap), np.uint64)
+    _check(lib().vbmc_get_ties(res.h, _ptr(out, C.c_uint64), cap, C.byref(n)))
+    return out[:min(n.value, cap)].astype(np.int64)

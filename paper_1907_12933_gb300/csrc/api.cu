@@ -1,0 +1,604 @@
+// api.cu -- host runtime behind include/vbmc.h.
+//
+// A vbmc_net holds the weights on the device plus the per-row norms that the
+// screens' error bounds use. A vbmc_result is a reusable workspace: the
+// per-query constants, the counters, the coverage masks, the verdict bitmap,
+// the tie list and the recheck queues, all allocated once. A verify call
+// enqueues: prologue (FP64 base pass, tables, constants) -> screen pass over
+// every point -> tighter passes over the queued points -> FP64 pass.
+#include "../../include/vbmc.h"
+#include "dev.cuh"
+#include "launch.h"
+#include "tc.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace vbmc;
+
+namespace {
+
+thread_local std::string g_err;
+
+vbmc_status fail(vbmc_status st, const std::string& msg) {
+    g_err = msg;
+    return st;
+}
+
+#define VB_CUDA(call)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(e_ == cudaErrorMemoryAllocation ? VBMC_ERR_OOM : VBMC_ERR_CUDA, \
+                        std::string(#call ": ") + cudaGetErrorString(e_));              \
+    } while (0)
+
+float round_up_f(double x) {
+    float f = (float)x;
+    if ((double)f < x) f = std::nextafter(f, INFINITY);
+    return f;
+}
+
+uint64_t space_size(int s, int k) {
+    const uint64_t R = (uint64_t)(2 * k + 1);
+    uint64_t n = 1;
+    for (int p = 0; p < s; ++p) {
+        if (n > (1ull << 62) / R) return 0;
+        n *= R;
+    }
+    return n;
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t n, std::vector<void*>& owned) {
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    if (e == cudaSuccess) owned.push_back((void*)*p);
+    return e;
+}
+
+}  // namespace
+
+struct vbmc_net {
+    NetView v{};
+    std::vector<void*> owned;
+    int n_sm = 0;
+    int device = 0;
+    TcNet tc{};  // tensor-core copies (built on first use)
+    bool tc_ready = false;
+    std::vector<std::vector<float>> hW, hb;  // host copies for tensor-core set-up
+};
+
+struct vbmc_result {
+    const vbmc_net* net = nullptr;
+    vbmc_caps caps{};
+    std::vector<void*> owned;
+    QueryView hq{};           // host copy of the device view
+    QueryView* d_q = nullptr;
+    Counters* d_cnt = nullptr;
+    Counters* h_cnt = nullptr;  // pinned
+    uint8_t* d_image = nullptr;
+    int* d_pix_in = nullptr;
+    unsigned long long* d_tp = nullptr;  // tile prefix {0, n_tiles}
+    unsigned long long* d_qcount = nullptr;  // 4 queue counters
+    QEntry* d_queue[3] = {nullptr, nullptr, nullptr};
+    double* d_margin = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_pro = nullptr, ev_scr = nullptr;
+    cudaStream_t last_stream = nullptr;
+    bool pending = false;
+    bool have_result = false;
+    int flip_words = 0, ss_words = 0;
+    // query of the last call (host copy)
+    std::vector<uint8_t> image;
+    std::vector<int32_t> pixels;
+    int s = 0, k = 0;
+    uint64_t lo = 0, hi = 0, n_space = 0;
+    vbmc_options opt{};
+    vbmc_summary sum{};
+};
+
+extern "C" const char* vbmc_last_error(void) { return g_err.c_str(); }
+
+extern "C" vbmc_status vbmc_net_create(const vbmc_mlp_desc* desc, vbmc_net** out) {
+    if (!desc || !out) return fail(VBMC_ERR_ARG, "null argument");
+    *out = nullptr;
+    const int L = desc->n_layers;
+    if (L < 1 || L > kMaxL) return fail(VBMC_ERR_ARG, "n_layers must be in [1, 8]");
+    if (!desc->dims || !desc->W || !desc->b) return fail(VBMC_ERR_ARG, "null dims/W/b");
+    if (desc->hidden_act < 0 || desc->hidden_act > 2) return fail(VBMC_ERR_ARG, "bad activation");
+    for (int l = 0; l <= L; ++l)
+        if (desc->dims[l] < 1 || (l > 0 && desc->dims[l] > kMaxWidth) || desc->dims[l] > (1 << 24))
+            return fail(VBMC_ERR_ARG, "layer width out of range");
+    if (desc->dims[L] < 2) return fail(VBMC_ERR_ARG, "output layer needs at least 2 classes");
+    for (int l = 0; l < L; ++l)
+        if (!desc->W[l] || !desc->b[l]) return fail(VBMC_ERR_ARG, "null weight pointer");
+
+    vbmc_net* n = new vbmc_net();
+    NetView& v = n->v;
+    v.L = L;
+    v.act = desc->hidden_act;
+    for (int l = 0; l <= L; ++l) v.dims[l] = desc->dims[l];
+    v.total = 0;
+    v.hmax = 0;
+    for (int l = 1; l <= L; ++l) {
+        v.noff[l] = v.total;
+        v.total += v.dims[l];
+        v.hmax = std::max(v.hmax, v.dims[l]);
+    }
+    v.noff[L + 1] = v.total;
+    long long ss = 0;
+    for (int l = 1; l < L; ++l) {
+        v.ssoff[l] = ss;
+        ss += (long long)v.dims[l] * v.dims[l + 1];
+    }
+    v.flip_words = (v.total + 31) / 32;
+    v.ss_words = (int)std::max<long long>(1, (ss + 31) / 32);
+    const double lam = desc->hidden_act == VBMC_ACT_SIGMOID ? 0.25 : 1.0;
+    cudaGetDevice(&n->device);
+    cudaDeviceGetAttribute(&n->n_sm, cudaDevAttrMultiProcessorCount, n->device);
+    n->hW.resize(L + 1);
+    n->hb.resize(L + 1);
+    for (int l = 1; l <= L; ++l) {
+        const int K = v.dims[l - 1], N = v.dims[l];
+        const float* W = desc->W[l - 1];
+        const float* b = desc->b[l - 1];
+        n->hW[l].assign(W, W + (size_t)N * K);
+        n->hb[l].assign(b, b + N);
+        std::vector<float> WT((size_t)N * K), rn(N);
+        double frob2 = 0.0;
+        for (int i = 0; i < N; ++i) {
+            double r2 = 0.0;
+            for (int j = 0; j < K; ++j) {
+                const double w = W[(size_t)i * K + j];
+                if (!std::isfinite(w)) {
+                    vbmc_net_free(n);
+                    return fail(VBMC_ERR_ARG, "non-finite weight");
+                }
+                r2 += w * w;
+                WT[(size_t)j * N + i] = W[(size_t)i * K + j];
+            }
+            rn[i] = round_up_f(std::sqrt(r2) * (1.0 + 1e-12));
+            frob2 += r2;
+        }
+        v.lamfrob[l] = round_up_f(lam * std::sqrt(frob2) * (1.0 + 1e-12));
+        const double u = std::ldexp(1.0, -24);
+        v.gam[l] = round_up_f(K * u / (1.0 - K * u));
+        float *dW, *dWT, *db, *drn;
+        cudaError_t e = dalloc(&dW, (size_t)N * K, n->owned);
+        if (e == cudaSuccess) e = dalloc(&dWT, (size_t)N * K, n->owned);
+        if (e == cudaSuccess) e = dalloc(&db, N, n->owned);
+        if (e == cudaSuccess) e = dalloc(&drn, N, n->owned);
+        if (e == cudaSuccess) e = cudaMemcpy(dW, W, sizeof(float) * N * K, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(dWT, WT.data(), sizeof(float) * N * K, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(db, b, sizeof(float) * N, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(drn, rn.data(), sizeof(float) * N, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            vbmc_net_free(n);
+            return fail(VBMC_ERR_OOM, std::string("net_create: ") + cudaGetErrorString(e));
+        }
+        v.W[l] = dW;
+        v.WT[l] = dWT;
+        v.b[l] = db;
+        v.rownorm[l] = drn;
+    }
+    *out = n;
+    return VBMC_OK;
+}
+
+extern "C" vbmc_status vbmc_net_free(vbmc_net* net) {
+    if (!net) return VBMC_OK;
+    tc_free(net->tc);
+    for (void* p : net->owned) cudaFree(p);
+    delete net;
+    return VBMC_OK;
+}
+
+extern "C" vbmc_status vbmc_mask_words(const vbmc_net* net, size_t* fw, size_t* sw) {
+    if (!net) return fail(VBMC_ERR_ARG, "null net");
+    if (fw) *fw = (size_t)net->v.flip_words;
+    if (sw) *sw = (size_t)net->v.ss_words;
+    return VBMC_OK;
+}
+
+extern "C" vbmc_status vbmc_result_create(const vbmc_net* net, const vbmc_caps* caps,
+                                          vbmc_result** out) {
+    if (!net || !caps || !out) return fail(VBMC_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (caps->max_s < 0 || caps->max_s > kMaxS) return fail(VBMC_ERR_ARG, "max_s out of range");
+    if (caps->max_k < 0 || caps->max_k > VBMC_MAX_K) return fail(VBMC_ERR_ARG, "max_k out of range");
+    vbmc_result* r = new vbmc_result();
+    r->net = net;
+    r->caps = *caps;
+    const NetView& v = net->v;
+    const int S = std::max(1, caps->max_s), RM = 2 * caps->max_k + 1;
+    const size_t T = v.total;
+    r->flip_words = v.flip_words;
+    r->ss_words = v.ss_words;
+    QueryView& q = r->hq;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](auto** p, size_t n) {
+        if (e == cudaSuccess) e = dalloc(p, n, r->owned);
+    };
+    A(&r->d_q, 1);
+    A(&r->d_cnt, 1);
+    A(&r->d_image, (size_t)v.dims[0]);
+    A(&r->d_pix_in, (size_t)S);
+    A(&q.pix, (size_t)S);
+    A(&q.dv, (size_t)S * RM);
+    A(&q.ub, T);
+    A(&q.hb, T);
+    A(&q.ub32, T);
+    A(&q.dub, T);
+    A(&q.thr, T);
+    A(&q.c1, T);
+    A(&q.c2, T);
+    A(&q.tab, (size_t)S * RM * v.dims[1]);
+    A(&q.kvec, (size_t)kMaxL + 1);
+    A(&q.flip, (size_t)v.flip_words);
+    A(&q.flip_tie, (size_t)v.flip_words);
+    A(&q.ss, (size_t)v.ss_words);
+    A(&q.ss_tie, (size_t)v.ss_words);
+    A(&q.ties, (size_t)std::max<uint32_t>(1, caps->ties_cap));
+    A(&r->d_tp, 2);
+    A(&r->d_qcount, 4);
+    A(&r->d_margin, 1);
+    if (caps->max_points) A(&q.bitmap, (size_t)((caps->max_points + 31) / 32));
+    const uint64_t qc = std::max<uint64_t>(1, caps->queue_cap);
+    for (int i = 0; i < 3; ++i) A(&r->d_queue[i], (size_t)qc);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&r->h_cnt, sizeof(Counters));
+    if (e == cudaSuccess) e = cudaEventCreate(&r->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&r->ev1);
+    if (e == cudaSuccess) e = cudaEventCreate(&r->ev_pro);
+    if (e == cudaSuccess) e = cudaEventCreate(&r->ev_scr);
+    if (e != cudaSuccess) {
+        vbmc_result_free(r);
+        return fail(VBMC_ERR_OOM, std::string("result_create: ") + cudaGetErrorString(e));
+    }
+    q.cnt = r->d_cnt;
+    q.bitmap_bits = caps->max_points;
+    q.ties_cap = caps->ties_cap;
+    *out = r;
+    return VBMC_OK;
+}
+
+extern "C" vbmc_status vbmc_result_free(vbmc_result* r) {
+    if (!r) return VBMC_OK;
+    if (r->pending && r->last_stream) cudaStreamSynchronize(r->last_stream);
+    for (void* p : r->owned) cudaFree(p);
+    if (r->h_cnt) cudaFreeHost(r->h_cnt);
+    if (r->ev0) cudaEventDestroy(r->ev0);
+    if (r->ev1) cudaEventDestroy(r->ev1);
+    if (r->ev_pro) cudaEventDestroy(r->ev_pro);
+    if (r->ev_scr) cudaEventDestroy(r->ev_scr);
+    delete r;
+    return VBMC_OK;
+}
+
+namespace {
+
+vbmc_status check_query_shape(const vbmc_result* r, int s, int k, uint64_t lo, uint64_t hi,
+                              const vbmc_options* opt, uint64_t* n_out, uint64_t* hi_out) {
+    if (s < 0 || s > r->caps.max_s) return fail(VBMC_ERR_ARG, "s exceeds the result's max_s");
+    if (k < 0 || k > r->caps.max_k) return fail(VBMC_ERR_ARG, "k exceeds the result's max_k");
+    const uint64_t n = space_size(s, k);
+    if (n == 0) return fail(VBMC_ERR_ARG, "R^s does not fit below 2^62");
+    if (hi == 0) hi = n;
+    if (hi > n || lo > hi) return fail(VBMC_ERR_ARG, "range [lo, hi) outside [0, R^s)");
+    if (opt && opt->bitmap && hi > r->caps.max_points)
+        return fail(VBMC_ERR_ARG, "verdict bitmap larger than the result's max_points");
+    if (opt && (opt->precision < 0 || opt->precision > VBMC_PREC_FP8))
+        return fail(VBMC_ERR_ARG, "bad precision");
+    *n_out = n;
+    *hi_out = hi;
+    return VBMC_OK;
+}
+
+// Enqueue the full pipeline for one query whose image/pixels are on the device.
+vbmc_status enqueue(vbmc_net* net, vbmc_result* r, const uint8_t* d_image, const int* d_pix, int s,
+                    int k, uint64_t lo, uint64_t hi, uint64_t n, const vbmc_options& opt,
+                    cudaStream_t st) {
+    const NetView& v = net->v;
+    QueryView q = r->hq;
+    q.s = s;
+    q.k = k;
+    q.R = 2 * k + 1;
+    q.qid = 0;
+    q.n_points = n;
+    q.lo = lo;
+    q.hi = hi;
+    q.image = d_image;
+    q.pix_in = d_pix;
+    if (!opt.coverage) q.flip = q.flip_tie = q.ss = q.ss_tie = nullptr;
+    if (!opt.bitmap) q.bitmap = nullptr;
+    VB_CUDA(cudaMemcpyAsync(r->d_q, &q, sizeof(QueryView), cudaMemcpyHostToDevice, st));
+    if (opt.coverage) {
+        VB_CUDA(cudaMemsetAsync(q.flip, 0, sizeof(uint32_t) * v.flip_words, st));
+        VB_CUDA(cudaMemsetAsync(q.flip_tie, 0, sizeof(uint32_t) * v.flip_words, st));
+        VB_CUDA(cudaMemsetAsync(q.ss, 0, sizeof(uint32_t) * v.ss_words, st));
+        VB_CUDA(cudaMemsetAsync(q.ss_tie, 0, sizeof(uint32_t) * v.ss_words, st));
+    }
+    if (opt.bitmap && hi > 0)
+        VB_CUDA(cudaMemsetAsync(q.bitmap, 0, sizeof(uint32_t) * ((hi + 31) / 32), st));
+    VB_CUDA(cudaMemsetAsync(r->d_qcount, 0, sizeof(unsigned long long) * 4, st));
+    VB_CUDA(cudaEventRecord(r->ev0, st));
+    launch_prologue(v, r->d_q, 1, s * q.R, st);
+    VB_CUDA(cudaEventRecord(r->ev_pro, st));
+    const unsigned long long cap = std::max<uint64_t>(1, r->caps.queue_cap);
+    Queue q64{r->d_queue[2], r->d_qcount + 2, cap};
+    if (hi > lo) {
+        if (opt.precision == VBMC_PREC_FP64) {
+            launch_fp64(v, r->d_q, 1, nullptr, nullptr, 0, lo, hi, net->n_sm, st);
+            VB_CUDA(cudaEventRecord(r->ev_scr, st));
+        } else if (opt.precision == VBMC_PREC_FP32) {
+            const int MT = simt_tile_points(v);
+            if (MT == 0) return fail(VBMC_ERR_UNSUPPORTED, "layer width above 1024");
+            const unsigned long long base = lo & ~31ull;
+            const unsigned long long tiles = (hi - base + MT - 1) / MT;
+            unsigned long long tp[2] = {0, tiles};
+            VB_CUDA(cudaMemcpyAsync(r->d_tp, tp, sizeof(tp), cudaMemcpyHostToDevice, st));
+            launch_screen_simt(v, r->d_q, 1, r->d_tp, tiles, nullptr, nullptr, 0, q64, 2, net->n_sm,
+                               st);
+            VB_CUDA(cudaEventRecord(r->ev_scr, st));
+            launch_fp64(v, r->d_q, 1, r->d_queue[2], r->d_qcount + 2, cap, 0, 0, net->n_sm, st);
+        } else {
+            if (!tc_supported(v, opt.precision))
+                return fail(VBMC_ERR_UNSUPPORTED, "tensor-core screen does not support this net/precision");
+            if (!net->tc_ready) {
+                vbmc_status sst = tc_build(net->tc, v, net->hW, net->hb);
+                if (sst != VBMC_OK) return sst;
+                net->tc_ready = true;
+            }
+            // tensor screen -> tensor 3x pass -> FP32 pass -> FP64 pass
+            Queue q3{r->d_queue[0], r->d_qcount + 0, cap};
+            Queue q32{r->d_queue[1], r->d_qcount + 1, cap};
+            vbmc_status sst = tc_launch_screen(net->tc, v, r->d_q, lo, hi, opt.precision, q3,
+                                               net->n_sm, st);
+            if (sst != VBMC_OK) return sst;
+            VB_CUDA(cudaEventRecord(r->ev_scr, st));
+            sst = tc_launch_gather(net->tc, v, r->d_q, r->d_queue[0], r->d_qcount + 0, cap,
+                                   opt.precision, q32, net->n_sm, st);
+            if (sst != VBMC_OK) return sst;
+            launch_screen_simt(v, r->d_q, 1, nullptr, 0, r->d_queue[1], r->d_qcount + 1, cap, q64,
+                               2, net->n_sm, st);
+            launch_fp64(v, r->d_q, 1, r->d_queue[2], r->d_qcount + 2, cap, 0, 0, net->n_sm, st);
+        }
+    }
+    if (hi <= lo) VB_CUDA(cudaEventRecord(r->ev_scr, st));
+    VB_CUDA(cudaGetLastError());
+    VB_CUDA(cudaEventRecord(r->ev1, st));
+    VB_CUDA(cudaMemcpyAsync(r->h_cnt, r->d_cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    r->last_stream = st;
+    r->pending = true;
+    r->have_result = true;
+    r->s = s;
+    r->k = k;
+    r->lo = lo;
+    r->hi = hi;
+    r->n_space = n;
+    r->opt = opt;
+    return VBMC_OK;
+}
+
+vbmc_status finish(vbmc_result* r) {
+    if (!r->have_result) return fail(VBMC_ERR_STATE, "no verify call on this result");
+    if (r->pending) {
+        VB_CUDA(cudaStreamSynchronize(r->last_stream));
+        r->pending = false;
+        const Counters& c = *r->h_cnt;
+        vbmc_summary& s = r->sum;
+        std::memset(&s, 0, sizeof(s));
+        s.D = c.D;
+        s.base_margin = c.base_margin;
+        s.n_points = r->hi - r->lo;
+        s.n_adversarial = c.n_adv;
+        s.first_witness = c.first;
+        s.n_ties = c.n_ties;
+        for (int i = 0; i < 3; ++i) s.n_recheck[i] = c.n_q[i];
+        float ms = 0.f, ms_p = 0.f, ms_s = 0.f;
+        cudaEventElapsedTime(&ms, r->ev0, r->ev1);
+        cudaEventElapsedTime(&ms_p, r->ev0, r->ev_pro);
+        cudaEventElapsedTime(&ms_s, r->ev_pro, r->ev_scr);
+        s.ms_device = ms;
+        s.ms_prologue = ms_p;
+        s.ms_screen = ms_s;
+        s.ms_recheck = ms - ms_p - ms_s;
+        if (r->lo != 0 || r->hi != r->n_space) s.verdict = VBMC_PARTIAL;
+        else if (c.n_adv) s.verdict = VBMC_UNSAFE;
+        else if (c.n_ties) s.verdict = VBMC_TIES_ONLY;
+        else s.verdict = VBMC_SAFE;
+        if (c.err & DERR_PIXELS) return fail(VBMC_ERR_ARG, "pixel list not distinct or out of range");
+        if (c.err & DERR_QUEUE) return fail(VBMC_ERR_OOM, "recheck queue overflow: raise caps.queue_cap");
+        if (c.err & DERR_TC_WAIT) return fail(VBMC_ERR_DEVICE, "tensor-core pipeline wait timed out");
+    }
+    return VBMC_OK;
+}
+
+}  // namespace
+
+extern "C" vbmc_status vbmc_verify_query_device(vbmc_net* net, const uint8_t* d_image, int32_t s,
+                                                const int32_t* d_pixels, int32_t k, uint64_t lo,
+                                                uint64_t hi, const vbmc_options* opt,
+                                                vbmc_result* res, void* stream) {
+    if (!net || !res || !d_image || (!d_pixels && s > 0) || !opt)
+        return fail(VBMC_ERR_ARG, "null argument");
+    if (res->net != net) return fail(VBMC_ERR_ARG, "result belongs to another net");
+    if (res->pending) {
+        vbmc_status st = finish(res);
+        if (st != VBMC_OK) return st;
+    }
+    uint64_t n, h;
+    vbmc_status st = check_query_shape(res, s, k, lo, hi, opt, &n, &h);
+    if (st != VBMC_OK) return st;
+    res->image.clear();
+    res->pixels.clear();
+    return enqueue(net, res, d_image, d_pixels, s, k, lo, h, n, *opt, (cudaStream_t)stream);
+}
+
+extern "C" vbmc_status vbmc_verify_query(vbmc_net* net, const vbmc_query* q, const vbmc_options* opt,
+                                         vbmc_result* res, void* stream) {
+    if (!net || !q || !res || !opt || !q->image || (!q->pixels && q->s > 0))
+        return fail(VBMC_ERR_ARG, "null argument");
+    if (res->net != net) return fail(VBMC_ERR_ARG, "result belongs to another net");
+    if (res->pending) {
+        vbmc_status st = finish(res);
+        if (st != VBMC_OK) return st;
+    }
+    uint64_t n, h;
+    vbmc_status st = check_query_shape(res, q->s, q->k, q->lo, q->hi, opt, &n, &h);
+    if (st != VBMC_OK) return st;
+    const int H0 = net->v.dims[0];
+    for (int p = 0; p < q->s; ++p) {
+        if (q->pixels[p] < 0 || q->pixels[p] >= H0) return fail(VBMC_ERR_ARG, "pixel index out of range");
+        for (int r = 0; r < p; ++r)
+            if (q->pixels[r] == q->pixels[p]) return fail(VBMC_ERR_ARG, "duplicate pixel index");
+    }
+    cudaStream_t stq = (cudaStream_t)stream;
+    VB_CUDA(cudaMemcpyAsync(res->d_image, q->image, H0, cudaMemcpyHostToDevice, stq));
+    if (q->s > 0)
+        VB_CUDA(cudaMemcpyAsync(res->d_pix_in, q->pixels, sizeof(int32_t) * q->s,
+                                cudaMemcpyHostToDevice, stq));
+    st = enqueue(net, res, res->d_image, res->d_pix_in, q->s, q->k, q->lo, h, n, *opt, stq);
+    if (st != VBMC_OK) return st;
+    res->image.assign(q->image, q->image + H0);
+    res->pixels.assign(q->pixels, q->pixels + q->s);
+    return finish(res);
+}
+
+extern "C" vbmc_status vbmc_result_summary(vbmc_result* res, vbmc_summary* out) {
+    if (!res || !out) return fail(VBMC_ERR_ARG, "null argument");
+    vbmc_status st = finish(res);
+    *out = res->sum;
+    return st;
+}
+
+extern "C" vbmc_status vbmc_get_witness(vbmc_result* res, uint64_t* index, int32_t* steps,
+                                        uint8_t* image, double* margin) {
+    if (!res) return fail(VBMC_ERR_ARG, "null argument");
+    vbmc_status st = finish(res);
+    if (st != VBMC_OK) return st;
+    const uint64_t t = res->sum.first_witness;
+    if (index) *index = t;
+    if (t == VBMC_NO_WITNESS) return VBMC_OK;
+    const int s = res->s, k = res->k, R = 2 * k + 1;
+    std::vector<int> d(s);
+    uint64_t tt = t;
+    for (int p = s - 1; p >= 0; --p) {
+        d[p] = (int)(tt % R);
+        tt /= R;
+    }
+    if (steps)
+        for (int p = 0; p < s; ++p) steps[p] = d[p] - k;
+    if (image) {
+        const int H0 = res->net->v.dims[0];
+        std::vector<uint8_t> img(H0);
+        std::vector<int32_t> pix(s);
+        if (!res->image.empty()) {
+            img = res->image;
+            pix = res->pixels;
+        } else {
+            VB_CUDA(cudaMemcpy(img.data(), res->hq.image ? res->hq.image : res->d_image, H0,
+                               cudaMemcpyDeviceToHost));
+            VB_CUDA(cudaMemcpy(pix.data(), res->hq.pix, sizeof(int) * s, cudaMemcpyDeviceToHost));
+        }
+        for (int p = 0; p < s; ++p) {
+            int v = img[pix[p]] + d[p] - k;
+            img[pix[p]] = (uint8_t)std::min(255, std::max(0, v));
+        }
+        std::memcpy(image, img.data(), H0);
+    }
+    if (margin) {
+        launch_margin64(res->net->v, res->d_q, t, res->d_margin, res->last_stream);
+        VB_CUDA(cudaGetLastError());
+        VB_CUDA(cudaMemcpyAsync(margin, res->d_margin, sizeof(double), cudaMemcpyDeviceToHost,
+                                res->last_stream));
+        VB_CUDA(cudaStreamSynchronize(res->last_stream));
+    }
+    return VBMC_OK;
+}
+
+extern "C" vbmc_status vbmc_get_coverage(vbmc_result* res, uint32_t* flip, size_t flip_words,
+                                         uint32_t* flip_tie, uint32_t* ss, size_t ss_words,
+                                         uint32_t* ss_tie, double* covered_fraction) {
+    if (!res) return fail(VBMC_ERR_ARG, "null argument");
+    vbmc_status st = finish(res);
+    if (st != VBMC_OK) return st;
+    if (!res->opt.coverage) return fail(VBMC_ERR_STATE, "coverage was off for the last call");
+    const NetView& v = res->net->v;
+    if ((flip || flip_tie) && flip_words < (size_t)v.flip_words)
+        return fail(VBMC_ERR_ARG, "flip buffer too small");
+    if ((ss || ss_tie || covered_fraction) && ss && ss_words < (size_t)v.ss_words)
+        return fail(VBMC_ERR_ARG, "ss buffer too small");
+    if (flip) VB_CUDA(cudaMemcpy(flip, res->hq.flip, 4ull * v.flip_words, cudaMemcpyDeviceToHost));
+    if (flip_tie)
+        VB_CUDA(cudaMemcpy(flip_tie, res->hq.flip_tie, 4ull * v.flip_words, cudaMemcpyDeviceToHost));
+    std::vector<uint32_t> tmp;
+    uint32_t* ssh = ss;
+    if (!ssh && covered_fraction) {
+        tmp.resize(v.ss_words);
+        ssh = tmp.data();
+    }
+    if (ssh) VB_CUDA(cudaMemcpy(ssh, res->hq.ss, 4ull * v.ss_words, cudaMemcpyDeviceToHost));
+    if (ss_tie) VB_CUDA(cudaMemcpy(ss_tie, res->hq.ss_tie, 4ull * v.ss_words, cudaMemcpyDeviceToHost));
+    if (covered_fraction) {
+        // Eq. 3: neurons in at least one SS-covered pair over all non-input neurons.
+        std::vector<char> cov(v.total, 0);
+        for (int l = 1; l < v.L; ++l) {
+            const int Hl = v.dims[l], Hn = v.dims[l + 1];
+            for (int j = 0; j < Hl; ++j)
+                for (int i = 0; i < Hn; ++i) {
+                    const unsigned long long b = v.ssoff[l] + (unsigned long long)j * Hn + i;
+                    if ((ssh[b >> 5] >> (b & 31)) & 1u) {
+                        cov[v.noff[l] + j] = 1;
+                        cov[v.noff[l + 1] + i] = 1;
+                    }
+                }
+        }
+        int c = 0;
+        for (char x : cov) c += x;
+        *covered_fraction = (double)c / (double)v.total;
+    }
+    return VBMC_OK;
+}
+
+extern "C" vbmc_status vbmc_get_verdict_bitmap(vbmc_result* res, uint32_t* words, size_t n_words) {
+    if (!res || !words) return fail(VBMC_ERR_ARG, "null argument");
+    vbmc_status st = finish(res);
+    if (st != VBMC_OK) return st;
+    if (!res->opt.bitmap) return fail(VBMC_ERR_STATE, "bitmap was off for the last call");
+    const size_t need = (size_t)((res->hi + 31) / 32);
+    if (n_words < need) return fail(VBMC_ERR_ARG, "bitmap buffer too small");
+    VB_CUDA(cudaMemcpy(words, res->hq.bitmap, 4 * need, cudaMemcpyDeviceToHost));
+    return VBMC_OK;
+}
+
+extern "C" vbmc_status vbmc_get_ties(vbmc_result* res, uint64_t* idx, size_t cap, uint64_t* n_ties) {
+    if (!res) return fail(VBMC_ERR_ARG, "null argument");
+    vbmc_status st = finish(res);
+    if (st != VBMC_OK) return st;
+    const uint64_t n = res->sum.n_ties;
+    if (n_ties) *n_ties = n;
+    const size_t kept = (size_t)std::min<uint64_t>(n, res->caps.ties_cap);
+    if (idx && cap) {
+        std::vector<uint64_t> t(kept);
+        if (kept) VB_CUDA(cudaMemcpy(t.data(), res->hq.ties, 8 * kept, cudaMemcpyDeviceToHost));
+        std::sort(t.begin(), t.end());
+        std::memcpy(idx, t.data(), 8 * std::min(cap, kept));
+    }
+    return VBMC_OK;
+}
+
+extern "C" vbmc_status vbmc_verify_batch(vbmc_net* net, const vbmc_query* queries, int32_t nq,
+                                         const vbmc_options* opt, vbmc_result* const* results,
+                                         void* stream) {
+    if (!net || (!queries && nq > 0) || !opt || (!results && nq > 0))
+        return fail(VBMC_ERR_ARG, "null argument");
+    for (int i = 0; i < nq; ++i) {
+        vbmc_status st = vbmc_verify_query(net, &queries[i], opt, results[i], stream);
+        if (st != VBMC_OK) return st;
+    }
+    return VBMC_OK;
+}

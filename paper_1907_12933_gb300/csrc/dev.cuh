@@ -1,0 +1,141 @@
+// dev.cuh -- device-side views shared by the kernels of the verifier.
+//
+// Layout in HBM (one net, one result workspace per query):
+//   net:    W_l fp32 [H_l][H_{l-1}] (row = neuron, Eq. 1), W_l^T fp32, b_l,
+//           per-row norms, bf16/fp16/e4m3 copies for the tensor screens
+//   query:  ub/hb (FP64 potentials/outputs of the unperturbed image, all
+//           layers back to back), per-neuron screen constants (fp32),
+//           layer-1 delta tables tab[p][d][j] (fp32), counters, masks,
+//           verdict bitmap, tie list
+//   queues: (query, point) pairs waiting for a tighter pass
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vbmc {
+
+constexpr int kMaxL = 8;
+constexpr int kMaxS = 16;
+constexpr int kMaxR = 255;
+constexpr int kMaxWidth = 1024;
+constexpr double kTau = 1e-9;  // tie band of margins and potentials
+
+enum { ACT_IDENTITY = 0, ACT_SIGMOID = 1, ACT_RELU = 2 };
+
+// Device error codes latched in Counters::err.
+enum : unsigned {
+    DERR_PIXELS = 1u,    // pixel list not distinct / out of range
+    DERR_QUEUE = 2u,     // a recheck queue overflowed
+    DERR_TIES = 4u,      // tie list truncated (not an error for results)
+    DERR_TC_WAIT = 8u,   // a tensor-core pipeline wait gave up
+};
+
+struct NetView {
+    int L;                  // weight layers
+    int act;                // hidden activation
+    int total;              // non-input neurons
+    int hmax;               // max width over layers 1..L
+    int dims[kMaxL + 1];    // H_0..H_L
+    int noff[kMaxL + 2];    // neuron offset of layer l (1..L) in concatenated vectors
+    long long ssoff[kMaxL + 1];  // SS bit offset of pair (l, l+1), l = 1..L-1
+    int flip_words, ss_words;
+    const float* W[kMaxL + 1];   // W[l], l = 1..L: [H_l][H_{l-1}]
+    const float* WT[kMaxL + 1];  // [H_{l-1}][H_l]
+    const float* b[kMaxL + 1];
+    const float* rownorm[kMaxL + 1];  // ||W_l,i||_2 (rounded up)
+    float lamfrob[kMaxL + 1];         // lambda * ||W_l||_F (rounded up; lambda: Lipschitz
+                                      // constant of the hidden activation)
+    float gam[kMaxL + 1];             // gamma_{H_{l-1}} = n u / (1 - n u), u = 2^-24
+};
+
+struct Counters {
+    unsigned long long n_adv;
+    unsigned long long first;    // smallest adversarial index
+    unsigned long long n_ties;
+    unsigned long long n_q[3];   // entries pushed to queue level 0 (tensor 3x), 1 (FP32), 2 (FP64)
+    unsigned long long n_points;
+    unsigned int err;
+    int D;
+    double base_margin;
+};
+
+struct QueryView {
+    int s, k, R, qid;
+    unsigned long long n_points, lo, hi;  // space size and checked range
+    const uint8_t* image;   // H_0 grey levels (device)
+    const int* pix_in;      // s pixel indices as given (device)
+    int* pix;               // validated copy
+    int* dv;                // [s][R]: clamp(v_p + d - k, 0, 255) - v_p
+    double* ub;             // [total] FP64 potentials of the unperturbed image
+    double* hb;             // [total] FP64 outputs (act(ub); output layer: ub)
+    float* ub32;            // [total] fp32(ub)
+    float* dub;             // [total] value error of fl(ub) (+ layer-1 table-sum error)
+    float* thr;             // [total] sign-certainty threshold: dub + 2 tau, or +inf when
+                            //         |ub| < tau (every evaluation is a sign tie)
+    float* c1;              // [total] delta-activation constants (see screen_simt.cu)
+    float* c2;
+    float* tab;             // [s][R][H_1] layer-1 deltas W_1[j][p] * dv / 255
+    float* kvec;            // [kMaxL+1] per-layer constant error-norm terms
+    Counters* cnt;
+    uint32_t* bitmap;       // verdict bits (nullptr: off)
+    unsigned long long bitmap_bits;
+    uint32_t *flip, *flip_tie, *ss, *ss_tie;  // nullptr: coverage off
+    unsigned long long* ties;
+    unsigned int ties_cap;
+};
+
+struct QEntry {
+    unsigned long long t;
+    unsigned int q;
+    unsigned int pad;
+};
+
+struct Queue {
+    QEntry* e;
+    unsigned long long* count;  // entries pushed (may exceed cap: overflow)
+    unsigned long long cap;
+};
+
+__device__ __forceinline__ void set_bit_atomic(uint32_t* w, unsigned long long b) {
+    atomicOr(&w[b >> 5], 1u << (unsigned)(b & 31));
+}
+
+__device__ __forceinline__ void queue_push(const Queue& Q, unsigned long long t, unsigned q,
+                                           Counters* cnt, int level) {
+    unsigned long long i = atomicAdd(Q.count, 1ull);
+    atomicAdd(&cnt->n_q[level], 1ull);
+    if (i < Q.cap) {
+        QEntry e;
+        e.t = t;
+        e.q = q;
+        e.pad = 0;
+        Q.e[i] = e;
+    } else {
+        atomicOr(&cnt->err, DERR_QUEUE);
+    }
+}
+
+// Record a certainly adversarial (non-tie) point.
+__device__ __forceinline__ void record_adversarial(const QueryView& Q, unsigned long long t) {
+    atomicAdd(&Q.cnt->n_adv, 1ull);
+    atomicMin(&Q.cnt->first, t);
+    if (Q.bitmap && t < Q.bitmap_bits) set_bit_atomic(Q.bitmap, t);
+}
+
+// Mixed-radix decode: first pixel most significant.
+__device__ __forceinline__ void decode_digits(unsigned long long t, int s, int R, int* d) {
+    if (t < 0xFFFFFFFFull) {
+        unsigned tt = (unsigned)t;
+        for (int p = s - 1; p >= 0; --p) {
+            d[p] = (int)(tt % (unsigned)R);
+            tt /= (unsigned)R;
+        }
+    } else {
+        for (int p = s - 1; p >= 0; --p) {
+            d[p] = (int)(t % (unsigned long long)R);
+            t /= (unsigned long long)R;
+        }
+    }
+}
+
+}  // namespace vbmc

@@ -1,0 +1,38 @@
+// launch.h -- host-side launchers of the device passes (internal).
+#pragma once
+#include "dev.cuh"
+
+namespace vbmc {
+
+// FP64 base pass, tables and screen constants for nq queries (d_qs on device).
+// max_sr: max over queries of s * R.
+void launch_prologue(const NetView& net, QueryView* d_qs, int nq, int max_sr, cudaStream_t st);
+
+// Shape class of the FP32 SIMT screen for a net (0: unsupported).
+int simt_variant(const NetView& net);
+
+// FP32 SIMT screen. Range mode (gather == nullptr): tiles of each query are
+// numbered tile_prefix[q] .. tile_prefix[q+1]-1, n_tiles in total. Gather
+// mode: the points are gather[0 .. *gather_count). Points the FP32 bound
+// cannot decide go to `out`.
+void launch_screen_simt(const NetView& net, const QueryView* d_qs, int nq,
+                        const unsigned long long* d_tile_prefix, unsigned long long n_tiles,
+                        const QEntry* gather, const unsigned long long* gather_count,
+                        unsigned long long gather_cap, Queue out, int out_level, int n_sm,
+                        cudaStream_t st);
+
+// Points per tile of the SIMT screen for this net.
+int simt_tile_points(const NetView& net);
+
+// FP64 pass: gather mode over a queue, or range mode over [lo, hi) of query 0
+// when gather == nullptr.
+void launch_fp64(const NetView& net, const QueryView* d_qs, int nq, const QEntry* gather,
+                 const unsigned long long* gather_count, unsigned long long gather_cap,
+                 unsigned long long range_lo, unsigned long long range_hi, int n_sm,
+                 cudaStream_t st);
+
+// FP64 margin of point t of query 0 into *d_out.
+void launch_margin64(const NetView& net, const QueryView* d_qs, unsigned long long t, double* d_out,
+                     cudaStream_t st);
+
+}  // namespace vbmc

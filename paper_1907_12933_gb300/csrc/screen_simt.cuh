@@ -1,0 +1,358 @@
+// screen_simt.cuh -- the plain FP32 path on CUDA cores, with a proven error bound.
+//
+// A CTA owns a tile of MT points (8 warps x PPW points). For each point:
+//   S1  decode t into s digits (first pixel most significant)
+//   S2  layer 1 incrementally: du_j = sum_p tab[p][d_p][j]            (Eq. 1)
+//   S3  sign test and delta activation dh = act(ub + du) - act(ub)    (Eq. 2, sign)
+//   S4  layers 2..L in FP32 on the deltas: du_l = W_l dh_{l-1}, weight
+//       chunks staged in shared memory, 128 accumulators per thread
+//   S5  logits, class, margin, adversarial flag                       (Eq. 10)
+//   S6  certain sign changes -> flip mask; SS-Cover pairs of the point
+//   S7  verdict bit, count, first witness; undecided points -> queue
+//
+// Error bound (per point, per layer, u = 2^-24, gamma_n = n u / (1 - n u)):
+//   N_l = ||dh_l||_2 as computed (rounded up), E_l = bound on ||dh_l - exact||_2
+//   X_l = gamma_{H_{l-1}} N_{l-1} + E_{l-1}
+//   |du_l,i - exact| <= ||W_l,i||_2 X_l              (dot-product error + propagated error)
+//   E_l = lambda ||W_l||_F X_l + kvec_l + u N_l      (lambda = 1 for ReLU, 1/4 for sigmoid)
+// A neuron's sign is certain when |fl(ub) + du| exceeds that bound plus the
+// constant threshold (fp32 rounding of ub, 2 tau); the verdict is certain
+// when every margin difference exceeds the combined bound. Anything else
+// sends the whole point to the next pass.
+#pragma once
+#include "dev.cuh"
+#include "launch.h"
+
+namespace vbmc {
+namespace simt {
+
+constexpr int KC = 8;
+constexpr int FCAP = 6;
+constexpr int THREADS = 256;
+
+template <int PPW, int NQ>
+struct SimtSmem {
+    static constexpr int MT = 8 * PPW;
+    static constexpr int HS = 32 * NQ;
+    static constexpr int WS = HS + 4;
+    float A[MT][HS];
+    float Wsm[2][KC][WS];
+    unsigned long long t[MT];
+    int q[MT];
+    int valid[MT];
+    int unc[MT];
+    int vstate[MT];
+    float N[MT];
+    float E[MT];
+    int fcnt[MT][kMaxL + 1];
+    short flist[MT][kMaxL + 1][FCAP];
+    unsigned char dig[MT][kMaxS];
+};
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Upper bound of sqrt of a non-negative sum of <= 1024 fp32 terms computed in fp32.
+__device__ __forceinline__ float norm_up(float s) {
+    return __fsqrt_ru(__fmul_ru(s, 1.0002f));
+}
+
+__device__ __forceinline__ float act_delta(int act, float du, float u, float c1, float c2) {
+    if (act == ACT_RELU) return fmaxf(du + c1, c2);
+    if (act == ACT_SIGMOID) return 1.0f / (1.0f + expf(-u)) - c2;
+    return du;
+}
+
+template <int PPW, int NQ>
+__global__ void __launch_bounds__(THREADS, 1)
+k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
+              const unsigned long long* __restrict__ tile_prefix, unsigned long long n_tiles,
+              const QEntry* __restrict__ gather, const unsigned long long* __restrict__ gather_count,
+              unsigned long long gather_cap, Queue out, int out_level) {
+    using Sm = SimtSmem<PPW, NQ>;
+    constexpr int MT = Sm::MT, HS = Sm::HS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Sm& S = *reinterpret_cast<Sm*>(smem_raw);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int L = net.L;
+
+    unsigned long long tiles = n_tiles;
+    unsigned long long gcount = 0;
+    if (gather) {
+        gcount = *gather_count;
+        if (gcount > gather_cap) gcount = gather_cap;
+        tiles = (gcount + MT - 1) / MT;
+    }
+
+    for (unsigned long long g = blockIdx.x; g < tiles; g += gridDim.x) {
+        // ---- S1: decode
+        if (lane < PPW) {
+            const int m = warp * PPW + lane;
+            unsigned long long t = 0;
+            int q = 0;
+            bool ok;
+            if (gather) {
+                unsigned long long idx = g * MT + m;
+                ok = idx < gcount;
+                if (ok) {
+                    QEntry e = gather[idx];
+                    t = e.t;
+                    q = (int)e.q;
+                }
+            } else {
+                int lo = 0, hi = nq - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (tile_prefix[mid] <= g) lo = mid; else hi = mid - 1;
+                }
+                q = lo;
+                const QueryView& Q = qs[q];
+                t = (Q.lo & ~31ull) + (g - tile_prefix[q]) * MT + m;
+                ok = t >= Q.lo && t < Q.hi;
+            }
+            S.t[m] = t;
+            S.q[m] = q;
+            S.valid[m] = ok;
+            S.unc[m] = 0;
+            S.vstate[m] = 0;
+#pragma unroll
+            for (int l = 0; l <= kMaxL; ++l) S.fcnt[m][l] = 0;
+            if (ok) {
+                const QueryView& Q = qs[q];
+                int d[kMaxS];
+                decode_digits(t, Q.s, Q.R, d);
+                for (int p = 0; p < Q.s; ++p) S.dig[m][p] = (unsigned char)d[p];
+            }
+        }
+        __syncwarp();
+
+        // ---- S2/S3: layer 1 from the delta tables
+        {
+            const int H1 = net.dims[1];
+            for (int r = 0; r < PPW; ++r) {
+                const int m = warp * PPW + r;
+                if (!S.valid[m]) continue;
+                const QueryView& Q = qs[S.q[m]];
+                const int R = Q.R, s = Q.s;
+                const float* tab = Q.tab;
+                int offs[kMaxS];
+                for (int p = 0; p < s; ++p) offs[p] = (p * R + S.dig[m][p]) * H1;
+                float nsum = 0.f;
+#pragma unroll
+                for (int qq = 0; qq < NQ; ++qq) {
+                    const int j = lane + 32 * qq;
+                    float dh = 0.f;
+                    if (j < H1) {
+                        float du = 0.f;
+                        for (int p = 0; p < s; ++p) du += __ldg(&tab[offs[p] + j]);
+                        const float ub = Q.ub32[j];
+                        const float u = ub + du;
+                        const float thr = Q.thr[j];
+                        if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > thr)) {
+                            S.unc[m] = 1;
+                        } else if ((u >= 0.f) != (ub >= 0.f)) {
+                            int idx = atomicAdd(&S.fcnt[m][1], 1);
+                            if (idx < FCAP) S.flist[m][1][idx] = (short)j;
+                            if (Q.flip) set_bit_atomic(Q.flip, j);
+                        }
+                        if (L > 1) dh = act_delta(net.act, du, u, Q.c1[j], Q.c2[j]);
+                        else dh = u;
+                        nsum = fmaf(dh, dh, nsum);
+                    }
+                    S.A[m][j] = dh;
+                }
+                nsum = warp_sum(nsum);
+                if (lane == 0) {
+                    const float N = norm_up(nsum);
+                    S.N[m] = N;
+                    S.E[m] = __fmaf_ru(0x1p-24f, N, Q.kvec[1]);
+                }
+            }
+            __syncwarp();
+        }
+
+        // ---- S4: dense layers on the deltas
+        for (int l = 2; l <= L; ++l) {
+            const int K = net.dims[l - 1], N = net.dims[l];
+            const float* __restrict__ W = net.W[l];
+            const int nchunks = (K + KC - 1) / KC;
+            float acc[PPW][NQ];
+#pragma unroll
+            for (int r = 0; r < PPW; ++r)
+#pragma unroll
+                for (int qq = 0; qq < NQ; ++qq) acc[r][qq] = 0.f;
+
+            auto load_chunk = [&](int c, int buf) {
+                for (int e = threadIdx.x; e < KC * HS; e += THREADS) {
+                    const int n = e / KC, kk = e % KC, k = c * KC + kk;
+                    S.Wsm[buf][kk][n] = (n < N && k < K) ? __ldg(&W[(size_t)n * K + k]) : 0.f;
+                }
+            };
+            __syncthreads();  // previous users of Wsm are done
+            load_chunk(0, 0);
+            __syncthreads();
+            for (int c = 0; c < nchunks; ++c) {
+                const int buf = c & 1;
+                if (c + 1 < nchunks) load_chunk(c + 1, buf ^ 1);
+#pragma unroll
+                for (int kk = 0; kk < KC; kk += 4) {
+                    float4 a4[PPW];
+#pragma unroll
+                    for (int r = 0; r < PPW; ++r)
+                        a4[r] = *reinterpret_cast<const float4*>(&S.A[warp * PPW + r][c * KC + kk]);
+#pragma unroll
+                    for (int k4 = 0; k4 < 4; ++k4) {
+                        float wv[NQ];
+#pragma unroll
+                        for (int qq = 0; qq < NQ; ++qq) wv[qq] = S.Wsm[buf][kk + k4][lane + 32 * qq];
+#pragma unroll
+                        for (int r = 0; r < PPW; ++r) {
+                            const float a = k4 == 0 ? a4[r].x : k4 == 1 ? a4[r].y : k4 == 2 ? a4[r].z : a4[r].w;
+#pragma unroll
+                            for (int qq = 0; qq < NQ; ++qq) acc[r][qq] = fmaf(a, wv[qq], acc[r][qq]);
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+
+            // epilogue of layer l
+            const float* rn = net.rownorm[l];
+            const int off = net.noff[l];
+            const float lf = net.lamfrob[l], gl = net.gam[l];
+#pragma unroll
+            for (int r = 0; r < PPW; ++r) {
+                const int m = warp * PPW + r;
+                if (!S.valid[m]) continue;
+                const QueryView& Q = qs[S.q[m]];
+                const float X = __fmaf_ru(gl, S.N[m], S.E[m]);
+                float nsum = 0.f, usum = 0.f;
+#pragma unroll
+                for (int qq = 0; qq < NQ; ++qq) {
+                    const int n = lane + 32 * qq;
+                    if (n < N) {
+                        const int gi = off + n;
+                        const float du = acc[r][qq];
+                        const float ub = Q.ub32[gi];
+                        const float u = ub + du;
+                        const float bound = __fmaf_ru(rn[n], X, Q.thr[gi]);
+                        if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound)) {
+                            S.unc[m] = 1;
+                        } else if ((u >= 0.f) != (ub >= 0.f)) {
+                            int idx = atomicAdd(&S.fcnt[m][l], 1);
+                            if (idx < FCAP) S.flist[m][l][idx] = (short)n;
+                            if (Q.flip) set_bit_atomic(Q.flip, gi);
+                        }
+                        if (l < L) {
+                            const float dh = act_delta(net.act, du, u, Q.c1[gi], Q.c2[gi]);
+                            nsum = fmaf(dh, dh, nsum);
+                            usum = fmaf(u, u, usum);
+                            S.A[m][n] = dh;
+                        } else {
+                            S.A[m][n] = u;
+                        }
+                    } else if (l < L && n < HS) {
+                        S.A[m][n] = 0.f;
+                    }
+                }
+                nsum = warp_sum(nsum);
+                usum = warp_sum(usum);
+                if (lane == 0) {
+                    if (l < L) {
+                        const float Nl = norm_up(nsum);
+                        float El = __fmaf_ru(lf, X, Q.kvec[l]);
+                        El = __fmaf_ru(0x1p-24f, Nl, El);
+                        if (net.act == ACT_SIGMOID) El = __fmaf_ru(0x1p-26f, norm_up(usum), El);
+                        S.N[m] = Nl;
+                        S.E[m] = El;
+                    } else {
+                        S.E[m] = X;  // X_L, for the verdict
+                    }
+                }
+            }
+            __syncwarp();
+        }
+
+        // ---- S5: verdict (layer L values are in A[m][0..H_L))
+        {
+            const int HL = net.dims[L], offL = net.noff[L];
+            const float* rn = net.rownorm[L];
+            for (int r = 0; r < PPW; ++r) {
+                const int m = warp * PPW + r;
+                if (!S.valid[m]) continue;
+                const QueryView& Q = qs[S.q[m]];
+                const int D = Q.cnt->D;
+                float X = S.E[m];
+                if (L == 1) X = 0.f;  // single layer: the table sums carry their own bound in thr
+                const float yD = S.A[m][D];
+                const float rD = L > 1 ? rn[D] : 0.f;
+                const float dD = Q.dub[offL + D];
+                bool unsafe = false, safe = true;
+                for (int o = lane; o < HL; o += 32) {
+                    if (o == D) continue;
+                    const float yo = S.A[m][o];
+                    const float diff = yD - yo;
+                    const float ro = L > 1 ? rn[o] : 0.f;
+                    float eb = __fmaf_ru(__fadd_ru(rD, ro), X,
+                                         __fadd_ru(__fadd_ru(dD, Q.dub[offL + o]), (float)(2.0 * kTau)));
+                    eb = __fmaf_ru(0x1p-23f, __fadd_ru(__fadd_ru(fabsf(yD), fabsf(yo)), fabsf(diff)), eb);
+                    if (diff < -eb) unsafe = true;
+                    else if (!(diff > eb)) safe = false;
+                }
+                unsafe = __any_sync(0xffffffffu, unsafe);
+                safe = __all_sync(0xffffffffu, safe);
+                if (lane == 0) S.vstate[m] = unsafe ? 1 : (safe ? 0 : 2);
+            }
+            __syncwarp();
+        }
+
+        // ---- S6/S7: per-point results
+        if (lane < PPW) {
+            const int m = warp * PPW + lane;
+            if (S.valid[m]) {
+                const QueryView& Q = qs[S.q[m]];
+                bool bad = S.unc[m] || S.vstate[m] == 2;
+                if (!bad && Q.ss)
+                    for (int l = 1; l < L; ++l)
+                        if (S.fcnt[m][l] == 1 && S.fcnt[m][l + 1] > FCAP) bad = true;
+                if (bad) {
+                    queue_push(out, S.t[m], (unsigned)S.q[m], Q.cnt, out_level);
+                } else {
+                    if (S.vstate[m] == 1) record_adversarial(Q, S.t[m]);
+                    if (Q.ss) {
+                        for (int l = 1; l < L; ++l) {
+                            if (S.fcnt[m][l] != 1) continue;
+                            const int j = S.flist[m][l][0];
+                            const int Hn = net.dims[l + 1];
+                            const int nt = S.fcnt[m][l + 1];
+                            for (int e = 0; e < nt; ++e)
+                                set_bit_atomic(Q.ss, (unsigned long long)net.ssoff[l] +
+                                                         (unsigned long long)j * Hn + S.flist[m][l + 1][e]);
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <int PPW, int NQ>
+void launch_variant(const NetView& net, const QueryView* d_qs, int nq, const unsigned long long* tp,
+                    unsigned long long n_tiles, const QEntry* gather, const unsigned long long* gc,
+                    unsigned long long gcap, Queue out, int level, int n_sm, cudaStream_t st) {
+    const size_t smem = sizeof(SimtSmem<PPW, NQ>);
+    auto kern = k_screen_simt<PPW, NQ>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = smem < 60000 ? 2 : 1;
+    unsigned long long grid = (unsigned long long)n_sm * per_sm;
+    if (!gather && n_tiles < grid) grid = n_tiles ? n_tiles : 1;
+    kern<<<(unsigned)grid, THREADS, smem, st>>>(net, d_qs, nq, tp, n_tiles, gather, gc, gcap, out,
+                                                level);
+}
+
+}  // namespace simt
+}  // namespace vbmc
