@@ -68,8 +68,7 @@ struct vbmc_net {
     std::vector<void*> owned;
     int n_sm = 0;
     int device = 0;
-    TcNet tc{};  // tensor-core copies (built on first use)
-    bool tc_ready = false;
+    TcNet tc{};  // tensor-core copies (built on first use per precision)
     std::vector<std::vector<float>> hW, hb;  // host copies for tensor-core set-up
 };
 
@@ -238,6 +237,8 @@ extern "C" vbmc_status vbmc_result_create(const vbmc_net* net, const vbmc_caps* 
     A(&q.c2, T);
     A(&q.tab, (size_t)S * RM * v.dims[1]);
     A(&q.kvec, (size_t)kMaxL + 1);
+    A(&q.cpos, (size_t)(kMaxL + 1) * 32);
+    A(&q.cneg, (size_t)(kMaxL + 1) * 32);
     A(&q.flip, (size_t)v.flip_words);
     A(&q.flip_tie, (size_t)v.flip_words);
     A(&q.ss, (size_t)v.ss_words);
@@ -347,11 +348,11 @@ vbmc_status enqueue(vbmc_net* net, vbmc_result* r, const uint8_t* d_image, const
         } else {
             if (!tc_supported(v, opt.precision))
                 return fail(VBMC_ERR_UNSUPPORTED, "tensor-core screen does not support this net/precision");
-            if (!net->tc_ready) {
-                vbmc_status sst = tc_build(net->tc, v, net->hW, net->hb);
-                if (sst != VBMC_OK) return sst;
-                net->tc_ready = true;
+            {
+                vbmc_status sst = tc_build(net->tc, v, net->hW, net->hb, opt.precision);
+                if (sst != VBMC_OK) return fail(sst, "tensor-core set-up failed");
             }
+            tc_launch_query_setup(net->tc, v, r->d_q, opt.precision, st);
             // tensor screen -> tensor 3x pass -> FP32 pass -> FP64 pass
             Queue q3{r->d_queue[0], r->d_qcount + 0, cap};
             Queue q32{r->d_queue[1], r->d_qcount + 1, cap};

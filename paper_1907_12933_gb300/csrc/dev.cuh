@@ -76,6 +76,8 @@ struct QueryView {
     float* c2;
     float* tab;             // [s][R][H_1] layer-1 deltas W_1[j][p] * dv / 255
     float* kvec;            // [kMaxL+1] per-layer constant error-norm terms
+    uint32_t* cpos;         // [kMaxL+1][32] tensor screen: columns whose sign never changes
+    uint32_t* cneg;         //   (pos: output change = input change; neg: output stays 0)
     Counters* cnt;
     uint32_t* bitmap;       // verdict bits (nullptr: off)
     unsigned long long bitmap_bits;

@@ -1,25 +1,1064 @@
-// tc.cu -- tensor-core screen (tcgen05). Placeholder until the kernel lands.
+// tc.cu -- tensor-core screen: layers 2..L of every point on tcgen05, BF16 or FP16
+// operands, FP32 accumulation in TMEM, weights by TMA, error bound per point.
+//
+// CTA = 128 points (one MMA M). Warp roles:
+//   warp 0      TMA producer: weight tiles [slice x 64] of W_l (K-major,
+//               128-byte swizzle) into a ring of NB 16 KB slots
+//   warp 1      TMEM owner (512 columns) and MMA issuer (one thread)
+//   warps 2..9  workers: build the layer-2 operand (incremental layer 1,
+//               Eq. 1, from the delta tables), drain each layer's
+//               accumulator from TMEM, apply ReLU in delta form, quantise to
+//               16-bit into the next layer's operand ring (NA 16 KB slots of
+//               128 rows x 64 K), and finish each point: margin and class
+//               (Eq. 10), sign changes and SS-Cover pairs (Sec. III-B).
+//
+// Delta form: every layer carries dh_l = h_l(point) - h_l(unperturbed image);
+// the FP64 values of the unperturbed image come from the prologue, so the
+// 16-bit rounding error scales with ||dh||, not ||h||.
+//
+// Error bound of du_l,i (per point, all norms 2-norms, u_acc = 2^-22 per
+// accumulated product, Wq = rounded weights, Wr = W - Wq [- Wlo]):
+//   |err| <= a_i (R + E + rho Lo + u_acc n (N + R + Lo)) + b_i (N + E)
+// with a_i = ||Wq_i (+ Wlo_i)||, b_i = ||Wr_i||, N = ||dh_{l-1}||,
+// R = ||dh_{l-1} - hi - lo|| (exact residual of the operand split),
+// Lo = ||lo||, E = bound on the error of dh_{l-1}. The error vector of a
+// whole layer propagates with spectral-norm bounds (sigma), the margin with
+// the norms of row differences of the output layer. Split mode (three
+// products hi*Wq + lo*Wq + hi*Wlo) is the tighter second pass.
+#include "dev.cuh"
+#include "launch.h"
 #include "tc.h"
+#include "tc_ptx.cuh"
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
 
 namespace vbmc {
 
-bool tc_supported(const NetView&, int) { return false; }
-vbmc_status tc_build(TcNet&, const NetView&, const std::vector<std::vector<float>>&,
-                     const std::vector<std::vector<float>>&) {
-    return VBMC_ERR_UNSUPPORTED;
+namespace {
+
+constexpr int TC_THREADS = 320;
+constexpr int NA = 4;
+constexpr int NB = 7;
+constexpr int SLOT = 16384;
+constexpr int FCAP = 4;
+constexpr int PMAX = 4;
+constexpr int MROWS = 128;
+
+struct TcSmem {
+    uint8_t A[NA][SLOT];
+    uint8_t B[NB][SLOT];
+    float souter[PMAX][512];
+    unsigned long long pref[PMAX];
+    unsigned long long t[MROWS];
+    int valid[MROWS];
+    int pidx[MROWS];
+    unsigned char dig[MROWS][kMaxS];
+    float N[MROWS], R[MROWS], Lo[MROWS], E[MROWS];
+    float part[2][MROWS][3];
+    int unc[MROWS];
+    int vst[MROWS];
+    int fcnt[MROWS][kTcMaxL + 1];
+    short flist[MROWS][kTcMaxL + 1][FCAP];
+    int npref;
+    int uniform_base;
+    unsigned long long bars[2 * NB + 2 * NA + 5];
+    uint32_t tmem_slot;
+    int abort_flag;
+};
+
+// bar indices
+__device__ __forceinline__ int BFULL(int i) { return i; }
+__device__ __forceinline__ int BEMPTY(int i) { return NB + i; }
+__device__ __forceinline__ int AFULL(int i) { return 2 * NB + i; }
+__device__ __forceinline__ int AEMPTY(int i) { return 2 * NB + NA + i; }
+constexpr int DFULL = 2 * NB + 2 * NA;
+constexpr int TFREE = DFULL + 1;
+constexpr int DRAINED = DFULL + 2;
+constexpr int FIN = DFULL + 3;
+
+__device__ __forceinline__ float norm_up(float s) { return __fsqrt_ru(__fmul_ru(s, 1.0002f)); }
+
+// Round two floats to a packed 16-bit pair (low half = first) and return the
+// rounded values as floats.
+template <bool BF>
+__device__ __forceinline__ uint32_t pack2(float x, float y, float& qx, float& qy) {
+    if (BF) {
+        __nv_bfloat162 p = __floats2bfloat162_rn(x, y);
+        qx = __low2float(p);
+        qy = __high2float(p);
+        return *reinterpret_cast<uint32_t*>(&p);
+    } else {
+        __half2 p = __floats2half2_rn(x, y);
+        qx = __low2float(p);
+        qy = __high2float(p);
+        return *reinterpret_cast<uint32_t*>(&p);
+    }
 }
+
+// Byte offset of 16-byte unit `u` (0..7) of row r in a 128-row x 128-byte slot,
+// 128-byte swizzle (the layout TMA writes and the MMA descriptor reads).
+__device__ __forceinline__ uint32_t sw_off(int r, int u) {
+    return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((u ^ (r & 7)) << 4));
+}
+
+template <bool SPLIT, bool BF>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restrict__ qs,
+     unsigned long long lo, unsigned long long hi, const QEntry* __restrict__ gather,
+     const unsigned long long* __restrict__ gcount, unsigned long long gcap, Queue out,
+     int out_level) {
+    extern __shared__ uint8_t smem_raw[];
+    TcSmem& S = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                           ~uintptr_t(1023));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const QueryView& Q = qs[0];
+    const int L = P.L;
+    volatile int* abortp = &S.abort_flag;
+
+    unsigned long long ntiles, base = 0, gn = 0;
+    if (gather) {
+        gn = *gcount;
+        if (gn > gcap) gn = gcap;
+        ntiles = (gn + MROWS - 1) / MROWS;
+    } else {
+        base = lo & ~31ull;
+        ntiles = hi > base ? (hi - base + MROWS - 1) / MROWS : 0;
+    }
+
+    auto bar = [&](int i) { return tc::smem_u32(&S.bars[i]); };
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NB; ++i) {
+            tc::mbar_init(bar(BFULL(i)), 1);
+            tc::mbar_init(bar(BEMPTY(i)), 1);
+        }
+        for (int i = 0; i < NA; ++i) {
+            tc::mbar_init(bar(AFULL(i)), 8);
+            tc::mbar_init(bar(AEMPTY(i)), 1);
+        }
+        tc::mbar_init(bar(DFULL), 1);
+        tc::mbar_init(bar(TFREE), 8);
+        tc::mbar_init(bar(DRAINED), 8);
+        tc::mbar_init(bar(FIN), 1);
+        S.abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tc::smem_u32(&S.tmem_slot), 512);
+        tc::tmem_relinquish();
+    }
+    if (warp == 0 && lane == 0)
+        for (int l = 2; l <= L; ++l) {
+            tc::prefetch_tmap(&P.tq[l]);
+            if (SPLIT) tc::prefetch_tmap(&P.tlo[l]);
+        }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = S.tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (unsigned long long g = blockIdx.x; g < ntiles && ok; g += gridDim.x)
+                for (int l = 2; l <= L && ok; ++l) {
+                    const TcLayer& ly = P.ly[l];
+                    for (int kc = 0; kc < ly.kch && ok; ++kc)
+                        for (int s = 0; s < ly.nslice && ok; ++s)
+                            for (int part = 0; part < (SPLIT ? 2 : 1); ++part) {
+                                const int slot = it % NB;
+                                if (!tc::mbar_wait(bar(BEMPTY(slot)), ((it / NB) & 1) ^ 1, abortp)) {
+                                    ok = false;
+                                    break;
+                                }
+                                tc::mbar_expect_tx(bar(BFULL(slot)), (uint32_t)ly.slice * 128u);
+                                tc::tma_load_2d(tc::smem_u32(S.B[slot]), part ? &P.tlo[l] : &P.tq[l],
+                                                kc * 64, s * ly.slice, bar(BFULL(slot)));
+                                ++it;
+                            }
+                }
+            if (!ok) {  // let the copies already issued land before the CTA leaves
+                for (uint32_t i = it > (uint32_t)NB ? it - NB : 0; i < it; ++i) {
+                    volatile int never = 0;
+                    for (int spin = 0; spin < (1 << 20); ++spin)
+                        if (tc::mbar_try(bar(BFULL(i % NB)), (i / NB) & 1)) break;
+                    (void)never;
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            uint32_t ait = 0, bit = 0, tile_i = 0, drit = 0;
+            bool ok = true;
+            for (unsigned long long g = blockIdx.x; g < ntiles && ok; g += gridDim.x, ++tile_i) {
+                if (!tc::mbar_wait(bar(TFREE), (tile_i & 1) ^ 1, abortp)) { ok = false; break; }
+                tc::tc_fence_after();
+                for (int l = 2; l <= L && ok; ++l) {
+                    const TcLayer& ly = P.ly[l];
+                    if (l >= 3 && ly.Npad > 64) {
+                        if (!tc::mbar_wait(bar(DRAINED), drit & 1, abortp)) { ok = false; break; }
+                        ++drit;
+                        tc::tc_fence_after();
+                    }
+                    const uint32_t idesc = tc::idesc_f16(128, ly.slice, BF);
+                    for (int kc = 0; kc < ly.kch && ok; ++kc) {
+                        const int a0 = ait % NA, a1 = (ait + 1) % NA;
+                        if (!tc::mbar_wait(bar(AFULL(a0)), (ait / NA) & 1, abortp)) { ok = false; break; }
+                        if (SPLIT && !tc::mbar_wait(bar(AFULL(a1)), ((ait + 1) / NA) & 1, abortp)) {
+                            ok = false;
+                            break;
+                        }
+                        tc::tc_fence_after();
+                        const uint32_t ab0 = tc::smem_u32(S.A[a0]), ab1 = tc::smem_u32(S.A[a1]);
+                        for (int s = 0; s < ly.nslice && ok; ++s) {
+                            const int b0 = bit % NB, b1 = (bit + 1) % NB;
+                            if (!tc::mbar_wait(bar(BFULL(b0)), (bit / NB) & 1, abortp)) { ok = false; break; }
+                            if (SPLIT && !tc::mbar_wait(bar(BFULL(b1)), ((bit + 1) / NB) & 1, abortp)) {
+                                ok = false;
+                                break;
+                            }
+                            tc::tc_fence_after();
+                            const uint32_t bb0 = tc::smem_u32(S.B[b0]), bb1 = tc::smem_u32(S.B[b1]);
+                            const uint32_t d = tmem + (uint32_t)(s * ly.slice);
+#pragma unroll
+                            for (int ks = 0; ks < 4; ++ks) {
+                                const uint64_t ad = tc::desc_sw128(ab0 + ks * 32);
+                                const uint64_t bd = tc::desc_sw128(bb0 + ks * 32);
+                                tc::mma_f16(d, ad, bd, idesc, (kc | ks) != 0);
+                                if (SPLIT) {
+                                    tc::mma_f16(d, tc::desc_sw128(ab1 + ks * 32), bd, idesc, 1);
+                                    tc::mma_f16(d, ad, tc::desc_sw128(bb1 + ks * 32), idesc, 1);
+                                }
+                            }
+                            tc::mma_commit(bar(BEMPTY(b0)));
+                            if (SPLIT) tc::mma_commit(bar(BEMPTY(b1)));
+                            bit += SPLIT ? 2 : 1;
+                        }
+                        tc::mma_commit(bar(AEMPTY(a0)));
+                        if (SPLIT) tc::mma_commit(bar(AEMPTY(a1)));
+                        ait += SPLIT ? 2 : 1;
+                    }
+                    tc::mma_commit(bar(DFULL));
+                }
+            }
+            // everything issued must finish before TMEM is released
+            tc::mma_commit(bar(FIN));
+            for (uint32_t spin = 0; spin < tc::kSpinLimit; ++spin) {
+                if (tc::mbar_try(bar(FIN), 0)) break;
+                if ((spin & 63) == 63) __nanosleep(64);
+            }
+        }
+    } else {
+        // -------------------------------------------------------------- workers
+        const int wid = warp - 2;            // 0..7
+        const int wtid = threadIdx.x - 64;   // 0..255
+        const int qd = warp & 3;             // TMEM lane quarter
+        const int hf = wid >> 2;             // column half in the drain phases
+        const int H0 = net.dims[0], H1 = net.dims[1];
+        const int s = Q.s, R = Q.R;
+        const int ni = s >= 2 ? 2 : s;       // inner digits handled per row
+        unsigned long long Rni = 1;
+        for (int i = 0; i < ni; ++i) Rni *= (unsigned long long)R;
+        uint32_t ait = 0, dit = 0;
+        const float uacc_base = 0x1p-22f * (SPLIT ? 3.f : 1.f);
+        (void)H0;
+        for (unsigned long long g = blockIdx.x; g < ntiles; g += gridDim.x) {
+            if (*abortp) break;
+            // ---- decode the tile's points
+            if (wtid < MROWS) {
+                const int r = wtid;
+                unsigned long long t = 0;
+                bool ok;
+                if (gather) {
+                    const unsigned long long idx = g * MROWS + r;
+                    ok = idx < gn;
+                    if (ok) t = gather[idx].t;
+                } else {
+                    t = base + g * MROWS + r;
+                    ok = t >= lo && t < hi;
+                }
+                S.t[r] = t;
+                S.valid[r] = ok;
+                S.unc[r] = 0;
+                S.vst[r] = 0;
+#pragma unroll
+                for (int l = 0; l <= kTcMaxL; ++l) S.fcnt[r][l] = 0;
+                int d[kMaxS];
+                decode_digits(ok ? t : 0, s, R, d);
+                for (int p = 0; p < s; ++p) S.dig[r][p] = (unsigned char)d[p];
+                S.pidx[r] = -1;
+            }
+            tc::named_bar_sync(1, 256);
+            // outer-prefix partial sums of layer 1 (range mode: consecutive points)
+            if (wtid == 0) {
+                int np = 0;
+                if (!gather && s > ni) {
+                    for (int r = 0; r < MROWS; ++r) {
+                        if (!S.valid[r]) continue;
+                        const unsigned long long pv = S.t[r] / Rni;
+                        int k = 0;
+                        while (k < np && S.pref[k] != pv) ++k;
+                        if (k == np && np < PMAX) S.pref[np++] = pv;
+                        S.pidx[r] = k < np ? k : -1;
+                    }
+                }
+                S.npref = np;
+            }
+            tc::named_bar_sync(1, 256);
+            for (int k = 0; k < S.npref; ++k) {
+                int dd[kMaxS];
+                decode_digits(S.pref[k], s - ni, R, dd);
+                for (int j = wtid; j < H1; j += 256) {
+                    float acc = 0.f;
+                    for (int p = 0; p < s - ni; ++p)
+                        acc += __ldg(&Q.tab[((size_t)p * R + dd[p]) * H1 + j]);
+                    S.souter[k][j] = acc;
+                }
+            }
+            tc::named_bar_sync(1, 256);
+
+            // ---- W1: layer-1 deltas -> operand of layer 2 (rows wid*16 .. +15)
+            {
+                float nsum[16], rsum[16], lsum[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) nsum[i] = rsum[i] = lsum[i] = 0.f;
+                const int kch = H1 / 64;
+                for (int c = 0; c < kch; ++c) {
+                    const int a0 = ait % NA, a1 = (ait + 1) % NA;
+                    tc::mbar_wait(bar(AEMPTY(a0)), ((ait / NA) & 1) ^ 1, abortp);
+                    if (SPLIT) tc::mbar_wait(bar(AEMPTY(a1)), (((ait + 1) / NA) & 1) ^ 1, abortp);
+                    const int j = 64 * c + 2 * lane;
+                    const uint32_t pm = Q.cpos[32 + (j >> 5)], nm = Q.cneg[32 + (j >> 5)];
+                    const uint32_t b0 = 1u << (j & 31), b1 = 1u << ((j + 1) & 31);
+                    const int cls0 = (nm & b0) ? 2 : (pm & b0) ? 1 : 0;  // 0 cross, 1 pos, 2 neg
+                    const int cls1 = (nm & b1) ? 2 : (pm & b1) ? 1 : 0;
+                    float ub0 = 0.f, ub1 = 0.f, th0 = 0.f, th1 = 0.f, c10 = 0.f, c11 = 0.f, c20 = 0.f, c21 = 0.f;
+                    if (cls0 == 0) { ub0 = Q.ub32[j]; th0 = Q.thr[j]; c10 = Q.c1[j]; c20 = Q.c2[j]; }
+                    if (cls1 == 0) { ub1 = Q.ub32[j + 1]; th1 = Q.thr[j + 1]; c11 = Q.c1[j + 1]; c21 = Q.c2[j + 1]; }
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int r = wid * 16 + i;
+                        float dh0 = 0.f, dh1 = 0.f;
+                        if (S.valid[r]) {
+                            float2 du;
+                            const int pi = S.pidx[r];
+                            if (pi >= 0) {
+                                du = *reinterpret_cast<const float2*>(&S.souter[pi][j]);
+                                for (int p = s - ni; p < s; ++p) {
+                                    const float2 tv = __ldg(reinterpret_cast<const float2*>(
+                                        &Q.tab[((size_t)p * R + S.dig[r][p]) * H1 + j]));
+                                    du.x += tv.x;
+                                    du.y += tv.y;
+                                }
+                            } else {
+                                du = make_float2(0.f, 0.f);
+                                for (int p = 0; p < s; ++p) {
+                                    const float2 tv = __ldg(reinterpret_cast<const float2*>(
+                                        &Q.tab[((size_t)p * R + S.dig[r][p]) * H1 + j]));
+                                    du.x += tv.x;
+                                    du.y += tv.y;
+                                }
+                            }
+                            if (cls0 == 1) dh0 = du.x;
+                            else if (cls0 == 0) {
+                                const float u = ub0 + du.x;
+                                if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > th0)) S.unc[r] = 1;
+                                else if ((u >= 0.f) != (ub0 >= 0.f)) {
+                                    const int k = atomicAdd(&S.fcnt[r][1], 1);
+                                    if (k < FCAP) S.flist[r][1][k] = (short)j;
+                                    if (Q.flip) set_bit_atomic(Q.flip, j);
+                                }
+                                dh0 = fmaxf(du.x + c10, c20);
+                            }
+                            if (cls1 == 1) dh1 = du.y;
+                            else if (cls1 == 0) {
+                                const float u = ub1 + du.y;
+                                if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > th1)) S.unc[r] = 1;
+                                else if ((u >= 0.f) != (ub1 >= 0.f)) {
+                                    const int k = atomicAdd(&S.fcnt[r][1], 1);
+                                    if (k < FCAP) S.flist[r][1][k] = (short)(j + 1);
+                                    if (Q.flip) set_bit_atomic(Q.flip, j + 1);
+                                }
+                                dh1 = fmaxf(du.y + c11, c21);
+                            }
+                        }
+                        float q0, q1;
+                        const uint32_t w = pack2<BF>(dh0, dh1, q0, q1);
+                        float r0 = dh0 - q0, r1 = dh1 - q1;
+                        const uint32_t off = sw_off(r, lane >> 2) + (lane & 3) * 4;
+                        *reinterpret_cast<uint32_t*>(&S.A[a0][off]) = w;
+                        if (SPLIT) {
+                            float l0, l1;
+                            const uint32_t wl = pack2<BF>(r0, r1, l0, l1);
+                            *reinterpret_cast<uint32_t*>(&S.A[a1][off]) = wl;
+                            lsum[i] = fmaf(l0, l0, fmaf(l1, l1, lsum[i]));
+                            r0 -= l0;
+                            r1 -= l1;
+                        }
+                        nsum[i] = fmaf(dh0, dh0, fmaf(dh1, dh1, nsum[i]));
+                        rsum[i] = fmaf(r0, r0, fmaf(r1, r1, rsum[i]));
+                    }
+                    tc::fence_proxy_async();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tc::mbar_arrive(bar(AFULL(a0)));
+                        if (SPLIT) tc::mbar_arrive(bar(AFULL(a1)));
+                    }
+                    ait += SPLIT ? 2 : 1;
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    float a = nsum[i], b = rsum[i], c = lsum[i];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        a += __shfl_xor_sync(0xffffffffu, a, o);
+                        b += __shfl_xor_sync(0xffffffffu, b, o);
+                        c += __shfl_xor_sync(0xffffffffu, c, o);
+                    }
+                    if (lane == i) {
+                        const int r = wid * 16 + i;
+                        const float N = norm_up(a);
+                        S.N[r] = N;
+                        S.R[r] = norm_up(b);
+                        S.Lo[r] = norm_up(c);
+                        S.E[r] = __fmaf_ru(0x1p-24f, N, Q.kvec[1]);
+                    }
+                }
+            }
+            tc::named_bar_sync(1, 256);
+
+            // ---- hidden layers: drain D_l, write the operand of layer l+1
+            const int r = 32 * qd + lane;
+            for (int l = 2; l < L; ++l) {
+                const TcLayer& ly = P.ly[l];
+                tc::mbar_wait(bar(DFULL), dit & 1, abortp);
+                ++dit;
+                tc::tc_fence_after();
+                const float Nn = S.N[r], Rr = S.R[r], Ll = S.Lo[r], Ee = S.E[r];
+                const float uacc = uacc_base * (float)ly.K;
+                const float Pa = __fmaf_ru(uacc, __fadd_ru(__fadd_ru(Nn, Rr), __fmul_ru(2.f, Ll)),
+                                           __fmaf_ru(SPLIT ? 0x1p-7f : 0.f, Ll, __fadd_ru(Rr, Ee)));
+                const float Pb = __fadd_ru(Nn, Ee);
+                const float* av = ly.a;
+                const float* bv = SPLIT ? ly.b3 : ly.b1;
+                const int off_l = net.noff[l];
+                float ns = 0.f, rs = 0.f, ls = 0.f;
+                const int nch = ly.Npad / 64;
+                for (int c = 0; c < nch; ++c) {
+                    const int a0 = ait % NA, a1 = (ait + 1) % NA;
+                    tc::mbar_wait(bar(AEMPTY(a0)), ((ait / NA) & 1) ^ 1, abortp);
+                    if (SPLIT) tc::mbar_wait(bar(AEMPTY(a1)), (((ait + 1) / NA) & 1) ^ 1, abortp);
+                    const int n0 = 64 * c + 32 * hf;
+                    float v[32];
+                    tc::tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)n0, v);
+                    const uint32_t pm = Q.cpos[l * 32 + (n0 >> 5)], nm = Q.cneg[l * 32 + (n0 >> 5)];
+                    uint32_t cross = ~(pm | nm);
+                    const bool rv = S.valid[r];
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        if (nm & (1u << i)) v[i] = 0.f;
+                    }
+                    while (cross) {
+                        const int i = __ffs(cross) - 1;
+                        cross &= cross - 1;
+                        const int n = n0 + i, gi = off_l + n;
+#pragma unroll
+                        for (int ii = 0; ii < 32; ++ii) {
+                            if (ii != i) continue;
+                            const float du = v[ii];
+                            const float ub = Q.ub32[gi];
+                            const float u = ub + du;
+                            const float bound = __fmaf_ru(av[n], Pa, __fmaf_ru(bv[n], Pb, Q.thr[gi]));
+                            if (rv) {
+                                if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound)) S.unc[r] = 1;
+                                else if ((u >= 0.f) != (ub >= 0.f)) {
+                                    const int k = atomicAdd(&S.fcnt[r][l], 1);
+                                    if (k < FCAP) S.flist[r][l][k] = (short)n;
+                                    if (Q.flip) set_bit_atomic(Q.flip, gi);
+                                }
+                            }
+                            v[ii] = fmaxf(du + Q.c1[gi], Q.c2[gi]);
+                        }
+                    }
+                    if (!rv) {
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) v[i] = 0.f;
+                    }
+                    uint32_t wq[16], wl[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        float q0, q1;
+                        wq[i] = pack2<BF>(v[2 * i], v[2 * i + 1], q0, q1);
+                        float r0 = v[2 * i] - q0, r1 = v[2 * i + 1] - q1;
+                        if (SPLIT) {
+                            float l0, l1;
+                            wl[i] = pack2<BF>(r0, r1, l0, l1);
+                            ls = fmaf(l0, l0, fmaf(l1, l1, ls));
+                            r0 -= l0;
+                            r1 -= l1;
+                        }
+                        ns = fmaf(v[2 * i], v[2 * i], fmaf(v[2 * i + 1], v[2 * i + 1], ns));
+                        rs = fmaf(r0, r0, fmaf(r1, r1, rs));
+                    }
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint32_t o = sw_off(r, hf * 4 + k);
+                        *reinterpret_cast<uint4*>(&S.A[a0][o]) =
+                            make_uint4(wq[4 * k], wq[4 * k + 1], wq[4 * k + 2], wq[4 * k + 3]);
+                        if (SPLIT)
+                            *reinterpret_cast<uint4*>(&S.A[a1][o]) =
+                                make_uint4(wl[4 * k], wl[4 * k + 1], wl[4 * k + 2], wl[4 * k + 3]);
+                    }
+                    tc::fence_proxy_async();
+                    tc::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) {
+                        tc::mbar_arrive(bar(AFULL(a0)));
+                        if (SPLIT) tc::mbar_arrive(bar(AFULL(a1)));
+                    }
+                    ait += SPLIT ? 2 : 1;
+                }
+                S.part[hf][r][0] = ns;
+                S.part[hf][r][1] = rs;
+                S.part[hf][r][2] = ls;
+                tc::tc_fence_before();
+                tc::named_bar_sync(1, 256);
+                if (hf == 0) {
+                    const float N = norm_up(S.part[0][r][0] + S.part[1][r][0]);
+                    const float Rn = norm_up(S.part[0][r][1] + S.part[1][r][1]);
+                    const float Lo = norm_up(S.part[0][r][2] + S.part[1][r][2]);
+                    // ||err(du_l)|| <= sA R + sB N + (sA + sB) E + sL Lo + uacc fq (N + R + 2 Lo)
+                    const float sA = SPLIT ? ly.sa : ly.sq, sB = SPLIT ? ly.sd3 : ly.sd1;
+                    float El = __fmul_ru(sA, Rr);
+                    El = __fmaf_ru(sB, Nn, El);
+                    El = __fmaf_ru(__fadd_ru(sA, sB), Ee, El);
+                    if (SPLIT) El = __fmaf_ru(ly.sl, Ll, El);
+                    El = __fmaf_ru(__fmul_ru(uacc, ly.fq), __fadd_ru(__fadd_ru(Nn, Rr), __fmul_ru(2.f, Ll)), El);
+                    El = __fadd_ru(El, Q.kvec[l]);
+                    El = __fmaf_ru(0x1p-24f, N, El);
+                    S.N[r] = N;
+                    S.R[r] = Rn;
+                    S.Lo[r] = Lo;
+                    S.E[r] = El;
+                }
+                if (l + 1 < L && P.ly[l + 1].Npad > 64) {
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(bar(DRAINED));
+                }
+                tc::named_bar_sync(1, 256);
+            }
+
+            // ---- output layer: margin, class, output signs
+            {
+                const TcLayer& ly = P.ly[L];
+                tc::mbar_wait(bar(DFULL), dit & 1, abortp);
+                ++dit;
+                tc::tc_fence_after();
+                if (hf == 0) {
+                    float v[32];
+                    tc::tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16), v);
+                    if (S.valid[r]) {
+                        const float Nn = S.N[r], Rr = S.R[r], Ll = S.Lo[r], Ee = S.E[r];
+                        const float uacc = uacc_base * (float)ly.K;
+                        const float Pa = __fmaf_ru(uacc, __fadd_ru(__fadd_ru(Nn, Rr), __fmul_ru(2.f, Ll)),
+                                                   __fmaf_ru(SPLIT ? 0x1p-7f : 0.f, Ll, __fadd_ru(Rr, Ee)));
+                        const float Pb = __fadd_ru(Nn, Ee);
+                        const float* av = ly.a;
+                        const float* bv = SPLIT ? ly.b3 : ly.b1;
+                        const int HL = ly.N, offL = net.noff[L];
+                        const int D = Q.cnt->D;
+                        float y[kTcMaxOut];
+#pragma unroll
+                        for (int o = 0; o < kTcMaxOut; ++o) y[o] = 0.f;
+                        bool unc = false;
+#pragma unroll
+                        for (int o = 0; o < kTcMaxOut; ++o) {
+                            if (o >= HL) break;
+                            const float ub = Q.ub32[offL + o];
+                            const float u = ub + v[o];
+                            y[o] = u;
+                            const float bound = __fmaf_ru(av[o], Pa, __fmaf_ru(bv[o], Pb, Q.thr[offL + o]));
+                            if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound)) unc = true;
+                            else if ((u >= 0.f) != (ub >= 0.f)) {
+                                const int k = atomicAdd(&S.fcnt[r][L], 1);
+                                if (k < FCAP) S.flist[r][L][k] = (short)o;
+                                if (Q.flip) set_bit_atomic(Q.flip, offL + o);
+                            }
+                        }
+                        float yD = 0.f;
+#pragma unroll
+                        for (int o = 0; o < kTcMaxOut; ++o)
+                            if (o == D) yD = y[o];
+                        const float dD = Q.dub[offL + D];
+                        bool unsafe = false, safe = true;
+                        const float* pr = P.pair + (size_t)D * HL * 5;
+#pragma unroll
+                        for (int o = 0; o < kTcMaxOut; ++o) {
+                            if (o >= HL) break;
+                            if (o == D) continue;
+                            const float diff = yD - y[o];
+                            const float* c5 = pr + o * 5;
+                            float eb = __fmul_ru(c5[0], __fadd_ru(Rr, 0.f));
+                            eb = __fmaf_ru(c5[1], Nn, eb);
+                            eb = __fmaf_ru(c5[2], Ee, eb);
+                            if (SPLIT) eb = __fmaf_ru(c5[3], Ll, eb);
+                            eb = __fmaf_ru(__fmul_ru(uacc, c5[4]), __fadd_ru(__fadd_ru(Nn, Rr), __fmul_ru(2.f, Ll)), eb);
+                            eb = __fadd_ru(eb, __fadd_ru(__fadd_ru(dD, Q.dub[offL + o]), (float)(2.0 * kTau)));
+                            eb = __fmaf_ru(0x1p-23f, __fadd_ru(__fadd_ru(fabsf(yD), fabsf(y[o])), fabsf(diff)), eb);
+                            if (diff < -eb) unsafe = true;
+                            else if (!(diff > eb)) safe = false;
+                        }
+                        S.vst[r] = unsafe ? 1 : (safe ? 0 : 2);
+                        if (unc) S.unc[r] = 1;
+                    }
+                }
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(bar(TFREE));
+                tc::named_bar_sync(1, 256);
+                // ---- per-point results
+                if (hf == 0) {
+                    const bool rv = S.valid[r];
+                    bool bad = rv && (S.unc[r] || S.vst[r] == 2);
+                    if (rv && !bad && Q.ss)
+                        for (int l = 1; l < L; ++l)
+                            if (S.fcnt[r][l] == 1 && S.fcnt[r][l + 1] > FCAP) bad = true;
+                    const unsigned long long t = S.t[r];
+                    if (bad) queue_push(out, t, 0u, Q.cnt, out_level);
+                    const bool adv = rv && !bad && S.vst[r] == 1;
+                    if (!gather) {
+                        const unsigned m = __ballot_sync(0xffffffffu, adv);
+                        if (m && lane == 0) {
+                            atomicAdd(&Q.cnt->n_adv, (unsigned long long)__popc(m));
+                            atomicMin(&Q.cnt->first, t + (unsigned)(__ffs(m) - 1));
+                            if (Q.bitmap && t < Q.bitmap_bits) atomicOr(&Q.bitmap[t >> 5], m);
+                        }
+                    } else if (adv) {
+                        record_adversarial(Q, t);
+                    }
+                    if (rv && !bad && Q.ss) {
+                        for (int l = 1; l < L; ++l) {
+                            if (S.fcnt[r][l] != 1) continue;
+                            const int j = S.flist[r][l][0];
+                            const int Hn = net.dims[l + 1];
+                            const int nt = S.fcnt[r][l + 1];
+                            for (int e = 0; e < nt; ++e)
+                                set_bit_atomic(Q.ss, (unsigned long long)net.ssoff[l] +
+                                                         (unsigned long long)j * Hn + S.flist[r][l + 1][e]);
+                        }
+                    }
+                }
+                tc::named_bar_sync(1, 256);
+            }
+        }
+    }
+    // ---- teardown: wait for outstanding tensor-core work, release TMEM
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, 512);
+    }
+    if (threadIdx.x == 0 && *abortp) atomicOr(&Q.cnt->err, DERR_TC_WAIT);
+}
+
+// ------------------------------------------------------------ per-query setup
+
+// Column classes of the tensor screen. A neuron whose |ub| exceeds a bound on
+// |du| over the whole box plus the screen's error bound keeps its sign at every
+// point: "pos" (output change = input change) or "neg" (output change 0). The
+// bound on |du| propagates interval bounds |dh_j| <= B_j through |W_l|.
+__global__ void k_tc_classes(const __grid_constant__ TcParams P, NetView net, QueryView* qs) {
+    __shared__ double Bh[1024];
+    __shared__ double red[64];
+    QueryView& Q = qs[blockIdx.x];
+    const int L = P.L, H1 = net.dims[1];
+    const double u24 = 0x1p-24;
+    const double uq = P.bf16 ? 0x1p-8 : 0x1p-11;
+    // layer 1
+    double part = 0.0;
+    for (int w = threadIdx.x; w < (kMaxL + 1) * 32; w += blockDim.x) {
+        Q.cpos[w] = 0u;
+        Q.cneg[w] = 0u;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < H1; j += blockDim.x) {
+        double b1 = 0.0;
+        for (int p = 0; p < Q.s; ++p) {
+            double mx = 0.0;
+            for (int d = 0; d < Q.R; ++d)
+                mx = fmax(mx, fabs((double)Q.tab[((size_t)p * Q.R + d) * H1 + j]));
+            b1 += mx;
+        }
+        b1 *= 1.0 + 1e-6;
+        const double ub = Q.ub[j];
+        const bool cross = !(fabs(ub) > (b1 + (double)Q.thr[j]) * (1.0 + 1e-6) + 4.0 * kTau);
+        if (!cross) atomicOr(ub >= 0.0 ? &Q.cpos[32 + (j >> 5)] : &Q.cneg[32 + (j >> 5)], 1u << (j & 31));
+        Bh[j] = (!cross && ub < 0.0) ? 0.0 : b1;
+        part += Bh[j] * Bh[j];
+    }
+    // block reduction helper
+    auto bsum = [&](double v) {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+        __syncthreads();
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+        __syncthreads();
+        return t;
+    };
+    double Nmax = sqrt(bsum(part)) * (1.0 + 1e-6);
+    double Emax = (double)Q.kvec[1] + u24 * Nmax;
+    // The classes serve both passes (one-term and split): every bound below is the
+    // larger of the two passes' bounds.
+    for (int l = 2; l < L; ++l) {
+        const TcLayer& ly = P.ly[l];
+        const int K = ly.K, N = ly.N;
+        const double Rmax = uq * Nmax + sqrt((double)K) * 0x1p-25;
+        const double Lmax = uq * Nmax;
+        const double u1 = K * 0x1p-22, u3 = 3.0 * K * 0x1p-22;
+        const double Pa1 = Rmax + Emax + u1 * (Nmax + Rmax);
+        const double Pa3 = Rmax + Emax + 0x1p-7 * Lmax + u3 * (Nmax + Rmax + 2.0 * Lmax);
+        const double Pb = Nmax + Emax;
+        __shared__ double Bn[1024];
+        double part2 = 0.0;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) {
+            const float* Wr = net.W[l] + (size_t)i * K;
+            double acc = 0.0;
+            for (int j = 0; j < K; ++j) acc += fabs((double)Wr[j]) * Bh[j];
+            const double em = fmax((double)ly.a[i] * Pa1 + (double)ly.b1[i] * Pb,
+                                   (double)ly.a[i] * Pa3 + (double)ly.b3[i] * Pb);
+            const double B = (acc * (1.0 + 1e-6) + em);
+            const int gi = net.noff[l] + i;
+            const double ub = Q.ub[gi];
+            const bool cross = !(fabs(ub) > (B + (double)Q.thr[gi]) * (1.0 + 1e-6) + 4.0 * kTau);
+            if (!cross)
+                atomicOr(ub >= 0.0 ? &Q.cpos[l * 32 + (i >> 5)] : &Q.cneg[l * 32 + (i >> 5)], 1u << (i & 31));
+            Bn[i] = (!cross && ub < 0.0) ? 0.0 : B;
+            part2 += Bn[i] * Bn[i];
+        }
+        __syncthreads();
+        const double E1 = ly.sq * Rmax + ly.sd1 * Nmax + (ly.sq + ly.sd1) * Emax + u1 * ly.fq * (Nmax + Rmax);
+        const double E3 = ly.sa * Rmax + ly.sd3 * Nmax + (ly.sa + ly.sd3) * Emax + (double)ly.sl * Lmax +
+                          u3 * ly.fq * (Nmax + Rmax + 2.0 * Lmax);
+        double El = fmax(E1, E3) + (double)Q.kvec[l];
+        Nmax = sqrt(bsum(part2)) * (1.0 + 1e-6);
+        El += u24 * Nmax;
+        Emax = El * (1.0 + 1e-6);
+        for (int i = threadIdx.x; i < N; i += blockDim.x) Bh[i] = Bn[i];
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------- host-side set-up
+
+// C = A * B^T for row-major A [M x K] and B [N x K], FP64 (small set-up GEMMs).
+__global__ void k_gemm_abt64(const double* A, const double* B, double* C, int M, int N, int K) {
+    __shared__ double As[16][17], Bs[16][17];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
+    double acc = 0.0;
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        As[ty][tx] = (row < M && k0 + tx < K) ? A[(size_t)row * K + k0 + tx] : 0.0;
+        Bs[ty][tx] = (blockIdx.x * 16 + ty < N && k0 + tx < K)
+                         ? B[(size_t)(blockIdx.x * 16 + ty) * K + k0 + tx]
+                         : 0.0;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc += As[ty][k] * Bs[tx][k];
+        __syncthreads();
+    }
+    if (row < M && col < N) C[(size_t)row * N + col] = acc;
+}
+
+// Rigorous upper bound of the spectral norm of A (m x n, host, row-major):
+// sigma^2 = lambda_max(G) <= ||G^(2^k)||_F^(1/2^k) for the Gram matrix G.
+double spectral_bound(const std::vector<double>& A, int m, int n) {
+    const bool rows = m <= n;  // G = A A^T (m x m) or A^T A (n x n)
+    const int g = rows ? m : n;
+    std::vector<double> At;
+    const std::vector<double>* src = &A;
+    int K = n;
+    if (!rows) {
+        At.resize((size_t)n * m);
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < n; ++j) At[(size_t)j * m + i] = A[(size_t)i * n + j];
+        src = &At;
+        K = m;
+    }
+    double *dA = nullptr, *dG = nullptr, *dH = nullptr;
+    cudaMalloc(&dA, sizeof(double) * src->size());
+    cudaMalloc(&dG, sizeof(double) * (size_t)g * g);
+    cudaMalloc(&dH, sizeof(double) * (size_t)g * g);
+    cudaMemcpy(dA, src->data(), sizeof(double) * src->size(), cudaMemcpyHostToDevice);
+    dim3 blk(16, 16), grd((g + 15) / 16, (g + 15) / 16);
+    k_gemm_abt64<<<grd, blk>>>(dA, dA, dG, g, g, K);
+    std::vector<double> h((size_t)g * g);
+    double logscale = 0.0;
+    const int squarings = 5;
+    for (int it = 0; it <= squarings; ++it) {
+        cudaMemcpy(h.data(), dG, sizeof(double) * h.size(), cudaMemcpyDeviceToHost);
+        double f = 0.0;
+        for (double x : h) f += x * x;
+        f = std::sqrt(f);
+        if (!(f > 0.0)) {
+            cudaFree(dA);
+            cudaFree(dG);
+            cudaFree(dH);
+            return 0.0;
+        }
+        // G_it = exp(logscale) * (current matrix); track the scale, normalise
+        logscale = (it == 0 ? 0.0 : 2.0 * logscale) + std::log(f);
+        for (double& x : h) x /= f;
+        if (it == squarings) break;
+        cudaMemcpy(dG, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice);
+        k_gemm_abt64<<<grd, blk>>>(dG, dG, dH, g, g, g);  // G symmetric: G G^T = G^2
+        std::swap(dG, dH);
+    }
+    cudaFree(dA);
+    cudaFree(dG);
+    cudaFree(dH);
+    // ||G^(2^k)||_F = exp(logscale); lambda_max <= exp(logscale / 2^k)
+    const double lam = std::exp(logscale / (double)(1 << squarings));
+    return std::sqrt(lam) * (1.0 + 1e-6);
+}
+
+float up_f(double x) {
+    float f = (float)x;
+    if ((double)f < x) f = std::nextafter(f, INFINITY);
+    return f;
+}
+
+template <bool BF>
+float q16(float x) {
+    if (BF) return __bfloat162float(__float2bfloat16_rn(x));
+    return __half2float(__float2half_rn(x));
+}
+
+}  // namespace
+
+bool tc_supported(const NetView& v, int precision) {
+    if (precision != VBMC_PREC_BF16 && precision != VBMC_PREC_FP16) return false;
+    if (v.act != ACT_RELU || v.L < 2 || v.L > kTcMaxL) return false;
+    if (v.dims[1] % 64 || v.dims[1] > 512) return false;
+    for (int l = 2; l < v.L; ++l)
+        if (v.dims[l] % 64 || v.dims[l] > 512) return false;
+    if (v.dims[v.L] > kTcMaxOut) return false;
+    return true;
+}
+
+template <bool BF>
+static vbmc_status build_prec(TcNet& tc, const NetView& v, const std::vector<std::vector<float>>& W,
+                              TcParams& P) {
+    using T = typename std::conditional<BF, __nv_bfloat16, __half>::type;
+    std::memset(&P, 0, sizeof(P));
+    P.L = v.L;
+    P.bf16 = BF ? 1 : 0;
+    PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&encode, 12000,
+                                         cudaEnableDefault, &qr) !=
+            cudaSuccess ||
+        !encode)
+        return VBMC_ERR_CUDA;
+    for (int l = 2; l <= v.L; ++l) {
+        const int K = v.dims[l - 1], N = v.dims[l];
+        const bool out = (l == v.L);
+        const int Npad = out ? (N <= 16 ? 16 : 32) : N;
+        TcLayer& ly = P.ly[l];
+        ly.K = K;
+        ly.N = N;
+        ly.Npad = Npad;
+        ly.slice = std::min(Npad, 128);
+        ly.nslice = Npad / ly.slice;
+        ly.kch = K / 64;
+        std::vector<T> hq((size_t)Npad * K), hlo((size_t)Npad * K);
+        std::vector<double> Wq((size_t)N * K), Wd1((size_t)N * K), Wd3((size_t)N * K), Wa((size_t)N * K),
+            Wl((size_t)N * K);
+        std::vector<float> a(Npad, 0.f), b1(Npad, 0.f), b3(Npad, 0.f);
+        double fq2 = 0.0;
+        for (int i = 0; i < Npad; ++i) {
+            double a2 = 0.0, d12 = 0.0, d32 = 0.0;
+            for (int j = 0; j < K; ++j) {
+                const float w = i < N ? W[l][(size_t)i * K + j] : 0.f;
+                const float wq = q16<BF>(w);
+                const float wl = q16<BF>(w - wq);
+                hq[(size_t)i * K + j] = BF ? (T)__float2bfloat16_rn(wq) : (T)__float2half_rn(wq);
+                hlo[(size_t)i * K + j] = BF ? (T)__float2bfloat16_rn(wl) : (T)__float2half_rn(wl);
+                if (i < N) {
+                    const double wa = (double)wq + (double)wl;
+                    Wq[(size_t)i * K + j] = wq;
+                    Wd1[(size_t)i * K + j] = (double)w - wq;
+                    Wd3[(size_t)i * K + j] = (double)w - wa;
+                    Wa[(size_t)i * K + j] = wa;
+                    Wl[(size_t)i * K + j] = wl;
+                }
+                a2 += (double)wq * wq;
+                d12 += ((double)w - wq) * ((double)w - wq);
+                d32 += ((double)w - wq - wl) * ((double)w - wq - wl);
+            }
+            fq2 += a2;
+            // split mode uses ||Wq + Wlo|| <= ||Wq|| + ||Wlo||; bound with 1 + 2^-7
+            a[i] = up_f(std::sqrt(a2) * (1.0 + 0x1p-7) * (1.0 + 1e-9));
+            b1[i] = up_f(std::sqrt(d12) * (1.0 + 1e-9));
+            b3[i] = up_f(std::sqrt(d32) * (1.0 + 1e-9));
+        }
+        ly.fq = up_f(std::sqrt(fq2) * (1.0 + 0x1p-7) * (1.0 + 1e-9));
+        // ||Wlo_i|| <= 2^-7 ||Wq_i|| (checked: the split bound relies on it)
+        for (int i = 0; i < N; ++i) {
+            double l2 = 0.0, q2 = 0.0;
+            for (int j = 0; j < K; ++j) {
+                l2 += Wl[(size_t)i * K + j] * Wl[(size_t)i * K + j];
+                q2 += Wq[(size_t)i * K + j] * Wq[(size_t)i * K + j];
+            }
+            if (l2 > 0x1p-14 * q2 * (1.0 + 1e-9)) return VBMC_ERR_UNSUPPORTED;
+        }
+        if (!out) {
+            ly.sq = up_f(spectral_bound(Wq, N, K));
+            ly.sa = up_f(spectral_bound(Wa, N, K));
+            ly.sl = up_f(spectral_bound(Wl, N, K));
+            ly.sd1 = up_f(spectral_bound(Wd1, N, K));
+            ly.sd3 = up_f(spectral_bound(Wd3, N, K));
+            if (!(ly.sq > 0.f) || !(ly.sa > 0.f)) return VBMC_ERR_CUDA;
+        } else {
+            // pair constants for the margin: ||Wa_D - Wa_o||, ||Wr_D - Wr_o|| (1x: b1 rows,
+            // split: b3 rows), ||W_D - W_o||, ||Wlo_D - Wlo_o||, a_D + a_o
+            std::vector<float> pair((size_t)N * N * 5, 0.f);
+            for (int D = 0; D < N; ++D)
+                for (int o = 0; o < N; ++o) {
+                    double A2 = 0.0, B12 = 0.0, B32 = 0.0, C2 = 0.0, L2 = 0.0, Q2 = 0.0;
+                    for (int j = 0; j < K; ++j) {
+                        const double wD = W[l][(size_t)D * K + j], wo = W[l][(size_t)o * K + j];
+                        const double dq = Wq[(size_t)D * K + j] - Wq[(size_t)o * K + j];
+                        const double da = Wa[(size_t)D * K + j] - Wa[(size_t)o * K + j];
+                        const double d1 = Wd1[(size_t)D * K + j] - Wd1[(size_t)o * K + j];
+                        const double d3 = Wd3[(size_t)D * K + j] - Wd3[(size_t)o * K + j];
+                        const double dl = Wl[(size_t)D * K + j] - Wl[(size_t)o * K + j];
+                        Q2 += dq * dq;
+                        A2 += da * da;
+                        B12 += d1 * d1;
+                        B32 += d3 * d3;
+                        C2 += (wD - wo) * (wD - wo);
+                        L2 += dl * dl;
+                    }
+                    float* c = &pair[((size_t)D * N + o) * 5];
+                    (void)B32;
+                    c[0] = up_f(std::sqrt(std::max(Q2, A2)) * (1.0 + 1e-9));
+                    c[1] = up_f(std::sqrt(std::max(B12, B32)) * (1.0 + 1e-9));
+                    c[2] = up_f(std::sqrt(C2) * (1.0 + 1e-9));
+                    c[3] = up_f(std::sqrt(L2) * (1.0 + 1e-9));
+                    c[4] = up_f(((double)a[D] + (double)a[o]) * (1.0 + 1e-9));
+                }
+            float* dp = nullptr;
+            if (cudaMalloc(&dp, sizeof(float) * pair.size()) != cudaSuccess) return VBMC_ERR_OOM;
+            tc.owned.push_back(dp);
+            cudaMemcpy(dp, pair.data(), sizeof(float) * pair.size(), cudaMemcpyHostToDevice);
+            P.pair = dp;
+        }
+        // device copies
+        T *dq = nullptr, *dl = nullptr;
+        float *da = nullptr, *db1 = nullptr, *db3 = nullptr;
+        if (cudaMalloc(&dq, sizeof(T) * hq.size()) != cudaSuccess) return VBMC_ERR_OOM;
+        tc.owned.push_back(dq);
+        if (cudaMalloc(&dl, sizeof(T) * hlo.size()) != cudaSuccess) return VBMC_ERR_OOM;
+        tc.owned.push_back(dl);
+        if (cudaMalloc(&da, sizeof(float) * Npad) != cudaSuccess) return VBMC_ERR_OOM;
+        tc.owned.push_back(da);
+        if (cudaMalloc(&db1, sizeof(float) * Npad) != cudaSuccess) return VBMC_ERR_OOM;
+        tc.owned.push_back(db1);
+        if (cudaMalloc(&db3, sizeof(float) * Npad) != cudaSuccess) return VBMC_ERR_OOM;
+        tc.owned.push_back(db3);
+        cudaMemcpy(dq, hq.data(), sizeof(T) * hq.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(dl, hlo.data(), sizeof(T) * hlo.size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(da, a.data(), sizeof(float) * Npad, cudaMemcpyHostToDevice);
+        cudaMemcpy(db1, b1.data(), sizeof(float) * Npad, cudaMemcpyHostToDevice);
+        cudaMemcpy(db3, b3.data(), sizeof(float) * Npad, cudaMemcpyHostToDevice);
+        ly.a = da;
+        ly.b1 = db1;
+        ly.b3 = db3;
+        const CUtensorMapDataType dt = BF ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+        cuuint64_t gdim[2] = {(cuuint64_t)K, (cuuint64_t)Npad};
+        cuuint64_t gstr[1] = {(cuuint64_t)K * 2};
+        cuuint32_t box[2] = {64, (cuuint32_t)ly.slice};
+        cuuint32_t estr[2] = {1, 1};
+        CUresult e1 = encode(&P.tq[l], dt, 2, dq, gdim, gstr, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        CUresult e2 = encode(&P.tlo[l], dt, 2, dl, gdim, gstr, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (e1 != CUDA_SUCCESS || e2 != CUDA_SUCCESS) return VBMC_ERR_CUDA;
+    }
+    if (cudaGetLastError() != cudaSuccess) return VBMC_ERR_CUDA;
+    return VBMC_OK;
+}
+
+vbmc_status tc_build(TcNet& tc, const NetView& v, const std::vector<std::vector<float>>& W,
+                     const std::vector<std::vector<float>>&, int precision) {
+    const int pi = precision == VBMC_PREC_BF16 ? 0 : 1;
+    if (tc.prec[pi].ready) return VBMC_OK;
+    vbmc_status st = pi == 0 ? build_prec<true>(tc, v, W, tc.prec[pi].p)
+                             : build_prec<false>(tc, v, W, tc.prec[pi].p);
+    if (st == VBMC_OK) tc.prec[pi].ready = true;
+    return st;
+}
+
 void tc_free(TcNet& tc) {
     for (void* p : tc.owned) cudaFree(p);
     tc.owned.clear();
+    tc.prec[0].ready = tc.prec[1].ready = false;
 }
-vbmc_status tc_launch_screen(TcNet&, const NetView&, const QueryView*, uint64_t, uint64_t, int, Queue,
-                             int, cudaStream_t) {
-    return VBMC_ERR_UNSUPPORTED;
+
+void tc_launch_query_setup(TcNet& tc, const NetView& v, QueryView* d_q, int precision,
+                           cudaStream_t st) {
+    const TcParams& P = tc.prec[precision == VBMC_PREC_BF16 ? 0 : 1].p;
+    k_tc_classes<<<1, 512, 0, st>>>(P, v, d_q);
 }
-vbmc_status tc_launch_gather(TcNet&, const NetView&, const QueryView*, const QEntry*,
-                             const unsigned long long*, unsigned long long, int, Queue, int,
-                             cudaStream_t) {
-    return VBMC_ERR_UNSUPPORTED;
+
+template <bool SPLIT, bool BF>
+static void launch_k(const TcParams& P, const NetView& v, const QueryView* d_q, uint64_t lo, uint64_t hi,
+                     const QEntry* g, const unsigned long long* gc, unsigned long long cap, Queue out,
+                     int level, int n_sm, cudaStream_t st) {
+    const size_t smem = sizeof(TcSmem) + 1024;
+    auto kern = k_tc<SPLIT, BF>;
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    unsigned grid = (unsigned)n_sm;
+    if (!g) {
+        const unsigned long long base = lo & ~31ull;
+        const unsigned long long tiles = hi > base ? (hi - base + MROWS - 1) / MROWS : 0;
+        if (tiles < grid) grid = (unsigned)(tiles ? tiles : 1);
+    }
+    kern<<<grid, TC_THREADS, smem, st>>>(P, v, d_q, lo, hi, g, gc, cap, out, level);
+}
+
+vbmc_status tc_launch_screen(TcNet& tc, const NetView& v, const QueryView* d_q, uint64_t lo,
+                             uint64_t hi, int precision, Queue out, int n_sm, cudaStream_t st) {
+    const bool bf = precision == VBMC_PREC_BF16;
+    const TcParams& P = tc.prec[bf ? 0 : 1].p;
+    if (bf) launch_k<false, true>(P, v, d_q, lo, hi, nullptr, nullptr, 0, out, 0, n_sm, st);
+    else launch_k<false, false>(P, v, d_q, lo, hi, nullptr, nullptr, 0, out, 0, n_sm, st);
+    return cudaGetLastError() == cudaSuccess ? VBMC_OK : VBMC_ERR_CUDA;
+}
+
+vbmc_status tc_launch_gather(TcNet& tc, const NetView& v, const QueryView* d_q, const QEntry* in,
+                             const unsigned long long* in_count, unsigned long long cap,
+                             int precision, Queue out, int n_sm, cudaStream_t st) {
+    const bool bf = precision == VBMC_PREC_BF16;
+    const TcParams& P = tc.prec[bf ? 0 : 1].p;
+    if (bf) launch_k<true, true>(P, v, d_q, 0, 0, in, in_count, cap, out, 1, n_sm, st);
+    else launch_k<true, false>(P, v, d_q, 0, 0, in, in_count, cap, out, 1, n_sm, st);
+    return cudaGetLastError() == cudaSuccess ? VBMC_OK : VBMC_ERR_CUDA;
 }
 
 }  // namespace vbmc

@@ -3,21 +3,54 @@
 #include "../../include/vbmc.h"
 #include "dev.cuh"
 
+#include <cudaTypedefs.h>
 #include <vector>
 
 namespace vbmc {
 
+constexpr int kTcMaxL = 6;     // weight layers the tensor path supports
+constexpr int kTcMaxOut = 32;  // classes (output width) it supports
+
+// Per layer l >= 2 of the tensor screen.
+struct TcLayer {
+    int K, N, Npad;        // inputs, outputs, outputs padded to the MMA width
+    int slice, nslice;     // N per MMA / weight tile (<= 128) and slices per K chunk
+    int kch;               // K / 64 chunks
+    const float* a;        // [Npad] ||Wq_i||_2 (rounded up)
+    const float* b1;       // [Npad] ||W_i - Wq_i||_2           (one-term screen)
+    const float* b3;       // [Npad] ||W_i - Wq_i - Wlo_i||_2   (split screen)
+    float sq, sa, sl;      // spectral-norm bounds of Wq, Wq + Wlo, Wlo
+    float sd1, sd3;        // spectral-norm bounds of W - Wq, W - Wq - Wlo
+    float fq;              // ||Wq||_F (1 + 2^-7) >= ||Wq + Wlo||_F
+};
+
+struct TcParams {
+    CUtensorMap tq[kTcMaxL + 1];   // Wq_l  [Npad][K], box 64 x slice, 128-byte swizzle
+    CUtensorMap tlo[kTcMaxL + 1];  // Wlo_l (split screen)
+    TcLayer ly[kTcMaxL + 1];
+    const float* pair;             // [H_L][H_L][5]: output-layer pair constants
+    int L;
+    int bf16;                      // 1: bf16 operands, 0: fp16
+};
+
+struct TcPrec {
+    bool ready = false;
+    TcParams p{};
+};
+
 struct TcNet {
-    void* d_wq[kMaxL + 1] = {};  // quantised weights per layer and precision (see tc.cu)
-    void* d_wlo[kMaxL + 1] = {};
-    float* d_consts = nullptr;
+    TcPrec prec[2];                // [0] bf16, [1] fp16
+    // per-query class masks live in the result; see tc.cu
     std::vector<void*> owned;
 };
 
 bool tc_supported(const NetView& v, int precision);
 vbmc_status tc_build(TcNet& tc, const NetView& v, const std::vector<std::vector<float>>& W,
-                     const std::vector<std::vector<float>>& b);
+                     const std::vector<std::vector<float>>& b, int precision);
 void tc_free(TcNet& tc);
+// Per-query constants of the tensor screen (column classes), after the prologue.
+void tc_launch_query_setup(TcNet& tc, const NetView& v, QueryView* d_q, int precision,
+                           cudaStream_t st);
 vbmc_status tc_launch_screen(TcNet& tc, const NetView& v, const QueryView* d_q, uint64_t lo,
                              uint64_t hi, int precision, Queue out, int n_sm, cudaStream_t st);
 vbmc_status tc_launch_gather(TcNet& tc, const NetView& v, const QueryView* d_q, const QEntry* in,
