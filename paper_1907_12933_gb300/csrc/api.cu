@@ -184,6 +184,15 @@ extern "C" vbmc_status vbmc_net_create(const vbmc_mlp_desc* desc, vbmc_net** out
         v.b[l] = db;
         v.rownorm[l] = drn;
     }
+    // tensor-core operands and bound constants, so that verify calls allocate nothing
+    for (int prec : {VBMC_PREC_BF16, VBMC_PREC_FP16}) {
+        if (!tc_supported(v, prec)) continue;
+        vbmc_status st = tc_build(n->tc, v, n->hW, n->hb, prec);
+        if (st != VBMC_OK) {
+            vbmc_net_free(n);
+            return fail(st, "tensor-core set-up failed");
+        }
+    }
     *out = n;
     return VBMC_OK;
 }
