@@ -134,7 +134,8 @@ typedef struct {
     uint64_t n_adversarial;    /* adversarial points (ties excluded)      */
     uint64_t first_witness;    /* smallest adversarial index, or NO_WITNESS */
     uint64_t n_ties;           /* points with |m| < 1e-9                  */
-    uint64_t n_recheck[3];     /* points re-run: tensor 3x, FP32, FP64    */
+    uint64_t n_recheck[4];     /* points re-run: tensor split, FP32,      *
+                                * double-float, FP64                      */
     double ms_device;          /* device time of the last verify call     */
     double ms_prologue;        /* of which: FP64 base pass and tables     */
     double ms_screen;          /* of which: first pass over every point   */

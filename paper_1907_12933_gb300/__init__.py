@@ -54,7 +54,7 @@ class _Summary(C.Structure):
     _fields_ = [("verdict", C.c_int32), ("D", C.c_int32), ("base_margin", C.c_double),
                 ("n_points", C.c_uint64), ("n_adversarial", C.c_uint64),
                 ("first_witness", C.c_uint64), ("n_ties", C.c_uint64),
-                ("n_recheck", C.c_uint64 * 3), ("ms_device", C.c_double),
+                ("n_recheck", C.c_uint64 * 4), ("ms_device", C.c_double),
                 ("ms_prologue", C.c_double), ("ms_screen", C.c_double),
                 ("ms_recheck", C.c_double)]
 

@@ -84,7 +84,7 @@ struct vbmc_result {
     int* d_pix_in = nullptr;
     unsigned long long* d_tp = nullptr;  // tile prefix {0, n_tiles}
     unsigned long long* d_qcount = nullptr;  // 4 queue counters
-    QEntry* d_queue[3] = {nullptr, nullptr, nullptr};
+    QEntry* d_queue[4] = {nullptr, nullptr, nullptr, nullptr};
     double* d_margin = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_pro = nullptr, ev_scr = nullptr;
     cudaStream_t last_stream = nullptr;
@@ -164,6 +164,37 @@ extern "C" vbmc_status vbmc_net_create(const vbmc_mlp_desc* desc, vbmc_net** out
             frob2 += r2;
         }
         v.lamfrob[l] = round_up_f(lam * std::sqrt(frob2) * (1.0 + 1e-12));
+        v.frob[l] = round_up_f(std::sqrt(frob2) * (1.0 + 1e-12));
+        if (l >= 2) {
+            std::vector<double> Wd((size_t)N * K);
+            for (size_t e = 0; e < Wd.size(); ++e) Wd[e] = W[e];
+            const double sg = spectral_bound(Wd, N, K);
+            if (!(sg > 0.0) && frob2 > 0.0) {
+                vbmc_net_free(n);
+                return fail(VBMC_ERR_CUDA, "spectral-norm bound failed");
+            }
+            v.sig[l] = round_up_f(sg);
+            v.lamsig[l] = round_up_f(lam * sg);
+        }
+        if (l == L) {
+            std::vector<float> pw((size_t)N * N);
+            for (int D = 0; D < N; ++D)
+                for (int o = 0; o < N; ++o) {
+                    double d2 = 0.0;
+                    for (int j = 0; j < K; ++j) {
+                        const double d = (double)W[(size_t)D * K + j] - (double)W[(size_t)o * K + j];
+                        d2 += d * d;
+                    }
+                    pw[(size_t)D * N + o] = round_up_f(std::sqrt(d2) * (1.0 + 1e-12));
+                }
+            float* dpw = nullptr;
+            if (dalloc(&dpw, pw.size(), n->owned) != cudaSuccess ||
+                cudaMemcpy(dpw, pw.data(), sizeof(float) * pw.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+                vbmc_net_free(n);
+                return fail(VBMC_ERR_OOM, "net_create: pair norms");
+            }
+            v.pairw = dpw;
+        }
         const double u = std::ldexp(1.0, -24);
         v.gam[l] = round_up_f(K * u / (1.0 - K * u));
         float *dW, *dWT, *db, *drn;
@@ -239,6 +270,7 @@ extern "C" vbmc_status vbmc_result_create(const vbmc_net* net, const vbmc_caps* 
     A(&q.dv, (size_t)S * RM);
     A(&q.ub, T);
     A(&q.hb, T);
+    A(&q.eub, T);
     A(&q.ub32, T);
     A(&q.dub, T);
     A(&q.thr, T);
@@ -258,7 +290,7 @@ extern "C" vbmc_status vbmc_result_create(const vbmc_net* net, const vbmc_caps* 
     A(&r->d_margin, 1);
     if (caps->max_points) A(&q.bitmap, (size_t)((caps->max_points + 31) / 32));
     const uint64_t qc = std::max<uint64_t>(1, caps->queue_cap);
-    for (int i = 0; i < 3; ++i) A(&r->d_queue[i], (size_t)qc);
+    for (int i = 0; i < 4; ++i) A(&r->d_queue[i], (size_t)qc);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&r->h_cnt, sizeof(Counters));
     if (e == cudaSuccess) e = cudaEventCreate(&r->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&r->ev1);
@@ -338,43 +370,44 @@ vbmc_status enqueue(vbmc_net* net, vbmc_result* r, const uint8_t* d_image, const
     launch_prologue(v, r->d_q, 1, s * q.R, st);
     VB_CUDA(cudaEventRecord(r->ev_pro, st));
     const unsigned long long cap = std::max<uint64_t>(1, r->caps.queue_cap);
-    Queue q64{r->d_queue[2], r->d_qcount + 2, cap};
+    // queue levels: 0 tensor split pass, 1 FP32 pass, 2 double-float pass, 3 FP64 pass
+    Queue qsplit{r->d_queue[0], r->d_qcount + 0, cap};
+    Queue q32{r->d_queue[1], r->d_qcount + 1, cap};
+    Queue qdf{r->d_queue[2], r->d_qcount + 2, cap};
+    Queue q64{r->d_queue[3], r->d_qcount + 3, cap};
     if (hi > lo) {
         if (opt.precision == VBMC_PREC_FP64) {
             launch_fp64(v, r->d_q, 1, nullptr, nullptr, 0, lo, hi, net->n_sm, st);
             VB_CUDA(cudaEventRecord(r->ev_scr, st));
-        } else if (opt.precision == VBMC_PREC_FP32) {
-            const int MT = simt_tile_points(v);
-            if (MT == 0) return fail(VBMC_ERR_UNSUPPORTED, "layer width above 1024");
-            const unsigned long long base = lo & ~31ull;
-            const unsigned long long tiles = (hi - base + MT - 1) / MT;
-            unsigned long long tp[2] = {0, tiles};
-            VB_CUDA(cudaMemcpyAsync(r->d_tp, tp, sizeof(tp), cudaMemcpyHostToDevice, st));
-            launch_screen_simt(v, r->d_q, 1, r->d_tp, tiles, nullptr, nullptr, 0, q64, 2, net->n_sm,
-                               st);
-            VB_CUDA(cudaEventRecord(r->ev_scr, st));
-            launch_fp64(v, r->d_q, 1, r->d_queue[2], r->d_qcount + 2, cap, 0, 0, net->n_sm, st);
         } else {
-            if (!tc_supported(v, opt.precision))
-                return fail(VBMC_ERR_UNSUPPORTED, "tensor-core screen does not support this net/precision");
-            {
+            if (opt.precision == VBMC_PREC_FP32) {
+                const int MT = simt_tile_points(v);
+                if (MT == 0) return fail(VBMC_ERR_UNSUPPORTED, "layer width above 1024");
+                const unsigned long long base = lo & ~31ull;
+                const unsigned long long tiles = (hi - base + MT - 1) / MT;
+                unsigned long long tp[2] = {0, tiles};
+                VB_CUDA(cudaMemcpyAsync(r->d_tp, tp, sizeof(tp), cudaMemcpyHostToDevice, st));
+                launch_screen_simt(v, r->d_q, 1, r->d_tp, tiles, nullptr, nullptr, 0, qdf, 2,
+                                   net->n_sm, st);
+                VB_CUDA(cudaEventRecord(r->ev_scr, st));
+            } else {
+                if (!tc_supported(v, opt.precision))
+                    return fail(VBMC_ERR_UNSUPPORTED,
+                                "tensor-core screen does not support this net/precision");
                 vbmc_status sst = tc_build(net->tc, v, net->hW, net->hb, opt.precision);
                 if (sst != VBMC_OK) return fail(sst, "tensor-core set-up failed");
+                tc_launch_query_setup(net->tc, v, r->d_q, opt.precision, st);
+                sst = tc_launch_screen(net->tc, v, r->d_q, lo, hi, opt.precision, qsplit, net->n_sm, st);
+                if (sst != VBMC_OK) return fail(sst, "tensor-core screen launch failed");
+                VB_CUDA(cudaEventRecord(r->ev_scr, st));
+                sst = tc_launch_gather(net->tc, v, r->d_q, r->d_queue[0], r->d_qcount + 0, cap,
+                                       opt.precision, q32, net->n_sm, st);
+                if (sst != VBMC_OK) return fail(sst, "tensor-core split pass launch failed");
+                launch_screen_simt(v, r->d_q, 1, nullptr, 0, r->d_queue[1], r->d_qcount + 1, cap,
+                                   qdf, 2, net->n_sm, st);
             }
-            tc_launch_query_setup(net->tc, v, r->d_q, opt.precision, st);
-            // tensor screen -> tensor 3x pass -> FP32 pass -> FP64 pass
-            Queue q3{r->d_queue[0], r->d_qcount + 0, cap};
-            Queue q32{r->d_queue[1], r->d_qcount + 1, cap};
-            vbmc_status sst = tc_launch_screen(net->tc, v, r->d_q, lo, hi, opt.precision, q3,
-                                               net->n_sm, st);
-            if (sst != VBMC_OK) return sst;
-            VB_CUDA(cudaEventRecord(r->ev_scr, st));
-            sst = tc_launch_gather(net->tc, v, r->d_q, r->d_queue[0], r->d_qcount + 0, cap,
-                                   opt.precision, q32, net->n_sm, st);
-            if (sst != VBMC_OK) return sst;
-            launch_screen_simt(v, r->d_q, 1, nullptr, 0, r->d_queue[1], r->d_qcount + 1, cap, q64,
-                               2, net->n_sm, st);
-            launch_fp64(v, r->d_q, 1, r->d_queue[2], r->d_qcount + 2, cap, 0, 0, net->n_sm, st);
+            launch_df(v, r->d_q, r->d_queue[2], r->d_qcount + 2, cap, q64, 3, net->n_sm, st);
+            launch_fp64(v, r->d_q, 1, r->d_queue[3], r->d_qcount + 3, cap, 0, 0, net->n_sm, st);
         }
     }
     if (hi <= lo) VB_CUDA(cudaEventRecord(r->ev_scr, st));
@@ -407,7 +440,7 @@ vbmc_status finish(vbmc_result* r) {
         s.n_adversarial = c.n_adv;
         s.first_witness = c.first;
         s.n_ties = c.n_ties;
-        for (int i = 0; i < 3; ++i) s.n_recheck[i] = c.n_q[i];
+        for (int i = 0; i < 4; ++i) s.n_recheck[i] = c.n_q[i];
         float ms = 0.f, ms_p = 0.f, ms_s = 0.f;
         cudaEventElapsedTime(&ms, r->ev0, r->ev1);
         cudaEventElapsedTime(&ms_p, r->ev0, r->ev_pro);

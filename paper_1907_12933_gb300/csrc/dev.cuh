@@ -46,13 +46,18 @@ struct NetView {
     float lamfrob[kMaxL + 1];         // lambda * ||W_l||_F (rounded up; lambda: Lipschitz
                                       // constant of the hidden activation)
     float gam[kMaxL + 1];             // gamma_{H_{l-1}} = n u / (1 - n u), u = 2^-24
+    float lamsig[kMaxL + 1];          // lambda * sigma_max(W_l) (rounded up)
+    float sig[kMaxL + 1];             // sigma_max(W_l) (rounded up)
+    float frob[kMaxL + 1];            // ||W_l||_F (rounded up)
+    const float* pairw;               // [H_L][H_L]: ||W_L,D - W_L,o||_2 (rounded up)
 };
 
 struct Counters {
     unsigned long long n_adv;
     unsigned long long first;    // smallest adversarial index
     unsigned long long n_ties;
-    unsigned long long n_q[3];   // entries pushed to queue level 0 (tensor 3x), 1 (FP32), 2 (FP64)
+    unsigned long long n_q[4];   // entries pushed to queue level 0 (tensor split), 1 (FP32),
+                                 // 2 (double-float), 3 (FP64)
     unsigned long long n_points;
     unsigned int err;
     int D;
@@ -68,6 +73,7 @@ struct QueryView {
     int* dv;                // [s][R]: clamp(v_p + d - k, 0, 255) - v_p
     double* ub;             // [total] FP64 potentials of the unperturbed image
     double* hb;             // [total] FP64 outputs (act(ub); output layer: ub)
+    double* eub;            // [total] bound on |ub - exact| from the FP64 base pass
     float* ub32;            // [total] fp32(ub)
     float* dub;             // [total] value error of fl(ub) (+ layer-1 table-sum error)
     float* thr;             // [total] sign-certainty threshold: dub + 2 tau, or +inf when
@@ -115,6 +121,40 @@ __device__ __forceinline__ void queue_push(const Queue& Q, unsigned long long t,
     } else {
         atomicOr(&cnt->err, DERR_QUEUE);
     }
+}
+
+// Warp-cooperative push: every lane of the warp calls it (converged); lanes with
+// want == true get one slot each from a single atomic per warp.
+__device__ __forceinline__ void queue_push_warp(const Queue& Q, bool want, unsigned long long t,
+                                                unsigned q, Counters* cnt, int level) {
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) {
+        base = atomicAdd(Q.count, (unsigned long long)__popc(m));
+        atomicAdd(&cnt->n_q[level], (unsigned long long)__popc(m));
+    }
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (want) {
+        const unsigned long long i = base + __popc(m & ((1u << lane) - 1u));
+        if (i < Q.cap) {
+            QEntry e;
+            e.t = t;
+            e.q = q;
+            e.pad = 0;
+            Q.e[i] = e;
+        } else {
+            atomicOr(&cnt->err, DERR_QUEUE);
+        }
+    }
+}
+
+// Set a bit that many points set: read first, write only if still clear.
+__device__ __forceinline__ void set_bit_once(uint32_t* w, unsigned long long b) {
+    const uint32_t m = 1u << (unsigned)(b & 31);
+    if (!(*reinterpret_cast<volatile uint32_t*>(&w[b >> 5]) & m)) atomicOr(&w[b >> 5], m);
 }
 
 // Record a certainly adversarial (non-tie) point.

@@ -1,0 +1,212 @@
+// df.cu -- double-float pass: points the FP32 bound could not decide, evaluated
+// with FP32 pairs (hi + lo, about 48 significant bits) on the CUDA cores, which
+// on this part run several times faster than FP64.
+//
+// One CTA per point. Layer 1 in FP64 (incremental, Eq. 1). Layers 2..L on the
+// deltas dh = h(point) - h(unperturbed), each weight (exact in FP32) times a
+// pair (hi, lo): the product's rounding error is recovered exactly with an
+// FMA, sums use TwoSum (Knuth), so a K-term dot product carries at most
+// (K + 2) 2^-46 sum_j |w_j||dh_j| <= (K + 2) 2^-46 ||W_i|| ||dh|| of error.
+// The error of the delta vector itself propagates with the spectral norm.
+// A sign (Sec. III-B) or the class (Eq. 10) is decided only when its value
+// clears the bound by 2 tau; if anything is left undecided the whole point
+// goes on to the FP64 pass and contributes nothing here.
+#include "dev.cuh"
+#include "launch.h"
+
+#include <cfloat>
+
+namespace vbmc {
+namespace {
+
+constexpr int TDF = 256;
+
+__device__ __forceinline__ double act64(int act, double u) {
+    if (act == ACT_SIGMOID) return 1.0 / (1.0 + exp(-u));
+    if (act == ACT_RELU) return u > 0.0 ? u : 0.0;
+    return u;
+}
+
+__device__ __forceinline__ double block_sum64(double v, double* red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    __syncthreads();
+    return t;
+}
+
+__global__ void __launch_bounds__(TDF)
+k_df(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__ gather,
+     const unsigned long long* __restrict__ gcount, unsigned long long gcap, Queue out,
+     int out_level) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int total = net.total, hmax = net.hmax;
+    double* u = reinterpret_cast<double*>(smem_raw);                  // [total]
+    float2* dh = reinterpret_cast<float2*>(u + total);                // [hmax]
+    unsigned char* fl = reinterpret_cast<unsigned char*>(dh + hmax);  // [total]
+    __shared__ double red[32];
+    __shared__ int nflip[kMaxL + 2], only[kMaxL + 2];
+    __shared__ int dstep[kMaxS];
+    __shared__ int undecided;
+
+    unsigned long long n = *gcount;
+    if (n > gcap) n = gcap;
+    const int L = net.L;
+    const double c46 = 0x1p-46, u52 = 0x1p-52;
+    const double lam = net.act == ACT_SIGMOID ? 0.25 : 1.0;
+    for (unsigned long long e = blockIdx.x; e < n; e += gridDim.x) {
+        const QEntry en = gather[e];
+        const unsigned long long t = en.t;
+        const QueryView& Q = qs[en.q];
+        if (threadIdx.x == 0) {
+            int d[kMaxS];
+            decode_digits(t, Q.s, Q.R, d);
+            for (int p = 0; p < Q.s; ++p) dstep[p] = Q.dv[p * Q.R + d[p]];
+            undecided = 0;
+        }
+        if (threadIdx.x <= kMaxL + 1) {
+            nflip[threadIdx.x] = 0;
+            only[threadIdx.x] = -1;
+        }
+        __syncthreads();
+        // ---- layer 1 in FP64; its signs are decided here
+        const int H0 = net.dims[0], H1 = net.dims[1];
+        double nsq = 0.0, esq = 0.0;
+        for (int j = threadIdx.x; j < H1; j += TDF) {
+            const double ub = Q.ub[j];
+            double a = ub, mag = fabs(ub);
+            for (int p = 0; p < Q.s; ++p) {
+                const double term = (double)net.W[1][(size_t)j * H0 + Q.pix[p]] * ((double)dstep[p] / 255.0);
+                a += term;
+                mag += fabs(term);
+            }
+            u[j] = a;
+            // |a - exact| <= base error + rounding of the s additions and the terms
+            const double err = Q.eub[j] + (Q.s + 3) * u52 * mag;
+            const bool certain = fabs(a) > err + 2.0 * kTau && fabs(ub) >= kTau;
+            if (!certain) undecided = 1;
+            fl[j] = certain && ((a >= 0.0) != (ub >= 0.0));
+            const double d = (L > 1 ? act64(net.act, a) : a) - Q.hb[j];
+            const float hi = (float)d;
+            dh[j] = make_float2(hi, (float)(d - (double)hi));
+            nsq += d * d;
+            const double ej = 2.0 * err + u52 * (fabs(a) + fabs(Q.hb[j])) * 4.0 + 0x1p-47 * fabs(d);
+            esq += ej * ej;
+        }
+        double N = sqrt(block_sum64(nsq, red)) * (1.0 + 1e-12);
+        double E = sqrt(block_sum64(esq, red)) * (1.0 + 1e-12);
+        // ---- layers 2..L in double-float
+        for (int l = 2; l <= L && !undecided; ++l) {
+            const int K = net.dims[l - 1], Nn = net.dims[l], off = net.noff[l];
+            const float* WT = net.WT[l];
+            const double cK = (K + 2) * c46;
+            double nsq2 = 0.0, esq2 = 0.0;
+            for (int i = threadIdx.x; i < Nn; i += TDF) {
+                float S = 0.f, s = 0.f;
+                for (int j = 0; j < K; ++j) {
+                    const float w = WT[(size_t)j * Nn + i];
+                    const float2 h = dh[j];
+                    const float p = __fmul_rn(w, h.x);
+                    float ep = __fmaf_rn(w, h.x, -p);
+                    ep = __fmaf_rn(w, h.y, ep);
+                    const float tt = __fadd_rn(S, p);
+                    const float z = __fsub_rn(tt, S);
+                    const float er = __fadd_rn(__fsub_rn(S, __fsub_rn(tt, z)), __fsub_rn(p, z));
+                    S = tt;
+                    s = __fadd_rn(s, __fadd_rn(er, ep));
+                }
+                const double ub = Q.ub[off + i];
+                const double ui = ub + ((double)S + (double)s);
+                u[off + i] = ui;
+                const double err = (double)net.rownorm[l][i] * (cK * N + E) + Q.eub[off + i] +
+                                   u52 * (fabs(ui) + fabs(ub));
+                const bool certain = fabs(ui) > err + 2.0 * kTau && fabs(ub) >= kTau;
+                if (!certain) undecided = 1;
+                fl[off + i] = certain && ((ui >= 0.0) != (ub >= 0.0));
+                if (l < L) {
+                    const double d = act64(net.act, ui) - Q.hb[off + i];
+                    nsq2 += d * d;
+                    const double ej = lam * (Q.eub[off + i] + u52 * (fabs(ui) + fabs(ub))) +
+                                      Q.eub[off + i] + u52 * (fabs(ui) + fabs(Q.hb[off + i])) * 4.0 +
+                                      0x1p-47 * fabs(d);
+                    esq2 += ej * ej;
+                }
+            }
+            __syncthreads();  // dh of layer l-1 fully consumed
+            if (l < L) {
+                for (int i = threadIdx.x; i < Nn; i += TDF) {
+                    const double d = act64(net.act, u[off + i]) - Q.hb[off + i];
+                    const float hi = (float)d;
+                    dh[i] = make_float2(hi, (float)(d - (double)hi));
+                }
+                // ||err(dh_l)|| <= lambda (sigma_l E + (K+2) 2^-46 ||W_l||_F N) + per-element rounding
+                const double En = lam * ((double)net.sig[l] * E + cK * (double)net.frob[l] * N);
+                N = sqrt(block_sum64(nsq2, red)) * (1.0 + 1e-12);
+                E = (En + sqrt(block_sum64(esq2, red))) * (1.0 + 1e-12);
+            }
+            __syncthreads();
+        }
+        // ---- verdict (Eq. 10) with the margin bound of each class pair
+        if (threadIdx.x == 0 && !undecided) {
+            const int HL = net.dims[L], offL = net.noff[L];
+            const double* y = u + offL;
+            const int D = Q.cnt->D;
+            const double cK = (net.dims[L - 1] + 2) * c46;
+            bool unsafe = false, safe = true;
+            for (int o = 0; o < HL; ++o) {
+                if (o == D) continue;
+                const double diff = y[D] - y[o];
+                double eb = ((double)net.rownorm[L][D] + (double)net.rownorm[L][o]) * cK * N +
+                            Q.eub[offL + D] + Q.eub[offL + o] + 2.0 * kTau +
+                            u52 * 2.0 * (fabs(y[D]) + fabs(y[o]) + fabs(Q.ub[offL + D]) + fabs(Q.ub[offL + o]));
+                eb += (L > 1 ? (double)net.pairw[D * HL + o] : 0.0) * E;
+                if (diff < -eb) unsafe = true;
+                else if (!(diff > eb)) safe = false;
+            }
+            if (!unsafe && !safe) undecided = 1;
+            if (!undecided && unsafe) record_adversarial(Q, t);
+        }
+        __syncthreads();
+        if (undecided) {
+            if (threadIdx.x == 0) queue_push(out, t, en.q, Q.cnt, out_level);
+        } else {
+            // sign changes and SS-Cover pairs; every decision here is certain (no ties)
+            for (int nn = threadIdx.x; nn < total; nn += TDF) {
+                if (!fl[nn]) continue;
+                int l = 1;
+                while (l < L && nn >= net.noff[l + 1]) ++l;
+                atomicAdd(&nflip[l], 1);
+                atomicMax(&only[l], nn - net.noff[l]);
+                if (Q.flip) set_bit_once(Q.flip, nn);
+            }
+            __syncthreads();
+            if (Q.ss) {
+                for (int l = 1; l < L; ++l) {
+                    if (nflip[l] != 1) continue;
+                    const int j = only[l], Hn = net.dims[l + 1], on = net.noff[l + 1];
+                    for (int i = threadIdx.x; i < Hn; i += TDF)
+                        if (fl[on + i])
+                            set_bit_once(Q.ss, (unsigned long long)net.ssoff[l] + (unsigned long long)j * Hn + i);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+void launch_df(const NetView& net, const QueryView* d_qs, const QEntry* gather,
+               const unsigned long long* gather_count, unsigned long long gather_cap, Queue out,
+               int out_level, int n_sm, cudaStream_t st) {
+    const size_t smem = sizeof(double) * net.total + sizeof(float2) * net.hmax + (size_t)net.total;
+    cudaFuncSetAttribute(k_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_df<<<(unsigned)n_sm * 8, TDF, smem, st>>>(net, d_qs, gather, gather_count, gather_cap, out,
+                                               out_level);
+}
+
+}  // namespace vbmc

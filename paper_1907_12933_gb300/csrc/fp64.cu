@@ -112,11 +112,11 @@ k_fp64(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__
             if (ch) {
                 atomicAdd(&nflip[l], 1);
                 atomicMax(&only[l], nn - net.noff[l]);
-                if (Q.flip) set_bit_atomic(Q.flip, nn);
+                if (Q.flip) set_bit_once(Q.flip, nn);
             }
             if (tie) {
                 atomicAdd(&ntie[l], 1);
-                if (Q.flip_tie) set_bit_atomic(Q.flip_tie, nn);
+                if (Q.flip_tie) set_bit_once(Q.flip_tie, nn);
             }
         }
         __syncthreads();
@@ -136,8 +136,8 @@ k_fp64(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__
                     for (int i = threadIdx.x; i < Hn; i += T64) {
                         const unsigned long long bit = (unsigned long long)net.ssoff[l] +
                                                        (unsigned long long)j * Hn + i;
-                        if (certain && fl[on + i]) set_bit_atomic(Q.ss, bit);
-                        else if (fl[on + i] || ti[on + i]) set_bit_atomic(Q.ss_tie, bit);
+                        if (certain && fl[on + i]) set_bit_once(Q.ss, bit);
+                        else if (fl[on + i] || ti[on + i]) set_bit_once(Q.ss_tie, bit);
                     }
                 }
             }

@@ -2,6 +2,8 @@
 #pragma once
 #include "dev.cuh"
 
+#include <vector>
+
 namespace vbmc {
 
 // FP64 base pass, tables and screen constants for nq queries (d_qs on device).
@@ -34,5 +36,15 @@ void launch_fp64(const NetView& net, const QueryView* d_qs, int nq, const QEntry
 // FP64 margin of point t of query 0 into *d_out.
 void launch_margin64(const NetView& net, const QueryView* d_qs, unsigned long long t, double* d_out,
                      cudaStream_t st);
+
+// Upper bound of the spectral norm of the row-major m x n matrix A (host data;
+// the squarings run on the current device).
+double spectral_bound(const std::vector<double>& A, int m, int n);
+
+// Double-float pass (FP32 pairs on CUDA cores) over a queue; points it cannot
+// decide go to `out`.
+void launch_df(const NetView& net, const QueryView* d_qs, const QEntry* gather,
+               const unsigned long long* gather_count, unsigned long long gather_cap, Queue out,
+               int out_level, int n_sm, cudaStream_t st);
 
 }  // namespace vbmc

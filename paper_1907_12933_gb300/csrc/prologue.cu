@@ -31,7 +31,7 @@ __global__ void k_pro_init(NetView net, QueryView* qs, int nq) {
         c->n_adv = 0;
         c->first = ~0ull;
         c->n_ties = 0;
-        c->n_q[0] = c->n_q[1] = c->n_q[2] = 0;
+        c->n_q[0] = c->n_q[1] = c->n_q[2] = c->n_q[3] = 0;
         c->n_points = Q.hi - Q.lo;
         c->err = ok ? 0u : DERR_PIXELS;
         c->D = 0;
@@ -57,7 +57,10 @@ __device__ __forceinline__ double act64(int act, double u) {
     return u;
 }
 
-// One warp per neuron i of layer l; lanes stride over the inputs.
+// One warp per neuron i of layer l; lanes stride over the inputs. Also bounds
+// the FP64 error of the result: rounding of the K products and sums,
+// (K + 2) 2^-53 (sum_j |w_j h_j| + |b|), plus the input errors propagated,
+// sum_j |w_j| e_j (the activations are 1-Lipschitz).
 __global__ void k_pro_layer(NetView net, QueryView* qs, int nq, int l) {
     const QueryView& Q = qs[blockIdx.y];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -65,19 +68,37 @@ __global__ void k_pro_layer(NetView net, QueryView* qs, int nq, int l) {
     const int K = net.dims[l - 1], N = net.dims[l];
     if (i >= N) return;
     const float* Wr = net.W[l] + (size_t)i * K;
-    double acc = 0.0;
+    double acc = 0.0, mag = 0.0, prop = 0.0;
     if (l == 1) {
-        for (int j = lane; j < K; j += 32) acc += (double)Wr[j] * ((double)Q.image[j] / 255.0);
+        for (int j = lane; j < K; j += 32) {
+            const double p = (double)Wr[j] * ((double)Q.image[j] / 255.0);
+            acc += p;
+            mag += fabs(p);
+        }
     } else {
         const double* h = Q.hb + net.noff[l - 1];
-        for (int j = lane; j < K; j += 32) acc += (double)Wr[j] * h[j];
+        const double* eh = Q.eub + net.noff[l - 1];
+        for (int j = lane; j < K; j += 32) {
+            const double p = (double)Wr[j] * h[j];
+            acc += p;
+            mag += fabs(p);
+            prop += fabs((double)Wr[j]) * eh[j];
+        }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        mag += __shfl_xor_sync(0xffffffffu, mag, o);
+        prop += __shfl_xor_sync(0xffffffffu, prop, o);
+    }
     if (lane == 0) {
-        double u = acc + (double)net.b[l][i];
+        const double bi = (double)net.b[l][i];
+        double u = acc + bi;
         Q.ub[net.noff[l] + i] = u;
         Q.hb[net.noff[l] + i] = (l < net.L) ? act64(net.act, u) : u;
+        // (x/255 carries one more rounding on layer 1; activations add 2^-50 |u|)
+        const double e = ((K + 4) * 0x1p-53 * (mag + fabs(bi)) + prop + 0x1p-50 * fabs(u)) * (1.0 + 1e-9);
+        Q.eub[net.noff[l] + i] = e;
     }
 }
 
@@ -117,7 +138,8 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 // Screen constants. With fl() the fp32 rounding and u = 2^-24:
-//  dub_n   = |fl(ub_n) - ub_n| + 1e-12 (1 + |ub_n|)   (+ e1_j on layer 1)
+//  dub_n   = |fl(ub_n) - ub_n| + eub_n   (+ e1_j on layer 1); eub bounds the FP64
+//            error of ub itself, so every screen decision holds in exact arithmetic
 //  thr_n   = dub_n + 2 tau, infinite when |ub_n| < tau (every evaluation of n is
 //            a sign tie)
 //  e1_j    = (gamma_{s+2} + 2u) * sum_p max_d |tab[p][d][j]|, the layer-1 table-sum error
@@ -150,7 +172,7 @@ __global__ void k_pro_finish(NetView net, QueryView* qs, int nq) {
             const int n = net.noff[l] + i;
             const double ub = Q.ub[n], hb = Q.hb[n];
             const float ub32 = __double2float_rn(ub);
-            const double dub = fabs((double)ub32 - ub) + 1e-12 * (1.0 + fabs(ub));
+            const double dub = fabs((double)ub32 - ub) + Q.eub[n];
             double e1 = 0.0;
             if (l == 1) {
                 double b1 = 0.0;
@@ -173,7 +195,7 @@ __global__ void k_pro_finish(NetView net, QueryView* qs, int nq) {
                 Q.c1[n] = ub32;
                 Q.c2[n] = __double2float_rn(hb);
             }
-            const double dhb = fabs((double)__double2float_rn(hb) - hb) + 1e-12 * (1.0 + fabs(hb));
+            const double dhb = fabs((double)__double2float_rn(hb) - hb) + Q.eub[n];
             if (l < L) {
                 if (net.act == ACT_RELU) {
                     ss_a += (e1 + dub) * (e1 + dub);

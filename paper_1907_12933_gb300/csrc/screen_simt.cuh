@@ -156,7 +156,7 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
                         } else if ((u >= 0.f) != (ub >= 0.f)) {
                             int idx = atomicAdd(&S.fcnt[m][1], 1);
                             if (idx < FCAP) S.flist[m][1][idx] = (short)j;
-                            if (Q.flip) set_bit_atomic(Q.flip, j);
+                            if (Q.flip) set_bit_once(Q.flip, j);
                         }
                         if (L > 1) dh = act_delta(net.act, du, u, Q.c1[j], Q.c2[j]);
                         else dh = u;
@@ -244,7 +244,7 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
                         } else if ((u >= 0.f) != (ub >= 0.f)) {
                             int idx = atomicAdd(&S.fcnt[m][l], 1);
                             if (idx < FCAP) S.flist[m][l][idx] = (short)n;
-                            if (Q.flip) set_bit_atomic(Q.flip, gi);
+                            if (Q.flip) set_bit_once(Q.flip, gi);
                         }
                         if (l < L) {
                             const float dh = act_delta(net.act, du, u, Q.c1[gi], Q.c2[gi]);
@@ -263,13 +263,15 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
                 if (lane == 0) {
                     if (l < L) {
                         const float Nl = norm_up(nsum);
-                        float El = __fmaf_ru(lf, X, Q.kvec[l]);
+                        // lambda (||W_l||_F gamma N_{l-1} + sigma_l E_{l-1}) + kvec_l
+                        float El = __fmaf_ru(__fmul_ru(lf, gl), S.N[m], Q.kvec[l]);
+                        El = __fmaf_ru(net.lamsig[l], S.E[m], El);
                         El = __fmaf_ru(0x1p-24f, Nl, El);
                         if (net.act == ACT_SIGMOID) El = __fmaf_ru(0x1p-26f, norm_up(usum), El);
                         S.N[m] = Nl;
                         S.E[m] = El;
                     } else {
-                        S.E[m] = X;  // X_L, for the verdict
+                        S.N[m] = __fmul_ru(gl, S.N[m]);  // gamma N_{L-1}: dot-product rounding
                     }
                 }
             }
@@ -285,8 +287,9 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
                 if (!S.valid[m]) continue;
                 const QueryView& Q = qs[S.q[m]];
                 const int D = Q.cnt->D;
-                float X = S.E[m];
-                if (L == 1) X = 0.f;  // single layer: the table sums carry their own bound in thr
+                // per output: rounding ||W_o|| gamma N; shared error ||W_D - W_o|| E
+                const float gN = L > 1 ? S.N[m] : 0.f;
+                const float Ep = L > 1 ? S.E[m] : 0.f;
                 const float yD = S.A[m][D];
                 const float rD = L > 1 ? rn[D] : 0.f;
                 const float dD = Q.dub[offL + D];
@@ -296,8 +299,10 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
                     const float yo = S.A[m][o];
                     const float diff = yD - yo;
                     const float ro = L > 1 ? rn[o] : 0.f;
-                    float eb = __fmaf_ru(__fadd_ru(rD, ro), X,
+                    const float pw = L > 1 ? net.pairw[D * HL + o] : 0.f;
+                    float eb = __fmaf_ru(__fadd_ru(rD, ro), gN,
                                          __fadd_ru(__fadd_ru(dD, Q.dub[offL + o]), (float)(2.0 * kTau)));
+                    eb = __fmaf_ru(pw, Ep, eb);
                     eb = __fmaf_ru(0x1p-23f, __fadd_ru(__fadd_ru(fabsf(yD), fabsf(yo)), fabsf(diff)), eb);
                     if (diff < -eb) unsafe = true;
                     else if (!(diff > eb)) safe = false;
@@ -309,30 +314,39 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
             __syncwarp();
         }
 
-        // ---- S6/S7: per-point results
-        if (lane < PPW) {
-            const int m = warp * PPW + lane;
-            if (S.valid[m]) {
-                const QueryView& Q = qs[S.q[m]];
-                bool bad = S.unc[m] || S.vstate[m] == 2;
-                if (!bad && Q.ss)
-                    for (int l = 1; l < L; ++l)
-                        if (S.fcnt[m][l] == 1 && S.fcnt[m][l + 1] > FCAP) bad = true;
-                if (bad) {
-                    queue_push(out, S.t[m], (unsigned)S.q[m], Q.cnt, out_level);
-                } else {
-                    if (S.vstate[m] == 1) record_adversarial(Q, S.t[m]);
-                    if (Q.ss) {
-                        for (int l = 1; l < L; ++l) {
-                            if (S.fcnt[m][l] != 1) continue;
-                            const int j = S.flist[m][l][0];
-                            const int Hn = net.dims[l + 1];
-                            const int nt = S.fcnt[m][l + 1];
-                            for (int e = 0; e < nt; ++e)
-                                set_bit_atomic(Q.ss, (unsigned long long)net.ssoff[l] +
-                                                         (unsigned long long)j * Hn + S.flist[m][l + 1][e]);
-                        }
+        // ---- S6/S7: per-point results (lane r < PPW holds point warp*PPW + r)
+        {
+            const int m = warp * PPW + (lane < PPW ? lane : 0);
+            const bool mine = lane < PPW && S.valid[m];
+            const QueryView& Q = qs[S.q[m]];
+            bool bad = mine && (S.unc[m] || S.vstate[m] == 2);
+            if (mine && !bad && Q.ss)
+                for (int l = 1; l < L; ++l)
+                    if (S.fcnt[m][l] == 1 && S.fcnt[m][l + 1] > FCAP) bad = true;
+            queue_push_warp(out, bad, S.t[m], (unsigned)S.q[m], Q.cnt, out_level);
+            const bool adv = mine && !bad && S.vstate[m] == 1;
+            // the warp's points are consecutive indices of one query in range mode
+            const unsigned am = __ballot_sync(0xffffffffu, adv);
+            if (am) {
+                if (!gather) {
+                    if (lane == __ffs(am) - 1) {
+                        atomicAdd(&Q.cnt->n_adv, (unsigned long long)__popc(am));
+                        atomicMin(&Q.cnt->first, S.t[m]);
                     }
+                    if (adv && Q.bitmap && S.t[m] < Q.bitmap_bits) set_bit_atomic(Q.bitmap, S.t[m]);
+                } else if (adv) {
+                    record_adversarial(Q, S.t[m]);
+                }
+            }
+            if (mine && !bad && Q.ss) {
+                for (int l = 1; l < L; ++l) {
+                    if (S.fcnt[m][l] != 1) continue;
+                    const int j = S.flist[m][l][0];
+                    const int Hn = net.dims[l + 1];
+                    const int nt = S.fcnt[m][l + 1];
+                    for (int e = 0; e < nt; ++e)
+                        set_bit_once(Q.ss, (unsigned long long)net.ssoff[l] +
+                                               (unsigned long long)j * Hn + S.flist[m][l + 1][e]);
                 }
             }
         }

@@ -65,6 +65,7 @@ struct TcSmem {
     int vst[MROWS];
     int fcnt[MROWS][kTcMaxL + 1];
     short flist[MROWS][kTcMaxL + 1][FCAP];
+    uint32_t cflip[256];   // sign changes seen by this CTA (flushed once at the end)
     int npref;
     int uniform_base;
     unsigned long long bars[2 * NB + 2 * NA + 5];
@@ -149,6 +150,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
         S.abort_flag = 0;
         tc::fence_mbar_init();
     }
+    for (int w = threadIdx.x; w < 256; w += blockDim.x) S.cflip[w] = 0u;
     if (warp == 1) {
         tc::tmem_alloc(tc::smem_u32(&S.tmem_slot), 512);
         tc::tmem_relinquish();
@@ -186,12 +188,11 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                             }
                 }
             if (!ok) {  // let the copies already issued land before the CTA leaves
-                for (uint32_t i = it > (uint32_t)NB ? it - NB : 0; i < it; ++i) {
-                    volatile int never = 0;
-                    for (int spin = 0; spin < (1 << 20); ++spin)
-                        if (tc::mbar_try(bar(BFULL(i % NB)), (i / NB) & 1)) break;
-                    (void)never;
-                }
+                const uint64_t t0 = tc::global_ns();
+                for (uint32_t i = it > (uint32_t)NB ? it - NB : 0; i < it; ++i)
+                    while (!tc::mbar_try(bar(BFULL(i % NB)), (i / NB) & 1) &&
+                           tc::global_ns() - t0 < tc::kWaitNs) {
+                    }
             }
         }
     } else if (warp == 1) {
@@ -252,9 +253,8 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
             }
             // everything issued must finish before TMEM is released
             tc::mma_commit(bar(FIN));
-            for (uint32_t spin = 0; spin < tc::kSpinLimit; ++spin) {
-                if (tc::mbar_try(bar(FIN), 0)) break;
-                if ((spin & 63) == 63) __nanosleep(64);
+            const uint64_t t0 = tc::global_ns();
+            while (!tc::mbar_try(bar(FIN), 0) && tc::global_ns() - t0 < tc::kWaitNs) {
             }
         }
     } else {
@@ -375,7 +375,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                                 else if ((u >= 0.f) != (ub0 >= 0.f)) {
                                     const int k = atomicAdd(&S.fcnt[r][1], 1);
                                     if (k < FCAP) S.flist[r][1][k] = (short)j;
-                                    if (Q.flip) set_bit_atomic(Q.flip, j);
+                                    atomicOr(&S.cflip[j >> 5], 1u << (j & 31));
                                 }
                                 dh0 = fmaxf(du.x + c10, c20);
                             }
@@ -386,7 +386,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                                 else if ((u >= 0.f) != (ub1 >= 0.f)) {
                                     const int k = atomicAdd(&S.fcnt[r][1], 1);
                                     if (k < FCAP) S.flist[r][1][k] = (short)(j + 1);
-                                    if (Q.flip) set_bit_atomic(Q.flip, j + 1);
+                                    atomicOr(&S.cflip[(j + 1) >> 5], 1u << ((j + 1) & 31));
                                 }
                                 dh1 = fmaxf(du.y + c11, c21);
                             }
@@ -483,7 +483,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                                 else if ((u >= 0.f) != (ub >= 0.f)) {
                                     const int k = atomicAdd(&S.fcnt[r][l], 1);
                                     if (k < FCAP) S.flist[r][l][k] = (short)n;
-                                    if (Q.flip) set_bit_atomic(Q.flip, gi);
+                                    atomicOr(&S.cflip[gi >> 5], 1u << (gi & 31));
                                 }
                             }
                             v[ii] = fmaxf(du + Q.c1[gi], Q.c2[gi]);
@@ -591,7 +591,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                             else if ((u >= 0.f) != (ub >= 0.f)) {
                                 const int k = atomicAdd(&S.fcnt[r][L], 1);
                                 if (k < FCAP) S.flist[r][L][k] = (short)o;
-                                if (Q.flip) set_bit_atomic(Q.flip, offL + o);
+                                atomicOr(&S.cflip[(offL + o) >> 5], 1u << ((offL + o) & 31));
                             }
                         }
                         float yD = 0.f;
@@ -633,7 +633,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         for (int l = 1; l < L; ++l)
                             if (S.fcnt[r][l] == 1 && S.fcnt[r][l + 1] > FCAP) bad = true;
                     const unsigned long long t = S.t[r];
-                    if (bad) queue_push(out, t, 0u, Q.cnt, out_level);
+                    queue_push_warp(out, bad, t, 0u, Q.cnt, out_level);
                     const bool adv = rv && !bad && S.vst[r] == 1;
                     if (!gather) {
                         const unsigned m = __ballot_sync(0xffffffffu, adv);
@@ -652,8 +652,8 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                             const int Hn = net.dims[l + 1];
                             const int nt = S.fcnt[r][l + 1];
                             for (int e = 0; e < nt; ++e)
-                                set_bit_atomic(Q.ss, (unsigned long long)net.ssoff[l] +
-                                                         (unsigned long long)j * Hn + S.flist[r][l + 1][e]);
+                                set_bit_once(Q.ss, (unsigned long long)net.ssoff[l] +
+                                                       (unsigned long long)j * Hn + S.flist[r][l + 1][e]);
                         }
                     }
                 }
@@ -664,6 +664,9 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
     // ---- teardown: wait for outstanding tensor-core work, release TMEM
     tc::tc_fence_before();
     __syncthreads();
+    if (Q.flip)
+        for (int w = threadIdx.x; w < net.flip_words && w < 256; w += blockDim.x)
+            if (S.cflip[w]) atomicOr(&Q.flip[w], S.cflip[w]);
     if (warp == 1) {
         __syncwarp();
         tc::tc_fence_after();
@@ -678,7 +681,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
 // |du| over the whole box plus the screen's error bound keeps its sign at every
 // point: "pos" (output change = input change) or "neg" (output change 0). The
 // bound on |du| propagates interval bounds |dh_j| <= B_j through |W_l|.
-__global__ void k_tc_classes(const __grid_constant__ TcParams P, NetView net, QueryView* qs) {
+__global__ void k_classes_tc(const __grid_constant__ TcParams P, NetView net, QueryView* qs) {
     __shared__ double Bh[1024];
     __shared__ double red[64];
     QueryView& Q = qs[blockIdx.x];
@@ -763,77 +766,6 @@ __global__ void k_tc_classes(const __grid_constant__ TcParams P, NetView net, Qu
 
 // ------------------------------------------------------- host-side set-up
 
-// C = A * B^T for row-major A [M x K] and B [N x K], FP64 (small set-up GEMMs).
-__global__ void k_gemm_abt64(const double* A, const double* B, double* C, int M, int N, int K) {
-    __shared__ double As[16][17], Bs[16][17];
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
-    double acc = 0.0;
-    for (int k0 = 0; k0 < K; k0 += 16) {
-        As[ty][tx] = (row < M && k0 + tx < K) ? A[(size_t)row * K + k0 + tx] : 0.0;
-        Bs[ty][tx] = (blockIdx.x * 16 + ty < N && k0 + tx < K)
-                         ? B[(size_t)(blockIdx.x * 16 + ty) * K + k0 + tx]
-                         : 0.0;
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < 16; ++k) acc += As[ty][k] * Bs[tx][k];
-        __syncthreads();
-    }
-    if (row < M && col < N) C[(size_t)row * N + col] = acc;
-}
-
-// Rigorous upper bound of the spectral norm of A (m x n, host, row-major):
-// sigma^2 = lambda_max(G) <= ||G^(2^k)||_F^(1/2^k) for the Gram matrix G.
-double spectral_bound(const std::vector<double>& A, int m, int n) {
-    const bool rows = m <= n;  // G = A A^T (m x m) or A^T A (n x n)
-    const int g = rows ? m : n;
-    std::vector<double> At;
-    const std::vector<double>* src = &A;
-    int K = n;
-    if (!rows) {
-        At.resize((size_t)n * m);
-        for (int i = 0; i < m; ++i)
-            for (int j = 0; j < n; ++j) At[(size_t)j * m + i] = A[(size_t)i * n + j];
-        src = &At;
-        K = m;
-    }
-    double *dA = nullptr, *dG = nullptr, *dH = nullptr;
-    cudaMalloc(&dA, sizeof(double) * src->size());
-    cudaMalloc(&dG, sizeof(double) * (size_t)g * g);
-    cudaMalloc(&dH, sizeof(double) * (size_t)g * g);
-    cudaMemcpy(dA, src->data(), sizeof(double) * src->size(), cudaMemcpyHostToDevice);
-    dim3 blk(16, 16), grd((g + 15) / 16, (g + 15) / 16);
-    k_gemm_abt64<<<grd, blk>>>(dA, dA, dG, g, g, K);
-    std::vector<double> h((size_t)g * g);
-    double logscale = 0.0;
-    const int squarings = 5;
-    for (int it = 0; it <= squarings; ++it) {
-        cudaMemcpy(h.data(), dG, sizeof(double) * h.size(), cudaMemcpyDeviceToHost);
-        double f = 0.0;
-        for (double x : h) f += x * x;
-        f = std::sqrt(f);
-        if (!(f > 0.0)) {
-            cudaFree(dA);
-            cudaFree(dG);
-            cudaFree(dH);
-            return 0.0;
-        }
-        // G_it = exp(logscale) * (current matrix); track the scale, normalise
-        logscale = (it == 0 ? 0.0 : 2.0 * logscale) + std::log(f);
-        for (double& x : h) x /= f;
-        if (it == squarings) break;
-        cudaMemcpy(dG, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice);
-        k_gemm_abt64<<<grd, blk>>>(dG, dG, dH, g, g, g);  // G symmetric: G G^T = G^2
-        std::swap(dG, dH);
-    }
-    cudaFree(dA);
-    cudaFree(dG);
-    cudaFree(dH);
-    // ||G^(2^k)||_F = exp(logscale); lambda_max <= exp(logscale / 2^k)
-    const double lam = std::exp(logscale / (double)(1 << squarings));
-    return std::sqrt(lam) * (1.0 + 1e-6);
-}
-
 float up_f(double x) {
     float f = (float)x;
     if ((double)f < x) f = std::nextafter(f, INFINITY);
@@ -855,6 +787,7 @@ bool tc_supported(const NetView& v, int precision) {
     for (int l = 2; l < v.L; ++l)
         if (v.dims[l] % 64 || v.dims[l] > 512) return false;
     if (v.dims[v.L] > kTcMaxOut) return false;
+    if (v.flip_words > 256) return false;
     return true;
 }
 
@@ -1023,7 +956,7 @@ void tc_free(TcNet& tc) {
 void tc_launch_query_setup(TcNet& tc, const NetView& v, QueryView* d_q, int precision,
                            cudaStream_t st) {
     const TcParams& P = tc.prec[precision == VBMC_PREC_BF16 ? 0 : 1].p;
-    k_tc_classes<<<1, 512, 0, st>>>(P, v, d_q);
+    k_classes_tc<<<1, 512, 0, st>>>(P, v, d_q);
 }
 
 template <bool SPLIT, bool BF>

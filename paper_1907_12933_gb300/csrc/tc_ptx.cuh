@@ -1,7 +1,7 @@
 // tc_ptx.cuh -- inline-PTX wrappers for the sm_103a tensor-core path:
 // mbarriers, TMA tiled loads, TMEM allocation, tcgen05.mma / commit / ld, and
-// the proxy fences between them. Every wait is bounded: after kSpinLimit polls
-// it gives up, latches an error code and returns false.
+// the proxy fences between them. Every wait is bounded in time: it gives up,
+// raises the CTA's abort flag and returns false.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -9,7 +9,6 @@
 namespace vbmc {
 namespace tc {
 
-constexpr uint32_t kSpinLimit = 1u << 26;  // ~seconds with nanosleep back-off
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -44,17 +43,29 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity to complete.
+// Bounded wait for the phase with the given parity to complete: gives up after
+// about two seconds (globaltimer) or when another role has already given up.
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+constexpr uint64_t kWaitNs = 2000000000ull;
+
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (uint32_t i = 1;; ++i) {
         if (mbar_try(bar, parity)) return true;
-        if ((i & 63) == 63) {
+        if ((i & 255) == 0) {
             if (*abort_flag) return false;
-            __nanosleep(64);
+            if (global_ns() - t0 > kWaitNs) {
+                *abort_flag = 1;
+                return false;
+            }
         }
     }
-    *abort_flag = 1;
-    return false;
 }
 
 // 2-D tiled TMA load global -> shared, completion counted on an mbarrier.
