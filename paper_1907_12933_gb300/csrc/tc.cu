@@ -58,6 +58,8 @@ struct TcSmem {
     unsigned long long t[MROWS];
     int valid[MROWS];
     int pidx[MROWS];
+    int4 rinfo[MROWS];     // layer-1 fast path: {prefix slot, inner table offsets a, b, valid}
+    int fast;              // every valid row of the tile uses the fast path
     unsigned char dig[MROWS][kMaxS];
     float N[MROWS], R[MROWS], Lo[MROWS], E[MROWS];
     float part[2][MROWS][3];
@@ -314,6 +316,22 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 S.npref = np;
             }
             tc::named_bar_sync(1, 256);
+            if (wtid < MROWS) {
+                const int r = wtid;
+                int4 ri;
+                ri.x = S.pidx[r];
+                ri.y = ni >= 2 ? ((s - 2) * R + S.dig[r][s - 2]) * H1 : 0;
+                ri.z = ni >= 1 ? ((s - 1) * R + S.dig[r][s - 1]) * H1 : 0;
+                ri.w = S.valid[r];
+                S.rinfo[r] = ri;
+            }
+            if (wtid == 0) {
+                int f = (!gather && ni == 2) ? 1 : 0;
+                for (int r = 0; r < MROWS && f; ++r)
+                    if (S.valid[r] && S.pidx[r] < 0) f = 0;
+                if (s == 2 && !gather) f = 1;  // no outer digits: the partial sum is 0
+                S.fast = f;
+            }
             for (int k = 0; k < S.npref; ++k) {
                 int dd[kMaxS];
                 decode_digits(S.pref[k], s - ni, R, dd);
@@ -326,50 +344,67 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
             }
             tc::named_bar_sync(1, 256);
 
-            // ---- W1: layer-1 deltas -> operand of layer 2 (rows wid*16 .. +15)
+            // ---- W1: layer-1 deltas -> operand of layer 2 (rows wid*16 .. +15,
+            //      lanes over column pairs 2*lane, 2*lane+1 of each 64-column chunk)
             {
                 float nsum[16], rsum[16], lsum[16];
 #pragma unroll
                 for (int i = 0; i < 16; ++i) nsum[i] = rsum[i] = lsum[i] = 0.f;
                 const int kch = H1 / 64;
+                const bool fast = S.fast;
+                const bool nosum = (s == 2);  // fast path without outer digits
                 for (int c = 0; c < kch; ++c) {
                     const int a0 = ait % NA, a1 = (ait + 1) % NA;
                     tc::mbar_wait(bar(AEMPTY(a0)), ((ait / NA) & 1) ^ 1, abortp);
                     if (SPLIT) tc::mbar_wait(bar(AEMPTY(a1)), (((ait + 1) / NA) & 1) ^ 1, abortp);
                     const int j = 64 * c + 2 * lane;
                     const uint32_t pm = Q.cpos[32 + (j >> 5)], nm = Q.cneg[32 + (j >> 5)];
-                    const uint32_t b0 = 1u << (j & 31), b1 = 1u << ((j + 1) & 31);
-                    const int cls0 = (nm & b0) ? 2 : (pm & b0) ? 1 : 0;  // 0 cross, 1 pos, 2 neg
-                    const int cls1 = (nm & b1) ? 2 : (pm & b1) ? 1 : 0;
-                    float ub0 = 0.f, ub1 = 0.f, th0 = 0.f, th1 = 0.f, c10 = 0.f, c11 = 0.f, c20 = 0.f, c21 = 0.f;
-                    if (cls0 == 0) { ub0 = Q.ub32[j]; th0 = Q.thr[j]; c10 = Q.c1[j]; c20 = Q.c2[j]; }
-                    if (cls1 == 0) { ub1 = Q.ub32[j + 1]; th1 = Q.thr[j + 1]; c11 = Q.c1[j + 1]; c21 = Q.c2[j + 1]; }
+                    const bool pos0 = pm >> (j & 31) & 1, neg0 = nm >> (j & 31) & 1;
+                    const bool pos1 = pm >> ((j + 1) & 31) & 1, neg1 = nm >> ((j + 1) & 31) & 1;
+                    const bool cr0 = !pos0 && !neg0, cr1 = !pos1 && !neg1;
+                    // dh = max(du + c1, c2) covers all classes: pos (0, -inf), neg (-inf, 0)
+                    const float c10 = cr0 ? Q.c1[j] : (pos0 ? 0.f : -INFINITY);
+                    const float c20 = cr0 ? Q.c2[j] : (pos0 ? -INFINITY : 0.f);
+                    const float c11 = cr1 ? Q.c1[j + 1] : (pos1 ? 0.f : -INFINITY);
+                    const float c21 = cr1 ? Q.c2[j + 1] : (pos1 ? -INFINITY : 0.f);
+                    const float ub0 = cr0 ? Q.ub32[j] : 0.f, ub1 = cr1 ? Q.ub32[j + 1] : 0.f;
+                    const float th0 = cr0 ? Q.thr[j] : 0.f, th1 = cr1 ? Q.thr[j + 1] : 0.f;
+                    const bool anyc = __any_sync(0xffffffffu, cr0 || cr1);
+                    const uint32_t lanepart = (lane & 3) * 4;
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
                         const int r = wid * 16 + i;
-                        float dh0 = 0.f, dh1 = 0.f;
-                        if (S.valid[r]) {
-                            float2 du;
-                            const int pi = S.pidx[r];
-                            if (pi >= 0) {
-                                du = *reinterpret_cast<const float2*>(&S.souter[pi][j]);
-                                for (int p = s - ni; p < s; ++p) {
-                                    const float2 tv = __ldg(reinterpret_cast<const float2*>(
-                                        &Q.tab[((size_t)p * R + S.dig[r][p]) * H1 + j]));
-                                    du.x += tv.x;
-                                    du.y += tv.y;
+                        const int4 ri = S.rinfo[r];
+                        float2 du;
+                        if (fast) {
+                            du = nosum ? make_float2(0.f, 0.f)
+                                       : *reinterpret_cast<const float2*>(&S.souter[ri.x][j]);
+                            const float2 ta = __ldg(reinterpret_cast<const float2*>(&Q.tab[ri.y + j]));
+                            const float2 tb = __ldg(reinterpret_cast<const float2*>(&Q.tab[ri.z + j]));
+                            du.x = (du.x + ta.x) + tb.x;
+                            du.y = (du.y + ta.y) + tb.y;
+                        } else {
+                            du = make_float2(0.f, 0.f);
+                            if (ri.w) {
+                                const int pi = S.pidx[r];
+                                int p0 = 0;
+                                if (pi >= 0) {
+                                    du = *reinterpret_cast<const float2*>(&S.souter[pi][j]);
+                                    p0 = s - ni;
                                 }
-                            } else {
-                                du = make_float2(0.f, 0.f);
-                                for (int p = 0; p < s; ++p) {
+                                for (int p = p0; p < s; ++p) {
                                     const float2 tv = __ldg(reinterpret_cast<const float2*>(
                                         &Q.tab[((size_t)p * R + S.dig[r][p]) * H1 + j]));
                                     du.x += tv.x;
                                     du.y += tv.y;
                                 }
                             }
-                            if (cls0 == 1) dh0 = du.x;
-                            else if (cls0 == 0) {
+                        }
+                        float dh0 = fmaxf(du.x + c10, c20);
+                        float dh1 = fmaxf(du.y + c11, c21);
+                        if (!ri.w) dh0 = dh1 = 0.f;
+                        if (anyc && ri.w) {
+                            if (cr0) {
                                 const float u = ub0 + du.x;
                                 if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > th0)) S.unc[r] = 1;
                                 else if ((u >= 0.f) != (ub0 >= 0.f)) {
@@ -377,10 +412,8 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                                     if (k < FCAP) S.flist[r][1][k] = (short)j;
                                     atomicOr(&S.cflip[j >> 5], 1u << (j & 31));
                                 }
-                                dh0 = fmaxf(du.x + c10, c20);
                             }
-                            if (cls1 == 1) dh1 = du.y;
-                            else if (cls1 == 0) {
+                            if (cr1) {
                                 const float u = ub1 + du.y;
                                 if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > th1)) S.unc[r] = 1;
                                 else if ((u >= 0.f) != (ub1 >= 0.f)) {
@@ -388,13 +421,14 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                                     if (k < FCAP) S.flist[r][1][k] = (short)(j + 1);
                                     atomicOr(&S.cflip[(j + 1) >> 5], 1u << ((j + 1) & 31));
                                 }
-                                dh1 = fmaxf(du.y + c11, c21);
                             }
                         }
                         float q0, q1;
                         const uint32_t w = pack2<BF>(dh0, dh1, q0, q1);
                         float r0 = dh0 - q0, r1 = dh1 - q1;
-                        const uint32_t off = sw_off(r, lane >> 2) + (lane & 3) * 4;
+                        // r & 7 == i & 7 (wid * 16 is a multiple of 8): swizzle known per i
+                        const uint32_t off = (uint32_t)((wid * 2 + (i >> 3)) * 1024 + (i & 7) * 128) +
+                                             ((((uint32_t)lane >> 2) ^ (uint32_t)(i & 7)) << 4) + lanepart;
                         *reinterpret_cast<uint32_t*>(&S.A[a0][off]) = w;
                         if (SPLIT) {
                             float l0, l1;
@@ -417,19 +451,19 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 }
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
-                    float a = nsum[i], b = rsum[i], c = lsum[i];
+                    float a = nsum[i], b = rsum[i], cc = lsum[i];
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
                         a += __shfl_xor_sync(0xffffffffu, a, o);
                         b += __shfl_xor_sync(0xffffffffu, b, o);
-                        c += __shfl_xor_sync(0xffffffffu, c, o);
+                        if (SPLIT) cc += __shfl_xor_sync(0xffffffffu, cc, o);
                     }
                     if (lane == i) {
                         const int r = wid * 16 + i;
                         const float N = norm_up(a);
                         S.N[r] = N;
                         S.R[r] = norm_up(b);
-                        S.Lo[r] = norm_up(c);
+                        S.Lo[r] = SPLIT ? norm_up(cc) : 0.f;
                         S.E[r] = __fmaf_ru(0x1p-24f, N, Q.kvec[1]);
                     }
                 }
@@ -461,20 +495,15 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     float v[32];
                     tc::tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)n0, v);
                     const uint32_t pm = Q.cpos[l * 32 + (n0 >> 5)], nm = Q.cneg[l * 32 + (n0 >> 5)];
-                    uint32_t cross = ~(pm | nm);
+                    const uint32_t cross = ~(pm | nm);
                     const bool rv = S.valid[r];
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
-                        if (nm & (1u << i)) v[i] = 0.f;
-                    }
-                    while (cross) {
-                        const int i = __ffs(cross) - 1;
-                        cross &= cross - 1;
-                        const int n = n0 + i, gi = off_l + n;
-#pragma unroll
-                        for (int ii = 0; ii < 32; ++ii) {
-                            if (ii != i) continue;
-                            const float du = v[ii];
+                        if (nm & (1u << i)) {
+                            v[i] = 0.f;
+                        } else if (cross & (1u << i)) {  // warp-uniform: column class
+                            const int n = n0 + i, gi = off_l + n;
+                            const float du = v[i];
                             const float ub = Q.ub32[gi];
                             const float u = ub + du;
                             const float bound = __fmaf_ru(av[n], Pa, __fmaf_ru(bv[n], Pb, Q.thr[gi]));
@@ -486,10 +515,10 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                                     atomicOr(&S.cflip[gi >> 5], 1u << (gi & 31));
                                 }
                             }
-                            v[ii] = fmaxf(du + Q.c1[gi], Q.c2[gi]);
+                            v[i] = fmaxf(du + Q.c1[gi], Q.c2[gi]);
                         }
                     }
-                    if (!rv) {
+                    if (!__all_sync(0xffffffffu, rv) && !rv) {
 #pragma unroll
                         for (int i = 0; i < 32; ++i) v[i] = 0.f;
                     }
