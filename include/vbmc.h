@@ -206,6 +206,44 @@ vbmc_status vbmc_get_ties(vbmc_result *res, uint64_t *idx, size_t cap, uint64_t 
 /* Message for the last failing call of this thread. */
 const char *vbmc_last_error(void);
 
+/* ---- For callers that cannot allocate device memory (no counterpart in the
+ * paper). A process embedded in another runtime's memory pool, or one whose
+ * allocator must not be re-entered, cannot call cudaMalloc. This entry point
+ * runs the exhaustive FP64 check of [lo, hi) (the same results as
+ * vbmc_verify_query with VBMC_PREC_FP64) and allocates nothing: all of its
+ * per-query scratch sits in one fixed device array inside the library, and
+ * the results go only into the caller's device buffers below.
+ *   - Limits: at most VBMC_NOALLOC_MAX_NEURONS non-input neurons and
+ *     s * (2k + 1) <= VBMC_NOALLOC_MAX_SR; larger queries get
+ *     VBMC_ERR_UNSUPPORTED.
+ *   - The array (128 KB) stays on every GPU that loads the library until the
+ *     process exits. The first call on a device looks up its address; make
+ *     that first call before capturing any stream into a graph.
+ *   - Every call shares the array: calls whose GPU work overlaps (different
+ *     streams, threads or processes sharing a context) race. Serialise them.
+ *   - The caller's buffers are cleared by each call. The net must come from
+ *     vbmc_net_create (done earlier, where allocation is allowed).
+ * Asynchronous on `stream`; the outputs are valid once the stream reaches the
+ * call's end. */
+#define VBMC_NOALLOC_MAX_NEURONS 4096
+#define VBMC_NOALLOC_MAX_SR 4096
+
+typedef struct {
+    uint64_t *counters;      /* [4]: adversarial count, first witness (UINT64_MAX: none),
+                                tie count, and class D of the unperturbed image in the
+                                low 32 bits with device error flags in the high 32 bits
+                                (nonzero: the pixel list was invalid)                  */
+    uint32_t *flip, *flip_tie, *ss, *ss_tie; /* coverage masks: all four, or all NULL   */
+    uint32_t *bitmap;        /* verdict bits (bit t), or NULL                           */
+    uint64_t bitmap_bits;    /* capacity of `bitmap` in bits                            */
+    uint64_t *ties;          /* tie indices, unordered, or NULL                         */
+    uint32_t ties_cap;
+} vbmc_noalloc_out;
+
+vbmc_status vbmc_verify_range_fp64_noalloc(const vbmc_net *net, const uint8_t *d_image, int32_t s,
+                                           const int32_t *d_pixels, int32_t k, uint64_t lo,
+                                           uint64_t hi, const vbmc_noalloc_out *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

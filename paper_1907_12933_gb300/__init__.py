@@ -59,6 +59,12 @@ class _Summary(C.Structure):
                 ("ms_recheck", C.c_double)]
 
 
+class _NoallocOut(C.Structure):
+    _fields_ = [("counters", C.c_void_p), ("flip", C.c_void_p), ("flip_tie", C.c_void_p),
+                ("ss", C.c_void_p), ("ss_tie", C.c_void_p), ("bitmap", C.c_void_p),
+                ("bitmap_bits", C.c_uint64), ("ties", C.c_void_p), ("ties_cap", C.c_uint32)]
+
+
 _lib = None
 
 
@@ -90,6 +96,8 @@ def lib():
             "vbmc_mask_words": [vp, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)],
             "vbmc_get_verdict_bitmap": [vp, C.POINTER(C.c_uint32), C.c_size_t],
             "vbmc_get_ties": [vp, C.POINTER(C.c_uint64), C.c_size_t, C.POINTER(C.c_uint64)],
+            "vbmc_verify_range_fp64_noalloc": [vp, vp, C.c_int32, vp, C.c_int32, C.c_uint64,
+                                               C.c_uint64, C.POINTER(_NoallocOut), vp],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -279,3 +287,22 @@ def get_ties(res: Result, cap: int = 1 << 16) -> np.ndarray:
     out = np.zeros(max(1, cap), np.uint64)
     _check(lib().vbmc_get_ties(res.h, _ptr(out, C.c_uint64), cap, C.byref(n)))
     return out[:min(n.value, cap)].astype(np.int64)
+
+
+def verify_range_fp64_noalloc(net: Net, d_image, d_pixels, k: int, lo: int, hi: int, counters,
+                              flip=None, flip_tie=None, ss=None, ss_tie=None, bitmap=None,
+                              ties=None, stream: int | None = None) -> None:
+    """vbmc_verify_range_fp64_noalloc: the FP64 check of [lo, hi) for callers that
+    cannot allocate device memory. Every argument is a CUDA tensor the caller owns
+    (counters: 4 x int64; masks and bitmap: int32 words; ties: int64); the library
+    allocates nothing. Enqueued on `stream`; read the outputs after it finishes."""
+    def ptr(t):
+        return None if t is None else t.data_ptr()
+    out = _NoallocOut(ptr(counters), ptr(flip), ptr(flip_tie), ptr(ss), ptr(ss_tie), ptr(bitmap),
+                      0 if bitmap is None else 32 * bitmap.numel(), ptr(ties),
+                      0 if ties is None else ties.numel())
+    st = current_stream() if stream is None else stream
+    _check(lib().vbmc_verify_range_fp64_noalloc(net.h, C.c_void_p(d_image.data_ptr()),
+                                                int(d_pixels.numel()),
+                                                C.c_void_p(d_pixels.data_ptr()), int(k), int(lo),
+                                                int(hi), C.byref(out), C.c_void_p(st)))

@@ -102,6 +102,11 @@ struct vbmc_result {
 
 extern "C" const char* vbmc_last_error(void) { return g_err.c_str(); }
 
+namespace vbmc {
+const NetView* net_view(const vbmc_net* net) { return &net->v; }
+vbmc_status set_error(vbmc_status st, const char* msg) { return fail(st, msg); }
+}  // namespace vbmc
+
 extern "C" vbmc_status vbmc_net_create(const vbmc_mlp_desc* desc, vbmc_net** out) {
     if (!desc || !out) return fail(VBMC_ERR_ARG, "null argument");
     *out = nullptr;

@@ -222,6 +222,14 @@ __global__ void k_pro_finish(NetView net, QueryView* qs, int nq) {
     }
 }
 
+void launch_pro_init(const NetView& net, QueryView* d_qs, int nq, cudaStream_t st) {
+    k_pro_init<<<nq, 256, 0, st>>>(net, d_qs, nq);
+}
+
+void launch_pro_layer(const NetView& net, QueryView* d_qs, int nq, int l, cudaStream_t st) {
+    k_pro_layer<<<dim3((net.dims[l] + 7) / 8, nq), 256, 0, st>>>(net, d_qs, nq, l);
+}
+
 void launch_prologue(const NetView& net, QueryView* d_qs, int nq, int max_sr, cudaStream_t st) {
     k_pro_init<<<nq, 256, 0, st>>>(net, d_qs, nq);
     for (int l = 1; l <= net.L; ++l) {
