@@ -66,6 +66,142 @@ __device__ __forceinline__ float act_delta(int act, float du, float u, float c1,
     return du;
 }
 
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// One dense layer l >= 2 for the tile: du = W_l dh_{l-1} (FP32 FMA, sequential over
+// k), then the sign tests, the delta activation and the per-point error terms.
+// NQA = neuron slots per lane actually used (1 for narrow output layers).
+template <int PPW, int NQ, int NQA>
+__device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView& net,
+                                            const QueryView* __restrict__ qs, int l, int warp,
+                                            int lane) {
+    constexpr int HS = SimtSmem<PPW, NQ>::HS;
+    constexpr int HW = 32 * NQA;  // columns of the weight chunk in use
+    const int L = net.L;
+    const int K = net.dims[l - 1], N = net.dims[l];
+    const float* __restrict__ WT = net.WT[l];  // [K][N]
+    const int nchunks = (K + KC - 1) / KC;
+    float acc[PPW][NQA];
+#pragma unroll
+    for (int r = 0; r < PPW; ++r)
+#pragma unroll
+        for (int qq = 0; qq < NQA; ++qq) acc[r][qq] = 0.f;
+
+    const bool vec = (N % 4) == 0;
+    auto load_chunk = [&](int c, int buf) {
+        if (vec) {
+            for (int e = threadIdx.x; e < KC * (HW / 4); e += THREADS) {
+                const int kk = e / (HW / 4), n = (e % (HW / 4)) * 4, k = c * KC + kk;
+                const bool ok = k < K && n < N;
+                cp_async16(&S.Wsm[buf][kk][n], ok ? (const void*)&WT[(size_t)k * N + n] : (const void*)WT, ok);
+            }
+        } else {
+            for (int e = threadIdx.x; e < KC * HW; e += THREADS) {
+                const int kk = e / HW, n = e % HW, k = c * KC + kk;
+                const bool ok = k < K && n < N;
+                cp_async4(&S.Wsm[buf][kk][n], ok ? (const void*)&WT[(size_t)k * N + n] : (const void*)WT, ok);
+            }
+        }
+        cp_async_commit();
+    };
+    __syncthreads();  // previous users of Wsm are done
+    load_chunk(0, 0);
+    for (int c = 0; c < nchunks; ++c) {
+        const int buf = c & 1;
+        cp_async_wait0();
+        __syncthreads();  // chunk c visible to all; chunk c-1's buffer free
+        if (c + 1 < nchunks) load_chunk(c + 1, buf ^ 1);
+#pragma unroll
+        for (int kk = 0; kk < KC; kk += 4) {
+            float4 a4[PPW];
+#pragma unroll
+            for (int r = 0; r < PPW; ++r)
+                a4[r] = *reinterpret_cast<const float4*>(&S.A[warp * PPW + r][c * KC + kk]);
+#pragma unroll
+            for (int k4 = 0; k4 < 4; ++k4) {
+                float wv[NQA];
+#pragma unroll
+                for (int qq = 0; qq < NQA; ++qq) wv[qq] = S.Wsm[buf][kk + k4][lane + 32 * qq];
+#pragma unroll
+                for (int r = 0; r < PPW; ++r) {
+                    const float a = k4 == 0 ? a4[r].x : k4 == 1 ? a4[r].y : k4 == 2 ? a4[r].z : a4[r].w;
+#pragma unroll
+                    for (int qq = 0; qq < NQA; ++qq) acc[r][qq] = fmaf(a, wv[qq], acc[r][qq]);
+                }
+            }
+        }
+    }
+
+    // epilogue of layer l
+    const float* rn = net.rownorm[l];
+    const int off = net.noff[l];
+    const float lf = net.lamfrob[l], gl = net.gam[l];
+#pragma unroll
+    for (int r = 0; r < PPW; ++r) {
+        const int m = warp * PPW + r;
+        if (!S.valid[m]) continue;
+        const QueryView& Q = qs[S.q[m]];
+        const float X = __fmaf_ru(gl, S.N[m], S.E[m]);
+        float nsum = 0.f, usum = 0.f;
+#pragma unroll
+        for (int qq = 0; qq < NQ; ++qq) {
+            const int n = lane + 32 * qq;
+            if (qq < NQA && n < N) {
+                const int gi = off + n;
+                const float du = acc[r][qq < NQA ? qq : 0];
+                const float ub = Q.ub32[gi];
+                const float u = ub + du;
+                const float bound = __fmaf_ru(rn[n], X, Q.thr[gi]);
+                if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound)) {
+                    S.unc[m] = 1;
+                } else if ((u >= 0.f) != (ub >= 0.f)) {
+                    int idx = atomicAdd(&S.fcnt[m][l], 1);
+                    if (idx < FCAP) S.flist[m][l][idx] = (short)n;
+                    if (Q.flip) set_bit_once(Q.flip, gi);
+                }
+                if (l < L) {
+                    const float dh = act_delta(net.act, du, u, Q.c1[gi], Q.c2[gi]);
+                    nsum = fmaf(dh, dh, nsum);
+                    usum = fmaf(u, u, usum);
+                    S.A[m][n] = dh;
+                } else {
+                    S.A[m][n] = u;
+                }
+            } else if (l < L && n < HS) {
+                S.A[m][n] = 0.f;
+            }
+        }
+        nsum = warp_sum(nsum);
+        usum = warp_sum(usum);
+        if (lane == 0) {
+            if (l < L) {
+                const float Nl = norm_up(nsum);
+                // lambda (||W_l||_F gamma N_{l-1} + sigma_l E_{l-1}) + kvec_l
+                float El = __fmaf_ru(__fmul_ru(lf, gl), S.N[m], Q.kvec[l]);
+                El = __fmaf_ru(net.lamsig[l], S.E[m], El);
+                El = __fmaf_ru(0x1p-24f, Nl, El);
+                if (net.act == ACT_SIGMOID) El = __fmaf_ru(0x1p-26f, norm_up(usum), El);
+                S.N[m] = Nl;
+                S.E[m] = El;
+            } else {
+                S.N[m] = __fmul_ru(gl, S.N[m]);  // gamma N_{L-1}: dot-product rounding
+            }
+        }
+    }
+    __syncwarp();
+}
+
 template <int PPW, int NQ>
 __global__ void __launch_bounds__(THREADS, 1)
 k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
@@ -176,106 +312,8 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
 
         // ---- S4: dense layers on the deltas
         for (int l = 2; l <= L; ++l) {
-            const int K = net.dims[l - 1], N = net.dims[l];
-            const float* __restrict__ W = net.W[l];
-            const int nchunks = (K + KC - 1) / KC;
-            float acc[PPW][NQ];
-#pragma unroll
-            for (int r = 0; r < PPW; ++r)
-#pragma unroll
-                for (int qq = 0; qq < NQ; ++qq) acc[r][qq] = 0.f;
-
-            auto load_chunk = [&](int c, int buf) {
-                for (int e = threadIdx.x; e < KC * HS; e += THREADS) {
-                    const int n = e / KC, kk = e % KC, k = c * KC + kk;
-                    S.Wsm[buf][kk][n] = (n < N && k < K) ? __ldg(&W[(size_t)n * K + k]) : 0.f;
-                }
-            };
-            __syncthreads();  // previous users of Wsm are done
-            load_chunk(0, 0);
-            __syncthreads();
-            for (int c = 0; c < nchunks; ++c) {
-                const int buf = c & 1;
-                if (c + 1 < nchunks) load_chunk(c + 1, buf ^ 1);
-#pragma unroll
-                for (int kk = 0; kk < KC; kk += 4) {
-                    float4 a4[PPW];
-#pragma unroll
-                    for (int r = 0; r < PPW; ++r)
-                        a4[r] = *reinterpret_cast<const float4*>(&S.A[warp * PPW + r][c * KC + kk]);
-#pragma unroll
-                    for (int k4 = 0; k4 < 4; ++k4) {
-                        float wv[NQ];
-#pragma unroll
-                        for (int qq = 0; qq < NQ; ++qq) wv[qq] = S.Wsm[buf][kk + k4][lane + 32 * qq];
-#pragma unroll
-                        for (int r = 0; r < PPW; ++r) {
-                            const float a = k4 == 0 ? a4[r].x : k4 == 1 ? a4[r].y : k4 == 2 ? a4[r].z : a4[r].w;
-#pragma unroll
-                            for (int qq = 0; qq < NQ; ++qq) acc[r][qq] = fmaf(a, wv[qq], acc[r][qq]);
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-
-            // epilogue of layer l
-            const float* rn = net.rownorm[l];
-            const int off = net.noff[l];
-            const float lf = net.lamfrob[l], gl = net.gam[l];
-#pragma unroll
-            for (int r = 0; r < PPW; ++r) {
-                const int m = warp * PPW + r;
-                if (!S.valid[m]) continue;
-                const QueryView& Q = qs[S.q[m]];
-                const float X = __fmaf_ru(gl, S.N[m], S.E[m]);
-                float nsum = 0.f, usum = 0.f;
-#pragma unroll
-                for (int qq = 0; qq < NQ; ++qq) {
-                    const int n = lane + 32 * qq;
-                    if (n < N) {
-                        const int gi = off + n;
-                        const float du = acc[r][qq];
-                        const float ub = Q.ub32[gi];
-                        const float u = ub + du;
-                        const float bound = __fmaf_ru(rn[n], X, Q.thr[gi]);
-                        if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound)) {
-                            S.unc[m] = 1;
-                        } else if ((u >= 0.f) != (ub >= 0.f)) {
-                            int idx = atomicAdd(&S.fcnt[m][l], 1);
-                            if (idx < FCAP) S.flist[m][l][idx] = (short)n;
-                            if (Q.flip) set_bit_once(Q.flip, gi);
-                        }
-                        if (l < L) {
-                            const float dh = act_delta(net.act, du, u, Q.c1[gi], Q.c2[gi]);
-                            nsum = fmaf(dh, dh, nsum);
-                            usum = fmaf(u, u, usum);
-                            S.A[m][n] = dh;
-                        } else {
-                            S.A[m][n] = u;
-                        }
-                    } else if (l < L && n < HS) {
-                        S.A[m][n] = 0.f;
-                    }
-                }
-                nsum = warp_sum(nsum);
-                usum = warp_sum(usum);
-                if (lane == 0) {
-                    if (l < L) {
-                        const float Nl = norm_up(nsum);
-                        // lambda (||W_l||_F gamma N_{l-1} + sigma_l E_{l-1}) + kvec_l
-                        float El = __fmaf_ru(__fmul_ru(lf, gl), S.N[m], Q.kvec[l]);
-                        El = __fmaf_ru(net.lamsig[l], S.E[m], El);
-                        El = __fmaf_ru(0x1p-24f, Nl, El);
-                        if (net.act == ACT_SIGMOID) El = __fmaf_ru(0x1p-26f, norm_up(usum), El);
-                        S.N[m] = Nl;
-                        S.E[m] = El;
-                    } else {
-                        S.N[m] = __fmul_ru(gl, S.N[m]);  // gamma N_{L-1}: dot-product rounding
-                    }
-                }
-            }
-            __syncwarp();
+            if (net.dims[l] > 32) dense_layer<PPW, NQ, NQ>(S, net, qs, l, warp, lane);
+            else dense_layer<PPW, NQ, 1>(S, net, qs, l, warp, lane);
         }
 
         // ---- S5: verdict (layer L values are in A[m][0..H_L))
