@@ -114,7 +114,8 @@ typedef struct {
     int32_t precision;  /* vbmc_precision                                  */
     int32_t coverage;   /* nonzero: compute sign-change and SS masks       */
     int32_t bitmap;     /* nonzero: record the per-point verdict bitmap    */
-    int32_t reserved;
+    int32_t graph;      /* batch: nonzero captures the passes into one CUDA
+                         * graph and launches it                          */
 } vbmc_options;
 
 /* Capacities fixed when a result handle is created. */
@@ -140,6 +141,8 @@ typedef struct {
     double ms_prologue;        /* of which: FP64 base pass and tables     */
     double ms_screen;          /* of which: first pass over every point   */
     double ms_recheck;         /* of which: all later passes              */
+    double ms_to_verdict;      /* device time from the query's prologue to
+                                * its final result (batch: per query)     */
 } vbmc_summary;
 
 typedef struct vbmc_net vbmc_net;
@@ -153,6 +156,13 @@ vbmc_status vbmc_net_free(vbmc_net *net);
 
 /* Allocate a reusable result workspace for queries on `net` within `caps`. */
 vbmc_status vbmc_result_create(const vbmc_net *net, const vbmc_caps *caps, vbmc_result **out);
+
+/* Allocate nq result workspaces that vbmc_verify_batch can serve with one
+ * launch per pass: out[i] must then be passed as results[i]. caps.queue_cap
+ * sizes the recheck queues the batch shares. Each handle is freed with
+ * vbmc_result_free. */
+vbmc_status vbmc_result_create_batch(const vbmc_net *net, const vbmc_caps *caps, int32_t nq,
+                                     vbmc_result **out);
 vbmc_status vbmc_result_free(vbmc_result *res);
 
 /* checkNN over the box (Sec. III-C): enumerate [lo, hi), decide the safety
@@ -169,8 +179,13 @@ vbmc_status vbmc_verify_query_device(vbmc_net *net, const uint8_t *d_image, int3
                                      const int32_t *d_pixels, int32_t k, uint64_t lo, uint64_t hi,
                                      const vbmc_options *opt, vbmc_result *res, void *stream);
 
-/* Many queries against one net in one pass: every query's points go to one
- * persistent launch per pass. results[i] receives query i. */
+/* Many queries against one net: with results from one vbmc_result_create_batch
+ * call (in order), every query's points go to one persistent launch per pass
+ * (tiles never span queries; rechecked points of all queries share the
+ * queues), optionally captured as one CUDA graph (opt->graph). Other result
+ * handles are served one query after another. results[i] receives query i;
+ * each summary's ms_to_verdict is that query's own time to a final result.
+ * Blocks until all results are final. */
 vbmc_status vbmc_verify_batch(vbmc_net *net, const vbmc_query *queries, int32_t nq,
                               const vbmc_options *opt, vbmc_result *const *results, void *stream);
 

@@ -42,7 +42,7 @@ class _Query(C.Structure):
 
 class _Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("coverage", C.c_int32), ("bitmap", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("graph", C.c_int32)]
 
 
 class _Caps(C.Structure):
@@ -56,7 +56,7 @@ class _Summary(C.Structure):
                 ("first_witness", C.c_uint64), ("n_ties", C.c_uint64),
                 ("n_recheck", C.c_uint64 * 4), ("ms_device", C.c_double),
                 ("ms_prologue", C.c_double), ("ms_screen", C.c_double),
-                ("ms_recheck", C.c_double)]
+                ("ms_recheck", C.c_double), ("ms_to_verdict", C.c_double)]
 
 
 class _NoallocOut(C.Structure):
@@ -82,6 +82,7 @@ def lib():
             "vbmc_net_free": [vp],
             "vbmc_result_create": [vp, C.POINTER(_Caps), C.POINTER(vp)],
             "vbmc_result_free": [vp],
+            "vbmc_result_create_batch": [vp, C.POINTER(_Caps), C.c_int32, C.POINTER(vp)],
             "vbmc_verify_query": [vp, C.POINTER(_Query), C.POINTER(_Options), vp, vp],
             "vbmc_verify_query_device": [vp, vp, C.c_int32, vp, C.c_int32, C.c_uint64,
                                          C.c_uint64, C.POINTER(_Options), vp, vp],
@@ -187,9 +188,24 @@ class Result:
             pass
 
 
-def _options(precision, coverage, bitmap):
+def result_create_batch(net: Net, nq: int, max_points: int = 0, max_s: int = MAX_S,
+                        max_k: int = 32, ties_cap: int = 1 << 12, queue_cap: int = 1 << 24) -> list:
+    """vbmc_result_create_batch: nq workspaces that vbmc_verify_batch serves together."""
+    caps = _Caps(max_points, max_s, max_k, ties_cap, queue_cap)
+    hs = (C.c_void_p * nq)()
+    _check(lib().vbmc_result_create_batch(net.h, C.byref(caps), nq, hs))
+    out = []
+    for i in range(nq):
+        r = Result.__new__(Result)
+        r.h = C.c_void_p(hs[i])
+        r.net = net
+        out.append(r)
+    return out
+
+
+def _options(precision, coverage, bitmap, graph=False):
     p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    return _Options(p, int(bool(coverage)), int(bool(bitmap)), 0)
+    return _Options(p, int(bool(coverage)), int(bool(bitmap)), int(bool(graph)))
 
 
 def _summary_dict(s: _Summary) -> dict:
@@ -197,7 +213,8 @@ def _summary_dict(s: _Summary) -> dict:
             "n_points": s.n_points, "n_adversarial": s.n_adversarial,
             "first_witness": None if s.first_witness == NO_WITNESS else int(s.first_witness),
             "n_ties": s.n_ties, "n_recheck": list(s.n_recheck), "ms_device": s.ms_device,
-            "ms_prologue": s.ms_prologue, "ms_screen": s.ms_screen, "ms_recheck": s.ms_recheck}
+            "ms_prologue": s.ms_prologue, "ms_screen": s.ms_screen, "ms_recheck": s.ms_recheck,
+            "ms_to_verdict": s.ms_to_verdict}
 
 
 def verify_query(net: Net, res: Result, image, pixels, k: int, lo: int = 0, hi: int = 0,
@@ -227,7 +244,7 @@ def verify_query_device(net: Net, res: Result, d_image, d_pixels, k: int, lo: in
 
 
 def verify_batch(net: Net, results: list, queries: list, precision="fp32",
-                 coverage: bool = True, bitmap: bool = False,
+                 coverage: bool = True, bitmap: bool = False, graph: bool = False,
                  stream: int | None = None) -> list:
     """vbmc_verify_batch: queries are dicts with image, pixels, k (and optional lo, hi)."""
     keep = []
@@ -239,7 +256,7 @@ def verify_batch(net: Net, results: list, queries: list, precision="fp32",
         qs[i] = _Query(_ptr(img, C.c_uint8), len(pix), _ptr(pix, C.c_int32), int(qd["k"]),
                        int(qd.get("lo", 0)), int(qd.get("hi", 0)))
     hs = (C.c_void_p * len(results))(*[r.h for r in results])
-    opt = _options(precision, coverage, bitmap)
+    opt = _options(precision, coverage, bitmap, graph)
     st = current_stream() if stream is None else stream
     _check(lib().vbmc_verify_batch(net.h, qs, len(queries), C.byref(opt), hs, C.c_void_p(st)))
     return [result_summary(r) for r in results]

@@ -72,7 +72,31 @@ struct vbmc_net {
     std::vector<std::vector<float>> hW, hb;  // host copies for tensor-core set-up
 };
 
+// Shared state of results created together by vbmc_result_create_batch: the
+// query views and counters of all members back to back (so one launch can
+// cover every query), one staging buffer for the queries' images and pixel
+// lists, and the recheck queues the batch passes share.
+struct BatchArena {
+    int nq = 0;
+    int refs = 0;
+    QueryView* d_qs = nullptr;
+    Counters* d_cnt = nullptr;
+    Counters* h_cnt = nullptr;  // pinned
+    unsigned long long* d_tp = nullptr;
+    uint8_t* d_stage = nullptr;
+    size_t stage_stride = 0;
+    unsigned long long* d_qcount = nullptr;
+    QEntry* d_queue[4] = {nullptr, nullptr, nullptr, nullptr};
+    uint64_t queue_cap = 0;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t gstream = nullptr;  // graph capture needs a capturable (non-legacy) stream
+    cudaEvent_t gev = nullptr;
+    std::vector<void*> owned;
+};
+
 struct vbmc_result {
+    BatchArena* arena = nullptr;
+    int slot = 0;
     const vbmc_net* net = nullptr;
     vbmc_caps caps{};
     std::vector<void*> owned;
@@ -98,6 +122,7 @@ struct vbmc_result {
     uint64_t lo = 0, hi = 0, n_space = 0;
     vbmc_options opt{};
     vbmc_summary sum{};
+    vbmc_status last_status = VBMC_OK;
 };
 
 extern "C" const char* vbmc_last_error(void) { return g_err.c_str(); }
@@ -248,8 +273,10 @@ extern "C" vbmc_status vbmc_mask_words(const vbmc_net* net, size_t* fw, size_t* 
     return VBMC_OK;
 }
 
-extern "C" vbmc_status vbmc_result_create(const vbmc_net* net, const vbmc_caps* caps,
-                                          vbmc_result** out) {
+namespace {
+
+vbmc_status create_result(const vbmc_net* net, const vbmc_caps* caps, BatchArena* arena, int slot,
+                          vbmc_result** out) {
     if (!net || !caps || !out) return fail(VBMC_ERR_ARG, "null argument");
     *out = nullptr;
     if (caps->max_s < 0 || caps->max_s > kMaxS) return fail(VBMC_ERR_ARG, "max_s out of range");
@@ -257,6 +284,9 @@ extern "C" vbmc_status vbmc_result_create(const vbmc_net* net, const vbmc_caps* 
     vbmc_result* r = new vbmc_result();
     r->net = net;
     r->caps = *caps;
+    r->arena = arena;
+    r->slot = slot;
+    if (arena) arena->refs++;  // released by vbmc_result_free, also on the failure path
     const NetView& v = net->v;
     const int S = std::max(1, caps->max_s), RM = 2 * caps->max_k + 1;
     const size_t T = v.total;
@@ -267,8 +297,13 @@ extern "C" vbmc_status vbmc_result_create(const vbmc_net* net, const vbmc_caps* 
     auto A = [&](auto** p, size_t n) {
         if (e == cudaSuccess) e = dalloc(p, n, r->owned);
     };
-    A(&r->d_q, 1);
-    A(&r->d_cnt, 1);
+    if (arena) {
+        r->d_q = arena->d_qs + slot;
+        r->d_cnt = arena->d_cnt + slot;
+    } else {
+        A(&r->d_q, 1);
+        A(&r->d_cnt, 1);
+    }
     A(&r->d_image, (size_t)v.dims[0]);
     A(&r->d_pix_in, (size_t)S);
     A(&q.pix, (size_t)S);
@@ -294,7 +329,10 @@ extern "C" vbmc_status vbmc_result_create(const vbmc_net* net, const vbmc_caps* 
     A(&r->d_qcount, 4);
     A(&r->d_margin, 1);
     if (caps->max_points) A(&q.bitmap, (size_t)((caps->max_points + 31) / 32));
-    const uint64_t qc = std::max<uint64_t>(1, caps->queue_cap);
+    // members of a batch keep small queues of their own (the batch shares the arena's)
+    uint64_t qc = std::max<uint64_t>(1, caps->queue_cap);
+    if (arena) qc = std::min<uint64_t>(qc, 1u << 16);
+    r->caps.queue_cap = qc;
     for (int i = 0; i < 4; ++i) A(&r->d_queue[i], (size_t)qc);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&r->h_cnt, sizeof(Counters));
     if (e == cudaSuccess) e = cudaEventCreate(&r->ev0);
@@ -312,10 +350,67 @@ extern "C" vbmc_status vbmc_result_create(const vbmc_net* net, const vbmc_caps* 
     return VBMC_OK;
 }
 
+void arena_release(BatchArena* a) {
+    if (!a || --a->refs > 0) return;
+    for (void* p : a->owned) cudaFree(p);
+    if (a->h_cnt) cudaFreeHost(a->h_cnt);
+    for (cudaEvent_t ev : a->ev)
+        if (ev) cudaEventDestroy(ev);
+    if (a->gev) cudaEventDestroy(a->gev);
+    if (a->gstream) cudaStreamDestroy(a->gstream);
+    delete a;
+}
+
+}  // namespace
+
+extern "C" vbmc_status vbmc_result_create(const vbmc_net* net, const vbmc_caps* caps,
+                                          vbmc_result** out) {
+    return create_result(net, caps, nullptr, 0, out);
+}
+
+extern "C" vbmc_status vbmc_result_create_batch(const vbmc_net* net, const vbmc_caps* caps,
+                                                int32_t nq, vbmc_result** out) {
+    if (!net || !caps || !out || nq <= 0) return fail(VBMC_ERR_ARG, "null argument or nq <= 0");
+    BatchArena* ar = new BatchArena();
+    ar->nq = nq;
+    ar->refs = 1;  // held by this call until every member exists
+    cudaError_t e = cudaSuccess;
+    auto A = [&](auto** p, size_t n) {
+        if (e == cudaSuccess) e = dalloc(p, n, ar->owned);
+    };
+    ar->stage_stride = ((size_t)net->v.dims[0] + sizeof(int32_t) * kMaxS + 15) & ~size_t(15);
+    A(&ar->d_qs, (size_t)nq);
+    A(&ar->d_cnt, (size_t)nq);
+    A(&ar->d_tp, (size_t)nq + 1);
+    A(&ar->d_stage, ar->stage_stride * (size_t)nq);
+    A(&ar->d_qcount, 4);
+    ar->queue_cap = std::max<uint64_t>(1, caps->queue_cap);
+    for (int i = 0; i < 4; ++i) A(&ar->d_queue[i], (size_t)ar->queue_cap);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&ar->h_cnt, sizeof(Counters) * (size_t)nq);
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&ar->ev[i]);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ar->gstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ar->gev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        arena_release(ar);
+        return fail(VBMC_ERR_OOM, std::string("result_create_batch: ") + cudaGetErrorString(e));
+    }
+    for (int i = 0; i < nq; ++i) {
+        vbmc_status st = create_result(net, caps, ar, i, &out[i]);
+        if (st != VBMC_OK) {
+            for (int j = 0; j < i; ++j) vbmc_result_free(out[j]);
+            arena_release(ar);
+            return st;
+        }
+    }
+    arena_release(ar);  // the members hold it now
+    return VBMC_OK;
+}
+
 extern "C" vbmc_status vbmc_result_free(vbmc_result* r) {
     if (!r) return VBMC_OK;
     if (r->pending && r->last_stream) cudaStreamSynchronize(r->last_stream);
     for (void* p : r->owned) cudaFree(p);
+    arena_release(r->arena);
     if (r->h_cnt) cudaFreeHost(r->h_cnt);
     if (r->ev0) cudaEventDestroy(r->ev0);
     if (r->ev1) cudaEventDestroy(r->ev1);
@@ -344,16 +439,95 @@ vbmc_status check_query_shape(const vbmc_result* r, int s, int k, uint64_t lo, u
     return VBMC_OK;
 }
 
-// Enqueue the full pipeline for one query whose image/pixels are on the device.
-vbmc_status enqueue(vbmc_net* net, vbmc_result* r, const uint8_t* d_image, const int* d_pix, int s,
-                    int k, uint64_t lo, uint64_t hi, uint64_t n, const vbmc_options& opt,
-                    cudaStream_t st) {
+// Tiles of the first pass for each query (sets QueryView::ntiles) and their
+// prefix; 0 tiles for the FP64 path (one block per point there).
+std::vector<unsigned long long> tile_prefix(const NetView& v, int precision, QueryView* hq, int nq) {
+    const int MT = precision == VBMC_PREC_FP64 ? 0
+                   : precision == VBMC_PREC_FP32 ? simt_tile_points(v)
+                                                 : tc_tile_points();
+    std::vector<unsigned long long> tp((size_t)nq + 1, 0);
+    for (int i = 0; i < nq; ++i) {
+        const unsigned long long base = hq[i].lo & ~31ull;
+        const unsigned long long t = (MT && hq[i].hi > hq[i].lo) ? (hq[i].hi - base + MT - 1) / MT : 0;
+        hq[i].ntiles = t;
+        tp[i + 1] = tp[i] + t;
+    }
+    return tp;
+}
+
+// Every pass for nq queries whose views (and tile prefix) are already on the
+// device. ev: start, after the prologue, after the first pass, end.
+vbmc_status enqueue_passes(vbmc_net* net, QueryView* d_qs, const QueryView* hq, int nq,
+                           const unsigned long long* d_tp, unsigned long long ntiles,
+                           unsigned long long* d_qcount, QEntry* const* d_queue,
+                           unsigned long long cap, const cudaEvent_t* ev, const vbmc_options& opt,
+                           cudaStream_t st, bool capturing = false) {
     const NetView& v = net->v;
+    // inside a stream capture an event record must be an explicit graph node
+    const unsigned evflag = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    auto record = [&](cudaEvent_t e) { return cudaEventRecordWithFlags(e, st, evflag); };
+    int max_sr = 0;
+    bool any = false;
+    for (int i = 0; i < nq; ++i) {
+        max_sr = std::max(max_sr, hq[i].s * hq[i].R);
+        any = any || hq[i].hi > hq[i].lo;
+    }
+    VB_CUDA(cudaMemsetAsync(d_qcount, 0, sizeof(unsigned long long) * 4, st));
+    VB_CUDA(record(ev[0]));
+    launch_prologue(v, d_qs, nq, max_sr, st);
+    VB_CUDA(record(ev[1]));
+    // queue levels: 0 tensor split pass, 1 FP32 pass, 2 double-float pass, 3 FP64 pass
+    Queue qsplit{d_queue[0], d_qcount + 0, cap};
+    Queue q32{d_queue[1], d_qcount + 1, cap};
+    Queue qdf{d_queue[2], d_qcount + 2, cap};
+    Queue q64{d_queue[3], d_qcount + 3, cap};
+    if (any && opt.precision == VBMC_PREC_FP64) {
+        for (int i = 0; i < nq; ++i)
+            if (hq[i].hi > hq[i].lo)
+                launch_fp64(v, d_qs + i, 1, nullptr, nullptr, 0, hq[i].lo, hq[i].hi, net->n_sm, st);
+        VB_CUDA(record(ev[2]));
+    } else if (any) {
+        if (opt.precision == VBMC_PREC_FP32) {
+            if (simt_tile_points(v) == 0) return fail(VBMC_ERR_UNSUPPORTED, "layer width above 1024");
+            launch_screen_simt(v, d_qs, nq, d_tp, ntiles, nullptr, nullptr, 0, qdf, 2, net->n_sm, st);
+            VB_CUDA(record(ev[2]));
+        } else {
+            if (!tc_supported(v, opt.precision))
+                return fail(VBMC_ERR_UNSUPPORTED, "tensor-core screen does not support this net/precision");
+            vbmc_status sst = tc_build(net->tc, v, net->hW, net->hb, opt.precision);
+            if (sst != VBMC_OK) return fail(sst, "tensor-core set-up failed");
+            tc_launch_query_setup(net->tc, v, d_qs, nq, opt.precision, st);
+            // one query: screen -> split tensor pass -> FP32; many: screen -> FP32 directly
+            sst = tc_launch_screen(net->tc, v, d_qs, nq, d_tp, ntiles, opt.precision,
+                                   nq == 1 ? qsplit : q32, nq == 1 ? 0 : 1, net->n_sm, st);
+            if (sst != VBMC_OK) return fail(sst, "tensor-core screen launch failed");
+            VB_CUDA(record(ev[2]));
+            if (nq == 1) {
+                sst = tc_launch_gather(net->tc, v, d_qs, d_queue[0], d_qcount + 0, cap, opt.precision,
+                                       q32, net->n_sm, st);
+                if (sst != VBMC_OK) return fail(sst, "tensor-core split pass launch failed");
+            }
+            launch_screen_simt(v, d_qs, nq, nullptr, 0, d_queue[1], d_qcount + 1, cap, qdf, 2,
+                               net->n_sm, st);
+        }
+        launch_df(v, d_qs, d_queue[2], d_qcount + 2, cap, q64, 3, net->n_sm, st);
+        launch_fp64(v, d_qs, nq, d_queue[3], d_qcount + 3, cap, 0, 0, net->n_sm, st);
+    } else {
+        VB_CUDA(record(ev[2]));
+    }
+    launch_stamp_final(d_qs, nq, st);
+    VB_CUDA(cudaGetLastError());
+    VB_CUDA(record(ev[3]));
+    return VBMC_OK;
+}
+
+QueryView make_view(const vbmc_result* r, const uint8_t* d_image, const int* d_pix, int s, int k,
+                    uint64_t lo, uint64_t hi, uint64_t n, const vbmc_options& opt, int qid) {
     QueryView q = r->hq;
     q.s = s;
     q.k = k;
     q.R = 2 * k + 1;
-    q.qid = 0;
+    q.qid = qid;
     q.n_points = n;
     q.lo = lo;
     q.hi = hi;
@@ -361,63 +535,21 @@ vbmc_status enqueue(vbmc_net* net, vbmc_result* r, const uint8_t* d_image, const
     q.pix_in = d_pix;
     if (!opt.coverage) q.flip = q.flip_tie = q.ss = q.ss_tie = nullptr;
     if (!opt.bitmap) q.bitmap = nullptr;
+    return q;
+}
+
+// Enqueue the full pipeline for one query whose image/pixels are on the device.
+vbmc_status enqueue(vbmc_net* net, vbmc_result* r, const uint8_t* d_image, const int* d_pix, int s,
+                    int k, uint64_t lo, uint64_t hi, uint64_t n, const vbmc_options& opt,
+                    cudaStream_t st) {
+    QueryView q = make_view(r, d_image, d_pix, s, k, lo, hi, n, opt, 0);
+    std::vector<unsigned long long> tp = tile_prefix(net->v, opt.precision, &q, 1);
     VB_CUDA(cudaMemcpyAsync(r->d_q, &q, sizeof(QueryView), cudaMemcpyHostToDevice, st));
-    if (opt.coverage) {
-        VB_CUDA(cudaMemsetAsync(q.flip, 0, sizeof(uint32_t) * v.flip_words, st));
-        VB_CUDA(cudaMemsetAsync(q.flip_tie, 0, sizeof(uint32_t) * v.flip_words, st));
-        VB_CUDA(cudaMemsetAsync(q.ss, 0, sizeof(uint32_t) * v.ss_words, st));
-        VB_CUDA(cudaMemsetAsync(q.ss_tie, 0, sizeof(uint32_t) * v.ss_words, st));
-    }
-    if (opt.bitmap && hi > 0)
-        VB_CUDA(cudaMemsetAsync(q.bitmap, 0, sizeof(uint32_t) * ((hi + 31) / 32), st));
-    VB_CUDA(cudaMemsetAsync(r->d_qcount, 0, sizeof(unsigned long long) * 4, st));
-    VB_CUDA(cudaEventRecord(r->ev0, st));
-    launch_prologue(v, r->d_q, 1, s * q.R, st);
-    VB_CUDA(cudaEventRecord(r->ev_pro, st));
-    const unsigned long long cap = std::max<uint64_t>(1, r->caps.queue_cap);
-    // queue levels: 0 tensor split pass, 1 FP32 pass, 2 double-float pass, 3 FP64 pass
-    Queue qsplit{r->d_queue[0], r->d_qcount + 0, cap};
-    Queue q32{r->d_queue[1], r->d_qcount + 1, cap};
-    Queue qdf{r->d_queue[2], r->d_qcount + 2, cap};
-    Queue q64{r->d_queue[3], r->d_qcount + 3, cap};
-    if (hi > lo) {
-        if (opt.precision == VBMC_PREC_FP64) {
-            launch_fp64(v, r->d_q, 1, nullptr, nullptr, 0, lo, hi, net->n_sm, st);
-            VB_CUDA(cudaEventRecord(r->ev_scr, st));
-        } else {
-            if (opt.precision == VBMC_PREC_FP32) {
-                const int MT = simt_tile_points(v);
-                if (MT == 0) return fail(VBMC_ERR_UNSUPPORTED, "layer width above 1024");
-                const unsigned long long base = lo & ~31ull;
-                const unsigned long long tiles = (hi - base + MT - 1) / MT;
-                unsigned long long tp[2] = {0, tiles};
-                VB_CUDA(cudaMemcpyAsync(r->d_tp, tp, sizeof(tp), cudaMemcpyHostToDevice, st));
-                launch_screen_simt(v, r->d_q, 1, r->d_tp, tiles, nullptr, nullptr, 0, qdf, 2,
-                                   net->n_sm, st);
-                VB_CUDA(cudaEventRecord(r->ev_scr, st));
-            } else {
-                if (!tc_supported(v, opt.precision))
-                    return fail(VBMC_ERR_UNSUPPORTED,
-                                "tensor-core screen does not support this net/precision");
-                vbmc_status sst = tc_build(net->tc, v, net->hW, net->hb, opt.precision);
-                if (sst != VBMC_OK) return fail(sst, "tensor-core set-up failed");
-                tc_launch_query_setup(net->tc, v, r->d_q, opt.precision, st);
-                sst = tc_launch_screen(net->tc, v, r->d_q, lo, hi, opt.precision, qsplit, net->n_sm, st);
-                if (sst != VBMC_OK) return fail(sst, "tensor-core screen launch failed");
-                VB_CUDA(cudaEventRecord(r->ev_scr, st));
-                sst = tc_launch_gather(net->tc, v, r->d_q, r->d_queue[0], r->d_qcount + 0, cap,
-                                       opt.precision, q32, net->n_sm, st);
-                if (sst != VBMC_OK) return fail(sst, "tensor-core split pass launch failed");
-                launch_screen_simt(v, r->d_q, 1, nullptr, 0, r->d_queue[1], r->d_qcount + 1, cap,
-                                   qdf, 2, net->n_sm, st);
-            }
-            launch_df(v, r->d_q, r->d_queue[2], r->d_qcount + 2, cap, q64, 3, net->n_sm, st);
-            launch_fp64(v, r->d_q, 1, r->d_queue[3], r->d_qcount + 3, cap, 0, 0, net->n_sm, st);
-        }
-    }
-    if (hi <= lo) VB_CUDA(cudaEventRecord(r->ev_scr, st));
-    VB_CUDA(cudaGetLastError());
-    VB_CUDA(cudaEventRecord(r->ev1, st));
+    VB_CUDA(cudaMemcpyAsync(r->d_tp, tp.data(), sizeof(unsigned long long) * 2, cudaMemcpyHostToDevice, st));
+    const cudaEvent_t ev[4] = {r->ev0, r->ev_pro, r->ev_scr, r->ev1};
+    vbmc_status sst = enqueue_passes(net, r->d_q, &q, 1, r->d_tp, tp[1], r->d_qcount, r->d_queue,
+                                     std::max<uint64_t>(1, r->caps.queue_cap), ev, opt, st);
+    if (sst != VBMC_OK) return sst;
     VB_CUDA(cudaMemcpyAsync(r->h_cnt, r->d_cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     r->last_stream = st;
     r->pending = true;
@@ -431,38 +563,47 @@ vbmc_status enqueue(vbmc_net* net, vbmc_result* r, const uint8_t* d_image, const
     return VBMC_OK;
 }
 
+void fill_summary(vbmc_result* r, const Counters& c, float ms, float ms_p, float ms_s) {
+    vbmc_summary& s = r->sum;
+    std::memset(&s, 0, sizeof(s));
+    s.D = c.D;
+    s.base_margin = c.base_margin;
+    s.n_points = r->hi - r->lo;
+    s.n_adversarial = c.n_adv;
+    s.first_witness = c.first;
+    s.n_ties = c.n_ties;
+    for (int i = 0; i < 4; ++i) s.n_recheck[i] = c.n_q[i];
+    s.ms_device = ms;
+    s.ms_prologue = ms_p;
+    s.ms_screen = ms_s;
+    s.ms_recheck = ms - ms_p - ms_s;
+    s.ms_to_verdict = c.t_final > c.t0 ? (double)(c.t_final - c.t0) * 1e-6 : 0.0;
+    if (r->lo != 0 || r->hi != r->n_space) s.verdict = VBMC_PARTIAL;
+    else if (c.n_adv) s.verdict = VBMC_UNSAFE;
+    else if (c.n_ties) s.verdict = VBMC_TIES_ONLY;
+    else s.verdict = VBMC_SAFE;
+}
+
+vbmc_status counters_status(const Counters& c) {
+    if (c.err & DERR_PIXELS) return fail(VBMC_ERR_ARG, "pixel list not distinct or out of range");
+    if (c.err & DERR_QUEUE) return fail(VBMC_ERR_OOM, "recheck queue overflow: raise caps.queue_cap");
+    if (c.err & DERR_TC_WAIT) return fail(VBMC_ERR_DEVICE, "tensor-core pipeline wait timed out");
+    return VBMC_OK;
+}
+
 vbmc_status finish(vbmc_result* r) {
     if (!r->have_result) return fail(VBMC_ERR_STATE, "no verify call on this result");
     if (r->pending) {
         VB_CUDA(cudaStreamSynchronize(r->last_stream));
         r->pending = false;
-        const Counters& c = *r->h_cnt;
-        vbmc_summary& s = r->sum;
-        std::memset(&s, 0, sizeof(s));
-        s.D = c.D;
-        s.base_margin = c.base_margin;
-        s.n_points = r->hi - r->lo;
-        s.n_adversarial = c.n_adv;
-        s.first_witness = c.first;
-        s.n_ties = c.n_ties;
-        for (int i = 0; i < 4; ++i) s.n_recheck[i] = c.n_q[i];
         float ms = 0.f, ms_p = 0.f, ms_s = 0.f;
         cudaEventElapsedTime(&ms, r->ev0, r->ev1);
         cudaEventElapsedTime(&ms_p, r->ev0, r->ev_pro);
         cudaEventElapsedTime(&ms_s, r->ev_pro, r->ev_scr);
-        s.ms_device = ms;
-        s.ms_prologue = ms_p;
-        s.ms_screen = ms_s;
-        s.ms_recheck = ms - ms_p - ms_s;
-        if (r->lo != 0 || r->hi != r->n_space) s.verdict = VBMC_PARTIAL;
-        else if (c.n_adv) s.verdict = VBMC_UNSAFE;
-        else if (c.n_ties) s.verdict = VBMC_TIES_ONLY;
-        else s.verdict = VBMC_SAFE;
-        if (c.err & DERR_PIXELS) return fail(VBMC_ERR_ARG, "pixel list not distinct or out of range");
-        if (c.err & DERR_QUEUE) return fail(VBMC_ERR_OOM, "recheck queue overflow: raise caps.queue_cap");
-        if (c.err & DERR_TC_WAIT) return fail(VBMC_ERR_DEVICE, "tensor-core pipeline wait timed out");
+        fill_summary(r, *r->h_cnt, ms, ms_p, ms_s);
+        r->last_status = counters_status(*r->h_cnt);
     }
-    return VBMC_OK;
+    return r->last_status;
 }
 
 }  // namespace
@@ -644,9 +785,111 @@ extern "C" vbmc_status vbmc_verify_batch(vbmc_net* net, const vbmc_query* querie
                                          void* stream) {
     if (!net || (!queries && nq > 0) || !opt || (!results && nq > 0))
         return fail(VBMC_ERR_ARG, "null argument");
-    for (int i = 0; i < nq; ++i) {
-        vbmc_status st = vbmc_verify_query(net, &queries[i], opt, results[i], stream);
-        if (st != VBMC_OK) return st;
+    if (nq == 0) return VBMC_OK;
+    BatchArena* ar = results[0] ? results[0]->arena : nullptr;
+    bool together = ar && ar->nq >= nq;
+    for (int i = 0; i < nq && together; ++i)
+        together = results[i] && results[i]->arena == ar && results[i]->slot == i && results[i]->net == net;
+    if (!together) {  // results not created together: one query after another
+        for (int i = 0; i < nq; ++i) {
+            vbmc_status st = vbmc_verify_query(net, &queries[i], opt, results[i], stream);
+            if (st != VBMC_OK) return st;
+        }
+        return VBMC_OK;
     }
-    return VBMC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (opt->graph) {
+        // capture on the batch's own stream, after everything already on the caller's
+        VB_CUDA(cudaEventRecord(ar->gev, st));
+        VB_CUDA(cudaStreamWaitEvent(ar->gstream, ar->gev, 0));
+        st = ar->gstream;
+    }
+    const NetView& v = net->v;
+    const int H0 = v.dims[0];
+    // validate, stage images and pixel lists in one buffer, build the views
+    std::vector<uint8_t> stage(ar->stage_stride * (size_t)nq, 0);
+    std::vector<QueryView> hq((size_t)nq);
+    std::vector<uint64_t> nsp((size_t)nq);
+    for (int i = 0; i < nq; ++i) {
+        const vbmc_query& q = queries[i];
+        vbmc_result* r = results[i];
+        if (r->pending) {
+            vbmc_status fs = finish(r);
+            if (fs != VBMC_OK) return fs;
+        }
+        if (!q.image || (!q.pixels && q.s > 0)) return fail(VBMC_ERR_ARG, "null query buffer");
+        uint64_t n, h;
+        vbmc_status cs = check_query_shape(r, q.s, q.k, q.lo, q.hi, opt, &n, &h);
+        if (cs != VBMC_OK) return cs;
+        for (int p = 0; p < q.s; ++p) {
+            if (q.pixels[p] < 0 || q.pixels[p] >= H0) return fail(VBMC_ERR_ARG, "pixel index out of range");
+            for (int rr = 0; rr < p; ++rr)
+                if (q.pixels[rr] == q.pixels[p]) return fail(VBMC_ERR_ARG, "duplicate pixel index");
+        }
+        uint8_t* slot = stage.data() + ar->stage_stride * (size_t)i;
+        std::memcpy(slot, q.image, (size_t)H0);
+        std::memcpy(slot + ((H0 + 3) & ~3), q.pixels, sizeof(int32_t) * (size_t)q.s);
+        const uint8_t* d_img = ar->d_stage + ar->stage_stride * (size_t)i;
+        const int* d_pix = reinterpret_cast<const int*>(d_img + ((H0 + 3) & ~3));
+        hq[i] = make_view(r, d_img, d_pix, q.s, q.k, q.lo, h, n, *opt, i);
+        nsp[i] = n;
+    }
+    std::vector<unsigned long long> tp = tile_prefix(v, opt->precision, hq.data(), nq);
+    VB_CUDA(cudaMemcpyAsync(ar->d_stage, stage.data(), stage.size(), cudaMemcpyHostToDevice, st));
+    VB_CUDA(cudaMemcpyAsync(ar->d_qs, hq.data(), sizeof(QueryView) * (size_t)nq, cudaMemcpyHostToDevice, st));
+    VB_CUDA(cudaMemcpyAsync(ar->d_tp, tp.data(), sizeof(unsigned long long) * tp.size(),
+                            cudaMemcpyHostToDevice, st));
+    vbmc_status sst;
+    if (opt->graph) {
+        // the passes as one CUDA graph (the host-to-device copies above stay outside)
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        VB_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        sst = enqueue_passes(net, ar->d_qs, hq.data(), nq, ar->d_tp, tp[nq], ar->d_qcount, ar->d_queue,
+                             ar->queue_cap, ar->ev, *opt, st, true);
+        cudaError_t ce = cudaStreamEndCapture(st, &g);
+        if (sst != VBMC_OK) {
+            if (g) cudaGraphDestroy(g);
+            return sst;
+        }
+        if (ce != cudaSuccess) return fail(VBMC_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&ge, g, 0);
+        if (ce == cudaSuccess) ce = cudaGraphLaunch(ge, st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        if (ge) cudaGraphExecDestroy(ge);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) return fail(VBMC_ERR_CUDA, std::string("graph: ") + cudaGetErrorString(ce));
+    } else {
+        sst = enqueue_passes(net, ar->d_qs, hq.data(), nq, ar->d_tp, tp[nq], ar->d_qcount, ar->d_queue,
+                             ar->queue_cap, ar->ev, *opt, st);
+        if (sst != VBMC_OK) return sst;
+    }
+    VB_CUDA(cudaMemcpyAsync(ar->h_cnt, ar->d_cnt, sizeof(Counters) * (size_t)nq, cudaMemcpyDeviceToHost, st));
+    VB_CUDA(cudaStreamSynchronize(st));
+    float ms = 0.f, ms_p = 0.f, ms_s = 0.f;
+    cudaEventElapsedTime(&ms, ar->ev[0], ar->ev[3]);
+    cudaEventElapsedTime(&ms_p, ar->ev[0], ar->ev[1]);
+    cudaEventElapsedTime(&ms_s, ar->ev[1], ar->ev[2]);
+    (void)cudaGetLastError();  // timing is informative only
+    vbmc_status result = VBMC_OK;
+    for (int i = 0; i < nq; ++i) {
+        vbmc_result* r = results[i];
+        const vbmc_query& q = queries[i];
+        r->last_stream = st;
+        r->pending = false;
+        r->have_result = true;
+        r->s = q.s;
+        r->k = q.k;
+        r->lo = q.lo;
+        r->hi = hq[i].hi;
+        r->n_space = nsp[i];
+        r->opt = *opt;
+        r->image.assign(q.image, q.image + H0);
+        r->pixels.assign(q.pixels, q.pixels + q.s);
+        r->hq.image = hq[i].image;
+        fill_summary(r, ar->h_cnt[i], ms, ms_p, ms_s);
+        r->last_status = counters_status(ar->h_cnt[i]);
+        if (r->last_status != VBMC_OK && result == VBMC_OK) result = r->last_status;
+    }
+    return result;
 }

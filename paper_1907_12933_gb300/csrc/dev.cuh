@@ -62,11 +62,22 @@ struct Counters {
     unsigned int err;
     int D;
     double base_margin;
+    unsigned long long t0;          // %globaltimer at the start of the query's prologue
+    unsigned long long t_screen;    // ... when its last screen tile finished
+    unsigned long long t_final;     // ... when its result became final
+    unsigned long long tiles_left;  // screen tiles not yet finished
 };
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
 
 struct QueryView {
     int s, k, R, qid;
     unsigned long long n_points, lo, hi;  // space size and checked range
+    unsigned long long ntiles;            // screen tiles of this query (time-to-verdict)
     const uint8_t* image;   // H_0 grey levels (device)
     const int* pix_in;      // s pixel indices as given (device)
     int* pix;               // validated copy

@@ -37,6 +37,9 @@ void launch_fp64(const NetView& net, const QueryView* d_qs, int nq, const QEntry
 void launch_margin64(const NetView& net, const QueryView* d_qs, unsigned long long t, double* d_out,
                      cudaStream_t st);
 
+// Stamp each query's time-to-verdict after the last pass.
+void launch_stamp_final(QueryView* d_qs, int nq, cudaStream_t st);
+
 // Single prologue steps (the allocation-free entry point runs these directly).
 void launch_pro_init(const NetView& net, QueryView* d_qs, int nq, cudaStream_t st);
 void launch_pro_layer(const NetView& net, QueryView* d_qs, int nq, int l, cudaStream_t st);

@@ -36,10 +36,25 @@ __global__ void k_pro_init(NetView net, QueryView* qs, int nq) {
         c->err = ok ? 0u : DERR_PIXELS;
         c->D = 0;
         c->base_margin = 0.0;
+        c->t0 = globaltimer_ns();
+        c->t_screen = c->t0;
+        c->t_final = 0;
+        c->tiles_left = Q.ntiles;
         for (int p = 0; p < Q.s; ++p) {
             int v = Q.pix_in[p];
             Q.pix[p] = (ok && v >= 0 && v < H0) ? v : 0;  // never index out of range
         }
+    }
+    // results start from zero on every call
+    if (Q.flip)
+        for (int w = threadIdx.x; w < net.flip_words; w += blockDim.x) Q.flip[w] = Q.flip_tie[w] = 0u;
+    if (Q.ss)
+        for (int w = threadIdx.x; w < net.ss_words; w += blockDim.x) Q.ss[w] = Q.ss_tie[w] = 0u;
+    if (Q.bitmap && Q.hi > 0) {
+        const unsigned long long nw = (Q.hi + 31) / 32;
+        uint4* b4 = reinterpret_cast<uint4*>(Q.bitmap);
+        for (unsigned long long w = threadIdx.x; w < nw / 4; w += blockDim.x) b4[w] = make_uint4(0, 0, 0, 0);
+        for (unsigned long long w = (nw / 4) * 4 + threadIdx.x; w < nw; w += blockDim.x) Q.bitmap[w] = 0u;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < Q.s * Q.R; e += blockDim.x) {
@@ -220,6 +235,20 @@ __global__ void k_pro_finish(NetView net, QueryView* qs, int nq) {
         }
         __syncthreads();
     }
+}
+
+// Time-to-verdict: a query none of whose points needed a later pass was final
+// when its screen finished; the others when the last pass finished (now).
+__global__ void k_stamp_final(QueryView* qs, int nq) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nq) return;
+    Counters* c = qs[q].cnt;
+    const unsigned long long later = c->n_q[0] + c->n_q[1] + c->n_q[2] + c->n_q[3];
+    c->t_final = (later || qs[q].ntiles == 0) ? globaltimer_ns() : c->t_screen;
+}
+
+void launch_stamp_final(QueryView* d_qs, int nq, cudaStream_t st) {
+    k_stamp_final<<<(nq + 127) / 128, 128, 0, st>>>(d_qs, nq);
 }
 
 void launch_pro_init(const NetView& net, QueryView* d_qs, int nq, cudaStream_t st) {

@@ -389,6 +389,13 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
             }
         }
         __syncwarp();
+        if (!gather) {  // time-to-verdict: the last tile of a query stamps the time
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const QueryView& Q = qs[S.q[0]];
+                if (atomicAdd(&Q.cnt->tiles_left, ~0ull) == 1ull) Q.cnt->t_screen = globaltimer_ns();
+            }
+        }
     }
 }
 

@@ -67,7 +67,8 @@ struct TcSmem {
     int vst[MROWS];
     int fcnt[MROWS][kTcMaxL + 1];
     short flist[MROWS][kTcMaxL + 1][FCAP];
-    uint32_t cflip[256];   // sign changes seen by this CTA (flushed once at the end)
+    uint32_t cflip[256];   // sign changes seen by this CTA for query curq (flushed on change)
+    int curq;
     int npref;
     int uniform_base;
     unsigned long long bars[2 * NB + 2 * NA + 5];
@@ -112,26 +113,26 @@ __device__ __forceinline__ uint32_t sw_off(int r, int u) {
 
 template <bool SPLIT, bool BF>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restrict__ qs,
-     unsigned long long lo, unsigned long long hi, const QEntry* __restrict__ gather,
+k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restrict__ qs, int nq,
+     const unsigned long long* __restrict__ tile_prefix, const QEntry* __restrict__ gather,
      const unsigned long long* __restrict__ gcount, unsigned long long gcap, Queue out,
      int out_level) {
     extern __shared__ uint8_t smem_raw[];
     TcSmem& S = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                            ~uintptr_t(1023));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const QueryView& Q = qs[0];
     const int L = P.L;
     volatile int* abortp = &S.abort_flag;
 
-    unsigned long long ntiles, base = 0, gn = 0;
+    // range mode: tiles of query q are tile_prefix[q] .. tile_prefix[q+1]-1, each
+    // tile 128 consecutive indices from (lo & ~31); gather mode: 128 queue entries
+    unsigned long long ntiles, gn = 0;
     if (gather) {
         gn = *gcount;
         if (gn > gcap) gn = gcap;
         ntiles = (gn + MROWS - 1) / MROWS;
     } else {
-        base = lo & ~31ull;
-        ntiles = hi > base ? (hi - base + MROWS - 1) / MROWS : 0;
+        ntiles = tile_prefix[nq];
     }
 
     auto bar = [&](int i) { return tc::smem_u32(&S.bars[i]); };
@@ -150,6 +151,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
         tc::mbar_init(bar(DRAINED), 8);
         tc::mbar_init(bar(FIN), 1);
         S.abort_flag = 0;
+        S.curq = -1;
         tc::fence_mbar_init();
     }
     for (int w = threadIdx.x; w < 256; w += blockDim.x) S.cflip[w] = 0u;
@@ -266,15 +268,39 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
         const int qd = warp & 3;             // TMEM lane quarter
         const int hf = wid >> 2;             // column half in the drain phases
         const int H0 = net.dims[0], H1 = net.dims[1];
-        const int s = Q.s, R = Q.R;
-        const int ni = s >= 2 ? 2 : s;       // inner digits handled per row
-        unsigned long long Rni = 1;
-        for (int i = 0; i < ni; ++i) Rni *= (unsigned long long)R;
         uint32_t ait = 0, dit = 0;
         const float uacc_base = 0x1p-22f * (SPLIT ? 3.f : 1.f);
         (void)H0;
         for (unsigned long long g = blockIdx.x; g < ntiles; g += gridDim.x) {
             if (*abortp) break;
+            int q = 0;
+            if (!gather) {
+                int a = 0, b = nq - 1;
+                while (a < b) {
+                    const int mid = (a + b + 1) >> 1;
+                    if (tile_prefix[mid] <= g) a = mid; else b = mid - 1;
+                }
+                q = a;
+            }
+            const QueryView& Q = qs[q];
+            const int s = Q.s, R = Q.R;
+            const int ni = s >= 2 ? 2 : s;       // inner digits handled per row
+            unsigned long long Rni = 1;
+            for (int i = 0; i < ni; ++i) Rni *= (unsigned long long)R;
+            const unsigned long long base = Q.lo & ~31ull;
+            const unsigned long long gq = gather ? 0 : g - tile_prefix[q];
+            if (q != S.curq) {  // this CTA's sign changes belong to the previous query
+                const int cq = S.curq;
+                if (cq >= 0)
+                    for (int w = wtid; w < net.flip_words && w < 256; w += 256)
+                        if (S.cflip[w]) {
+                            if (qs[cq].flip) atomicOr(&qs[cq].flip[w], S.cflip[w]);
+                            S.cflip[w] = 0u;
+                        }
+                tc::named_bar_sync(1, 256);
+                if (wtid == 0) S.curq = q;
+                tc::named_bar_sync(1, 256);
+            }
             // ---- decode the tile's points
             if (wtid < MROWS) {
                 const int r = wtid;
@@ -285,8 +311,8 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     ok = idx < gn;
                     if (ok) t = gather[idx].t;
                 } else {
-                    t = base + g * MROWS + r;
-                    ok = t >= lo && t < hi;
+                    t = base + gq * MROWS + r;
+                    ok = t >= Q.lo && t < Q.hi;
                 }
                 S.t[r] = t;
                 S.valid[r] = ok;
@@ -662,7 +688,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         for (int l = 1; l < L; ++l)
                             if (S.fcnt[r][l] == 1 && S.fcnt[r][l + 1] > FCAP) bad = true;
                     const unsigned long long t = S.t[r];
-                    queue_push_warp(out, bad, t, 0u, Q.cnt, out_level);
+                    queue_push_warp(out, bad, t, (unsigned)q, Q.cnt, out_level);
                     const bool adv = rv && !bad && S.vst[r] == 1;
                     if (!gather) {
                         const unsigned m = __ballot_sync(0xffffffffu, adv);
@@ -676,7 +702,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     }
                     if (rv && !bad && Q.ss) {
                         for (int l = 1; l < L; ++l) {
-                            if (S.fcnt[r][l] != 1) continue;
+                            if (S.fcnt[r][l] != 1) continue;  // SS needs exactly one change
                             const int j = S.flist[r][l][0];
                             const int Hn = net.dims[l + 1];
                             const int nt = S.fcnt[r][l + 1];
@@ -687,21 +713,24 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     }
                 }
                 tc::named_bar_sync(1, 256);
+                if (!gather && wtid == 0 &&
+                    atomicAdd(&Q.cnt->tiles_left, ~0ull) == 1ull)  // last tile of this query
+                    Q.cnt->t_screen = globaltimer_ns();
             }
         }
     }
     // ---- teardown: wait for outstanding tensor-core work, release TMEM
     tc::tc_fence_before();
     __syncthreads();
-    if (Q.flip)
+    if (S.curq >= 0 && qs[S.curq].flip)
         for (int w = threadIdx.x; w < net.flip_words && w < 256; w += blockDim.x)
-            if (S.cflip[w]) atomicOr(&Q.flip[w], S.cflip[w]);
+            if (S.cflip[w]) atomicOr(&qs[S.curq].flip[w], S.cflip[w]);
     if (warp == 1) {
         __syncwarp();
         tc::tc_fence_after();
         tc::tmem_dealloc(tmem, 512);
     }
-    if (threadIdx.x == 0 && *abortp) atomicOr(&Q.cnt->err, DERR_TC_WAIT);
+    if (threadIdx.x == 0 && *abortp) atomicOr(&qs[S.curq >= 0 ? S.curq : 0].cnt->err, DERR_TC_WAIT);
 }
 
 // ------------------------------------------------------------ per-query setup
@@ -825,6 +854,7 @@ static vbmc_status build_prec(TcNet& tc, const NetView& v, const std::vector<std
                               TcParams& P) {
     using T = typename std::conditional<BF, __nv_bfloat16, __half>::type;
     std::memset(&P, 0, sizeof(P));
+    (void)cudaGetLastError();  // start from a clean error state
     P.L = v.L;
     P.bf16 = BF ? 1 : 0;
     PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -982,34 +1012,32 @@ void tc_free(TcNet& tc) {
     tc.prec[0].ready = tc.prec[1].ready = false;
 }
 
-void tc_launch_query_setup(TcNet& tc, const NetView& v, QueryView* d_q, int precision,
+void tc_launch_query_setup(TcNet& tc, const NetView& v, QueryView* d_q, int nq, int precision,
                            cudaStream_t st) {
     const TcParams& P = tc.prec[precision == VBMC_PREC_BF16 ? 0 : 1].p;
-    k_classes_tc<<<1, 512, 0, st>>>(P, v, d_q);
+    k_classes_tc<<<nq, 512, 0, st>>>(P, v, d_q);
 }
 
 template <bool SPLIT, bool BF>
-static void launch_k(const TcParams& P, const NetView& v, const QueryView* d_q, uint64_t lo, uint64_t hi,
-                     const QEntry* g, const unsigned long long* gc, unsigned long long cap, Queue out,
-                     int level, int n_sm, cudaStream_t st) {
+static void launch_k(const TcParams& P, const NetView& v, const QueryView* d_q, int nq,
+                     const unsigned long long* tp, unsigned long long ntiles, const QEntry* g,
+                     const unsigned long long* gc, unsigned long long cap, Queue out, int level,
+                     int n_sm, cudaStream_t st) {
     const size_t smem = sizeof(TcSmem) + 1024;
     auto kern = k_tc<SPLIT, BF>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     unsigned grid = (unsigned)n_sm;
-    if (!g) {
-        const unsigned long long base = lo & ~31ull;
-        const unsigned long long tiles = hi > base ? (hi - base + MROWS - 1) / MROWS : 0;
-        if (tiles < grid) grid = (unsigned)(tiles ? tiles : 1);
-    }
-    kern<<<grid, TC_THREADS, smem, st>>>(P, v, d_q, lo, hi, g, gc, cap, out, level);
+    if (!g && ntiles < grid) grid = (unsigned)(ntiles ? ntiles : 1);
+    kern<<<grid, TC_THREADS, smem, st>>>(P, v, d_q, nq, tp, g, gc, cap, out, level);
 }
 
-vbmc_status tc_launch_screen(TcNet& tc, const NetView& v, const QueryView* d_q, uint64_t lo,
-                             uint64_t hi, int precision, Queue out, int n_sm, cudaStream_t st) {
+vbmc_status tc_launch_screen(TcNet& tc, const NetView& v, const QueryView* d_q, int nq,
+                             const unsigned long long* d_tile_prefix, unsigned long long ntiles,
+                             int precision, Queue out, int out_level, int n_sm, cudaStream_t st) {
     const bool bf = precision == VBMC_PREC_BF16;
     const TcParams& P = tc.prec[bf ? 0 : 1].p;
-    if (bf) launch_k<false, true>(P, v, d_q, lo, hi, nullptr, nullptr, 0, out, 0, n_sm, st);
-    else launch_k<false, false>(P, v, d_q, lo, hi, nullptr, nullptr, 0, out, 0, n_sm, st);
+    if (bf) launch_k<false, true>(P, v, d_q, nq, d_tile_prefix, ntiles, nullptr, nullptr, 0, out, out_level, n_sm, st);
+    else launch_k<false, false>(P, v, d_q, nq, d_tile_prefix, ntiles, nullptr, nullptr, 0, out, out_level, n_sm, st);
     return cudaGetLastError() == cudaSuccess ? VBMC_OK : VBMC_ERR_CUDA;
 }
 
@@ -1018,9 +1046,11 @@ vbmc_status tc_launch_gather(TcNet& tc, const NetView& v, const QueryView* d_q, 
                              int precision, Queue out, int n_sm, cudaStream_t st) {
     const bool bf = precision == VBMC_PREC_BF16;
     const TcParams& P = tc.prec[bf ? 0 : 1].p;
-    if (bf) launch_k<true, true>(P, v, d_q, 0, 0, in, in_count, cap, out, 1, n_sm, st);
-    else launch_k<true, false>(P, v, d_q, 0, 0, in, in_count, cap, out, 1, n_sm, st);
+    if (bf) launch_k<true, true>(P, v, d_q, 1, nullptr, 0, in, in_count, cap, out, 1, n_sm, st);
+    else launch_k<true, false>(P, v, d_q, 1, nullptr, 0, in, in_count, cap, out, 1, n_sm, st);
     return cudaGetLastError() == cudaSuccess ? VBMC_OK : VBMC_ERR_CUDA;
 }
+
+int tc_tile_points() { return MROWS; }
 
 }  // namespace vbmc

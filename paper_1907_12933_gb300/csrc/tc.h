@@ -49,10 +49,14 @@ vbmc_status tc_build(TcNet& tc, const NetView& v, const std::vector<std::vector<
                      const std::vector<std::vector<float>>& b, int precision);
 void tc_free(TcNet& tc);
 // Per-query constants of the tensor screen (column classes), after the prologue.
-void tc_launch_query_setup(TcNet& tc, const NetView& v, QueryView* d_q, int precision,
+void tc_launch_query_setup(TcNet& tc, const NetView& v, QueryView* d_q, int nq, int precision,
                            cudaStream_t st);
-vbmc_status tc_launch_screen(TcNet& tc, const NetView& v, const QueryView* d_q, uint64_t lo,
-                             uint64_t hi, int precision, Queue out, int n_sm, cudaStream_t st);
+// Screen over nq queries: tiles of query q are d_tile_prefix[q] .. d_tile_prefix[q+1]-1
+// (ntiles in total), each tc_tile_points() consecutive indices from (lo & ~31).
+vbmc_status tc_launch_screen(TcNet& tc, const NetView& v, const QueryView* d_q, int nq,
+                             const unsigned long long* d_tile_prefix, unsigned long long ntiles,
+                             int precision, Queue out, int out_level, int n_sm, cudaStream_t st);
+int tc_tile_points();
 vbmc_status tc_launch_gather(TcNet& tc, const NetView& v, const QueryView* d_q, const QEntry* in,
                              const unsigned long long* in_count, unsigned long long cap,
                              int precision, Queue out, int n_sm, cudaStream_t st);

@@ -94,15 +94,20 @@ def test_config3_net_small_box(vb):
     compare(run_gpu(vb, net, q, "fp32"), oracle.verify(net, q), net, q)
 
 
-def test_config4_net_batch(vb):
-    """784-256-256-10 ReLU net, 6 uneven queries through verify_batch."""
-    w = synth.workload("mlp784x256x256_relu_batch4096", nq=6, s_range=(1, 3), k_range=(3, 10))
+@pytest.mark.parametrize("prec,graph", [("fp32", False), ("bf16", False), ("bf16", True),
+                                        ("fp64", False)])
+def test_config4_net_batch(vb, prec, graph):
+    """784-256-256-10 ReLU net, 24 uneven queries through one vbmc_verify_batch call
+    (one launch per pass over every query), each checked against the oracle."""
+    w = synth.workload("mlp784x256x256_relu_batch4096", nq=24, s_range=(1, 3), k_range=(3, 10))
     net = w["net"]
     vnet = vb.Net(net)
     qs = w["queries"]
-    results = [vb.Result(vnet, max_points=oracle.space_size(len(q["pixels"]), q["k"]),
-                         max_s=3, max_k=10, queue_cap=1 << 16) for q in qs]
-    sums = vb.verify_batch(vnet, results, qs, precision="fp32", coverage=True, bitmap=True)
+    nmax = max(oracle.space_size(len(q["pixels"]), q["k"]) for q in qs)
+    results = vb.result_create_batch(vnet, len(qs), max_points=nmax, max_s=3, max_k=10,
+                                     queue_cap=1 << 18)
+    sums = vb.verify_batch(vnet, results, qs, precision=prec, coverage=True, bitmap=True,
+                           graph=graph)
     for q, r, s in zip(qs, results, sums):
         o = oracle.verify(net, q)
         g = {"summary": s, "n": oracle.space_size(len(q["pixels"]), q["k"])}
@@ -111,6 +116,9 @@ def test_config4_net_batch(vb):
         g["ties"] = np.sort(vb.get_ties(r))
         g["witness"] = vb.get_witness(r, len(q["pixels"]), 784)
         compare(g, o, net, q)
+        assert s["ms_to_verdict"] > 0.0
+    for r in results:
+        r.free()
 
 
 @pytest.mark.parametrize("prec", PLAIN)
