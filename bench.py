@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nq", type=int, default=512,
+                    help="batched workload: number of queries (the full workload has 4096)")
+    ap.add_argument("--graph", action="store_true", help="batched workload: CUDA-graph launch")
     return ap.parse_args()
 
 
@@ -138,19 +141,77 @@ def screen_flops_per_point(dims, s):
     return 2 * dense + s * dims[1]
 
 
-def launches_per_step(precision, L):
+def launches_per_step(precision, L, batch=False):
+    """Kernels of the library per verify call (cudaMemset/cudaMemcpy not counted)."""
     pro = 1 + L + 1 + 1  # init, L base layers, tables, finish
     if precision == "fp64":
-        return pro + 1
+        return pro + 1 + 1  # FP64 range pass per query (1 here), time stamps
     if precision == "fp32":
-        return pro + 2  # screen, FP64 pass
-    return pro + 4  # tensor screen, tensor 3x pass, FP32 pass, FP64 pass
+        return pro + 4  # FP32 screen, double-float pass, FP64 pass, time stamps
+    # column classes, tensor screen, [split tensor pass], FP32, double-float, FP64, stamps
+    return pro + (6 if batch else 7)
 
 
 # -------------------------------------------------------------------- main
 
+def main_batch(a):
+    """Batched uneven queries (784-256-256-10 ReLU): one vbmc_verify_batch call per
+    step over nq queries; value = all queries' points / step time; p50/p99 of the
+    per-query time to a final verdict."""
+    import torch
+    import paper_1907_12933_gb300 as vb
+    from paper_1907_12933_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    w = synth.workload(a.workload, nq=a.nq)
+    net_d, cfg, qs = w["net"], w["cfg"], w["queries"]
+    pts = sum((2 * q["k"] + 1) ** len(q["pixels"]) for q in qs)
+    vnet = vb.Net(net_d)
+    res = vb.result_create_batch(vnet, len(qs), max_points=0, max_s=max(len(q["pixels"]) for q in qs),
+                                 max_k=max(q["k"] for q in qs), queue_cap=1 << 24)
+    for _ in range(a.warmup):
+        vb.verify_batch(vnet, res, qs, precision=a.precision, coverage=True, bitmap=False,
+                        graph=a.graph)
+    clocks = Clocks()
+    clocks.start()
+    times, ttv = [], []
+    for _ in range(a.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sums = vb.verify_batch(vnet, res, qs, precision=a.precision, coverage=True, bitmap=False,
+                               graph=a.graph)
+        times.append(time.perf_counter() - t0)
+        ttv = [x["ms_to_verdict"] for x in sums]
+    ck = clocks.stop(torch.cuda.current_device())
+    ms = 1000.0 * statistics.median(times)
+    dev_ms = sums[0]["ms_device"]
+    line = {"metric": METRIC, "value": pts / (dev_ms / 1000.0), "unit": UNIT, "n_gpus": 1,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": dev_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "fp16": "f16"}[a.precision],
+            "data": "synthetic",
+            "config": {"workload": a.workload, "dims": cfg["dims"], "queries": len(qs),
+                       "points_total": pts, "s_range": cfg["s_range"], "k_range": cfg["k_range"],
+                       "graph": a.graph, "precision": a.precision},
+            "e2e": {"value": pts / (ms / 1000.0), "unit": UNIT,
+                    "h2d_bytes_per_step": len(qs) * (cfg["dims"][0] + 24),
+                    "d2h_bytes_per_step": len(qs) * 96},
+            "time_to_verdict_ms": {"p50": float(np.percentile(ttv, 50)),
+                                   "p99": float(np.percentile(ttv, 99)), "max": float(max(ttv))},
+            "verdicts": {"unsafe": sum(x["verdict"] == "UNSAFE" for x in sums),
+                         "safe": sum(x["verdict"] == "SAFE" for x in sums),
+                         "ties_only": sum(x["verdict"] == "TIES_ONLY" for x in sums),
+                         "n_recheck": [sum(x["n_recheck"][i] for x in sums) for i in range(4)]},
+            "gpu_launches": a.steps * launches_per_step(a.precision, len(cfg["dims"]) - 1, batch=True)}
+    if ck:
+        line["clocks"] = ck
+    print(json.dumps(line))
+
+
 def main():
     a = parse()
+    if "batch" in a.workload and a.impl == "ours":
+        return main_batch(a)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     w = synth.workload(a.workload)
