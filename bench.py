@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--nq", type=int, default=512,
                     help="batched workload: number of queries (the full workload has 4096)")
     ap.add_argument("--graph", action="store_true", help="batched workload: CUDA-graph launch")
+    ap.add_argument("--train-queries", type=int, default=1500,
+                    help="tile-proposal workload: selected training queries (exact labels)")
+    ap.add_argument("--test-queries", type=int, default=200,
+                    help="tile-proposal workload: selected held-out queries")
     return ap.parse_args()
 
 
@@ -208,10 +212,110 @@ def main_batch(a):
     print(json.dumps(line))
 
 
+def main_proposal(a):
+    """Learned tile proposal (784-512-512-10 ReLU net, s = 6, k = 7, 64 tiles of
+    177,979 points): exact per-tile labels for the training queries, GPU training
+    with early stopping, then on held-out queries that hold a witness the device
+    time to the first witness with the learned tile order and with plain index
+    order (vbmc_search_query; a SAFE verdict needs every tile either way)."""
+    import torch
+    import paper_1907_12933_gb300 as vb
+    from paper_1907_12933_gb300 import build
+    from paper_1907_12933_gb300 import proposal as P
+    build.build()
+    torch.cuda.set_device(0)
+    w = synth.workload(a.workload)
+    net_d, cfg = w["net"], w["cfg"]
+    vnet = vb.Net(net_d)
+    H0, T = cfg["dims"][0], cfg["n_tiles"]
+    t0 = time.perf_counter()
+
+    def pick(split, want):
+        # candidates are drawn until `want` pass the reach filter (about 1 in 50 does)
+        got_q, got_x, start = [], [], 0
+        while len(got_q) < want and start < 200 * want:
+            c = synth.proposal_candidates(split, 20 * want, start=start)
+            X, reach, _ = P.features(vnet, c, H0)
+            idx = P.select_by_reach(reach)[:want - len(got_q)]
+            got_q += [c[i] for i in idx]
+            got_x.append(X[torch.from_numpy(idx).cuda()].contiguous())
+            start += len(c)
+        return got_q, torch.cat(got_x).contiguous(), start
+
+    qtr, Xtr, ntr_c = pick("train", a.train_queries)
+    qte, Xte, nte_c = pick("test", a.test_queries)
+    Ttr, ctr, lab_s = P.labels(vnet, qtr, T, precision=a.precision)
+    _, cte, lab_te_s = P.labels(vnet, qte, T, precision=a.precision)
+    nv = len(qtr) // 5
+    prop = vb.Proposal((3 * H0, 256, 256, T), max_batch=256, seed=1)
+    tt = time.perf_counter()
+    hist = P.train(prop, Xtr[nv:].contiguous(), Ttr[nv:].contiguous(), Xtr[:nv].contiguous(),
+                   ctr[:nv], max_epochs=24, lr=1e-3, weight_decay=1e-4, patience=4)
+    train_s = time.perf_counter() - tt
+    learned = P.orders(prop, Xte)
+    plain = np.tile(np.arange(T), (len(qte), 1))
+    unsafe = np.nonzero(cte.sum(axis=1) > 0)[0]
+    sel = unsafe
+    qs = [qte[i] for i in sel]
+    P.search_all(vnet, qs[:a.warmup], learned[sel[:a.warmup]], precision=a.precision)
+    clocks = Clocks()
+    clocks.start()
+    wall = {}
+    res = {}
+    for name, od in (("plain", plain), ("learned", learned)):
+        tw = time.perf_counter()
+        res[name] = P.search_all(vnet, qs, od[sel], precision=a.precision)
+        wall[name] = time.perf_counter() - tw
+    ck = clocks.stop(torch.cuda.current_device())
+
+    def dist_(v):
+        v = np.asarray(v, dtype=np.float64)
+        return {"mean": float(v.mean()), "p50": float(np.percentile(v, 50)),
+                "p90": float(np.percentile(v, 90)), "p99": float(np.percentile(v, 99))}
+
+    ms = {n: [r["ms_to_witness"] for r in res[n]] for n in res}
+    tiles = {n: [r["tiles_checked"] for r in res[n]] for n in res}
+    for n in res:
+        for r, i in zip(res[n], sel):
+            assert r["verdict"] == "UNSAFE" and cte[i, r["witness_tile"]] > 0
+    line = {"metric": "time to first witness (learned tile order)", "value": dist_(ms["learned"])["mean"],
+            "unit": "ms", "n_gpus": 1, "steps": len(qs), "warmup": a.warmup,
+            "ms_per_step": dist_(ms["learned"])["mean"], "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": {"fp32": "f32", "bf16": "bf16", "fp16": "f16", "fp64": "f64"}[a.precision],
+            "data": "synthetic",
+            "config": {"workload": a.workload, "dims": cfg["dims"], "s": cfg["s"], "k": cfg["k"],
+                       "n_tiles": T, "proposal": [3 * H0, 256, 256, T],
+                       "train_queries": len(qtr), "train_candidates": ntr_c,
+                       "test_queries": len(qte), "test_candidates": nte_c,
+                       "filter": "first-order reach >= 0.5",
+                       "l2": "not flushed: every query's points are new work"},
+            "time_to_first_witness_ms": {"learned": dist_(ms["learned"]), "plain": dist_(ms["plain"])},
+            "tiles_to_first_witness": {"learned": dist_(tiles["learned"]), "plain": dist_(tiles["plain"])},
+            "speedup_mean": float(np.mean(ms["plain"]) / np.mean(ms["learned"])),
+            "e2e": {"value": 1000.0 * wall["learned"] / len(qs), "unit": "ms",
+                    "plain": 1000.0 * wall["plain"] / len(qs),
+                    "h2d_bytes_per_step": H0 + 4 * cfg["s"] + 4 * T, "d2h_bytes_per_step": 256},
+            "labels": {"train_s": lab_s, "test_s": lab_te_s,
+                       "train_unsafe_frac": float((ctr.sum(1) > 0).mean()),
+                       "witness_tiles_mean": float((ctr > 0).sum(1).mean())},
+            "training": {"seconds": train_s, "best_epoch": hist["best_epoch"],
+                         "val_rank": hist["val_rank"]},
+            # per search: set-up (init, L base layers, tables, finish, column classes)
+            # plus 6 per checked tile (screen, split pass, FP32, double-float, FP64, stamps)
+            "gpu_launches": int(sum(len(cfg["dims"]) + 3 + 6 * t for n in tiles for t in tiles[n])),
+            "wall_s": time.perf_counter() - t0}
+    if ck:
+        line["clocks"] = ck
+    print(json.dumps(line))
+    prop.free()
+
+
 def main():
     a = parse()
     if "batch" in a.workload and a.impl == "ours":
         return main_batch(a)
+    if a.workload.startswith("proposal") and a.impl == "ours":
+        return main_proposal(a)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     w = synth.workload(a.workload)

@@ -221,6 +221,92 @@ vbmc_status vbmc_get_ties(vbmc_result *res, uint64_t *idx, size_t cap, uint64_t 
 /* Message for the last failing call of this thread. */
 const char *vbmc_last_error(void);
 
+/* ---- Tile-ordered search for a first witness.
+ * The index space [0, n) of a query (n = R^s) is cut into n_tiles contiguous
+ * tiles of ceil(n / n_tiles) points (the last one ragged; tiles past n are
+ * empty). vbmc_search_query checks the tiles in the order given by `order`
+ * (a permutation of 0..n_tiles-1, host memory) with the same exact pipeline
+ * as vbmc_verify_query, and stops after the first tile that holds a point
+ * violating Eq. 10. Without any witness every tile is checked, and the
+ * verdict is the one vbmc_verify_query gives (SAFE or TIES_ONLY). After the
+ * call, vbmc_result_summary reports the checked points (n_points), the
+ * adversarial points found in the checked tiles, and the smallest of them
+ * (first_witness, the first in index order within the witness tile); the
+ * verdict is UNSAFE once a witness is found, PARTIAL is never reported.
+ * Coverage masks and the verdict bitmap, when requested, cover the checked
+ * tiles only. Blocks until the search ends. */
+typedef struct {
+    int32_t tiles_checked;      /* tiles checked, the witness tile included        */
+    int32_t witness_tile;       /* tile holding the first witness found, or -1     */
+    uint64_t points_checked;
+    double ms_to_witness;       /* device time from the start of the query's set-up
+                                   to the end of the witness tile (or of the last
+                                   tile without a witness)                          */
+} vbmc_search_out;
+
+vbmc_status vbmc_search_query(vbmc_net *net, const vbmc_query *query, int32_t n_tiles,
+                              const int32_t *order, const vbmc_options *opt, vbmc_result *res,
+                              vbmc_search_out *out, void *stream);
+
+/* Adversarial points per tile (n_tiles tiles as above) from the verdict bitmap
+ * of the result's last call, which must have covered the whole space with the
+ * bitmap on. counts: n_tiles uint64 in host memory. */
+vbmc_status vbmc_tile_counts(vbmc_result *res, int32_t n_tiles, uint64_t *counts);
+
+/* ---- Learned tile proposal: a 3-layer MLP (F -> H1 -> H2 -> T, ReLU hidden
+ * layers) trained on the GPU to rank the T tiles of a query so that
+ * vbmc_search_query meets a witness sooner. Weights are FP32 masters; the
+ * scoring forward and the training forward round weights and activations to
+ * BF16 (FP32 accumulation). Not a part of the exact check: any order yields
+ * the same verdicts. All pointers named d_* are device memory. */
+typedef struct vbmc_proposal vbmc_proposal;
+
+/* He-normal weights from `seed`, zero biases; max_batch bounds B below.
+ * n_tiles in [2, 1024]. */
+vbmc_status vbmc_proposal_create(int32_t n_features, int32_t h1, int32_t h2, int32_t n_tiles,
+                                 int32_t max_batch, uint64_t seed, vbmc_proposal **out);
+vbmc_status vbmc_proposal_free(vbmc_proposal *p);
+
+/* Features of nq queries on a ReLU net, 3 * H_0 floats per query (row-major
+ * [nq][3 * H_0]): the image / 255; at the p-th listed pixel the place value
+ * R^-p of its digit, 0 elsewhere; and that place value times the input
+ * gradient of the margin y_D - y_r (runner-up r) at the unperturbed image,
+ * times k / 255, over the margin, clipped to [-16, 16]. d_images: [nq][H_0]
+ * bytes; d_pixels: [nq][pix_stride] int32 (the first s[q] used); d_s, d_k:
+ * [nq] int32. d_reach[q] (optional): sum over the listed pixels of
+ * |gradient| * k / 255 over the margin (the first-order reach of the box);
+ * d_margin[q] (optional): the FP32 margin. Asynchronous on `stream`. */
+vbmc_status vbmc_proposal_features(const vbmc_net *net, const uint8_t *d_images,
+                                   const int32_t *d_pixels, const int32_t *d_s, const int32_t *d_k,
+                                   int32_t pix_stride, int32_t nq, float *d_features,
+                                   float *d_reach, float *d_margin, void *stream);
+
+/* Tile scores [B][T] of B feature rows [B][F]; with d_order non-NULL also
+ * each row's tile order [B][T] (descending score, lower tile first on equal
+ * scores). Asynchronous on `stream`. */
+vbmc_status vbmc_proposal_scores(vbmc_proposal *p, const float *d_X, int32_t B, float *d_scores,
+                                 int32_t *d_order, void *stream);
+
+/* Loss and gradients of a batch: d_T [B][T] holds 0/1 witness labels per tile;
+ * loss = mean over rows with a witness tile of -sum_i (t_i / sum t) log
+ * softmax(z)_i. bf16 = 0 runs the forward in FP32 (for gradient checks).
+ * *h_loss (optional) receives the loss; the call then waits for the stream.
+ * Gradients are read with vbmc_proposal_params. */
+vbmc_status vbmc_proposal_grads(vbmc_proposal *p, const float *d_X, const float *d_T, int32_t B,
+                                int32_t bf16, float *h_loss, void *stream);
+
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) with decoupled weight decay on
+ * the weights, from the gradients of a BF16-forward batch. */
+vbmc_status vbmc_proposal_train_step(vbmc_proposal *p, const float *d_X, const float *d_T, int32_t B,
+                                     float lr, float weight_decay, float *h_loss, void *stream);
+
+/* Copy layer l (1..3) weights [H_l][H_{l-1}], biases and last gradients to
+ * host buffers (any may be NULL), or set the weights and biases. Synchronous. */
+vbmc_status vbmc_proposal_params(vbmc_proposal *p, int32_t layer, float *h_W, float *h_b,
+                                 float *h_gW, float *h_gb);
+vbmc_status vbmc_proposal_set_params(vbmc_proposal *p, int32_t layer, const float *h_W,
+                                     const float *h_b);
+
 /* ---- For callers that cannot allocate device memory (no counterpart in the
  * paper). A process embedded in another runtime's memory pool, or one whose
  * allocator must not be re-entered, cannot call cudaMalloc. This entry point

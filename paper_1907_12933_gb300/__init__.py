@@ -59,6 +59,11 @@ class _Summary(C.Structure):
                 ("ms_recheck", C.c_double), ("ms_to_verdict", C.c_double)]
 
 
+class _SearchOut(C.Structure):
+    _fields_ = [("tiles_checked", C.c_int32), ("witness_tile", C.c_int32),
+                ("points_checked", C.c_uint64), ("ms_to_witness", C.c_double)]
+
+
 class _NoallocOut(C.Structure):
     _fields_ = [("counters", C.c_void_p), ("flip", C.c_void_p), ("flip_tie", C.c_void_p),
                 ("ss", C.c_void_p), ("ss_tie", C.c_void_p), ("bitmap", C.c_void_p),
@@ -99,6 +104,21 @@ def lib():
             "vbmc_get_ties": [vp, C.POINTER(C.c_uint64), C.c_size_t, C.POINTER(C.c_uint64)],
             "vbmc_verify_range_fp64_noalloc": [vp, vp, C.c_int32, vp, C.c_int32, C.c_uint64,
                                                C.c_uint64, C.POINTER(_NoallocOut), vp],
+            "vbmc_search_query": [vp, C.POINTER(_Query), C.c_int32, C.POINTER(C.c_int32),
+                                  C.POINTER(_Options), vp, C.POINTER(_SearchOut), vp],
+            "vbmc_tile_counts": [vp, C.c_int32, C.POINTER(C.c_uint64)],
+            "vbmc_proposal_create": [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                     C.c_uint64, C.POINTER(vp)],
+            "vbmc_proposal_free": [vp],
+            "vbmc_proposal_features": [vp, vp, vp, vp, vp, C.c_int32, C.c_int32, vp, vp, vp, vp],
+            "vbmc_proposal_scores": [vp, vp, C.c_int32, vp, vp, vp],
+            "vbmc_proposal_grads": [vp, vp, vp, C.c_int32, C.c_int32, C.POINTER(C.c_float), vp],
+            "vbmc_proposal_train_step": [vp, vp, vp, C.c_int32, C.c_float, C.c_float,
+                                         C.POINTER(C.c_float), vp],
+            "vbmc_proposal_params": [vp, C.c_int32, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                     C.POINTER(C.c_float), C.POINTER(C.c_float)],
+            "vbmc_proposal_set_params": [vp, C.c_int32, C.POINTER(C.c_float),
+                                         C.POINTER(C.c_float)],
         }
         for name, args in sig.items():
             f = getattr(L, name)
@@ -323,3 +343,108 @@ def verify_range_fp64_noalloc(net: Net, d_image, d_pixels, k: int, lo: int, hi: 
                                                 int(d_pixels.numel()),
                                                 C.c_void_p(d_pixels.data_ptr()), int(k), int(lo),
                                                 int(hi), C.byref(out), C.c_void_p(st)))
+
+
+def search_query(net: Net, res: Result, image, pixels, k: int, order, precision="bf16",
+                 coverage: bool = False, bitmap: bool = False,
+                 stream: int | None = None) -> dict:
+    """vbmc_search_query: check the len(order) contiguous tiles of the query's space in
+    the given order and stop after the first tile holding a witness. Returns the
+    search record merged into the result summary."""
+    img = np.ascontiguousarray(image, dtype=np.uint8)
+    pix = np.ascontiguousarray(pixels, dtype=np.int32)
+    o = np.ascontiguousarray(order, dtype=np.int32)
+    q = _Query(_ptr(img, C.c_uint8), len(pix), _ptr(pix, C.c_int32), int(k), 0, 0)
+    opt = _options(precision, coverage, bitmap)
+    out = _SearchOut()
+    st = current_stream() if stream is None else stream
+    _check(lib().vbmc_search_query(net.h, C.byref(q), len(o), _ptr(o, C.c_int32), C.byref(opt),
+                                   res.h, C.byref(out), C.c_void_p(st)))
+    d = result_summary(res)
+    d.update(tiles_checked=out.tiles_checked,
+             witness_tile=None if out.witness_tile < 0 else out.witness_tile,
+             points_checked=int(out.points_checked), ms_to_witness=out.ms_to_witness)
+    return d
+
+
+def tile_counts(res: Result, n_tiles: int) -> np.ndarray:
+    """vbmc_tile_counts: adversarial points per contiguous tile of the last full check."""
+    out = np.zeros(n_tiles, np.uint64)
+    _check(lib().vbmc_tile_counts(res.h, int(n_tiles), _ptr(out, C.c_uint64)))
+    return out.astype(np.int64)
+
+
+def proposal_features(net: Net, d_images, d_pixels, d_s, d_k, d_features, d_reach=None,
+                      d_margin=None, stream: int | None = None) -> None:
+    """vbmc_proposal_features on CUDA tensors: images uint8 [nq, H0], pixels int32
+    [nq, stride], s and k int32 [nq]; features float32 [nq, 3 * H0]; optional reach
+    and margin float32 [nq]."""
+    nq, stride = int(d_pixels.shape[0]), int(d_pixels.shape[1])
+    st = current_stream() if stream is None else stream
+    _check(lib().vbmc_proposal_features(
+        net.h, C.c_void_p(d_images.data_ptr()), C.c_void_p(d_pixels.data_ptr()),
+        C.c_void_p(d_s.data_ptr()), C.c_void_p(d_k.data_ptr()), stride, nq,
+        C.c_void_p(d_features.data_ptr()),
+        None if d_reach is None else C.c_void_p(d_reach.data_ptr()),
+        None if d_margin is None else C.c_void_p(d_margin.data_ptr()), C.c_void_p(st)))
+
+
+class Proposal:
+    """vbmc_proposal_*: the tile-ranking MLP with its GPU training step."""
+
+    def __init__(self, dims=(2352, 256, 256, 64), max_batch: int = 256, seed: int = 1):
+        self.dims = tuple(int(d) for d in dims)
+        self.max_batch = int(max_batch)
+        h = C.c_void_p()
+        _check(lib().vbmc_proposal_create(*self.dims, self.max_batch, int(seed), C.byref(h)))
+        self.h = h
+
+    def scores(self, d_X, d_scores, d_order=None, stream: int | None = None) -> None:
+        st = current_stream() if stream is None else stream
+        _check(lib().vbmc_proposal_scores(
+            self.h, C.c_void_p(d_X.data_ptr()), int(d_X.shape[0]), C.c_void_p(d_scores.data_ptr()),
+            None if d_order is None else C.c_void_p(d_order.data_ptr()), C.c_void_p(st)))
+
+    def grads(self, d_X, d_T, bf16: bool = False, stream: int | None = None) -> float:
+        loss = C.c_float()
+        st = current_stream() if stream is None else stream
+        _check(lib().vbmc_proposal_grads(self.h, C.c_void_p(d_X.data_ptr()),
+                                         C.c_void_p(d_T.data_ptr()), int(d_X.shape[0]),
+                                         int(bool(bf16)), C.byref(loss), C.c_void_p(st)))
+        return loss.value
+
+    def train_step(self, d_X, d_T, lr: float, weight_decay: float = 0.0,
+                   want_loss: bool = False, stream: int | None = None):
+        loss = C.c_float()
+        st = current_stream() if stream is None else stream
+        _check(lib().vbmc_proposal_train_step(
+            self.h, C.c_void_p(d_X.data_ptr()), C.c_void_p(d_T.data_ptr()), int(d_X.shape[0]),
+            float(lr), float(weight_decay), C.byref(loss) if want_loss else None, C.c_void_p(st)))
+        return loss.value if want_loss else None
+
+    def params(self, layer: int) -> dict:
+        n_out, n_in = self.dims[layer], self.dims[layer - 1]
+        W = np.zeros((n_out, n_in), np.float32)
+        b = np.zeros(n_out, np.float32)
+        gW = np.zeros((n_out, n_in), np.float32)
+        gb = np.zeros(n_out, np.float32)
+        _check(lib().vbmc_proposal_params(self.h, layer, _ptr(W, C.c_float), _ptr(b, C.c_float),
+                                          _ptr(gW, C.c_float), _ptr(gb, C.c_float)))
+        return {"W": W, "b": b, "gW": gW, "gb": gb}
+
+    def set_params(self, layer: int, W, b) -> None:
+        Wc = np.ascontiguousarray(W, dtype=np.float32)
+        bc = np.ascontiguousarray(b, dtype=np.float32)
+        assert Wc.shape == (self.dims[layer], self.dims[layer - 1]) and bc.shape == (self.dims[layer],)
+        _check(lib().vbmc_proposal_set_params(self.h, layer, _ptr(Wc, C.c_float), _ptr(bc, C.c_float)))
+
+    def free(self):
+        if getattr(self, "h", None) is not None and _lib is not None:
+            lib().vbmc_proposal_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass

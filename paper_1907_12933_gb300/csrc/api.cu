@@ -455,13 +455,20 @@ std::vector<unsigned long long> tile_prefix(const NetView& v, int precision, Que
     return tp;
 }
 
+// Stages of enqueue_passes: per-query set-up (prologue and tensor-core column
+// classes) and the passes over the points of [lo, hi).
+enum { STAGE_SETUP = 1, STAGE_PASSES = 2, STAGE_ALL = 3 };
+
 // Every pass for nq queries whose views (and tile prefix) are already on the
-// device. ev: start, after the prologue, after the first pass, end.
+// device. ev: start, after the prologue, after the first pass, end. The set-up
+// stage resets the counters and clears the masks and the verdict bitmap over
+// [0, hi); everything else it computes depends on the box, not on [lo, hi),
+// so one set-up over the whole space serves passes over any sub-ranges.
 vbmc_status enqueue_passes(vbmc_net* net, QueryView* d_qs, const QueryView* hq, int nq,
                            const unsigned long long* d_tp, unsigned long long ntiles,
                            unsigned long long* d_qcount, QEntry* const* d_queue,
                            unsigned long long cap, const cudaEvent_t* ev, const vbmc_options& opt,
-                           cudaStream_t st, bool capturing = false) {
+                           cudaStream_t st, bool capturing = false, int stages = STAGE_ALL) {
     const NetView& v = net->v;
     // inside a stream capture an event record must be an explicit graph node
     const unsigned evflag = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
@@ -472,10 +479,19 @@ vbmc_status enqueue_passes(vbmc_net* net, QueryView* d_qs, const QueryView* hq, 
         max_sr = std::max(max_sr, hq[i].s * hq[i].R);
         any = any || hq[i].hi > hq[i].lo;
     }
+    const bool tensor = opt.precision != VBMC_PREC_FP64 && opt.precision != VBMC_PREC_FP32;
     VB_CUDA(cudaMemsetAsync(d_qcount, 0, sizeof(unsigned long long) * 4, st));
     VB_CUDA(record(ev[0]));
-    launch_prologue(v, d_qs, nq, max_sr, st);
+    if (stages & STAGE_SETUP) launch_prologue(v, d_qs, nq, max_sr, st);
     VB_CUDA(record(ev[1]));
+    if (tensor && any) {
+        if (!tc_supported(v, opt.precision))
+            return fail(VBMC_ERR_UNSUPPORTED, "tensor-core screen does not support this net/precision");
+        vbmc_status sst = tc_build(net->tc, v, net->hW, net->hb, opt.precision);
+        if (sst != VBMC_OK) return fail(sst, "tensor-core set-up failed");
+        if (stages & STAGE_SETUP) tc_launch_query_setup(net->tc, v, d_qs, nq, opt.precision, st);
+    }
+    if (!(stages & STAGE_PASSES)) return VBMC_OK;
     // queue levels: 0 tensor split pass, 1 FP32 pass, 2 double-float pass, 3 FP64 pass
     Queue qsplit{d_queue[0], d_qcount + 0, cap};
     Queue q32{d_queue[1], d_qcount + 1, cap};
@@ -492,13 +508,8 @@ vbmc_status enqueue_passes(vbmc_net* net, QueryView* d_qs, const QueryView* hq, 
             launch_screen_simt(v, d_qs, nq, d_tp, ntiles, nullptr, nullptr, 0, qdf, 2, net->n_sm, st);
             VB_CUDA(record(ev[2]));
         } else {
-            if (!tc_supported(v, opt.precision))
-                return fail(VBMC_ERR_UNSUPPORTED, "tensor-core screen does not support this net/precision");
-            vbmc_status sst = tc_build(net->tc, v, net->hW, net->hb, opt.precision);
-            if (sst != VBMC_OK) return fail(sst, "tensor-core set-up failed");
-            tc_launch_query_setup(net->tc, v, d_qs, nq, opt.precision, st);
             // one query: screen -> split tensor pass -> FP32; many: screen -> FP32 directly
-            sst = tc_launch_screen(net->tc, v, d_qs, nq, d_tp, ntiles, opt.precision,
+            vbmc_status sst = tc_launch_screen(net->tc, v, d_qs, nq, d_tp, ntiles, opt.precision,
                                    nq == 1 ? qsplit : q32, nq == 1 ? 0 : 1, net->n_sm, st);
             if (sst != VBMC_OK) return fail(sst, "tensor-core screen launch failed");
             VB_CUDA(record(ev[2]));
@@ -892,4 +903,125 @@ extern "C" vbmc_status vbmc_verify_batch(vbmc_net* net, const vbmc_query* querie
         if (r->last_status != VBMC_OK && result == VBMC_OK) result = r->last_status;
     }
     return result;
+}
+
+extern "C" vbmc_status vbmc_search_query(vbmc_net* net, const vbmc_query* q, int32_t n_tiles,
+                                         const int32_t* order, const vbmc_options* opt, vbmc_result* res,
+                                         vbmc_search_out* out, void* stream) {
+    if (!net || !q || !res || !opt || !order || !q->image || (!q->pixels && q->s > 0))
+        return fail(VBMC_ERR_ARG, "null argument");
+    if (res->net != net) return fail(VBMC_ERR_ARG, "result belongs to another net");
+    if (n_tiles < 1) return fail(VBMC_ERR_ARG, "n_tiles must be positive");
+    if (res->pending) {
+        vbmc_status st = finish(res);
+        if (st != VBMC_OK) return st;
+    }
+    uint64_t n, h;
+    vbmc_status st = check_query_shape(res, q->s, q->k, 0, 0, opt, &n, &h);
+    if (st != VBMC_OK) return st;
+    if (q->lo != 0 || (q->hi != 0 && q->hi != n))
+        return fail(VBMC_ERR_ARG, "a search covers the whole space: lo and hi must be 0");
+    std::vector<char> seen((size_t)n_tiles, 0);
+    for (int i = 0; i < n_tiles; ++i) {
+        if (order[i] < 0 || order[i] >= n_tiles || seen[order[i]])
+            return fail(VBMC_ERR_ARG, "order is not a permutation of the tiles");
+        seen[order[i]] = 1;
+    }
+    const int H0 = net->v.dims[0];
+    for (int p = 0; p < q->s; ++p) {
+        if (q->pixels[p] < 0 || q->pixels[p] >= H0) return fail(VBMC_ERR_ARG, "pixel index out of range");
+        for (int r = 0; r < p; ++r)
+            if (q->pixels[r] == q->pixels[p]) return fail(VBMC_ERR_ARG, "duplicate pixel index");
+    }
+    cudaStream_t sq = (cudaStream_t)stream;
+    VB_CUDA(cudaMemcpyAsync(res->d_image, q->image, H0, cudaMemcpyHostToDevice, sq));
+    if (q->s > 0)
+        VB_CUDA(cudaMemcpyAsync(res->d_pix_in, q->pixels, sizeof(int32_t) * q->s, cudaMemcpyHostToDevice, sq));
+    const unsigned long long cap = std::max<uint64_t>(1, res->caps.queue_cap);
+    // set-up once over the whole space: counters, cleared masks and bitmap, tables
+    QueryView qv = make_view(res, res->d_image, res->d_pix_in, q->s, q->k, 0, n, n, *opt, 0);
+    std::vector<unsigned long long> tp = tile_prefix(net->v, opt->precision, &qv, 1);
+    VB_CUDA(cudaMemcpyAsync(res->d_q, &qv, sizeof(QueryView), cudaMemcpyHostToDevice, sq));
+    const cudaEvent_t ev_set[4] = {res->ev0, res->ev_pro, res->ev_pro, res->ev_pro};
+    st = enqueue_passes(net, res->d_q, &qv, 1, res->d_tp, tp[1], res->d_qcount, res->d_queue, cap, ev_set,
+                        *opt, sq, false, STAGE_SETUP);
+    if (st != VBMC_OK) return st;
+    const cudaEvent_t ev_tile[4] = {res->ev_scr, res->ev_scr, res->ev_scr, res->ev1};
+    const uint64_t tsize = (n + n_tiles - 1) / n_tiles;
+    vbmc_search_out so{0, -1, 0, 0.0};
+    vbmc_status run = VBMC_OK;
+    bool any_tile = false;
+    for (int i = 0; i < n_tiles; ++i) {
+        const uint64_t lo = (uint64_t)order[i] * tsize;
+        const uint64_t hi = std::min<uint64_t>(n, lo + tsize);
+        so.tiles_checked += 1;
+        if (lo >= hi) continue;
+        qv.lo = lo;
+        qv.hi = hi;
+        tp = tile_prefix(net->v, opt->precision, &qv, 1);
+        VB_CUDA(cudaMemcpyAsync(res->d_q, &qv, sizeof(QueryView), cudaMemcpyHostToDevice, sq));
+        VB_CUDA(cudaMemcpyAsync(res->d_tp, tp.data(), sizeof(unsigned long long) * 2, cudaMemcpyHostToDevice,
+                                sq));
+        st = enqueue_passes(net, res->d_q, &qv, 1, res->d_tp, tp[1], res->d_qcount, res->d_queue, cap, ev_tile,
+                            *opt, sq, false, STAGE_PASSES);
+        if (st != VBMC_OK) return st;
+        any_tile = true;
+        VB_CUDA(cudaMemcpyAsync(res->h_cnt, res->d_cnt, sizeof(Counters), cudaMemcpyDeviceToHost, sq));
+        VB_CUDA(cudaStreamSynchronize(sq));
+        so.points_checked += hi - lo;
+        run = counters_status(*res->h_cnt);
+        if (run != VBMC_OK) break;
+        if (res->h_cnt->n_adv > 0) {
+            so.witness_tile = order[i];
+            break;
+        }
+    }
+    if (!any_tile) {
+        VB_CUDA(cudaEventRecord(res->ev1, sq));
+        VB_CUDA(cudaMemcpyAsync(res->h_cnt, res->d_cnt, sizeof(Counters), cudaMemcpyDeviceToHost, sq));
+    }
+    VB_CUDA(cudaStreamSynchronize(sq));
+    float ms = 0.f, ms_p = 0.f;
+    cudaEventElapsedTime(&ms, res->ev0, res->ev1);
+    cudaEventElapsedTime(&ms_p, res->ev0, res->ev_pro);
+    so.ms_to_witness = ms;
+    res->last_stream = sq;
+    res->pending = false;
+    res->have_result = true;
+    res->s = q->s;
+    res->k = q->k;
+    res->lo = 0;
+    res->hi = n;
+    res->n_space = n;
+    res->opt = *opt;
+    res->image.assign(q->image, q->image + H0);
+    res->pixels.assign(q->pixels, q->pixels + q->s);
+    fill_summary(res, *res->h_cnt, ms, ms_p, 0.f);
+    res->sum.n_points = so.points_checked;
+    if (run == VBMC_OK) run = counters_status(*res->h_cnt);
+    if (run != VBMC_OK) res->sum.verdict = VBMC_PARTIAL;
+    res->last_status = run;
+    if (out) *out = so;
+    return run;
+}
+
+extern "C" vbmc_status vbmc_tile_counts(vbmc_result* res, int32_t n_tiles, uint64_t* counts) {
+    if (!res || !counts) return fail(VBMC_ERR_ARG, "null argument");
+    if (n_tiles < 1) return fail(VBMC_ERR_ARG, "n_tiles must be positive");
+    vbmc_status st = finish(res);
+    if (st != VBMC_OK) return st;
+    if (!res->opt.bitmap) return fail(VBMC_ERR_STATE, "bitmap was off for the last call");
+    if (res->lo != 0 || res->hi != res->n_space)
+        return fail(VBMC_ERR_STATE, "the last call did not cover the whole space");
+    unsigned long long* d = nullptr;
+    VB_CUDA(cudaMalloc(&d, sizeof(unsigned long long) * n_tiles));
+    launch_tile_counts(res->hq.bitmap, res->n_space, n_tiles, d, res->last_stream);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(counts, d, sizeof(unsigned long long) * n_tiles, cudaMemcpyDeviceToHost,
+                            res->last_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(res->last_stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(VBMC_ERR_CUDA, cudaGetErrorString(e));
+    return VBMC_OK;
 }

@@ -54,4 +54,9 @@ void launch_df(const NetView& net, const QueryView* d_qs, const QEntry* gather,
                const unsigned long long* gather_count, unsigned long long gather_cap, Queue out,
                int out_level, int n_sm, cudaStream_t st);
 
+// Adversarial points of each of n_tiles contiguous tiles of [0, n) (tiles of
+// ceil(n / n_tiles) points) from a verdict bitmap, into d_counts[n_tiles].
+void launch_tile_counts(const uint32_t* d_bitmap, unsigned long long n, int n_tiles,
+                        unsigned long long* d_counts, cudaStream_t st);
+
 }  // namespace vbmc

@@ -15,4 +15,5 @@ from .gen import (  # noqa: F401
     make_queries,
     WORKLOADS,
     workload,
+    proposal_candidates,
 )

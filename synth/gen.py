@@ -117,8 +117,11 @@ WORKLOADS = {
     "mlp784x256x256_relu_batch4096": dict(seed=1004, dims=[784, 256, 256, 10], act="relu",
                                           w_var=2.0, bias="zero", nq=4096,
                                           s_range=(2, 6), k_range=(3, 10)),
-    "proposal_mlp784x512x512_s6k7": dict(seed=1005, dims=[784, 512, 512, 10], act="relu",
-                                         w_var=2.0, bias="zero", s=6, k=7),
+    # the 784-512-512-10 net above (net_seed 1002); training queries from seed
+    # 1005, held-out queries from seed 1006; 64 contiguous tiles per query
+    "proposal_mlp784x512x512_s6k7": dict(seed=1005, net_seed=1002, test_seed=1006,
+                                         dims=[784, 512, 512, 10], act="relu", w_var=2.0,
+                                         bias="zero", s=6, k=7, n_tiles=64),
 }
 
 
@@ -126,7 +129,8 @@ def workload(name: str, **override) -> dict:
     """Net plus query (or queries) of a named workload; keyword overrides shrink it."""
     cfg = dict(WORKLOADS[name])
     cfg.update(override)
-    net = make_net(cfg["seed"], cfg["dims"], cfg["act"], cfg["w_var"], cfg["bias"])
+    net = make_net(cfg.get("net_seed", cfg["seed"]), cfg["dims"], cfg["act"], cfg["w_var"],
+                   cfg["bias"])
     out = {"name": name, "net": net, "cfg": cfg}
     if "nq" in cfg:
         out["queries"] = make_queries(cfg["seed"], cfg["nq"], cfg["dims"][0],
@@ -134,3 +138,12 @@ def workload(name: str, **override) -> dict:
     else:
         out["query"] = make_query(cfg["seed"], 0, cfg["dims"][0], cfg["s"], cfg["k"])
     return out
+
+
+def proposal_candidates(split: str, n: int, start: int = 0, **override) -> list:
+    """Candidate queries of the tile-proposal workload: 'train' or 'test' split,
+    queries start .. start + n - 1, each with its own image and s pixels."""
+    cfg = dict(WORKLOADS["proposal_mlp784x512x512_s6k7"])
+    cfg.update(override)
+    seed = cfg["seed"] if split == "train" else cfg["test_seed"]
+    return [make_query(seed, i, cfg["dims"][0], cfg["s"], cfg["k"]) for i in range(start, start + n)]
