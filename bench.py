@@ -49,6 +49,13 @@ def parse():
     ap.add_argument("--nq", type=int, default=512,
                     help="batched workload: number of queries (the full workload has 4096)")
     ap.add_argument("--graph", action="store_true", help="batched workload: CUDA-graph launch")
+    ap.add_argument("--schedule", default="small_first", choices=["given", "small_first"],
+                    help="batched workload: tile order over the queries")
+    ap.add_argument("--s", type=int, default=None,
+                    help="override the workload's pixel count (smaller cases for profiling)")
+    ap.add_argument("--k", type=int, default=None, help="override the workload's step bound")
+    ap.add_argument("--queue-cap", type=int, default=1 << 27,
+                    help="batched workload: capacity of each shared recheck queue (entries)")
     ap.add_argument("--train-queries", type=int, default=1500,
                     help="tile-proposal workload: selected training queries (exact labels)")
     ap.add_argument("--test-queries", type=int, default=200,
@@ -171,11 +178,13 @@ def main_batch(a):
     net_d, cfg, qs = w["net"], w["cfg"], w["queries"]
     pts = sum((2 * q["k"] + 1) ** len(q["pixels"]) for q in qs)
     vnet = vb.Net(net_d)
+    # one-time launch-shape tuning, cached next to the build (not part of a step)
+    tuning = vb.autotune(vnet, os.path.join(ROOT, "paper_1907_12933_gb300", "_build", "tuning.jsonl"))
     res = vb.result_create_batch(vnet, len(qs), max_points=0, max_s=max(len(q["pixels"]) for q in qs),
-                                 max_k=max(q["k"] for q in qs), queue_cap=1 << 24)
+                                 max_k=max(q["k"] for q in qs), queue_cap=a.queue_cap)
     for _ in range(a.warmup):
         vb.verify_batch(vnet, res, qs, precision=a.precision, coverage=True, bitmap=False,
-                        graph=a.graph)
+                        graph=a.graph, schedule=a.schedule)
     clocks = Clocks()
     clocks.start()
     times, ttv = [], []
@@ -183,7 +192,7 @@ def main_batch(a):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sums = vb.verify_batch(vnet, res, qs, precision=a.precision, coverage=True, bitmap=False,
-                               graph=a.graph)
+                               graph=a.graph, schedule=a.schedule)
         times.append(time.perf_counter() - t0)
         ttv = [x["ms_to_verdict"] for x in sums]
     ck = clocks.stop(torch.cuda.current_device())
@@ -196,7 +205,9 @@ def main_batch(a):
             "data": "synthetic",
             "config": {"workload": a.workload, "dims": cfg["dims"], "queries": len(qs),
                        "points_total": pts, "s_range": cfg["s_range"], "k_range": cfg["k_range"],
-                       "graph": a.graph, "precision": a.precision},
+                       "graph": a.graph, "precision": a.precision, "schedule": a.schedule,
+                       "tuning": {k: tuning[k] for k in ("simt_range", "simt_range_ctas", "simt_gather",
+                                                         "simt_gather_ctas", "df_ctas", "from_cache")}},
             "e2e": {"value": pts / (ms / 1000.0), "unit": UNIT,
                     "h2d_bytes_per_step": len(qs) * (cfg["dims"][0] + 24),
                     "d2h_bytes_per_step": len(qs) * 96},
@@ -206,7 +217,9 @@ def main_batch(a):
                          "safe": sum(x["verdict"] == "SAFE" for x in sums),
                          "ties_only": sum(x["verdict"] == "TIES_ONLY" for x in sums),
                          "n_recheck": [sum(x["n_recheck"][i] for x in sums) for i in range(4)]},
-            "gpu_launches": a.steps * launches_per_step(a.precision, len(cfg["dims"]) - 1, batch=True)}
+            # the smallest-first schedule runs min(8, queries) waves, each a full chain of passes
+            "gpu_launches": a.steps * launches_per_step(a.precision, len(cfg["dims"]) - 1, batch=True)
+            * (min(8, len(qs)) if a.schedule == "small_first" else 1)}
     if ck:
         line["clocks"] = ck
     print(json.dumps(line))
@@ -318,7 +331,8 @@ def main():
         return main_proposal(a)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    w = synth.workload(a.workload)
+    over = {key: val for key, val in (("s", a.s), ("k", a.k)) if val is not None}
+    w = synth.workload(a.workload, **over)
     net_d, cfg = w["net"], w["cfg"]
     q = rank_query(w, rank)
     s, k = len(q["pixels"]), q["k"]

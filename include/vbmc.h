@@ -110,12 +110,20 @@ typedef struct {
     uint64_t lo, hi;
 } vbmc_query;
 
+enum { VBMC_SCHED_GIVEN = 0, VBMC_SCHED_SMALL_FIRST = 1 };
+
 typedef struct {
     int32_t precision;  /* vbmc_precision                                  */
     int32_t coverage;   /* nonzero: compute sign-change and SS masks       */
     int32_t bitmap;     /* nonzero: record the per-point verdict bitmap    */
     int32_t graph;      /* batch: nonzero captures the passes into one CUDA
                          * graph and launches it                          */
+    int32_t schedule;   /* batch: VBMC_SCHED_GIVEN checks all queries' tiles
+                         * in the given order, then their rechecks.
+                         * VBMC_SCHED_SMALL_FIRST sorts the queries by point
+                         * count (shortest job first) and runs them in up to
+                         * 8 waves of about equal work, each a full chain of
+                         * passes: a query is final when its wave ends   */
 } vbmc_options;
 
 /* Capacities fixed when a result handle is created. */
@@ -220,6 +228,31 @@ vbmc_status vbmc_get_ties(vbmc_result *res, uint64_t *idx, size_t cap, uint64_t 
 
 /* Message for the last failing call of this thread. */
 const char *vbmc_last_error(void);
+
+/* ---- Launch-shape autotuning. The FP32 pass (over index ranges, and over
+ * queued points) comes in four variants that hold layers up to 32, 256, 512
+ * and 1024 neurons with 128, 128, 64 and 32 points per tile; it and the
+ * double-float pass also take a number of CTAs per SM. vbmc_autotune times
+ * every variant that fits the net, at 1, 2 and 4 CTAs per SM, and the
+ * double-float pass at 2, 4, 8 and 16 CTAs per SM, on a sample box of the
+ * net (s <= 4 pixels, R^s >= 2^17 points), keeps the fastest of each, and
+ * applies them to the net. With cache_path set, a file of JSON lines keyed by
+ * the net's shape, activation, SM count and compute capability is read first
+ * (a hit skips the timing) and updated after a measurement. The choice never
+ * changes results, only speed. Blocks until done; allocates a temporary
+ * result workspace. */
+typedef struct {
+    int32_t simt_range, simt_range_ctas;   /* FP32 pass over ranges: variant, CTAs/SM */
+    int32_t simt_gather, simt_gather_ctas; /* FP32 pass over queued points            */
+    int32_t df_ctas;                       /* double-float pass CTAs/SM               */
+    int32_t from_cache;                    /* 1: read from cache_path                 */
+    double ms_range, ms_gather, ms_df;     /* best times measured (0 from the cache)  */
+} vbmc_tuning;
+
+vbmc_status vbmc_autotune(vbmc_net *net, const char *cache_path, vbmc_tuning *out);
+
+/* Apply given launch shapes (0 in a field: the built-in choice). */
+vbmc_status vbmc_set_tuning(vbmc_net *net, const vbmc_tuning *t);
 
 /* ---- Tile-ordered search for a first witness.
  * The index space [0, n) of a query (n = R^s) is cut into n_tiles contiguous

@@ -42,7 +42,10 @@ class _Query(C.Structure):
 
 class _Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("coverage", C.c_int32), ("bitmap", C.c_int32),
-                ("graph", C.c_int32)]
+                ("graph", C.c_int32), ("schedule", C.c_int32)]
+
+
+SCHEDULES = {"given": 0, "small_first": 1}
 
 
 class _Caps(C.Structure):
@@ -62,6 +65,13 @@ class _Summary(C.Structure):
 class _SearchOut(C.Structure):
     _fields_ = [("tiles_checked", C.c_int32), ("witness_tile", C.c_int32),
                 ("points_checked", C.c_uint64), ("ms_to_witness", C.c_double)]
+
+
+class _Tuning(C.Structure):
+    _fields_ = [("simt_range", C.c_int32), ("simt_range_ctas", C.c_int32),
+                ("simt_gather", C.c_int32), ("simt_gather_ctas", C.c_int32),
+                ("df_ctas", C.c_int32), ("from_cache", C.c_int32), ("ms_range", C.c_double),
+                ("ms_gather", C.c_double), ("ms_df", C.c_double)]
 
 
 class _NoallocOut(C.Structure):
@@ -107,6 +117,8 @@ def lib():
             "vbmc_search_query": [vp, C.POINTER(_Query), C.c_int32, C.POINTER(C.c_int32),
                                   C.POINTER(_Options), vp, C.POINTER(_SearchOut), vp],
             "vbmc_tile_counts": [vp, C.c_int32, C.POINTER(C.c_uint64)],
+            "vbmc_autotune": [vp, C.c_char_p, C.POINTER(_Tuning)],
+            "vbmc_set_tuning": [vp, C.POINTER(_Tuning)],
             "vbmc_proposal_create": [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                      C.c_uint64, C.POINTER(vp)],
             "vbmc_proposal_free": [vp],
@@ -223,9 +235,10 @@ def result_create_batch(net: Net, nq: int, max_points: int = 0, max_s: int = MAX
     return out
 
 
-def _options(precision, coverage, bitmap, graph=False):
+def _options(precision, coverage, bitmap, graph=False, schedule="given"):
     p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
-    return _Options(p, int(bool(coverage)), int(bool(bitmap)), int(bool(graph)))
+    sc = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
+    return _Options(p, int(bool(coverage)), int(bool(bitmap)), int(bool(graph)), sc)
 
 
 def _summary_dict(s: _Summary) -> dict:
@@ -265,8 +278,9 @@ def verify_query_device(net: Net, res: Result, d_image, d_pixels, k: int, lo: in
 
 def verify_batch(net: Net, results: list, queries: list, precision="fp32",
                  coverage: bool = True, bitmap: bool = False, graph: bool = False,
-                 stream: int | None = None) -> list:
-    """vbmc_verify_batch: queries are dicts with image, pixels, k (and optional lo, hi)."""
+                 schedule="given", stream: int | None = None) -> list:
+    """vbmc_verify_batch: queries are dicts with image, pixels, k (and optional lo, hi);
+    schedule 'given' or 'small_first' (tiles of smaller spaces first)."""
     keep = []
     qs = (_Query * len(queries))()
     for i, qd in enumerate(queries):
@@ -276,7 +290,7 @@ def verify_batch(net: Net, results: list, queries: list, precision="fp32",
         qs[i] = _Query(_ptr(img, C.c_uint8), len(pix), _ptr(pix, C.c_int32), int(qd["k"]),
                        int(qd.get("lo", 0)), int(qd.get("hi", 0)))
     hs = (C.c_void_p * len(results))(*[r.h for r in results])
-    opt = _options(precision, coverage, bitmap, graph)
+    opt = _options(precision, coverage, bitmap, graph, schedule)
     st = current_stream() if stream is None else stream
     _check(lib().vbmc_verify_batch(net.h, qs, len(queries), C.byref(opt), hs, C.c_void_p(st)))
     return [result_summary(r) for r in results]
@@ -343,6 +357,21 @@ def verify_range_fp64_noalloc(net: Net, d_image, d_pixels, k: int, lo: int, hi: 
                                                 int(d_pixels.numel()),
                                                 C.c_void_p(d_pixels.data_ptr()), int(k), int(lo),
                                                 int(hi), C.byref(out), C.c_void_p(st)))
+
+
+def autotune(net: Net, cache_path: str | None = None) -> dict:
+    """vbmc_autotune: time the FP32 and double-float pass launch shapes on a sample
+    box of the net, apply the fastest, and cache them (JSON lines) in cache_path."""
+    t = _Tuning()
+    _check(lib().vbmc_autotune(net.h, None if cache_path is None else cache_path.encode(),
+                               C.byref(t)))
+    return {f: getattr(t, f) for f, _ in _Tuning._fields_}
+
+
+def set_tuning(net: Net, **fields) -> None:
+    """vbmc_set_tuning: apply launch shapes (missing fields: the built-in choice)."""
+    t = _Tuning(**{k: int(v) for k, v in fields.items() if k in dict(_Tuning._fields_)})
+    _check(lib().vbmc_set_tuning(net.h, C.byref(t)))
 
 
 def search_query(net: Net, res: Result, image, pixels, k: int, order, precision="bf16",

@@ -79,7 +79,8 @@ struct vbmc_net {
 struct BatchArena {
     int nq = 0;
     int refs = 0;
-    QueryView* d_qs = nullptr;
+    QueryView* d_qs = nullptr;      // member views by slot (what the result handles read)
+    QueryView* d_qs_run = nullptr;  // the same views in the batch call's schedule order
     Counters* d_cnt = nullptr;
     Counters* h_cnt = nullptr;  // pinned
     unsigned long long* d_tp = nullptr;
@@ -89,6 +90,7 @@ struct BatchArena {
     QEntry* d_queue[4] = {nullptr, nullptr, nullptr, nullptr};
     uint64_t queue_cap = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t evw = nullptr;       // marks between waves (not read)
     cudaStream_t gstream = nullptr;  // graph capture needs a capturable (non-legacy) stream
     cudaEvent_t gev = nullptr;
     std::vector<void*> owned;
@@ -356,6 +358,7 @@ void arena_release(BatchArena* a) {
     if (a->h_cnt) cudaFreeHost(a->h_cnt);
     for (cudaEvent_t ev : a->ev)
         if (ev) cudaEventDestroy(ev);
+    if (a->evw) cudaEventDestroy(a->evw);
     if (a->gev) cudaEventDestroy(a->gev);
     if (a->gstream) cudaStreamDestroy(a->gstream);
     delete a;
@@ -380,14 +383,16 @@ extern "C" vbmc_status vbmc_result_create_batch(const vbmc_net* net, const vbmc_
     };
     ar->stage_stride = ((size_t)net->v.dims[0] + sizeof(int32_t) * kMaxS + 15) & ~size_t(15);
     A(&ar->d_qs, (size_t)nq);
+    A(&ar->d_qs_run, (size_t)nq);
     A(&ar->d_cnt, (size_t)nq);
-    A(&ar->d_tp, (size_t)nq + 1);
+    A(&ar->d_tp, 2 * (size_t)nq + 2);  // one tile prefix per wave, back to back
     A(&ar->d_stage, ar->stage_stride * (size_t)nq);
     A(&ar->d_qcount, 4);
     ar->queue_cap = std::max<uint64_t>(1, caps->queue_cap);
     for (int i = 0; i < 4; ++i) A(&ar->d_queue[i], (size_t)ar->queue_cap);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ar->h_cnt, sizeof(Counters) * (size_t)nq);
     for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&ar->ev[i]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ar->evw);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ar->gstream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ar->gev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
@@ -846,18 +851,72 @@ extern "C" vbmc_status vbmc_verify_batch(vbmc_net* net, const vbmc_query* querie
         nsp[i] = n;
     }
     std::vector<unsigned long long> tp = tile_prefix(v, opt->precision, hq.data(), nq);
+    // run order: the passes see the views in schedule order (each view still
+    // points at its own result's counters and buffers; queue entries index
+    // the run order)
+    std::vector<int> perm((size_t)nq);
+    for (int i = 0; i < nq; ++i) perm[i] = i;
+    if (opt->schedule == VBMC_SCHED_SMALL_FIRST)
+        std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) {
+            return hq[a].hi - hq[a].lo < hq[b].hi - hq[b].lo;
+        });
+    std::vector<QueryView> hrun((size_t)nq);
+    for (int j = 0; j < nq; ++j) {
+        hrun[j] = hq[perm[j]];
+        hrun[j].qid = j;
+    }
+    // waves: the smallest-first schedule runs the queries in up to 8 waves of
+    // about equal work, each its own chain of passes, so the queries of an early
+    // wave are final when that wave ends (and each wave's rechecks queue alone)
+    std::vector<int> wave_at{0};
+    if (opt->schedule == VBMC_SCHED_SMALL_FIRST) {
+        unsigned long long total = 0, acc = 0;
+        for (int j = 0; j < nq; ++j) total += hrun[j].hi - hrun[j].lo;
+        const int W = std::min(8, nq);
+        for (int j = 0; j < nq; ++j) {
+            acc += hrun[j].hi - hrun[j].lo;
+            const int w = (int)wave_at.size();
+            if (w < W && j + 1 < nq && (double)acc >= (double)total * w / W) wave_at.push_back(j + 1);
+        }
+    }
+    wave_at.push_back(nq);
+    const int n_waves = (int)wave_at.size() - 1;
+    // per-wave tile prefixes, back to back: wave w's starts at tp_at[w]
+    std::vector<unsigned long long> tpall;
+    std::vector<size_t> tp_at;
+    std::vector<unsigned long long> wave_tiles;
+    for (int w = 0; w < n_waves; ++w) {
+        const int j0 = wave_at[w], j1 = wave_at[w + 1];
+        const std::vector<unsigned long long> t = tile_prefix(v, opt->precision, hrun.data() + j0, j1 - j0);
+        tp_at.push_back(tpall.size());
+        tpall.insert(tpall.end(), t.begin(), t.end());
+        wave_tiles.push_back(t.back());
+    }
     VB_CUDA(cudaMemcpyAsync(ar->d_stage, stage.data(), stage.size(), cudaMemcpyHostToDevice, st));
     VB_CUDA(cudaMemcpyAsync(ar->d_qs, hq.data(), sizeof(QueryView) * (size_t)nq, cudaMemcpyHostToDevice, st));
-    VB_CUDA(cudaMemcpyAsync(ar->d_tp, tp.data(), sizeof(unsigned long long) * tp.size(),
+    VB_CUDA(cudaMemcpyAsync(ar->d_qs_run, hrun.data(), sizeof(QueryView) * (size_t)nq,
                             cudaMemcpyHostToDevice, st));
+    VB_CUDA(cudaMemcpyAsync(ar->d_tp, tpall.data(), sizeof(unsigned long long) * tpall.size(),
+                            cudaMemcpyHostToDevice, st));
+    auto run_waves = [&](bool capturing) -> vbmc_status {
+        for (int w = 0; w < n_waves; ++w) {
+            const int j0 = wave_at[w], j1 = wave_at[w + 1];
+            const cudaEvent_t evs[4] = {w == 0 ? ar->ev[0] : ar->evw, w == 0 ? ar->ev[1] : ar->evw,
+                                        w == 0 ? ar->ev[2] : ar->evw, w == n_waves - 1 ? ar->ev[3] : ar->evw};
+            vbmc_status ws = enqueue_passes(net, ar->d_qs_run + j0, hrun.data() + j0, j1 - j0,
+                                            ar->d_tp + tp_at[w], wave_tiles[w], ar->d_qcount, ar->d_queue,
+                                            ar->queue_cap, evs, *opt, st, capturing);
+            if (ws != VBMC_OK) return ws;
+        }
+        return VBMC_OK;
+    };
     vbmc_status sst;
     if (opt->graph) {
         // the passes as one CUDA graph (the host-to-device copies above stay outside)
         cudaGraph_t g = nullptr;
         cudaGraphExec_t ge = nullptr;
         VB_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        sst = enqueue_passes(net, ar->d_qs, hq.data(), nq, ar->d_tp, tp[nq], ar->d_qcount, ar->d_queue,
-                             ar->queue_cap, ar->ev, *opt, st, true);
+        sst = run_waves(true);
         cudaError_t ce = cudaStreamEndCapture(st, &g);
         if (sst != VBMC_OK) {
             if (g) cudaGraphDestroy(g);
@@ -871,8 +930,7 @@ extern "C" vbmc_status vbmc_verify_batch(vbmc_net* net, const vbmc_query* querie
         cudaGraphDestroy(g);
         if (ce != cudaSuccess) return fail(VBMC_ERR_CUDA, std::string("graph: ") + cudaGetErrorString(ce));
     } else {
-        sst = enqueue_passes(net, ar->d_qs, hq.data(), nq, ar->d_tp, tp[nq], ar->d_qcount, ar->d_queue,
-                             ar->queue_cap, ar->ev, *opt, st);
+        sst = run_waves(false);
         if (sst != VBMC_OK) return sst;
     }
     VB_CUDA(cudaMemcpyAsync(ar->h_cnt, ar->d_cnt, sizeof(Counters) * (size_t)nq, cudaMemcpyDeviceToHost, st));
@@ -998,6 +1056,7 @@ extern "C" vbmc_status vbmc_search_query(vbmc_net* net, const vbmc_query* q, int
     res->pixels.assign(q->pixels, q->pixels + q->s);
     fill_summary(res, *res->h_cnt, ms, ms_p, 0.f);
     res->sum.n_points = so.points_checked;
+    res->sum.ms_to_verdict = ms;
     if (run == VBMC_OK) run = counters_status(*res->h_cnt);
     if (run != VBMC_OK) res->sum.verdict = VBMC_PARTIAL;
     res->last_status = run;
@@ -1023,5 +1082,235 @@ extern "C" vbmc_status vbmc_tile_counts(vbmc_result* res, int32_t n_tiles, uint6
     if (e == cudaSuccess) e = cudaStreamSynchronize(res->last_stream);
     cudaFree(d);
     if (e != cudaSuccess) return fail(VBMC_ERR_CUDA, cudaGetErrorString(e));
+    return VBMC_OK;
+}
+
+// ------------------------------------------------------------------ autotuning
+
+namespace {
+
+__global__ void k_fill_queue(QEntry* e, unsigned long long n, unsigned long long stride) {
+    const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    QEntry x;
+    x.t = i * stride;
+    x.q = 0;
+    x.pad = 0;
+    e[i] = x;
+}
+
+std::string tune_key(const vbmc_net* net) {
+    cudaDeviceProp p{};
+    cudaGetDeviceProperties(&p, net->device);
+    std::string k = "passes=fp32,df;dims=";
+    for (int l = 0; l <= net->v.L; ++l) k += (l ? "x" : "") + std::to_string(net->v.dims[l]);
+    k += ";act=" + std::to_string(net->v.act) + ";sm=" + std::to_string(net->n_sm) +
+         ";cc=" + std::to_string(p.major * 10 + p.minor);
+    return k;
+}
+
+bool json_int(const std::string& line, const char* name, int* v) {
+    const std::string pat = std::string("\"") + name + "\": ";
+    const size_t i = line.find(pat);
+    if (i == std::string::npos) return false;
+    *v = std::atoi(line.c_str() + i + pat.size());
+    return true;
+}
+
+// One JSON object per line: {"key": "...", "simt_range": v, ...}.
+bool cache_lookup(const char* path, const std::string& key, vbmc_tuning* t) {
+    FILE* f = path ? std::fopen(path, "r") : nullptr;
+    if (!f) return false;
+    char buf[1024];
+    bool hit = false;
+    const std::string pat = "\"key\": \"" + key + "\"";
+    while (!hit && std::fgets(buf, sizeof(buf), f)) {
+        const std::string line(buf);
+        if (line.find(pat) == std::string::npos) continue;
+        hit = json_int(line, "simt_range", &t->simt_range) &&
+              json_int(line, "simt_range_ctas", &t->simt_range_ctas) &&
+              json_int(line, "simt_gather", &t->simt_gather) &&
+              json_int(line, "simt_gather_ctas", &t->simt_gather_ctas) &&
+              json_int(line, "df_ctas", &t->df_ctas);
+    }
+    std::fclose(f);
+    return hit;
+}
+
+bool cache_store(const char* path, const std::string& key, const vbmc_tuning& t) {
+    std::vector<std::string> keep;
+    const std::string pat = "\"key\": \"" + key + "\"";
+    if (FILE* f = std::fopen(path, "r")) {
+        char buf[1024];
+        while (std::fgets(buf, sizeof(buf), f)) {
+            std::string line(buf);
+            if (line.find(pat) == std::string::npos && line.find("\"key\"") != std::string::npos)
+                keep.push_back(line);
+        }
+        std::fclose(f);
+    }
+    char row[1024];
+    std::snprintf(row, sizeof(row),
+                  "{\"key\": \"%s\", \"simt_range\": %d, \"simt_range_ctas\": %d, \"simt_gather\": %d, "
+                  "\"simt_gather_ctas\": %d, \"df_ctas\": %d, \"ms_range\": %.4f, \"ms_gather\": %.4f, "
+                  "\"ms_df\": %.4f}\n",
+                  key.c_str(), t.simt_range, t.simt_range_ctas, t.simt_gather, t.simt_gather_ctas, t.df_ctas,
+                  t.ms_range, t.ms_gather, t.ms_df);
+    keep.push_back(row);
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "w");
+    if (!f) return false;
+    for (const std::string& l : keep) std::fputs(l.c_str(), f);
+    std::fclose(f);
+    return std::rename(tmp.c_str(), path) == 0;
+}
+
+void apply_tuning(vbmc_net* net, const vbmc_tuning& t) {
+    net->v.simt_var_range = t.simt_range;
+    net->v.simt_ctas_range = t.simt_range_ctas;
+    net->v.simt_var_gather = t.simt_gather;
+    net->v.simt_ctas_gather = t.simt_gather_ctas;
+    net->v.df_ctas = t.df_ctas;
+}
+
+}  // namespace
+
+extern "C" vbmc_status vbmc_set_tuning(vbmc_net* net, const vbmc_tuning* t) {
+    if (!net || !t) return fail(VBMC_ERR_ARG, "null argument");
+    apply_tuning(net, *t);
+    return VBMC_OK;
+}
+
+extern "C" vbmc_status vbmc_autotune(vbmc_net* net, const char* cache_path, vbmc_tuning* out) {
+    if (!net) return fail(VBMC_ERR_ARG, "null argument");
+    const NetView& v = net->v;
+    if (simt_variant_default(v) == 0) return fail(VBMC_ERR_UNSUPPORTED, "layer width above 1024");
+    const std::string key = tune_key(net);
+    vbmc_tuning t{};
+    if (cache_lookup(cache_path, key, &t)) {
+        t.from_cache = 1;
+        apply_tuning(net, t);
+        if (out) *out = t;
+        return VBMC_OK;
+    }
+    // sample box: s <= 4 pixels spread over the input, k so that R^s >= 2^17
+    const int H0 = v.dims[0];
+    const int s = std::min(4, H0);
+    int k = 1;
+    while (k < VBMC_MAX_K && space_size(s, k) < (1ull << 17)) ++k;
+    const uint64_t n = space_size(s, k);
+    std::vector<uint8_t> img((size_t)H0);
+    for (int j = 0; j < H0; ++j) img[j] = (uint8_t)((j * 37 + 11) & 255);
+    std::vector<int32_t> pix((size_t)s);
+    for (int p = 0; p < s; ++p) pix[p] = (int32_t)(((long long)p * H0) / s);
+    vbmc_caps caps{n, s, k, 1u << 12, n};
+    vbmc_result* r = nullptr;
+    vbmc_status st = create_result(net, &caps, nullptr, 0, &r);
+    if (st != VBMC_OK) return st;
+    struct Guard {
+        vbmc_result* r;
+        ~Guard() { vbmc_result_free(r); }
+    } guard{r};
+    const vbmc_options o32{VBMC_PREC_FP32, 1, 0, 0, VBMC_SCHED_GIVEN};
+    const vbmc_query q{img.data(), s, pix.data(), k, 0, 0};
+    const vbmc_tuning saved{v.simt_var_range, v.simt_ctas_range, v.simt_var_gather, v.simt_ctas_gather,
+                            v.df_ctas, 0, 0.0, 0.0, 0.0};
+    cudaStream_t sq = nullptr;
+    VB_CUDA(cudaStreamCreateWithFlags(&sq, cudaStreamNonBlocking));
+    struct SGuard {
+        cudaStream_t s;
+        ~SGuard() { cudaStreamDestroy(s); }
+    } sguard{sq};
+    st = vbmc_verify_query(net, &q, &o32, r, sq);  // prologue, tables, warm-up
+    if (st != VBMC_OK) return st;
+    cudaEvent_t e0, e1;
+    VB_CUDA(cudaEventCreate(&e0));
+    VB_CUDA(cudaEventCreate(&e1));
+    const unsigned long long cap = caps.queue_cap;
+    Queue qdf{r->d_queue[2], r->d_qcount + 2, cap};
+    Queue q64{r->d_queue[3], r->d_qcount + 3, cap};
+    auto time_it = [&](auto&& launch) {
+        float best = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaMemsetAsync(r->d_qcount + 2, 0, sizeof(unsigned long long) * 2, sq);
+            cudaEventRecord(e0, sq);
+            launch();
+            cudaEventRecord(e1, sq);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            best = std::min(best, ms);
+        }
+        return best;
+    };
+    int max_smem = 0;
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, net->device);
+    // FP32 pass over the whole box (range mode) and over the same points queued
+    std::vector<unsigned long long> qn{n};
+    VB_CUDA(cudaMemsetAsync(r->d_qcount + 1, 0, sizeof(unsigned long long), sq));
+    k_fill_queue<<<(unsigned)((n + 255) / 256), 256, 0, sq>>>(r->d_queue[1], n, 1);
+    VB_CUDA(cudaMemcpyAsync(r->d_qcount + 1, qn.data(), sizeof(unsigned long long), cudaMemcpyHostToDevice, sq));
+    float best_r = 1e30f, best_g = 1e30f;
+    for (int var = 1; var <= 4; ++var) {
+        if (v.hmax > simt_variant_width(var)) continue;
+        const size_t sm = simt_variant_smem(var);
+        for (int ctas = 1; ctas <= 4; ctas *= 2) {
+            if ((size_t)ctas * (sm + 1024) > (size_t)max_smem) continue;
+            net->v.simt_var_range = net->v.simt_var_gather = var;
+            net->v.simt_ctas_range = net->v.simt_ctas_gather = ctas;
+            QueryView qv = make_view(r, r->d_image, r->d_pix_in, s, k, 0, n, n, o32, 0);
+            std::vector<unsigned long long> tp = tile_prefix(net->v, VBMC_PREC_FP32, &qv, 1);
+            VB_CUDA(cudaMemcpyAsync(r->d_q, &qv, sizeof(QueryView), cudaMemcpyHostToDevice, sq));
+            VB_CUDA(cudaMemcpyAsync(r->d_tp, tp.data(), sizeof(unsigned long long) * 2, cudaMemcpyHostToDevice, sq));
+            const float mr = time_it([&] {
+                launch_screen_simt(net->v, r->d_q, 1, r->d_tp, tp[1], nullptr, nullptr, 0, qdf, 2, net->n_sm, sq);
+            });
+            const float mg = time_it([&] {
+                launch_screen_simt(net->v, r->d_q, 1, nullptr, 0, r->d_queue[1], r->d_qcount + 1, cap, qdf, 2,
+                                   net->n_sm, sq);
+            });
+            if (mr < best_r) {
+                best_r = mr;
+                t.simt_range = var;
+                t.simt_range_ctas = ctas;
+            }
+            if (mg < best_g) {
+                best_g = mg;
+                t.simt_gather = var;
+                t.simt_gather_ctas = ctas;
+            }
+        }
+    }
+    // double-float pass over 8192 queued points spread over the box
+    const unsigned long long ndf = std::min<unsigned long long>(8192, n);
+    std::vector<unsigned long long> dn{ndf};
+    k_fill_queue<<<(unsigned)((ndf + 255) / 256), 256, 0, sq>>>(r->d_queue[1], ndf, n / ndf);
+    VB_CUDA(cudaMemcpyAsync(r->d_qcount + 1, dn.data(), sizeof(unsigned long long), cudaMemcpyHostToDevice, sq));
+    float best_d = 1e30f;
+    for (int per = 2; per <= 16; per *= 2) {
+        net->v.df_ctas = per;
+        const float md = time_it([&] {
+            launch_df(net->v, r->d_q, r->d_queue[1], r->d_qcount + 1, cap, q64, 3, net->n_sm, sq);
+        });
+        if (md < best_d) {
+            best_d = md;
+            t.df_ctas = per;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const cudaError_t ce = cudaStreamSynchronize(sq);
+    if (ce != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        apply_tuning(net, saved);
+        return fail(VBMC_ERR_CUDA, std::string("autotune: ") + cudaGetErrorString(ce));
+    }
+    t.ms_range = best_r;
+    t.ms_gather = best_g;
+    t.ms_df = best_d;
+    t.from_cache = 0;
+    apply_tuning(net, t);
+    if (cache_path && !cache_store(cache_path, key, t))
+        return fail(VBMC_ERR_ARG, "autotune: cannot write the cache file");
+    if (out) *out = t;
     return VBMC_OK;
 }

@@ -50,6 +50,10 @@ struct NetView {
     float sig[kMaxL + 1];             // sigma_max(W_l) (rounded up)
     float frob[kMaxL + 1];            // ||W_l||_F (rounded up)
     const float* pairw;               // [H_L][H_L]: ||W_L,D - W_L,o||_2 (rounded up)
+    // launch shapes (0: the built-in choice; set by vbmc_autotune)
+    int simt_var_range, simt_var_gather;    // FP32 pass variant, 1..4
+    int simt_ctas_range, simt_ctas_gather;  // FP32 pass CTAs per SM
+    int df_ctas;                            // double-float pass CTAs per SM
 };
 
 struct Counters {
@@ -63,9 +67,9 @@ struct Counters {
     int D;
     double base_margin;
     unsigned long long t0;          // %globaltimer at the start of the query's prologue
-    unsigned long long t_screen;    // ... when its last screen tile finished
-    unsigned long long t_final;     // ... when its result became final
-    unsigned long long tiles_left;  // screen tiles not yet finished
+    unsigned long long t_final;     // ... when its result became final (0: not yet)
+    unsigned long long work;        // unfinished units: screen tiles not yet done plus
+                                    // queued points not yet resolved (see work_done)
 };
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -119,10 +123,24 @@ __device__ __forceinline__ void set_bit_atomic(uint32_t* w, unsigned long long b
     atomicOr(&w[b >> 5], 1u << (unsigned)(b & 31));
 }
 
+// Time to verdict. Counters::work starts at the query's number of screen
+// tiles; every queued point adds one (in the push helpers below) and every
+// finished tile or resolved queued point takes one away, after the pushes it
+// caused. The update that takes it to zero stamps t_final: from then on no
+// pass changes the query's result. The push helpers fence after their
+// increments, and callers reach work_done only after a barrier that follows
+// their pushes, so the count cannot reach zero while a push is outstanding.
+__device__ __forceinline__ void work_done(Counters* c, unsigned long long n) {
+    __threadfence();
+    if (n && atomicAdd(&c->work, 0ull - n) == n) c->t_final = globaltimer_ns();
+}
+
 __device__ __forceinline__ void queue_push(const Queue& Q, unsigned long long t, unsigned q,
                                            Counters* cnt, int level) {
     unsigned long long i = atomicAdd(Q.count, 1ull);
     atomicAdd(&cnt->n_q[level], 1ull);
+    atomicAdd(&cnt->work, 1ull);
+    __threadfence();
     if (i < Q.cap) {
         QEntry e;
         e.t = t;
@@ -135,7 +153,8 @@ __device__ __forceinline__ void queue_push(const Queue& Q, unsigned long long t,
 }
 
 // Warp-cooperative push: every lane of the warp calls it (converged); lanes with
-// want == true get one slot each from a single atomic per warp.
+// want == true get one slot each from a single atomic per warp. Lanes may hold
+// points of different queries: each query's counters get its own lanes' count.
 __device__ __forceinline__ void queue_push_warp(const Queue& Q, bool want, unsigned long long t,
                                                 unsigned q, Counters* cnt, int level) {
     const unsigned m = __ballot_sync(0xffffffffu, want);
@@ -143,11 +162,16 @@ __device__ __forceinline__ void queue_push_warp(const Queue& Q, bool want, unsig
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(m) - 1;
     unsigned long long base = 0;
-    if (lane == leader) {
-        base = atomicAdd(Q.count, (unsigned long long)__popc(m));
-        atomicAdd(&cnt->n_q[level], (unsigned long long)__popc(m));
-    }
+    if (lane == leader) base = atomicAdd(Q.count, (unsigned long long)__popc(m));
     base = __shfl_sync(0xffffffffu, base, leader);
+    if (want) {
+        const unsigned peers = __match_any_sync(m, reinterpret_cast<unsigned long long>(cnt));
+        if (lane == __ffs(peers) - 1) {
+            atomicAdd(&cnt->n_q[level], (unsigned long long)__popc(peers));
+            atomicAdd(&cnt->work, (unsigned long long)__popc(peers));
+            __threadfence();
+        }
+    }
     if (want) {
         const unsigned long long i = base + __popc(m & ((1u << lane) - 1u));
         if (i < Q.cap) {

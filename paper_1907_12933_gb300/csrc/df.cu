@@ -195,6 +195,7 @@ k_df(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__ g
             }
         }
         __syncthreads();
+        if (threadIdx.x == 0) work_done(Q.cnt, 1);  // time to verdict: this point is resolved
     }
 }
 
@@ -205,8 +206,9 @@ void launch_df(const NetView& net, const QueryView* d_qs, const QEntry* gather,
                int out_level, int n_sm, cudaStream_t st) {
     const size_t smem = sizeof(double) * net.total + sizeof(float2) * net.hmax + (size_t)net.total;
     cudaFuncSetAttribute(k_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_df<<<(unsigned)n_sm * 8, TDF, smem, st>>>(net, d_qs, gather, gather_count, gather_cap, out,
-                                               out_level);
+    const int per_sm = (net.df_ctas >= 1 && net.df_ctas <= 32) ? net.df_ctas : 8;
+    k_df<<<(unsigned)(n_sm * per_sm), TDF, smem, st>>>(net, d_qs, gather, gather_count, gather_cap, out,
+                                                      out_level);
 }
 
 }  // namespace vbmc

@@ -161,6 +161,7 @@ k_fp64(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__
             } else if (am != D) {
                 record_adversarial(Q, t);
             }
+            if (gather) work_done(Q.cnt, 1);  // time to verdict: this queued point is resolved
         }
         __syncthreads();
     }

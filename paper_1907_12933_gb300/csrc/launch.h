@@ -23,8 +23,14 @@ void launch_screen_simt(const NetView& net, const QueryView* d_qs, int nq,
                         unsigned long long gather_cap, Queue out, int out_level, int n_sm,
                         cudaStream_t st);
 
-// Points per tile of the SIMT screen for this net.
+// Points per tile of the SIMT screen for this net (its range-pass variant).
 int simt_tile_points(const NetView& net);
+
+// FP32 pass variants 1..4: widest layer held, points per tile, shared memory.
+int simt_variant_width(int var);
+int simt_variant_default(const NetView& net);
+int simt_variant_points(int var);
+size_t simt_variant_smem(int var);
 
 // FP64 pass: gather mode over a queue, or range mode over [lo, hi) of query 0
 // when gather == nullptr.

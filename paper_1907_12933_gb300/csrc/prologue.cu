@@ -37,9 +37,8 @@ __global__ void k_pro_init(NetView net, QueryView* qs, int nq) {
         c->D = 0;
         c->base_margin = 0.0;
         c->t0 = globaltimer_ns();
-        c->t_screen = c->t0;
         c->t_final = 0;
-        c->tiles_left = Q.ntiles;
+        c->work = Q.ntiles;
         for (int p = 0; p < Q.s; ++p) {
             int v = Q.pix_in[p];
             Q.pix[p] = (ok && v >= 0 && v < H0) ? v : 0;  // never index out of range
@@ -237,14 +236,13 @@ __global__ void k_pro_finish(NetView net, QueryView* qs, int nq) {
     }
 }
 
-// Time-to-verdict: a query none of whose points needed a later pass was final
-// when its screen finished; the others when the last pass finished (now).
+// Time to verdict of queries whose work count never reached zero inside a pass
+// (no screen tiles: empty ranges and the FP64-only path): the end of the last pass.
 __global__ void k_stamp_final(QueryView* qs, int nq) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nq) return;
     Counters* c = qs[q].cnt;
-    const unsigned long long later = c->n_q[0] + c->n_q[1] + c->n_q[2] + c->n_q[3];
-    c->t_final = (later || qs[q].ntiles == 0) ? globaltimer_ns() : c->t_screen;
+    if (c->t_final == 0) c->t_final = globaltimer_ns();
 }
 
 void launch_stamp_final(QueryView* d_qs, int nq, cudaStream_t st) {

@@ -12,20 +12,48 @@ VB_SIMT_DECL(2)
 VB_SIMT_DECL(3)
 VB_SIMT_DECL(4)
 
-int simt_variant(const NetView& net) {
-    if (net.hmax <= 32) return 1;
-    if (net.hmax <= 256) return 2;
-    if (net.hmax <= 512) return 3;
-    if (net.hmax <= 1024) return 4;
+// Widest layer each variant holds: 32 * NQ neurons (NQ accumulators per lane).
+int simt_variant_width(int var) {
+    switch (var) {
+        case 1: return 32;
+        case 2: return 256;
+        case 3: return 512;
+        case 4: return 1024;
+    }
     return 0;
 }
 
-int simt_tile_points(const NetView& net) {
-    switch (simt_variant(net)) {
+// The narrowest variant that holds the net's widest layer.
+int simt_variant_default(const NetView& net) {
+    for (int var = 1; var <= 4; ++var)
+        if (net.hmax <= simt_variant_width(var)) return var;
+    return 0;
+}
+
+// Variant of the range passes (tuned, else the narrowest that fits).
+int simt_variant(const NetView& net) {
+    const int t = net.simt_var_range;
+    return (t >= 1 && t <= 4 && net.hmax <= simt_variant_width(t)) ? t : simt_variant_default(net);
+}
+
+int simt_variant_points(int var) {
+    switch (var) {
         case 1: return simt::SimtSmem<16, 1>::MT;
         case 2: return simt::SimtSmem<16, 8>::MT;
         case 3: return simt::SimtSmem<8, 16>::MT;
         case 4: return simt::SimtSmem<4, 32>::MT;
+    }
+    return 0;
+}
+
+int simt_tile_points(const NetView& net) { return simt_variant_points(simt_variant(net)); }
+
+size_t simt_variant_smem(int var) {
+    switch (var) {
+        case 1: return sizeof(simt::SimtSmem<16, 1>);
+        case 2: return sizeof(simt::SimtSmem<16, 8>);
+        case 3: return sizeof(simt::SimtSmem<8, 16>);
+        case 4: return sizeof(simt::SimtSmem<4, 32>);
     }
     return 0;
 }
@@ -35,7 +63,12 @@ void launch_screen_simt(const NetView& net, const QueryView* d_qs, int nq,
                         const QEntry* gather, const unsigned long long* gc,
                         unsigned long long gcap, Queue out, int level, int n_sm,
                         cudaStream_t st) {
-    switch (simt_variant(net)) {
+    int var = simt_variant(net);
+    if (gather) {
+        const int t = net.simt_var_gather;
+        var = (t >= 1 && t <= 4 && net.hmax <= simt_variant_width(t)) ? t : simt_variant_default(net);
+    }
+    switch (var) {
         case 1: launch_simt_v1(net, d_qs, nq, tp, n_tiles, gather, gc, gcap, out, level, n_sm, st); break;
         case 2: launch_simt_v2(net, d_qs, nq, tp, n_tiles, gather, gc, gcap, out, level, n_sm, st); break;
         case 3: launch_simt_v3(net, d_qs, nq, tp, n_tiles, gather, gc, gcap, out, level, n_sm, st); break;

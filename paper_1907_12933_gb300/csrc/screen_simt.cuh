@@ -389,12 +389,17 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
             }
         }
         __syncwarp();
-        if (!gather) {  // time-to-verdict: the last tile of a query stamps the time
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                const QueryView& Q = qs[S.q[0]];
-                if (atomicAdd(&Q.cnt->tiles_left, ~0ull) == 1ull) Q.cnt->t_screen = globaltimer_ns();
+        if (gather) {  // time to verdict: this warp's queued points are resolved
+            const int m = warp * PPW + (lane < PPW ? lane : 0);
+            const bool mine = lane < PPW && S.valid[m];
+            const unsigned vm = __ballot_sync(0xffffffffu, mine);
+            if (mine) {
+                const unsigned peers = __match_any_sync(vm, S.q[m]);
+                if (lane == __ffs(peers) - 1) work_done(qs[S.q[m]].cnt, __popc(peers));
             }
+        } else {  // time to verdict: one screen tile of the query is done
+            __syncthreads();
+            if (threadIdx.x == 0) work_done(qs[S.q[0]].cnt, 1);
         }
     }
 }
@@ -407,6 +412,8 @@ void launch_variant(const NetView& net, const QueryView* d_qs, int nq, const uns
     auto kern = k_screen_simt<PPW, NQ>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = smem < 60000 ? 2 : 1;
+    const int tuned = gather ? net.simt_ctas_gather : net.simt_ctas_range;
+    if (tuned >= 1 && tuned <= 8) per_sm = tuned;
     unsigned long long grid = (unsigned long long)n_sm * per_sm;
     if (!gather && n_tiles < grid) grid = n_tiles ? n_tiles : 1;
     kern<<<(unsigned)grid, THREADS, smem, st>>>(net, d_qs, nq, tp, n_tiles, gather, gc, gcap, out,

@@ -713,9 +713,8 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     }
                 }
                 tc::named_bar_sync(1, 256);
-                if (!gather && wtid == 0 &&
-                    atomicAdd(&Q.cnt->tiles_left, ~0ull) == 1ull)  // last tile of this query
-                    Q.cnt->t_screen = globaltimer_ns();
+                // time to verdict: a screen tile done, or this tile's queued points resolved
+                if (wtid == 0) work_done(Q.cnt, gather ? (g * MROWS + MROWS <= gn ? MROWS : gn - g * MROWS) : 1);
             }
         }
     }

@@ -94,11 +94,14 @@ def test_config3_net_small_box(vb):
     compare(run_gpu(vb, net, q, "fp32"), oracle.verify(net, q), net, q)
 
 
-@pytest.mark.parametrize("prec,graph", [("fp32", False), ("bf16", False), ("bf16", True),
-                                        ("fp64", False)])
-def test_config4_net_batch(vb, prec, graph):
+@pytest.mark.parametrize("prec,graph,schedule", [("fp32", False, "given"), ("bf16", False, "given"),
+                                                 ("bf16", True, "small_first"),
+                                                 ("fp32", False, "small_first"),
+                                                 ("fp64", False, "given")])
+def test_config4_net_batch(vb, prec, graph, schedule):
     """784-256-256-10 ReLU net, 24 uneven queries through one vbmc_verify_batch call
-    (one launch per pass over every query), each checked against the oracle."""
+    (one launch per pass over every query), each checked against the oracle; with
+    the smallest-first schedule the tiles run in another order than the results."""
     w = synth.workload("mlp784x256x256_relu_batch4096", nq=24, s_range=(1, 3), k_range=(3, 10))
     net = w["net"]
     vnet = vb.Net(net)
@@ -107,7 +110,7 @@ def test_config4_net_batch(vb, prec, graph):
     results = vb.result_create_batch(vnet, len(qs), max_points=nmax, max_s=3, max_k=10,
                                      queue_cap=1 << 18)
     sums = vb.verify_batch(vnet, results, qs, precision=prec, coverage=True, bitmap=True,
-                           graph=graph)
+                           graph=graph, schedule=schedule)
     for q, r, s in zip(qs, results, sums):
         o = oracle.verify(net, q)
         g = {"summary": s, "n": oracle.space_size(len(q["pixels"]), q["k"])}
@@ -116,7 +119,7 @@ def test_config4_net_batch(vb, prec, graph):
         g["ties"] = np.sort(vb.get_ties(r))
         g["witness"] = vb.get_witness(r, len(q["pixels"]), 784)
         compare(g, o, net, q)
-        assert s["ms_to_verdict"] > 0.0
+        assert 0.0 < s["ms_to_verdict"] <= s["ms_device"] + 1e-3
     for r in results:
         r.free()
 
@@ -207,3 +210,26 @@ def test_fullsize_config2_sampled(vb):
             assert int(t) in ties
         else:
             assert bit(int(t)) == int(p["adversarial"]), t
+
+
+def test_autotune_cache_and_parity(vb, tmp_path):
+    """Tuned launch shapes come back from the cache unchanged, and any shape gives
+    the oracle's results (the tuned one and a forced wide variant)."""
+    w = synth.workload("mlp784x256x256_relu_batch4096", nq=3, s_range=(2, 2), k_range=(6, 6))
+    net = w["net"]
+    vnet = vb.Net(net)
+    path = str(tmp_path / "tuning.jsonl")
+    t1 = vb.autotune(vnet, path)
+    assert t1["from_cache"] == 0 and t1["ms_range"] > 0 and t1["ms_df"] > 0
+    assert t1["simt_range"] in (2, 3, 4) and t1["simt_gather"] in (2, 3, 4)
+    assert t1["df_ctas"] in (2, 4, 8, 16)
+    t2 = vb.autotune(vb.Net(net), path)
+    assert t2["from_cache"] == 1
+    for f in ("simt_range", "simt_range_ctas", "simt_gather", "simt_gather_ctas", "df_ctas"):
+        assert t2[f] == t1[f]
+    q = w["queries"][0]
+    o = oracle.verify(net, q)
+    for prec in ("fp32", "bf16"):
+        compare(run_gpu(vb, net, q, prec, vbnet=vnet), o, net, q)
+    vb.set_tuning(vnet, simt_range=4, simt_range_ctas=1, simt_gather=4, simt_gather_ctas=2, df_ctas=3)
+    compare(run_gpu(vb, net, q, "fp32", vbnet=vnet), o, net, q)
