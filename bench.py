@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--graph", action="store_true", help="batched workload: CUDA-graph launch")
     ap.add_argument("--schedule", default="small_first", choices=["given", "small_first"],
                     help="batched workload: tile order over the queries")
+    ap.add_argument("--no-coverage", action="store_true",
+                    help="skip the coverage masks (verdicts only; not the headline workload)")
     ap.add_argument("--s", type=int, default=None,
                     help="override the workload's pixel count (smaller cases for profiling)")
     ap.add_argument("--k", type=int, default=None, help="override the workload's step bound")
@@ -152,9 +154,14 @@ def screen_flops_per_point(dims, s):
     return 2 * dense + s * dims[1]
 
 
-def launches_per_step(precision, L, batch=False):
+def launches_per_step(precision, L, batch=False, n_points=0):
     """Kernels of the library per verify call (cudaMemset/cudaMemcpy not counted)."""
     pro = 1 + L + 1 + 1  # init, L base layers, tables, finish
+    if precision == "fp8":
+        # per chunk of 2^20 points: layer 1, GEMM + stats per hidden layer >= 2, output
+        # layer, FP32, double-float and FP64 passes; then the final work count, stamps
+        chunks = max(1, -(-n_points // (1 << 20)))
+        return pro + chunks * (1 + 2 * (L - 2) + 1 + 3) + 2
     if precision == "fp64":
         return pro + 1 + 1  # FP64 range pass per query (1 here), time stamps
     if precision == "fp32":
@@ -381,7 +388,8 @@ def main():
 
     # ---- device-resident steps (value)
     for _ in range(a.warmup):
-        vb.verify_query_device(vnet, res, d_img, d_pix, k, precision=a.precision)
+        vb.verify_query_device(vnet, res, d_img, d_pix, k, precision=a.precision,
+                               coverage=not a.no_coverage)
         vb.result_summary(res)
     clocks = Clocks()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -394,7 +402,8 @@ def main():
     for i in range(a.steps):
         flush.zero_()
         ev[i][0].record(stream)
-        vb.verify_query_device(vnet, res, d_img, d_pix, k, precision=a.precision)
+        vb.verify_query_device(vnet, res, d_img, d_pix, k, precision=a.precision,
+                               coverage=not a.no_coverage)
         ev[i][1].record(stream)
         sm = vb.result_summary(res)
         screen_ms.append(sm["ms_screen"])
@@ -418,9 +427,11 @@ def main():
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        vb.verify_query(vnet, res, q["image"], q["pixels"], k, precision=a.precision)
+        vb.verify_query(vnet, res, q["image"], q["pixels"], k, precision=a.precision,
+                        coverage=not a.no_coverage)
         vb.get_verdict_bitmap(res, n_pts)
-        vb.get_coverage(res)
+        if not a.no_coverage:
+            vb.get_coverage(res)
         e2e_ms.append(1000.0 * (time.perf_counter() - t0))
     e2e_local = torch.tensor([statistics.median(e2e_ms)], dtype=torch.float64, device=dev)
     if world > 1:
@@ -456,13 +467,14 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": a.workload, "dims": cfg["dims"], "act": cfg["act"],
                            "s": s, "k": k, "points_per_query": n_pts, "precision": a.precision,
+                           "coverage": not a.no_coverage,
                            "queries": "one per rank (rank r: query r of the workload seed)",
                            "l2": "flushed between timed steps (256 MB write)",
                            "parallelism": f"dp{world}" if world > 1 else "single GPU"},
                 "e2e": {"value": e2e_value, "unit": UNIT,
                         "h2d_bytes_per_step": int(cfg["dims"][0] + 4 * s),
                         "d2h_bytes_per_step": int(4 * ((n_pts + 31) // 32) + 8 * fw + 8 * sw + 128)},
-                "gpu_launches": a.steps * launches_per_step(a.precision, L),
+                "gpu_launches": a.steps * launches_per_step(a.precision, L, n_points=n_pts),
                 "roofline": roof,
                 "verdict": {"verdict": last["verdict"], "n_adversarial": last["n_adversarial"],
                             "first_witness": last["first_witness"], "n_ties": last["n_ties"],

@@ -254,6 +254,13 @@ vbmc_status vbmc_autotune(vbmc_net *net, const char *cache_path, vbmc_tuning *ou
 /* Apply given launch shapes (0 in a field: the built-in choice). */
 vbmc_status vbmc_set_tuning(vbmc_net *net, const vbmc_tuning *t);
 
+/* Accumulation error per product that the FP8 screen's bound assumes for this
+ * net's device, relative to the sum of |products|: 2^-22 when the set-up
+ * self-test found the E4M3 MMA's sums exact to 23 significand bits (the FP32
+ * model of the 16-bit screens), 2^-13 otherwise. Builds the FP8 weights on
+ * first use. */
+vbmc_status vbmc_fp8_accumulation_unit(vbmc_net *net, double *unit);
+
 /* ---- Tile-ordered search for a first witness.
  * The index space [0, n) of a query (n = R^s) is cut into n_tiles contiguous
  * tiles of ceil(n / n_tiles) points (the last one ragged; tiles past n are

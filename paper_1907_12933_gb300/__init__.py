@@ -118,6 +118,7 @@ def lib():
                                   C.POINTER(_Options), vp, C.POINTER(_SearchOut), vp],
             "vbmc_tile_counts": [vp, C.c_int32, C.POINTER(C.c_uint64)],
             "vbmc_autotune": [vp, C.c_char_p, C.POINTER(_Tuning)],
+            "vbmc_fp8_accumulation_unit": [vp, C.POINTER(C.c_double)],
             "vbmc_set_tuning": [vp, C.POINTER(_Tuning)],
             "vbmc_proposal_create": [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                      C.c_uint64, C.POINTER(vp)],
@@ -357,6 +358,13 @@ def verify_range_fp64_noalloc(net: Net, d_image, d_pixels, k: int, lo: int, hi: 
                                                 int(d_pixels.numel()),
                                                 C.c_void_p(d_pixels.data_ptr()), int(k), int(lo),
                                                 int(hi), C.byref(out), C.c_void_p(st)))
+
+
+def fp8_accumulation_unit(net: Net) -> float:
+    """vbmc_fp8_accumulation_unit: the per-product accumulation error the FP8 bound uses."""
+    u = C.c_double()
+    _check(lib().vbmc_fp8_accumulation_unit(net.h, C.byref(u)))
+    return u.value
 
 
 def autotune(net: Net, cache_path: str | None = None) -> dict:

@@ -10,6 +10,7 @@
 #include "dev.cuh"
 #include "launch.h"
 #include "tc.h"
+#include "wide.h"
 
 #include <algorithm>
 #include <cmath>
@@ -69,6 +70,7 @@ struct vbmc_net {
     int n_sm = 0;
     int device = 0;
     TcNet tc{};  // tensor-core copies (built on first use per precision)
+    WideNet wide{};  // rounded copies for the wide-layer path (built on first use per type)
     std::vector<std::vector<float>> hW, hb;  // host copies for tensor-core set-up
 };
 
@@ -112,6 +114,7 @@ struct vbmc_result {
     unsigned long long* d_qcount = nullptr;  // 4 queue counters
     QEntry* d_queue[4] = {nullptr, nullptr, nullptr, nullptr};
     double* d_margin = nullptr;
+    WideWork ww{};  // chunk workspace of the wide-layer path (allocated on first use)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_pro = nullptr, ev_scr = nullptr;
     cudaStream_t last_stream = nullptr;
     bool pending = false;
@@ -263,6 +266,7 @@ extern "C" vbmc_status vbmc_net_create(const vbmc_mlp_desc* desc, vbmc_net** out
 extern "C" vbmc_status vbmc_net_free(vbmc_net* net) {
     if (!net) return VBMC_OK;
     tc_free(net->tc);
+    wide_free(net->wide);
     for (void* p : net->owned) cudaFree(p);
     delete net;
     return VBMC_OK;
@@ -415,6 +419,7 @@ extern "C" vbmc_status vbmc_result_free(vbmc_result* r) {
     if (!r) return VBMC_OK;
     if (r->pending && r->last_stream) cudaStreamSynchronize(r->last_stream);
     for (void* p : r->owned) cudaFree(p);
+    wide_work_free(r->ww);
     arena_release(r->arena);
     if (r->h_cnt) cudaFreeHost(r->h_cnt);
     if (r->ev0) cudaEventDestroy(r->ev0);
@@ -453,7 +458,10 @@ std::vector<unsigned long long> tile_prefix(const NetView& v, int precision, Que
     std::vector<unsigned long long> tp((size_t)nq + 1, 0);
     for (int i = 0; i < nq; ++i) {
         const unsigned long long base = hq[i].lo & ~31ull;
-        const unsigned long long t = (MT && hq[i].hi > hq[i].lo) ? (hq[i].hi - base + MT - 1) / MT : 0;
+        unsigned long long t = (MT && hq[i].hi > hq[i].lo) ? (hq[i].hi - base + MT - 1) / MT : 0;
+        if (precision == VBMC_PREC_FP8 || ((precision == VBMC_PREC_BF16 || precision == VBMC_PREC_FP16) &&
+                                           !tc_supported(v, precision)))
+            t = hq[i].hi > hq[i].lo ? 1 : 0;  // the wide-layer path: one unit, its chunk loop
         hq[i].ntiles = t;
         tp[i + 1] = tp[i] + t;
     }
@@ -473,7 +481,8 @@ vbmc_status enqueue_passes(vbmc_net* net, QueryView* d_qs, const QueryView* hq, 
                            const unsigned long long* d_tp, unsigned long long ntiles,
                            unsigned long long* d_qcount, QEntry* const* d_queue,
                            unsigned long long cap, const cudaEvent_t* ev, const vbmc_options& opt,
-                           cudaStream_t st, bool capturing = false, int stages = STAGE_ALL) {
+                           cudaStream_t st, bool capturing = false, int stages = STAGE_ALL,
+                           WideWork* ww = nullptr) {
     const NetView& v = net->v;
     // inside a stream capture an event record must be an explicit graph node
     const unsigned evflag = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
@@ -484,7 +493,23 @@ vbmc_status enqueue_passes(vbmc_net* net, QueryView* d_qs, const QueryView* hq, 
         max_sr = std::max(max_sr, hq[i].s * hq[i].R);
         any = any || hq[i].hi > hq[i].lo;
     }
-    const bool tensor = opt.precision != VBMC_PREC_FP64 && opt.precision != VBMC_PREC_FP32;
+    // 16-bit screens: the fused kernel where it fits, else the wide-layer path;
+    // E4M3 always takes the wide-layer path
+    const bool tensor16 = opt.precision == VBMC_PREC_BF16 || opt.precision == VBMC_PREC_FP16;
+    const bool wide = opt.precision == VBMC_PREC_FP8 || (tensor16 && !tc_supported(v, opt.precision));
+    const bool tensor = tensor16 && !wide;
+    const int wtype = wide_type(opt.precision);
+    if (wide && any) {
+        if (nq != 1 || !ww) return fail(VBMC_ERR_UNSUPPORTED, "the wide-layer tensor screen serves one query per call");
+        if (!wide_supported(v))
+            return fail(VBMC_ERR_UNSUPPORTED,
+                        "tensor-core screen does not support this net/precision (wide layers: ReLU, hidden widths "
+                        "a multiple of 256 up to 1024, at most 32 outputs)");
+        vbmc_status fs = wide_build(net->wide, v, net->hW, wtype);
+        if (fs != VBMC_OK) return fail(fs, "wide-layer tensor set-up failed (self-test or weight preparation)");
+        fs = wide_work_alloc(*ww, v);
+        if (fs != VBMC_OK) return fail(fs, "wide-layer chunk workspace allocation failed");
+    }
     VB_CUDA(cudaMemsetAsync(d_qcount, 0, sizeof(unsigned long long) * 4, st));
     VB_CUDA(record(ev[0]));
     if (stages & STAGE_SETUP) launch_prologue(v, d_qs, nq, max_sr, st);
@@ -502,7 +527,12 @@ vbmc_status enqueue_passes(vbmc_net* net, QueryView* d_qs, const QueryView* hq, 
     Queue q32{d_queue[1], d_qcount + 1, cap};
     Queue qdf{d_queue[2], d_qcount + 2, cap};
     Queue q64{d_queue[3], d_qcount + 3, cap};
-    if (any && opt.precision == VBMC_PREC_FP64) {
+    if (any && wide) {
+        VB_CUDA(record(ev[2]));
+        vbmc_status fs = wide_run(net->wide, wtype, *ww, v, d_qs, hq[0].lo, hq[0].hi, d_qcount, d_queue, cap,
+                                  net->n_sm, st);
+        if (fs != VBMC_OK) return fail(fs, "wide-layer tensor screen launch failed");
+    } else if (any && opt.precision == VBMC_PREC_FP64) {
         for (int i = 0; i < nq; ++i)
             if (hq[i].hi > hq[i].lo)
                 launch_fp64(v, d_qs + i, 1, nullptr, nullptr, 0, hq[i].lo, hq[i].hi, net->n_sm, st);
@@ -564,7 +594,8 @@ vbmc_status enqueue(vbmc_net* net, vbmc_result* r, const uint8_t* d_image, const
     VB_CUDA(cudaMemcpyAsync(r->d_tp, tp.data(), sizeof(unsigned long long) * 2, cudaMemcpyHostToDevice, st));
     const cudaEvent_t ev[4] = {r->ev0, r->ev_pro, r->ev_scr, r->ev1};
     vbmc_status sst = enqueue_passes(net, r->d_q, &q, 1, r->d_tp, tp[1], r->d_qcount, r->d_queue,
-                                     std::max<uint64_t>(1, r->caps.queue_cap), ev, opt, st);
+                                     std::max<uint64_t>(1, r->caps.queue_cap), ev, opt, st, false, STAGE_ALL,
+                                     &r->ww);
     if (sst != VBMC_OK) return sst;
     VB_CUDA(cudaMemcpyAsync(r->h_cnt, r->d_cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     r->last_stream = st;
@@ -806,7 +837,10 @@ extern "C" vbmc_status vbmc_verify_batch(vbmc_net* net, const vbmc_query* querie
     bool together = ar && ar->nq >= nq;
     for (int i = 0; i < nq && together; ++i)
         together = results[i] && results[i]->arena == ar && results[i]->slot == i && results[i]->net == net;
-    if (!together) {  // results not created together: one query after another
+    // results not created together, or a precision whose screen serves one query
+    // at a time (the wide-layer path): one query after another
+    if (!together || opt->precision == VBMC_PREC_FP8 ||
+        ((opt->precision == VBMC_PREC_BF16 || opt->precision == VBMC_PREC_FP16) && !tc_supported(net->v, opt->precision))) {
         for (int i = 0; i < nq; ++i) {
             vbmc_status st = vbmc_verify_query(net, &queries[i], opt, results[i], stream);
             if (st != VBMC_OK) return st;
@@ -1002,7 +1036,7 @@ extern "C" vbmc_status vbmc_search_query(vbmc_net* net, const vbmc_query* q, int
     VB_CUDA(cudaMemcpyAsync(res->d_q, &qv, sizeof(QueryView), cudaMemcpyHostToDevice, sq));
     const cudaEvent_t ev_set[4] = {res->ev0, res->ev_pro, res->ev_pro, res->ev_pro};
     st = enqueue_passes(net, res->d_q, &qv, 1, res->d_tp, tp[1], res->d_qcount, res->d_queue, cap, ev_set,
-                        *opt, sq, false, STAGE_SETUP);
+                        *opt, sq, false, STAGE_SETUP, &res->ww);
     if (st != VBMC_OK) return st;
     const cudaEvent_t ev_tile[4] = {res->ev_scr, res->ev_scr, res->ev_scr, res->ev1};
     const uint64_t tsize = (n + n_tiles - 1) / n_tiles;
@@ -1021,7 +1055,7 @@ extern "C" vbmc_status vbmc_search_query(vbmc_net* net, const vbmc_query* q, int
         VB_CUDA(cudaMemcpyAsync(res->d_tp, tp.data(), sizeof(unsigned long long) * 2, cudaMemcpyHostToDevice,
                                 sq));
         st = enqueue_passes(net, res->d_q, &qv, 1, res->d_tp, tp[1], res->d_qcount, res->d_queue, cap, ev_tile,
-                            *opt, sq, false, STAGE_PASSES);
+                            *opt, sq, false, STAGE_PASSES, &res->ww);
         if (st != VBMC_OK) return st;
         any_tile = true;
         VB_CUDA(cudaMemcpyAsync(res->h_cnt, res->d_cnt, sizeof(Counters), cudaMemcpyDeviceToHost, sq));
@@ -1312,5 +1346,15 @@ extern "C" vbmc_status vbmc_autotune(vbmc_net* net, const char* cache_path, vbmc
     if (cache_path && !cache_store(cache_path, key, t))
         return fail(VBMC_ERR_ARG, "autotune: cannot write the cache file");
     if (out) *out = t;
+    return VBMC_OK;
+}
+
+extern "C" vbmc_status vbmc_fp8_accumulation_unit(vbmc_net* net, double* unit) {
+    if (!net || !unit) return fail(VBMC_ERR_ARG, "null argument");
+    if (!wide_supported(net->v))
+        return fail(VBMC_ERR_UNSUPPORTED, "FP8 screen needs a ReLU net with hidden widths a multiple of 256 up to 1024");
+    const vbmc_status st = wide_build(net->wide, net->v, net->hW, WIDE_E4M3);
+    if (st != VBMC_OK) return fail(st, "FP8 set-up failed (self-test or weight preparation)");
+    *unit = (double)net->wide.prec[WIDE_E4M3].acc_unit;
     return VBMC_OK;
 }

@@ -88,7 +88,7 @@ k_df(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__ g
             // |a - exact| <= base error + rounding of the s additions and the terms
             const double err = Q.eub[j] + (Q.s + 3) * u52 * mag;
             const bool certain = fabs(a) > err + 2.0 * kTau && fabs(ub) >= kTau;
-            if (!certain) undecided = 1;
+            if (!certain && Q.flip) undecided = 1;  // signs matter only for coverage
             fl[j] = certain && ((a >= 0.0) != (ub >= 0.0));
             const double d = (L > 1 ? act64(net.act, a) : a) - Q.hb[j];
             const float hi = (float)d;
@@ -125,7 +125,7 @@ k_df(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__ g
                 const double err = (double)net.rownorm[l][i] * (cK * N + E) + Q.eub[off + i] +
                                    u52 * (fabs(ui) + fabs(ub));
                 const bool certain = fabs(ui) > err + 2.0 * kTau && fabs(ub) >= kTau;
-                if (!certain) undecided = 1;
+                if (!certain && Q.flip) undecided = 1;  // signs matter only for coverage
                 fl[off + i] = certain && ((ui >= 0.0) != (ub >= 0.0));
                 if (l < L) {
                     const double d = act64(net.act, ui) - Q.hb[off + i];

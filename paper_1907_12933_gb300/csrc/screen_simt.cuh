@@ -164,7 +164,7 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
                 const float u = ub + du;
                 const float bound = __fmaf_ru(rn[n], X, Q.thr[gi]);
                 if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound)) {
-                    S.unc[m] = 1;
+                    if (Q.flip) S.unc[m] = 1;  // signs matter only for coverage
                 } else if ((u >= 0.f) != (ub >= 0.f)) {
                     int idx = atomicAdd(&S.fcnt[m][l], 1);
                     if (idx < FCAP) S.flist[m][l][idx] = (short)n;
@@ -288,7 +288,7 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
                         const float u = ub + du;
                         const float thr = Q.thr[j];
                         if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > thr)) {
-                            S.unc[m] = 1;
+                            if (Q.flip) S.unc[m] = 1;  // signs matter only for coverage
                         } else if ((u >= 0.f) != (ub >= 0.f)) {
                             int idx = atomicAdd(&S.fcnt[m][1], 1);
                             if (idx < FCAP) S.flist[m][1][idx] = (short)j;

@@ -429,7 +429,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         float dh0 = fmaxf(du.x + c10, c20);
                         float dh1 = fmaxf(du.y + c11, c21);
                         if (!ri.w) dh0 = dh1 = 0.f;
-                        if (anyc && ri.w) {
+                        if (anyc && ri.w && Q.flip) {  // signs matter only for coverage
                             if (cr0) {
                                 const float u = ub0 + du.x;
                                 if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > th0)) S.unc[r] = 1;
@@ -533,7 +533,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                             const float ub = Q.ub32[gi];
                             const float u = ub + du;
                             const float bound = __fmaf_ru(av[n], Pa, __fmaf_ru(bv[n], Pb, Q.thr[gi]));
-                            if (rv) {
+                            if (rv && Q.flip) {  // signs matter only for coverage
                                 if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound)) S.unc[r] = 1;
                                 else if ((u >= 0.f) != (ub >= 0.f)) {
                                     const int k = atomicAdd(&S.fcnt[r][l], 1);
@@ -642,7 +642,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                             const float u = ub + v[o];
                             y[o] = u;
                             const float bound = __fmaf_ru(av[o], Pa, __fmaf_ru(bv[o], Pb, Q.thr[offL + o]));
-                            if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound)) unc = true;
+                            if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound)) unc = Q.flip != nullptr;
                             else if ((u >= 0.f) != (ub >= 0.f)) {
                                 const int k = atomicAdd(&S.fcnt[r][L], 1);
                                 if (k < FCAP) S.flist[r][L][k] = (short)o;
@@ -845,6 +845,13 @@ bool tc_supported(const NetView& v, int precision) {
         if (v.dims[l] % 64 || v.dims[l] > 512) return false;
     if (v.dims[v.L] > kTcMaxOut) return false;
     if (v.flip_words > 256) return false;
+    // a layer l >= 3 wider than 64 reuses the accumulator columns of layer l-1, so
+    // its MMAs start only after layer l-1 is drained: the drain must fit the
+    // operand ring (at most NA chunks of 64)
+    for (int l = 3; l <= v.L; ++l) {
+        const int Npad = l == v.L ? (v.dims[l] <= 16 ? 16 : 32) : v.dims[l];
+        if (Npad > 64 && v.dims[l - 1] / 64 > NA) return false;
+    }
     return true;
 }
 
