@@ -170,6 +170,45 @@ def launches_per_step(precision, L, batch=False, n_points=0):
     return pro + (6 if batch else 7)
 
 
+def pass_rooflines(precision, dims, s, n_pts, sums, pk, pk_kind):
+    """Roofline of each pass of a verify call (CUDA-event times from the library,
+    medians over the timed steps) and, at the top level, the pass that took
+    longest. Algorithmic work: 2 sum_{l>=2} H_{l-1} H_l + s H_1 FLOP per point
+    that the pass evaluates (the split tensor pass: three products). Peaks: the
+    measured BF16 tensor peak (FP16 the same, E4M3 twice: nominal ratios); the
+    FP32 ALU peak 152 SM x 128 lanes x 2 FLOP x sm_max_mhz; double-float costs
+    11 FP32 instructions per multiply-add, so its peak is the FP32 one x 2/11;
+    FP64 the nominal 1.25 TFLOP/s (no measured FP64 peak)."""
+    fpp = screen_flops_per_point(dims, s)
+    mhz = pk.get("sm_max_mhz", 2070.0)
+    alu = 152 * 128 * 2 * mhz * 1e6 / 1e12
+    tensor = pk.get("bf16_tflops", 1900.0) * (2.0 if precision == "fp8" else 1.0)
+    tkind = pk_kind + (" bf16 x2 (fp8 nominal ratio)" if precision == "fp8" else " bf16 burst")
+    med = lambda xs: statistics.median(xs)  # noqa: E731
+    last = sums[-1]
+    nq = last["n_recheck"]
+    first = {"fp64": ("alu", 1.25, "nominal FP64 ALU"), "fp32": ("alu", alu, "derived FP32 ALU")}.get(
+        precision, ("tensor", tensor, tkind))
+    rows = [("screen (first pass over every point)", med([x["ms_screen"] for x in sums]), fpp * n_pts) + first,
+            ("split tensor pass", med([x["ms_pass"][0] for x in sums]), 3 * fpp * nq[0], "tensor", tensor, tkind),
+            ("FP32 pass", med([x["ms_pass"][1] for x in sums]), fpp * nq[1], "alu", alu, "derived FP32 ALU"),
+            ("double-float pass", med([x["ms_pass"][2] for x in sums]), fpp * nq[2], "alu", alu * 2 / 11,
+             "derived FP32 ALU x 2/11"),
+            ("FP64 pass", med([x["ms_pass"][3] for x in sums]), fpp * nq[3], "alu", 1.25, "nominal FP64 ALU")]
+    passes = []
+    for name, ms, flops, bound, peak, kind in rows:
+        if ms <= 0.0:
+            continue
+        ach = flops / (ms / 1000.0) / 1e12
+        passes.append({"kernel": name, "launch_ms": ms, "flops_per_launch": flops, "bound": bound,
+                       "achieved": ach, "peak": peak, "peak_kind": kind, "frac": ach / peak})
+    top = max(passes, key=lambda x: x["launch_ms"])
+    roof = {"bound": top["bound"], "achieved": top["achieved"], "peak": top["peak"], "unit": "TFLOP/s",
+            "frac": top["frac"], "traffic": None, "kernel": top["kernel"], "peak_kind": top["peak_kind"],
+            "flops_per_launch": top["flops_per_launch"], "launch_ms": top["launch_ms"], "passes": passes}
+    return roof
+
+
 # -------------------------------------------------------------------- main
 
 def main_batch(a):
@@ -406,7 +445,6 @@ def main():
                                coverage=not a.no_coverage)
         ev[i][1].record(stream)
         sm = vb.result_summary(res)
-        screen_ms.append(sm["ms_screen"])
         sums.append(sm)
     torch.cuda.synchronize()
     barrier()
@@ -442,23 +480,7 @@ def main():
         last = sums[-1]
         pk, pk_kind = peaks()
         L = len(cfg["dims"]) - 1
-        scr_ms = statistics.median(screen_ms)
-        flops = screen_flops_per_point(cfg["dims"], s) * n_pts
-        if a.precision in ("bf16", "fp16", "fp8"):
-            peak = pk.get("bf16_tflops", 1900.0)
-            if a.precision == "fp8":
-                peak *= 2.0
-            roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": peak,
-                    "peak_kind": pk_kind + (" bf16 x2 (fp8 nominal ratio)" if a.precision == "fp8" else " bf16 burst")}
-        else:
-            mhz = pk.get("sm_max_mhz", 2070.0)
-            peak = 152 * 128 * 2 * mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 FLOP x clock
-            roof = {"bound": "alu", "unit": "TFLOP/s", "peak": peak,
-                    "peak_kind": "derived: 152 SM x 128 FP32 lanes x 2 FLOP x sm_max_mhz"}
-        achieved = flops / (scr_ms / 1000.0) / 1e12
-        roof.update({"achieved": achieved, "frac": achieved / peak, "traffic": None,
-                     "kernel": "screen pass (first pass over every point)",
-                     "flops_per_launch": flops, "launch_ms": scr_ms})
+        roof = pass_rooflines(a.precision, cfg["dims"], s, n_pts, sums, pk, pk_kind)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -479,7 +501,8 @@ def main():
                 "verdict": {"verdict": last["verdict"], "n_adversarial": last["n_adversarial"],
                             "first_witness": last["first_witness"], "n_ties": last["n_ties"],
                             "n_recheck": last["n_recheck"], "ms_prologue": last["ms_prologue"],
-                            "ms_screen": last["ms_screen"], "ms_recheck": last["ms_recheck"]},
+                            "ms_screen": last["ms_screen"], "ms_recheck": last["ms_recheck"],
+                            "ms_pass": dict(zip(("split", "fp32", "double_float", "fp64"), last["ms_pass"]))},
                 "wall_s": wall}
         if ck:
             line["clocks"] = ck

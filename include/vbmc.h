@@ -151,6 +151,10 @@ typedef struct {
     double ms_recheck;         /* of which: all later passes              */
     double ms_to_verdict;      /* device time from the query's prologue to
                                 * its final result (batch: per query)     */
+    double ms_pass[4];         /* of the recheck time: split tensor pass,
+                                * FP32 pass, double-float pass, FP64 pass
+                                * (batch: first wave; wide-layer path: all
+                                * in ms_screen, its chunks interleave)     */
 } vbmc_summary;
 
 typedef struct vbmc_net vbmc_net;

@@ -59,7 +59,8 @@ class _Summary(C.Structure):
                 ("first_witness", C.c_uint64), ("n_ties", C.c_uint64),
                 ("n_recheck", C.c_uint64 * 4), ("ms_device", C.c_double),
                 ("ms_prologue", C.c_double), ("ms_screen", C.c_double),
-                ("ms_recheck", C.c_double), ("ms_to_verdict", C.c_double)]
+                ("ms_recheck", C.c_double), ("ms_to_verdict", C.c_double),
+                ("ms_pass", C.c_double * 4)]
 
 
 class _SearchOut(C.Structure):
@@ -248,7 +249,7 @@ def _summary_dict(s: _Summary) -> dict:
             "first_witness": None if s.first_witness == NO_WITNESS else int(s.first_witness),
             "n_ties": s.n_ties, "n_recheck": list(s.n_recheck), "ms_device": s.ms_device,
             "ms_prologue": s.ms_prologue, "ms_screen": s.ms_screen, "ms_recheck": s.ms_recheck,
-            "ms_to_verdict": s.ms_to_verdict}
+            "ms_to_verdict": s.ms_to_verdict, "ms_pass": list(s.ms_pass)}
 
 
 def verify_query(net: Net, res: Result, image, pixels, k: int, lo: int = 0, hi: int = 0,

@@ -91,7 +91,7 @@ struct BatchArena {
     unsigned long long* d_qcount = nullptr;
     QEntry* d_queue[4] = {nullptr, nullptr, nullptr, nullptr};
     uint64_t queue_cap = 0;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[7] = {};  // start, prologue, screen, end, split, FP32, double-float
     cudaEvent_t evw = nullptr;       // marks between waves (not read)
     cudaStream_t gstream = nullptr;  // graph capture needs a capturable (non-legacy) stream
     cudaEvent_t gev = nullptr;
@@ -116,6 +116,7 @@ struct vbmc_result {
     double* d_margin = nullptr;
     WideWork ww{};  // chunk workspace of the wide-layer path (allocated on first use)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_pro = nullptr, ev_scr = nullptr;
+    cudaEvent_t ev_split = nullptr, ev_f32 = nullptr, ev_df = nullptr;  // after each recheck pass
     cudaStream_t last_stream = nullptr;
     bool pending = false;
     bool have_result = false;
@@ -345,6 +346,9 @@ vbmc_status create_result(const vbmc_net* net, const vbmc_caps* caps, BatchArena
     if (e == cudaSuccess) e = cudaEventCreate(&r->ev1);
     if (e == cudaSuccess) e = cudaEventCreate(&r->ev_pro);
     if (e == cudaSuccess) e = cudaEventCreate(&r->ev_scr);
+    if (e == cudaSuccess) e = cudaEventCreate(&r->ev_split);
+    if (e == cudaSuccess) e = cudaEventCreate(&r->ev_f32);
+    if (e == cudaSuccess) e = cudaEventCreate(&r->ev_df);
     if (e != cudaSuccess) {
         vbmc_result_free(r);
         return fail(VBMC_ERR_OOM, std::string("result_create: ") + cudaGetErrorString(e));
@@ -395,7 +399,7 @@ extern "C" vbmc_status vbmc_result_create_batch(const vbmc_net* net, const vbmc_
     ar->queue_cap = std::max<uint64_t>(1, caps->queue_cap);
     for (int i = 0; i < 4; ++i) A(&ar->d_queue[i], (size_t)ar->queue_cap);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ar->h_cnt, sizeof(Counters) * (size_t)nq);
-    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaEventCreate(&ar->ev[i]);
+    for (int i = 0; i < 7 && e == cudaSuccess; ++i) e = cudaEventCreate(&ar->ev[i]);
     if (e == cudaSuccess) e = cudaEventCreate(&ar->evw);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ar->gstream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ar->gev, cudaEventDisableTiming);
@@ -426,6 +430,8 @@ extern "C" vbmc_status vbmc_result_free(vbmc_result* r) {
     if (r->ev1) cudaEventDestroy(r->ev1);
     if (r->ev_pro) cudaEventDestroy(r->ev_pro);
     if (r->ev_scr) cudaEventDestroy(r->ev_scr);
+    for (cudaEvent_t x : {r->ev_split, r->ev_f32, r->ev_df})
+        if (x) cudaEventDestroy(x);
     delete r;
     return VBMC_OK;
 }
@@ -453,7 +459,8 @@ vbmc_status check_query_shape(const vbmc_result* r, int s, int k, uint64_t lo, u
 // prefix; 0 tiles for the FP64 path (one block per point there).
 std::vector<unsigned long long> tile_prefix(const NetView& v, int precision, QueryView* hq, int nq) {
     const int MT = precision == VBMC_PREC_FP64 ? 0
-                   : precision == VBMC_PREC_FP32 ? simt_tile_points(v)
+                   : precision == VBMC_PREC_FP32 ? (nq == 1 && small_supported(v) ? small_tile_points()
+                                                                                 : simt_tile_points(v))
                                                  : tc_tile_points();
     std::vector<unsigned long long> tp((size_t)nq + 1, 0);
     for (int i = 0; i < nq; ++i) {
@@ -473,7 +480,8 @@ std::vector<unsigned long long> tile_prefix(const NetView& v, int precision, Que
 enum { STAGE_SETUP = 1, STAGE_PASSES = 2, STAGE_ALL = 3 };
 
 // Every pass for nq queries whose views (and tile prefix) are already on the
-// device. ev: start, after the prologue, after the first pass, end. The set-up
+// device. ev: start, after the prologue, after the first pass, end, after the
+// split tensor pass, after the FP32 pass, after the double-float pass. The set-up
 // stage resets the counters and clears the masks and the verdict bitmap over
 // [0, hi); everything else it computes depends on the box, not on [lo, hi),
 // so one set-up over the whole space serves passes over any sub-ranges.
@@ -527,21 +535,33 @@ vbmc_status enqueue_passes(vbmc_net* net, QueryView* d_qs, const QueryView* hq, 
     Queue q32{d_queue[1], d_qcount + 1, cap};
     Queue qdf{d_queue[2], d_qcount + 2, cap};
     Queue q64{d_queue[3], d_qcount + 3, cap};
+    auto record_rest = [&]() -> cudaError_t {  // passes that did not run take no time
+        for (int i : {4, 5, 6}) {
+            const cudaError_t e = record(ev[i]);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
     if (any && wide) {
-        VB_CUDA(record(ev[2]));
+        // the chunk loop interleaves the screen and the rechecks: all of it counts as screen
         vbmc_status fs = wide_run(net->wide, wtype, *ww, v, d_qs, hq[0].lo, hq[0].hi, d_qcount, d_queue, cap,
                                   net->n_sm, st);
         if (fs != VBMC_OK) return fail(fs, "wide-layer tensor screen launch failed");
+        VB_CUDA(record(ev[2]));
+        VB_CUDA(record_rest());
     } else if (any && opt.precision == VBMC_PREC_FP64) {
         for (int i = 0; i < nq; ++i)
             if (hq[i].hi > hq[i].lo)
                 launch_fp64(v, d_qs + i, 1, nullptr, nullptr, 0, hq[i].lo, hq[i].hi, net->n_sm, st);
         VB_CUDA(record(ev[2]));
+        VB_CUDA(record_rest());
     } else if (any) {
         if (opt.precision == VBMC_PREC_FP32) {
             if (simt_tile_points(v) == 0) return fail(VBMC_ERR_UNSUPPORTED, "layer width above 1024");
             launch_screen_simt(v, d_qs, nq, d_tp, ntiles, nullptr, nullptr, 0, qdf, 2, net->n_sm, st);
             VB_CUDA(record(ev[2]));
+            VB_CUDA(record(ev[4]));
+            VB_CUDA(record(ev[5]));
         } else {
             // one query: screen -> split tensor pass -> FP32; many: screen -> FP32 directly
             vbmc_status sst = tc_launch_screen(net->tc, v, d_qs, nq, d_tp, ntiles, opt.precision,
@@ -553,13 +573,17 @@ vbmc_status enqueue_passes(vbmc_net* net, QueryView* d_qs, const QueryView* hq, 
                                        q32, net->n_sm, st);
                 if (sst != VBMC_OK) return fail(sst, "tensor-core split pass launch failed");
             }
+            VB_CUDA(record(ev[4]));
             launch_screen_simt(v, d_qs, nq, nullptr, 0, d_queue[1], d_qcount + 1, cap, qdf, 2,
                                net->n_sm, st);
+            VB_CUDA(record(ev[5]));
         }
         launch_df(v, d_qs, d_queue[2], d_qcount + 2, cap, q64, 3, net->n_sm, st);
+        VB_CUDA(record(ev[6]));
         launch_fp64(v, d_qs, nq, d_queue[3], d_qcount + 3, cap, 0, 0, net->n_sm, st);
     } else {
         VB_CUDA(record(ev[2]));
+        VB_CUDA(record_rest());
     }
     launch_stamp_final(d_qs, nq, st);
     VB_CUDA(cudaGetLastError());
@@ -592,7 +616,7 @@ vbmc_status enqueue(vbmc_net* net, vbmc_result* r, const uint8_t* d_image, const
     std::vector<unsigned long long> tp = tile_prefix(net->v, opt.precision, &q, 1);
     VB_CUDA(cudaMemcpyAsync(r->d_q, &q, sizeof(QueryView), cudaMemcpyHostToDevice, st));
     VB_CUDA(cudaMemcpyAsync(r->d_tp, tp.data(), sizeof(unsigned long long) * 2, cudaMemcpyHostToDevice, st));
-    const cudaEvent_t ev[4] = {r->ev0, r->ev_pro, r->ev_scr, r->ev1};
+    const cudaEvent_t ev[7] = {r->ev0, r->ev_pro, r->ev_scr, r->ev1, r->ev_split, r->ev_f32, r->ev_df};
     vbmc_status sst = enqueue_passes(net, r->d_q, &q, 1, r->d_tp, tp[1], r->d_qcount, r->d_queue,
                                      std::max<uint64_t>(1, r->caps.queue_cap), ev, opt, st, false, STAGE_ALL,
                                      &r->ww);
@@ -610,7 +634,8 @@ vbmc_status enqueue(vbmc_net* net, vbmc_result* r, const uint8_t* d_image, const
     return VBMC_OK;
 }
 
-void fill_summary(vbmc_result* r, const Counters& c, float ms, float ms_p, float ms_s) {
+void fill_summary(vbmc_result* r, const Counters& c, float ms, float ms_p, float ms_s,
+                  const float* ms_pass = nullptr) {
     vbmc_summary& s = r->sum;
     std::memset(&s, 0, sizeof(s));
     s.D = c.D;
@@ -624,6 +649,7 @@ void fill_summary(vbmc_result* r, const Counters& c, float ms, float ms_p, float
     s.ms_prologue = ms_p;
     s.ms_screen = ms_s;
     s.ms_recheck = ms - ms_p - ms_s;
+    for (int i = 0; i < 4; ++i) s.ms_pass[i] = ms_pass ? ms_pass[i] : 0.0;
     s.ms_to_verdict = c.t_final > c.t0 ? (double)(c.t_final - c.t0) * 1e-6 : 0.0;
     if (r->lo != 0 || r->hi != r->n_space) s.verdict = VBMC_PARTIAL;
     else if (c.n_adv) s.verdict = VBMC_UNSAFE;
@@ -647,7 +673,13 @@ vbmc_status finish(vbmc_result* r) {
         cudaEventElapsedTime(&ms, r->ev0, r->ev1);
         cudaEventElapsedTime(&ms_p, r->ev0, r->ev_pro);
         cudaEventElapsedTime(&ms_s, r->ev_pro, r->ev_scr);
-        fill_summary(r, *r->h_cnt, ms, ms_p, ms_s);
+        float mp[4] = {0.f, 0.f, 0.f, 0.f};
+        cudaEventElapsedTime(&mp[0], r->ev_scr, r->ev_split);
+        cudaEventElapsedTime(&mp[1], r->ev_split, r->ev_f32);
+        cudaEventElapsedTime(&mp[2], r->ev_f32, r->ev_df);
+        cudaEventElapsedTime(&mp[3], r->ev_df, r->ev1);
+        (void)cudaGetLastError();  // timing is informative only
+        fill_summary(r, *r->h_cnt, ms, ms_p, ms_s, mp);
         r->last_status = counters_status(*r->h_cnt);
     }
     return r->last_status;
@@ -935,8 +967,11 @@ extern "C" vbmc_status vbmc_verify_batch(vbmc_net* net, const vbmc_query* querie
     auto run_waves = [&](bool capturing) -> vbmc_status {
         for (int w = 0; w < n_waves; ++w) {
             const int j0 = wave_at[w], j1 = wave_at[w + 1];
-            const cudaEvent_t evs[4] = {w == 0 ? ar->ev[0] : ar->evw, w == 0 ? ar->ev[1] : ar->evw,
-                                        w == 0 ? ar->ev[2] : ar->evw, w == n_waves - 1 ? ar->ev[3] : ar->evw};
+            // pass times are those of the first wave
+            const cudaEvent_t evs[7] = {w == 0 ? ar->ev[0] : ar->evw, w == 0 ? ar->ev[1] : ar->evw,
+                                        w == 0 ? ar->ev[2] : ar->evw, w == n_waves - 1 ? ar->ev[3] : ar->evw,
+                                        w == 0 ? ar->ev[4] : ar->evw, w == 0 ? ar->ev[5] : ar->evw,
+                                        w == 0 ? ar->ev[6] : ar->evw};
             vbmc_status ws = enqueue_passes(net, ar->d_qs_run + j0, hrun.data() + j0, j1 - j0,
                                             ar->d_tp + tp_at[w], wave_tiles[w], ar->d_qcount, ar->d_queue,
                                             ar->queue_cap, evs, *opt, st, capturing);
@@ -973,6 +1008,13 @@ extern "C" vbmc_status vbmc_verify_batch(vbmc_net* net, const vbmc_query* querie
     cudaEventElapsedTime(&ms, ar->ev[0], ar->ev[3]);
     cudaEventElapsedTime(&ms_p, ar->ev[0], ar->ev[1]);
     cudaEventElapsedTime(&ms_s, ar->ev[1], ar->ev[2]);
+    float mp[4] = {0.f, 0.f, 0.f, 0.f};
+    if (n_waves == 1) {
+        cudaEventElapsedTime(&mp[0], ar->ev[2], ar->ev[4]);
+        cudaEventElapsedTime(&mp[1], ar->ev[4], ar->ev[5]);
+        cudaEventElapsedTime(&mp[2], ar->ev[5], ar->ev[6]);
+        cudaEventElapsedTime(&mp[3], ar->ev[6], ar->ev[3]);
+    }
     (void)cudaGetLastError();  // timing is informative only
     vbmc_status result = VBMC_OK;
     for (int i = 0; i < nq; ++i) {
@@ -990,7 +1032,7 @@ extern "C" vbmc_status vbmc_verify_batch(vbmc_net* net, const vbmc_query* querie
         r->image.assign(q.image, q.image + H0);
         r->pixels.assign(q.pixels, q.pixels + q.s);
         r->hq.image = hq[i].image;
-        fill_summary(r, ar->h_cnt[i], ms, ms_p, ms_s);
+        fill_summary(r, ar->h_cnt[i], ms, ms_p, ms_s, mp);
         r->last_status = counters_status(ar->h_cnt[i]);
         if (r->last_status != VBMC_OK && result == VBMC_OK) result = r->last_status;
     }
@@ -1034,11 +1076,13 @@ extern "C" vbmc_status vbmc_search_query(vbmc_net* net, const vbmc_query* q, int
     QueryView qv = make_view(res, res->d_image, res->d_pix_in, q->s, q->k, 0, n, n, *opt, 0);
     std::vector<unsigned long long> tp = tile_prefix(net->v, opt->precision, &qv, 1);
     VB_CUDA(cudaMemcpyAsync(res->d_q, &qv, sizeof(QueryView), cudaMemcpyHostToDevice, sq));
-    const cudaEvent_t ev_set[4] = {res->ev0, res->ev_pro, res->ev_pro, res->ev_pro};
+    const cudaEvent_t ev_set[7] = {res->ev0,    res->ev_pro, res->ev_pro, res->ev_pro,
+                                   res->ev_pro, res->ev_pro, res->ev_pro};
     st = enqueue_passes(net, res->d_q, &qv, 1, res->d_tp, tp[1], res->d_qcount, res->d_queue, cap, ev_set,
                         *opt, sq, false, STAGE_SETUP, &res->ww);
     if (st != VBMC_OK) return st;
-    const cudaEvent_t ev_tile[4] = {res->ev_scr, res->ev_scr, res->ev_scr, res->ev1};
+    const cudaEvent_t ev_tile[7] = {res->ev_scr, res->ev_scr, res->ev_scr, res->ev1,
+                                    res->ev_scr, res->ev_scr, res->ev_scr};
     const uint64_t tsize = (n + n_tiles - 1) / n_tiles;
     vbmc_search_out so{0, -1, 0, 0.0};
     vbmc_status run = VBMC_OK;

@@ -2,7 +2,8 @@
 // with FP32 pairs (hi + lo, about 48 significant bits) on the CUDA cores, which
 // on this part run several times faster than FP64.
 //
-// One CTA per point. Layer 1 in FP64 (incremental, Eq. 1). Layers 2..L on the
+// Four points per CTA (each weight load serves all four). Layer 1 in FP64
+// (incremental, Eq. 1). Layers 2..L on the
 // deltas dh = h(point) - h(unperturbed), each weight (exact in FP32) times a
 // pair (hi, lo): the product's rounding error is recovered exactly with an
 // FMA, sums use TwoSum (Knuth), so a K-term dot product carries at most
@@ -39,163 +40,209 @@ __device__ __forceinline__ double block_sum64(double v, double* red) {
     return t;
 }
 
+// PB points per CTA (one weight load serves all of them). Per point b: its
+// potentials u[b], delta pair dh[b], certain sign changes fl[b].
+template <int PB>
 __global__ void __launch_bounds__(TDF)
 k_df(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__ gather,
      const unsigned long long* __restrict__ gcount, unsigned long long gcap, Queue out,
      int out_level) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int total = net.total, hmax = net.hmax;
-    double* u = reinterpret_cast<double*>(smem_raw);                  // [total]
-    float2* dh = reinterpret_cast<float2*>(u + total);                // [hmax]
-    unsigned char* fl = reinterpret_cast<unsigned char*>(dh + hmax);  // [total]
+    double* u = reinterpret_cast<double*>(smem_raw);                       // [PB][total]
+    float2* dh = reinterpret_cast<float2*>(u + (size_t)PB * total);        // [PB][hmax]
+    unsigned char* fl = reinterpret_cast<unsigned char*>(dh + (size_t)PB * hmax);  // [PB][total]
     __shared__ double red[32];
-    __shared__ int nflip[kMaxL + 2], only[kMaxL + 2];
-    __shared__ int dstep[kMaxS];
-    __shared__ int undecided;
+    __shared__ int nflip[PB][kMaxL + 2], only[PB][kMaxL + 2];
+    __shared__ int dstep[PB][kMaxS];
+    __shared__ int undecided[PB], valid[PB];
+    __shared__ unsigned long long tpt[PB];
+    __shared__ unsigned qpt[PB];
 
     unsigned long long n = *gcount;
     if (n > gcap) n = gcap;
     const int L = net.L;
     const double c46 = 0x1p-46, u52 = 0x1p-52;
     const double lam = net.act == ACT_SIGMOID ? 0.25 : 1.0;
-    for (unsigned long long e = blockIdx.x; e < n; e += gridDim.x) {
-        const QEntry en = gather[e];
-        const unsigned long long t = en.t;
-        const QueryView& Q = qs[en.q];
-        if (threadIdx.x == 0) {
-            int d[kMaxS];
-            decode_digits(t, Q.s, Q.R, d);
-            for (int p = 0; p < Q.s; ++p) dstep[p] = Q.dv[p * Q.R + d[p]];
-            undecided = 0;
+    for (unsigned long long e0 = (unsigned long long)blockIdx.x * PB; e0 < n;
+         e0 += (unsigned long long)gridDim.x * PB) {
+        if (threadIdx.x < PB) {
+            const int b = threadIdx.x;
+            const bool ok = e0 + b < n;
+            valid[b] = ok;
+            undecided[b] = 0;
+            if (ok) {
+                const QEntry en = gather[e0 + b];
+                tpt[b] = en.t;
+                qpt[b] = en.q;
+                const QueryView& Q = qs[en.q];
+                int d[kMaxS];
+                decode_digits(en.t, Q.s, Q.R, d);
+                for (int p = 0; p < Q.s; ++p) dstep[b][p] = Q.dv[p * Q.R + d[p]];
+            }
         }
-        if (threadIdx.x <= kMaxL + 1) {
-            nflip[threadIdx.x] = 0;
-            only[threadIdx.x] = -1;
+        if (threadIdx.x < PB * (kMaxL + 2)) {
+            nflip[threadIdx.x / (kMaxL + 2)][threadIdx.x % (kMaxL + 2)] = 0;
+            only[threadIdx.x / (kMaxL + 2)][threadIdx.x % (kMaxL + 2)] = -1;
         }
         __syncthreads();
+        double N[PB], E[PB];
         // ---- layer 1 in FP64; its signs are decided here
         const int H0 = net.dims[0], H1 = net.dims[1];
-        double nsq = 0.0, esq = 0.0;
-        for (int j = threadIdx.x; j < H1; j += TDF) {
-            const double ub = Q.ub[j];
-            double a = ub, mag = fabs(ub);
-            for (int p = 0; p < Q.s; ++p) {
-                const double term = (double)net.W[1][(size_t)j * H0 + Q.pix[p]] * ((double)dstep[p] / 255.0);
-                a += term;
-                mag += fabs(term);
+        for (int b = 0; b < PB; ++b) {
+            double nsq = 0.0, esq = 0.0;
+            if (valid[b]) {
+                const QueryView& Q = qs[qpt[b]];
+                for (int j = threadIdx.x; j < H1; j += TDF) {
+                    const double ub = Q.ub[j];
+                    double a = ub, mag = fabs(ub);
+                    for (int p = 0; p < Q.s; ++p) {
+                        const double term =
+                            (double)net.W[1][(size_t)j * H0 + Q.pix[p]] * ((double)dstep[b][p] / 255.0);
+                        a += term;
+                        mag += fabs(term);
+                    }
+                    u[(size_t)b * total + j] = a;
+                    // |a - exact| <= base error + rounding of the s additions and the terms
+                    const double err = Q.eub[j] + (Q.s + 3) * u52 * mag;
+                    const bool certain = fabs(a) > err + 2.0 * kTau && fabs(ub) >= kTau;
+                    if (!certain && Q.flip) undecided[b] = 1;  // signs matter only for coverage
+                    fl[(size_t)b * total + j] = certain && ((a >= 0.0) != (ub >= 0.0));
+                    const double d = (L > 1 ? act64(net.act, a) : a) - Q.hb[j];
+                    const float hi = (float)d;
+                    dh[(size_t)b * hmax + j] = make_float2(hi, (float)(d - (double)hi));
+                    nsq += d * d;
+                    const double ej = 2.0 * err + u52 * (fabs(a) + fabs(Q.hb[j])) * 4.0 + 0x1p-47 * fabs(d);
+                    esq += ej * ej;
+                }
             }
-            u[j] = a;
-            // |a - exact| <= base error + rounding of the s additions and the terms
-            const double err = Q.eub[j] + (Q.s + 3) * u52 * mag;
-            const bool certain = fabs(a) > err + 2.0 * kTau && fabs(ub) >= kTau;
-            if (!certain && Q.flip) undecided = 1;  // signs matter only for coverage
-            fl[j] = certain && ((a >= 0.0) != (ub >= 0.0));
-            const double d = (L > 1 ? act64(net.act, a) : a) - Q.hb[j];
-            const float hi = (float)d;
-            dh[j] = make_float2(hi, (float)(d - (double)hi));
-            nsq += d * d;
-            const double ej = 2.0 * err + u52 * (fabs(a) + fabs(Q.hb[j])) * 4.0 + 0x1p-47 * fabs(d);
-            esq += ej * ej;
+            N[b] = sqrt(block_sum64(nsq, red)) * (1.0 + 1e-12);
+            E[b] = sqrt(block_sum64(esq, red)) * (1.0 + 1e-12);
         }
-        double N = sqrt(block_sum64(nsq, red)) * (1.0 + 1e-12);
-        double E = sqrt(block_sum64(esq, red)) * (1.0 + 1e-12);
-        // ---- layers 2..L in double-float
-        for (int l = 2; l <= L && !undecided; ++l) {
+        // ---- layers 2..L in double-float, PB points per weight load
+        for (int l = 2; l <= L; ++l) {
+            bool any = false;
+            for (int b = 0; b < PB; ++b) any = any || (valid[b] && !undecided[b]);
+            if (!any) break;
             const int K = net.dims[l - 1], Nn = net.dims[l], off = net.noff[l];
             const float* WT = net.WT[l];
             const double cK = (K + 2) * c46;
-            double nsq2 = 0.0, esq2 = 0.0;
+            double nsq2[PB], esq2[PB];
+            for (int b = 0; b < PB; ++b) nsq2[b] = esq2[b] = 0.0;
             for (int i = threadIdx.x; i < Nn; i += TDF) {
-                float S = 0.f, s = 0.f;
+                float S[PB], sl[PB];
+#pragma unroll
+                for (int b = 0; b < PB; ++b) S[b] = sl[b] = 0.f;
                 for (int j = 0; j < K; ++j) {
                     const float w = WT[(size_t)j * Nn + i];
-                    const float2 h = dh[j];
-                    const float p = __fmul_rn(w, h.x);
-                    float ep = __fmaf_rn(w, h.x, -p);
-                    ep = __fmaf_rn(w, h.y, ep);
-                    const float tt = __fadd_rn(S, p);
-                    const float z = __fsub_rn(tt, S);
-                    const float er = __fadd_rn(__fsub_rn(S, __fsub_rn(tt, z)), __fsub_rn(p, z));
-                    S = tt;
-                    s = __fadd_rn(s, __fadd_rn(er, ep));
+#pragma unroll
+                    for (int b = 0; b < PB; ++b) {
+                        const float2 h = dh[(size_t)b * hmax + j];
+                        const float pr = __fmul_rn(w, h.x);
+                        float ep = __fmaf_rn(w, h.x, -pr);
+                        ep = __fmaf_rn(w, h.y, ep);
+                        const float tt = __fadd_rn(S[b], pr);
+                        const float z = __fsub_rn(tt, S[b]);
+                        const float er = __fadd_rn(__fsub_rn(S[b], __fsub_rn(tt, z)), __fsub_rn(pr, z));
+                        S[b] = tt;
+                        sl[b] = __fadd_rn(sl[b], __fadd_rn(er, ep));
+                    }
                 }
-                const double ub = Q.ub[off + i];
-                const double ui = ub + ((double)S + (double)s);
-                u[off + i] = ui;
-                const double err = (double)net.rownorm[l][i] * (cK * N + E) + Q.eub[off + i] +
-                                   u52 * (fabs(ui) + fabs(ub));
-                const bool certain = fabs(ui) > err + 2.0 * kTau && fabs(ub) >= kTau;
-                if (!certain && Q.flip) undecided = 1;  // signs matter only for coverage
-                fl[off + i] = certain && ((ui >= 0.0) != (ub >= 0.0));
-                if (l < L) {
-                    const double d = act64(net.act, ui) - Q.hb[off + i];
-                    nsq2 += d * d;
-                    const double ej = lam * (Q.eub[off + i] + u52 * (fabs(ui) + fabs(ub))) +
-                                      Q.eub[off + i] + u52 * (fabs(ui) + fabs(Q.hb[off + i])) * 4.0 +
-                                      0x1p-47 * fabs(d);
-                    esq2 += ej * ej;
+#pragma unroll
+                for (int b = 0; b < PB; ++b) {
+                    if (!valid[b] || undecided[b]) continue;
+                    const QueryView& Q = qs[qpt[b]];
+                    const double ub = Q.ub[off + i];
+                    const double ui = ub + ((double)S[b] + (double)sl[b]);
+                    u[(size_t)b * total + off + i] = ui;
+                    const double err = (double)net.rownorm[l][i] * (cK * N[b] + E[b]) + Q.eub[off + i] +
+                                       u52 * (fabs(ui) + fabs(ub));
+                    const bool certain = fabs(ui) > err + 2.0 * kTau && fabs(ub) >= kTau;
+                    if (!certain && Q.flip) undecided[b] = 1;  // signs matter only for coverage
+                    fl[(size_t)b * total + off + i] = certain && ((ui >= 0.0) != (ub >= 0.0));
+                    if (l < L) {
+                        const double d = act64(net.act, ui) - Q.hb[off + i];
+                        nsq2[b] += d * d;
+                        const double ej = lam * (Q.eub[off + i] + u52 * (fabs(ui) + fabs(ub))) +
+                                          Q.eub[off + i] + u52 * (fabs(ui) + fabs(Q.hb[off + i])) * 4.0 +
+                                          0x1p-47 * fabs(d);
+                        esq2[b] += ej * ej;
+                    }
                 }
             }
             __syncthreads();  // dh of layer l-1 fully consumed
             if (l < L) {
-                for (int i = threadIdx.x; i < Nn; i += TDF) {
-                    const double d = act64(net.act, u[off + i]) - Q.hb[off + i];
-                    const float hi = (float)d;
-                    dh[i] = make_float2(hi, (float)(d - (double)hi));
+                for (int b = 0; b < PB; ++b) {
+                    if (valid[b]) {
+                        const QueryView& Q = qs[qpt[b]];
+                        for (int i = threadIdx.x; i < Nn; i += TDF) {
+                            const double d = act64(net.act, u[(size_t)b * total + off + i]) - Q.hb[off + i];
+                            const float hi = (float)d;
+                            dh[(size_t)b * hmax + i] = make_float2(hi, (float)(d - (double)hi));
+                        }
+                    }
+                    // ||err(dh_l)|| <= lambda (sigma_l E + (K+2) 2^-46 ||W_l||_F N) + per-element rounding
+                    const double En = lam * ((double)net.sig[l] * E[b] + cK * (double)net.frob[l] * N[b]);
+                    N[b] = sqrt(block_sum64(nsq2[b], red)) * (1.0 + 1e-12);
+                    E[b] = (En + sqrt(block_sum64(esq2[b], red))) * (1.0 + 1e-12);
                 }
-                // ||err(dh_l)|| <= lambda (sigma_l E + (K+2) 2^-46 ||W_l||_F N) + per-element rounding
-                const double En = lam * ((double)net.sig[l] * E + cK * (double)net.frob[l] * N);
-                N = sqrt(block_sum64(nsq2, red)) * (1.0 + 1e-12);
-                E = (En + sqrt(block_sum64(esq2, red))) * (1.0 + 1e-12);
             }
             __syncthreads();
         }
-        // ---- verdict (Eq. 10) with the margin bound of each class pair
-        if (threadIdx.x == 0 && !undecided) {
+        // ---- verdict (Eq. 10) with the margin bound of each class pair: thread b
+        if (threadIdx.x < PB && valid[threadIdx.x] && !undecided[threadIdx.x]) {
+            const int b = threadIdx.x;
+            const QueryView& Q = qs[qpt[b]];
             const int HL = net.dims[L], offL = net.noff[L];
-            const double* y = u + offL;
+            const double* y = u + (size_t)b * total + offL;
             const int D = Q.cnt->D;
             const double cK = (net.dims[L - 1] + 2) * c46;
             bool unsafe = false, safe = true;
             for (int o = 0; o < HL; ++o) {
                 if (o == D) continue;
                 const double diff = y[D] - y[o];
-                double eb = ((double)net.rownorm[L][D] + (double)net.rownorm[L][o]) * cK * N +
+                double eb = ((double)net.rownorm[L][D] + (double)net.rownorm[L][o]) * cK * N[b] +
                             Q.eub[offL + D] + Q.eub[offL + o] + 2.0 * kTau +
                             u52 * 2.0 * (fabs(y[D]) + fabs(y[o]) + fabs(Q.ub[offL + D]) + fabs(Q.ub[offL + o]));
-                eb += (L > 1 ? (double)net.pairw[D * HL + o] : 0.0) * E;
+                eb += (L > 1 ? (double)net.pairw[D * HL + o] : 0.0) * E[b];
                 if (diff < -eb) unsafe = true;
                 else if (!(diff > eb)) safe = false;
             }
-            if (!unsafe && !safe) undecided = 1;
-            if (!undecided && unsafe) record_adversarial(Q, t);
+            if (!unsafe && !safe) undecided[b] = 1;
+            if (!undecided[b] && unsafe) record_adversarial(Q, tpt[b]);
         }
         __syncthreads();
-        if (undecided) {
-            if (threadIdx.x == 0) queue_push(out, t, en.q, Q.cnt, out_level);
-        } else {
-            // sign changes and SS-Cover pairs; every decision here is certain (no ties)
-            for (int nn = threadIdx.x; nn < total; nn += TDF) {
-                if (!fl[nn]) continue;
-                int l = 1;
-                while (l < L && nn >= net.noff[l + 1]) ++l;
-                atomicAdd(&nflip[l], 1);
-                atomicMax(&only[l], nn - net.noff[l]);
-                if (Q.flip) set_bit_once(Q.flip, nn);
-            }
-            __syncthreads();
-            if (Q.ss) {
-                for (int l = 1; l < L; ++l) {
-                    if (nflip[l] != 1) continue;
-                    const int j = only[l], Hn = net.dims[l + 1], on = net.noff[l + 1];
-                    for (int i = threadIdx.x; i < Hn; i += TDF)
-                        if (fl[on + i])
-                            set_bit_once(Q.ss, (unsigned long long)net.ssoff[l] + (unsigned long long)j * Hn + i);
+        for (int b = 0; b < PB; ++b) {
+            if (!valid[b]) continue;
+            const QueryView& Q = qs[qpt[b]];
+            if (undecided[b]) {
+                if (threadIdx.x == 0) queue_push(out, tpt[b], qpt[b], Q.cnt, out_level);
+            } else {
+                // sign changes and SS-Cover pairs; every decision here is certain (no ties)
+                const unsigned char* flb = fl + (size_t)b * total;
+                for (int nn = threadIdx.x; nn < total; nn += TDF) {
+                    if (!flb[nn]) continue;
+                    int l = 1;
+                    while (l < L && nn >= net.noff[l + 1]) ++l;
+                    atomicAdd(&nflip[b][l], 1);
+                    atomicMax(&only[b][l], nn - net.noff[l]);
+                    if (Q.flip) set_bit_once(Q.flip, nn);
+                }
+                __syncthreads();
+                if (Q.ss) {
+                    for (int l = 1; l < L; ++l) {
+                        if (nflip[b][l] != 1) continue;
+                        const int j = only[b][l], Hn = net.dims[l + 1], on = net.noff[l + 1];
+                        for (int i = threadIdx.x; i < Hn; i += TDF)
+                            if (flb[on + i])
+                                set_bit_once(Q.ss, (unsigned long long)net.ssoff[l] + (unsigned long long)j * Hn + i);
+                    }
                 }
             }
+            __syncthreads();
+            if (threadIdx.x == 0) work_done(Q.cnt, 1);  // time to verdict: this point is resolved
         }
         __syncthreads();
-        if (threadIdx.x == 0) work_done(Q.cnt, 1);  // time to verdict: this point is resolved
     }
 }
 
@@ -204,11 +251,12 @@ k_df(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__ g
 void launch_df(const NetView& net, const QueryView* d_qs, const QEntry* gather,
                const unsigned long long* gather_count, unsigned long long gather_cap, Queue out,
                int out_level, int n_sm, cudaStream_t st) {
-    const size_t smem = sizeof(double) * net.total + sizeof(float2) * net.hmax + (size_t)net.total;
-    cudaFuncSetAttribute(k_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    const int per_sm = (net.df_ctas >= 1 && net.df_ctas <= 32) ? net.df_ctas : 8;
-    k_df<<<(unsigned)(n_sm * per_sm), TDF, smem, st>>>(net, d_qs, gather, gather_count, gather_cap, out,
-                                                      out_level);
+    constexpr int PB = 4;
+    const size_t smem = PB * (sizeof(double) * net.total + sizeof(float2) * net.hmax + (size_t)net.total);
+    cudaFuncSetAttribute(k_df<PB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int per_sm = (net.df_ctas >= 1 && net.df_ctas <= 32) ? net.df_ctas : 4;
+    k_df<PB><<<(unsigned)(n_sm * per_sm), TDF, smem, st>>>(net, d_qs, gather, gather_count, gather_cap, out,
+                                                          out_level);
 }
 
 }  // namespace vbmc

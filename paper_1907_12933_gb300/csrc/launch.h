@@ -26,6 +26,14 @@ void launch_screen_simt(const NetView& net, const QueryView* d_qs, int nq,
 // Points per tile of the SIMT screen for this net (its range-pass variant).
 int simt_tile_points(const NetView& net);
 
+// The FP32 pass for small nets (every layer at most 32 neurons, one thread per
+// point): used for single-query calls; its tiles hold small_tile_points().
+bool small_supported(const NetView& net);
+int small_tile_points();
+void launch_small(const NetView& net, const QueryView* d_qs, const unsigned long long* tp,
+                  unsigned long long n_tiles, const QEntry* gather, const unsigned long long* gc,
+                  unsigned long long gcap, Queue out, int level, int n_sm, cudaStream_t st);
+
 // FP32 pass variants 1..4: widest layer held, points per tile, shared memory.
 int simt_variant_width(int var);
 int simt_variant_default(const NetView& net);

@@ -63,6 +63,10 @@ void launch_screen_simt(const NetView& net, const QueryView* d_qs, int nq,
                         const QEntry* gather, const unsigned long long* gc,
                         unsigned long long gcap, Queue out, int level, int n_sm,
                         cudaStream_t st) {
+    if (nq == 1 && small_supported(net)) {  // one thread per point
+        launch_small(net, d_qs, tp, n_tiles, gather, gc, gcap, out, level, n_sm, st);
+        return;
+    }
     int var = simt_variant(net);
     if (gather) {
         const int t = net.simt_var_gather;
