@@ -415,6 +415,8 @@ def main():
     dev = torch.device("cuda")
     stream = torch.cuda.current_stream()
     vnet = vb.Net(net_d)
+    # one-time launch-shape tuning, cached next to the build (not part of a step)
+    tuning = vb.autotune(vnet, os.path.join(ROOT, "paper_1907_12933_gb300", "_build", "tuning.jsonl"))
     res = vb.Result(vnet, max_points=n_pts, max_s=s, max_k=k, ties_cap=1 << 16,
                     queue_cap=n_pts)
     d_img = torch.tensor(q["image"], dtype=torch.uint8, device=dev)
@@ -490,6 +492,8 @@ def main():
                 "config": {"workload": a.workload, "dims": cfg["dims"], "act": cfg["act"],
                            "s": s, "k": k, "points_per_query": n_pts, "precision": a.precision,
                            "coverage": not a.no_coverage,
+                           "tuning": {key: tuning[key] for key in ("simt_range", "simt_range_ctas", "simt_gather",
+                                                                   "simt_gather_ctas", "df_ctas", "from_cache")},
                            "queries": "one per rank (rank r: query r of the workload seed)",
                            "l2": "flushed between timed steps (256 MB write)",
                            "parallelism": f"dp{world}" if world > 1 else "single GPU"},
