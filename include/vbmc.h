@@ -233,6 +233,45 @@ vbmc_status vbmc_get_ties(vbmc_result *res, uint64_t *idx, size_t cap, uint64_t 
 /* Message for the last failing call of this thread. */
 const char *vbmc_last_error(void);
 
+/* ---- The covering methods over a set of input pairs (Sec. III-B; no
+ * enumeration). For every pair (x1, x2) of H_0-byte images (grey levels), the
+ * FP64 potentials of both inputs decide, per non-input neuron n and layer k:
+ *   sc(n)  sign change (sign(u) = 1 iff u >= 0)
+ *   vc(n)  value change: no sign change and max(|u1|, |u2|) >= g min(|u1|, |u2|)
+ *   dc(k)  distance change: no neuron of layer k changes sign and the Euclidean
+ *          distance of the layer's potential vectors is at least d
+ * and the four covers are ORed over all pairs:
+ *   SS (i, j)  i the only sign change of layer k, sc(j)   pair layout (as in
+ *   SV (i, j)  i the only sign change of layer k, vc(j)    vbmc_get_coverage)
+ *   DS (k, j)  dc(k) and sc(j)   layer layout: bit of neuron j (its index among
+ *   DV (k, j)  dc(k) and vc(j)   the non-input neurons); covers (any i of k, j)
+ * Undecided tests (|u| < 1e-9, |max - g min| <= 1e-9, |dist - d| <= 1e-9) go
+ * to the tie masks as for SS. Every mask pointer is device memory of
+ * vbmc_mask_words words (flip words for flip, DS, DV; SS words for SS, SV) or
+ * NULL; masks are cleared by the call. Asynchronous on `stream`. */
+typedef struct {
+    double g; /* value-change ratio (>= 1)      */
+    double d; /* distance-change bound (>= 0)   */
+} vbmc_cover_params;
+
+typedef struct {
+    uint32_t *flip, *flip_tie;   /* sign changes                 */
+    uint32_t *ss, *ss_tie;       /* SS-Cover, pair layout        */
+    uint32_t *sv, *sv_tie;       /* SV-Cover, pair layout        */
+    uint32_t *ds, *ds_tie;       /* DS-Cover, layer layout       */
+    uint32_t *dv, *dv_tie;       /* DV-Cover, layer layout       */
+} vbmc_pair_masks;
+
+vbmc_status vbmc_pair_coverage(const vbmc_net *net, const uint8_t *d_images1, const uint8_t *d_images2,
+                               int32_t n_pairs, const vbmc_cover_params *params,
+                               const vbmc_pair_masks *out, void *stream);
+
+/* Eq. 3-6: fraction of non-input neurons that belong to at least one covered
+ * pair of a host mask in pair layout (SS, SV) or layer layout (DS, DV). */
+enum { VBMC_LAYOUT_PAIRS = 0, VBMC_LAYOUT_LAYER = 1 };
+vbmc_status vbmc_covered_fraction(const vbmc_net *net, int32_t layout, const uint32_t *mask,
+                                  double *fraction);
+
 /* ---- Launch-shape autotuning. The FP32 pass (over index ranges, and over
  * queued points) comes in four variants that hold layers up to 32, 256, 512
  * and 1024 neurons with 128, 128, 64 and 32 points per tile; it and the

@@ -9,6 +9,9 @@ from .oracle import (  # noqa: F401
     eval_point,
     forward,
     pair_coverage,
+    pair_covers,
+    pairs_coverage,
+    layer_pair_fraction,
     ss_covered_fraction,
     space_size,
     digits,

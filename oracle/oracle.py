@@ -59,6 +59,12 @@ def configure(lib):
     lib.orc_pair_coverage.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), C.c_double] + \
         [C.POINTER(C.c_uint32)] * 4
+    lib.orc_pair_covers.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                    C.POINTER(C.c_double), C.c_double, C.c_double, C.c_double] + \
+        [C.POINTER(C.c_uint32)] * 6
+    lib.orc_pair_covers.restype = None
+    lib.orc_layer_pair_fraction.argtypes = [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_uint32)]
+    lib.orc_layer_pair_fraction.restype = C.c_double
     lib.orc_ss_covered_fraction.argtypes = [C.c_int, C.POINTER(C.c_int),
                                             C.POINTER(C.c_uint32)]
     lib.orc_ss_covered_fraction.restype = C.c_double
@@ -198,3 +204,41 @@ def ss_covered_fraction(dims, ss) -> float:
     m = np.ascontiguousarray(ss, dtype=np.uint32)
     return float(_load().orc_ss_covered_fraction(len(dims) - 1, _ptr(d, C.c_int),
                                                  _ptr(m, C.c_uint32)))
+
+
+def pair_covers(dims, u1, u2, g: float, d: float, tau: float = TAU) -> dict:
+    """DS, DV (per layer-(k+1) neuron bit) and SV (SS layout) masks of one input
+    pair, each with its tie mask (Sec. III-B)."""
+    lib = _load()
+    dd = np.ascontiguousarray(dims, dtype=np.int32)
+    a = np.ascontiguousarray(u1, dtype=np.float64)
+    b = np.ascontiguousarray(u2, dtype=np.float64)
+    fw, sw = mask_words(list(dims))
+    m = [np.zeros(fw, np.uint32) for _ in range(4)] + [np.zeros(sw, np.uint32) for _ in range(2)]
+    lib.orc_pair_covers(len(dims) - 1, _ptr(dd, C.c_int), _ptr(a, C.c_double), _ptr(b, C.c_double),
+                        tau, g, d, *[_ptr(x, C.c_uint32) for x in m])
+    return dict(ds=m[0], ds_tie=m[1], dv=m[2], dv_tie=m[3], sv=m[4], sv_tie=m[5])
+
+
+def layer_pair_fraction(dims, mask) -> float:
+    """Eq. 4 / Eq. 6 covered fraction from a DS or DV mask."""
+    dd = np.ascontiguousarray(dims, dtype=np.int32)
+    m = np.ascontiguousarray(mask, dtype=np.uint32)
+    return float(_load().orc_layer_pair_fraction(len(dims) - 1, _ptr(dd, C.c_int), _ptr(m, C.c_uint32)))
+
+
+def pairs_coverage(net: dict, images1, images2, g: float, d: float, tau: float = TAU) -> dict:
+    """Every cover (sign changes, SS, DS, SV, DV and their tie masks) ORed over a set
+    of input pairs, from the FP64 potentials of each image."""
+    dims = net["dims"]
+    fw, sw = mask_words(list(dims))
+    acc = {k: np.zeros(fw, np.uint32) for k in ("flip", "flip_tie", "ds", "ds_tie", "dv", "dv_tie")}
+    acc.update({k: np.zeros(sw, np.uint32) for k in ("ss", "ss_tie", "sv", "sv_tie")})
+    for x1, x2 in zip(images1, images2):
+        u1 = forward(net, np.asarray(x1, np.float64) / 255.0)
+        u2 = forward(net, np.asarray(x2, np.float64) / 255.0)
+        for k, v in pair_coverage(dims, u1, u2, tau).items():
+            acc[k] |= v
+        for k, v in pair_covers(dims, u1, u2, g, d, tau).items():
+            acc[k] |= v
+    return acc

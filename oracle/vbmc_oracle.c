@@ -262,6 +262,118 @@ double orc_ss_covered_fraction(int L, const int *dims, const uint32_t *ss)
     return (double)c / (double)total;
 }
 
+/* ---------------------------------------------------- the other covers */
+
+/*
+ * Sec. III-B, for one input pair (potentials u1, u2 of every non-input neuron):
+ *   vc(n): the sign did not change and the value changed by the ratio g:
+ *          max(|u1|, |u2|) >= g min(|u1|, |u2|)   (g > 1; the ratio is taken in
+ *          whichever direction is >= 1)
+ *   dc(k): no neuron of layer k changed sign and the Euclidean distance of the
+ *          layer's potential vectors is at least d
+ *   DS  pair (any i in layer k, j in layer k+1): dc(k) and sc(j)
+ *   DV  pair (any i in layer k, j in layer k+1): dc(k) and vc(j)
+ *   SV  pair (i in layer k, j in layer k+1): i is the only neuron of layer k
+ *       that changed sign, and vc(j)
+ * DS and DV are recorded per (layer k+1, neuron j): bit (offset of layer k+1 in
+ * the non-input neurons) + j; SV uses the SS layout.
+ * Ties, as for SS: a sign with |u| < tau in either input, a ratio test
+ * |max - g min| <= tau, or a distance test |dist - d| <= tau is undecided; a
+ * pair that holds only under some resolution of the undecided tests goes to
+ * the tie mask, one that holds for every resolution to the mask itself.
+ */
+void orc_pair_covers(int L, const int *dims, const double *u1, const double *u2, double tau,
+                     double g, double d, uint32_t *ds, uint32_t *ds_tie, uint32_t *dv,
+                     uint32_t *dv_tie, uint32_t *sv, uint32_t *sv_tie)
+{
+    int total = orc_total_neurons(L, dims);
+    char *fl = (char *)malloc((size_t)total);  /* certain sign change      */
+    char *ti = (char *)malloc((size_t)total);  /* sign tie                 */
+    char *vc = (char *)malloc((size_t)total);  /* certain value change     */
+    char *vt = (char *)malloc((size_t)total);  /* value change undecided   */
+    for (int n = 0; n < total; n++) {
+        ti[n] = (fabs(u1[n]) < tau) || (fabs(u2[n]) < tau);
+        fl[n] = (orc_sign(u1[n]) != orc_sign(u2[n])) && !ti[n];
+        double a = fabs(u1[n]), b = fabs(u2[n]);
+        double big = a > b ? a : b, small = a > b ? b : a;
+        double test = big - g * small;
+        vc[n] = !fl[n] && !ti[n] && test > tau;
+        vt[n] = !fl[n] && !vc[n] && (ti[n] || fabs(test) <= tau);
+    }
+    int off = 0;
+    uint64_t pair_off = 0;
+    for (int l = 1; l < L; l++) {
+        int Hl = dims[l], Hn = dims[l + 1];
+        int n_flip = 0, n_tie = 0, only = -1;
+        double dist2 = 0.0;
+        for (int j = 0; j < Hl; j++) {
+            if (fl[off + j]) { n_flip++; only = j; }
+            if (ti[off + j]) n_tie++;
+            double e = u1[off + j] - u2[off + j];
+            dist2 += e * e;
+        }
+        double dist = sqrt(dist2);
+        int dc_cert = n_flip == 0 && n_tie == 0 && dist - d > tau;
+        int dc_poss = n_flip == 0 && dist - d >= -tau;
+        for (int i = 0; i < Hn; i++) {
+            int ni = off + Hl + i;
+            uint64_t bit = (uint64_t)(off + Hl + i);
+            /* DS */
+            if (dc_cert && fl[ni]) { if (ds) set_bit(ds, bit); }
+            else if (dc_poss && (fl[ni] || ti[ni])) { if (ds_tie) set_bit(ds_tie, bit); }
+            /* DV */
+            if (dc_cert && vc[ni]) { if (dv) set_bit(dv, bit); }
+            else if (dc_poss && (vc[ni] || vt[ni])) { if (dv_tie) set_bit(dv_tie, bit); }
+        }
+        /* SV: the "only changed neuron" rule of SS with a value change above */
+        for (int j = 0; j < Hl; j++) {
+            int certain = (n_tie == 0 && n_flip == 1 && j == only);
+            int possible = certain || (n_tie > 0 && ((n_flip == 1 && j == only) ||
+                                                     (n_flip == 0 && ti[off + j])));
+            if (!possible) continue;
+            for (int i = 0; i < Hn; i++) {
+                int ni = off + Hl + i;
+                uint64_t bit = pair_off + (uint64_t)j * Hn + i;
+                if (certain && vc[ni]) {
+                    if (sv) set_bit(sv, bit);
+                } else if (vc[ni] || vt[ni]) {
+                    if (sv_tie) set_bit(sv_tie, bit);
+                }
+            }
+        }
+        off += Hl;
+        pair_off += (uint64_t)Hl * Hn;
+    }
+    free(fl);
+    free(ti);
+    free(vc);
+    free(vt);
+}
+
+/* Eq. 4 / Eq. 6: fraction of non-input neurons in at least one DS (DV) covered
+ * pair; a bit of layer k+1 neuron j covers the pairs (i, j) for every i in layer k. */
+double orc_layer_pair_fraction(int L, const int *dims, const uint32_t *mask)
+{
+    int total = orc_total_neurons(L, dims);
+    char *cov = (char *)calloc((size_t)total, 1);
+    int off = 0;
+    for (int l = 1; l < L; l++) {
+        int Hl = dims[l], Hn = dims[l + 1];
+        for (int i = 0; i < Hn; i++) {
+            uint64_t bit = (uint64_t)(off + Hl + i);
+            if ((mask[bit >> 5] >> (bit & 31)) & 1u) {
+                cov[off + Hl + i] = 1;
+                for (int j = 0; j < Hl; j++) cov[off + j] = 1;
+            }
+        }
+        off += Hl;
+    }
+    int c = 0;
+    for (int n = 0; n < total; n++) c += cov[n];
+    free(cov);
+    return (double)c / (double)total;
+}
+
 /* ---------------------------------------------------------- enumeration */
 
 typedef struct {

@@ -75,6 +75,17 @@ class _Tuning(C.Structure):
                 ("ms_gather", C.c_double), ("ms_df", C.c_double)]
 
 
+class _CoverParams(C.Structure):
+    _fields_ = [("g", C.c_double), ("d", C.c_double)]
+
+
+PAIR_MASKS = ("flip", "flip_tie", "ss", "ss_tie", "sv", "sv_tie", "ds", "ds_tie", "dv", "dv_tie")
+
+
+class _PairMasks(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in PAIR_MASKS]
+
+
 class _NoallocOut(C.Structure):
     _fields_ = [("counters", C.c_void_p), ("flip", C.c_void_p), ("flip_tie", C.c_void_p),
                 ("ss", C.c_void_p), ("ss_tie", C.c_void_p), ("bitmap", C.c_void_p),
@@ -120,6 +131,9 @@ def lib():
             "vbmc_tile_counts": [vp, C.c_int32, C.POINTER(C.c_uint64)],
             "vbmc_autotune": [vp, C.c_char_p, C.POINTER(_Tuning)],
             "vbmc_fp8_accumulation_unit": [vp, C.POINTER(C.c_double)],
+            "vbmc_pair_coverage": [vp, vp, vp, C.c_int32, C.POINTER(_CoverParams),
+                                   C.POINTER(_PairMasks), vp],
+            "vbmc_covered_fraction": [vp, C.c_int32, C.POINTER(C.c_uint32), C.POINTER(C.c_double)],
             "vbmc_set_tuning": [vp, C.POINTER(_Tuning)],
             "vbmc_proposal_create": [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                      C.c_uint64, C.POINTER(vp)],
@@ -486,3 +500,33 @@ class Proposal:
             self.free()
         except Exception:  # noqa: BLE001 - interpreter shutdown
             pass
+
+
+def pair_coverage(net: Net, images1, images2, g: float = 2.0, d: float = 1.0,
+                  stream: int | None = None) -> dict:
+    """vbmc_pair_coverage over n image pairs (uint8 arrays [n, H0]): every cover
+    mask (flip, SS, SV, DS, DV and their tie masks, uint32 words) and the Eq. 3-6
+    fractions of SS, SV, DS and DV."""
+    import torch
+    a = np.ascontiguousarray(images1, dtype=np.uint8)
+    b = np.ascontiguousarray(images2, dtype=np.uint8)
+    assert a.shape == b.shape
+    fw, sw = net.mask_words()
+    words = {k: (fw if k in ("flip", "flip_tie", "ds", "ds_tie", "dv", "dv_tie") else sw) for k in PAIR_MASKS}
+    dev = {k: torch.zeros(max(1, n), dtype=torch.int32, device="cuda") for k, n in words.items()}
+    da = torch.from_numpy(a).to("cuda")
+    db = torch.from_numpy(b).to("cuda")
+    masks = _PairMasks(*[dev[k].data_ptr() for k in PAIR_MASKS])
+    params = _CoverParams(float(g), float(d))
+    st = current_stream() if stream is None else stream
+    _check(lib().vbmc_pair_coverage(net.h, C.c_void_p(da.data_ptr()), C.c_void_p(db.data_ptr()),
+                                    int(a.shape[0]) if a.ndim > 1 else 0, C.byref(params),
+                                    C.byref(masks), C.c_void_p(st)))
+    torch.cuda.synchronize()
+    out = {k: dev[k].cpu().numpy().view(np.uint32)[:words[k]] for k in PAIR_MASKS}
+    for name, layout in (("ss", 0), ("sv", 0), ("ds", 1), ("dv", 1)):
+        m = np.ascontiguousarray(out[name]) if len(out[name]) else np.zeros(1, np.uint32)
+        f = C.c_double()
+        _check(lib().vbmc_covered_fraction(net.h, layout, _ptr(m, C.c_uint32), C.byref(f)))
+        out[name + "_fraction"] = f.value
+    return out
