@@ -101,13 +101,25 @@ typedef struct {
 
 /* Query: base image (H_0 grey levels), s distinct pixel indices in digit
  * order, step bound k, and the index range [lo, hi) to check (hi = 0: the
- * whole space). Host pointers. */
+ * whole space). Host pointers.
+ * filter (0: every point of the box) restricts the checked points:
+ *   VBMC_FILTER_L2     the perturbed image lies in the Euclidean ball of
+ *                      Eq. 9 on the grid: sum over the s pixels of the clipped
+ *                      change in grey levels squared <= l2_max (for a radius b
+ *                      on the [0, 1] scale, l2_max = floor((255 b)^2))
+ *   VBMC_FILTER_SHELL  the point lies on the box's boundary: some pixel is
+ *                      moved by exactly k steps (one shell of the k-shell order)
+ * Filtered-out points are not checked or counted (n_points counts the rest). */
+enum { VBMC_FILTER_L2 = 1, VBMC_FILTER_SHELL = 2 };
+
 typedef struct {
     const uint8_t *image;
     int32_t s;
     const int32_t *pixels;
     int32_t k;
     uint64_t lo, hi;
+    int32_t filter;
+    int64_t l2_max;
 } vbmc_query;
 
 enum { VBMC_SCHED_GIVEN = 0, VBMC_SCHED_SMALL_FIRST = 1 };
@@ -303,6 +315,25 @@ vbmc_status vbmc_set_tuning(vbmc_net *net, const vbmc_tuning *t);
  * model of the 16-bit screens), 2^-13 otherwise. Builds the FP8 weights on
  * first use. */
 vbmc_status vbmc_fp8_accumulation_unit(vbmc_net *net, double *unit);
+
+/* ---- k-shell order: the shells r = 0, 1, ..., k (points whose largest step
+ * is exactly r, checked as the box of radius r restricted to its boundary)
+ * one after another, stopping after the first shell that holds a point
+ * violating Eq. 10; the smallest L-infinity witness comes first (the bound of
+ * the incremental check grows until a counterexample or the bound k). The
+ * query's own filter (VBMC_FILTER_L2) applies as well; lo and hi must be 0.
+ * After the call the result holds the last shell checked (its summary, and
+ * vbmc_get_witness with steps in [-radius, radius]). Without a witness every
+ * shell was checked: the box is SAFE when n_ties is 0. Blocks until done. */
+typedef struct {
+    int32_t radius;           /* shell of the first witness, -1: none up to k */
+    uint64_t points_checked;  /* over all shells checked                      */
+    uint64_t n_ties;          /* margin ties over all shells checked          */
+    double ms_device;         /* device time over all shells checked          */
+} vbmc_shell_out;
+
+vbmc_status vbmc_shell_search(vbmc_net *net, const vbmc_query *query, const vbmc_options *opt,
+                              vbmc_result *res, vbmc_shell_out *out, void *stream);
 
 /* ---- Tile-ordered search for a first witness.
  * The index space [0, n) of a query (n = R^s) is cut into n_tiles contiguous

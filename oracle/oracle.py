@@ -45,7 +45,7 @@ class _Query(C.Structure):
                 ("ss_tie", C.POINTER(C.c_uint32)), ("ties", C.POINTER(C.c_uint64)),
                 ("ties_cap", C.c_uint64), ("D", C.c_int), ("base_margin", C.c_double),
                 ("n_points", C.c_uint64), ("n_adv", C.c_uint64), ("first_witness", C.c_uint64),
-                ("n_ties", C.c_uint64)]
+                ("n_ties", C.c_uint64), ("filter", C.c_int), ("l2max", C.c_longlong)]
 
 
 def configure(lib):
@@ -140,6 +140,8 @@ def verify(net: dict, query: dict, lo: int = 0, hi: int = 0, coverage: bool = Tr
     q.pixels = _ptr(pix, C.c_int)
     q.k = k
     q.lo, q.hi, q.tau = lo, hi, TAU
+    q.filter = int(query.get("filter", 0))
+    q.l2max = int(query.get("l2_max", 0))
     q.bitmap = _ptr(bm, C.c_uint32) if bitmap else None
     if coverage:
         q.flip, q.flip_tie, q.ss, q.ss_tie = [_ptr(m, C.c_uint32) for m in masks]

@@ -67,6 +67,13 @@ typedef struct {
     int D;
     double base_margin;
     uint64_t n_points, n_adv, first_witness, n_ties;
+    /* input: which points of the box are checked (0: all). Bit 1: the perturbed
+     * image within the Euclidean ball of Eq. 9 on the grid, sum over the pixels
+     * of (clipped change in grey levels)^2 <= l2max. Bit 2: the point on the
+     * box's boundary, some pixel moved by exactly k steps (a k-shell). Points
+     * outside are neither checked nor counted. */
+    int filter;
+    long long l2max;
 } orc_query;
 
 /* ---------------------------------------------------------------- basics */
@@ -384,7 +391,7 @@ typedef struct {
     uint64_t a, b;           /* this worker's range */
     size_t flip_words, ss_words;
     uint32_t *flip, *flip_tie, *ss, *ss_tie;
-    uint64_t n_adv, first, n_ties, ties_len, ties_cap;
+    uint64_t n_adv, first, n_ties, ties_len, ties_cap, n_points;
     uint64_t *ties;
     int status;
 } orc_work;
@@ -405,7 +412,27 @@ static void *orc_worker(void *arg)
     char *fl = (char *)malloc((size_t)total);
     char *ti = (char *)malloc((size_t)total);
     w->first = UINT64_MAX;
+    int R = 2 * q->k + 1;
     for (uint64_t t = w->a; t < w->b; t++) {
+        if (q->filter) {
+            /* digits of t, first pixel most significant; digit d is the step d - k */
+            uint64_t tt = t;
+            long long s2 = 0;
+            int on_shell = q->k == 0;
+            for (int p = q->s - 1; p >= 0; p--) {
+                int d = (int)(tt % (uint64_t)R);
+                tt /= (uint64_t)R;
+                int v = q->image[q->pixels[p]];
+                int vp = v + d - q->k;
+                if (vp < 0) vp = 0;
+                if (vp > 255) vp = 255;
+                s2 += (long long)(vp - v) * (vp - v);
+                if (d == 0 || d == R - 1) on_shell = 1;
+            }
+            if ((q->filter & 1) && s2 > q->l2max) continue;
+            if ((q->filter & 2) && !on_shell) continue;
+        }
+        w->n_points++;
         orc_point_image(net, q->image, q->s, q->pixels, q->k, t, x);
         orc_forward(net, x, u, h0, h1);
         const double *y = u + (total - HL);
@@ -491,10 +518,12 @@ int orc_verify(const orc_net *net, orc_query *q, int nthreads)
         pthread_create(&th[i], NULL, orc_worker, w);
     }
     q->n_adv = 0; q->n_ties = 0; q->first_witness = UINT64_MAX;
+    q->n_points = 0;
     uint64_t tl = 0;
     for (int i = 0; i < nthreads; i++) {
         pthread_join(th[i], NULL);
         orc_work *w = &ws[i];
+        q->n_points += w->n_points;
         q->n_adv += w->n_adv;
         q->n_ties += w->n_ties;
         if (w->first < q->first_witness) q->first_witness = w->first;

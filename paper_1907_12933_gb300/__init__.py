@@ -37,7 +37,15 @@ class _MlpDesc(C.Structure):
 class _Query(C.Structure):
     _fields_ = [("image", C.POINTER(C.c_uint8)), ("s", C.c_int32),
                 ("pixels", C.POINTER(C.c_int32)), ("k", C.c_int32), ("lo", C.c_uint64),
-                ("hi", C.c_uint64)]
+                ("hi", C.c_uint64), ("filter", C.c_int32), ("l2_max", C.c_int64)]
+
+
+FILTER_L2, FILTER_SHELL = 1, 2
+
+
+def l2_max_of(radius: float) -> int:
+    """l2_max for a Euclidean radius on the [0, 1] pixel scale (Eq. 9)."""
+    return int(np.floor((255.0 * radius) ** 2 + 1e-9))
 
 
 class _Options(C.Structure):
@@ -86,6 +94,11 @@ class _PairMasks(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in PAIR_MASKS]
 
 
+class _ShellOut(C.Structure):
+    _fields_ = [("radius", C.c_int32), ("points_checked", C.c_uint64), ("n_ties", C.c_uint64),
+                ("ms_device", C.c_double)]
+
+
 class _NoallocOut(C.Structure):
     _fields_ = [("counters", C.c_void_p), ("flip", C.c_void_p), ("flip_tie", C.c_void_p),
                 ("ss", C.c_void_p), ("ss_tie", C.c_void_p), ("bitmap", C.c_void_p),
@@ -129,6 +142,7 @@ def lib():
             "vbmc_search_query": [vp, C.POINTER(_Query), C.c_int32, C.POINTER(C.c_int32),
                                   C.POINTER(_Options), vp, C.POINTER(_SearchOut), vp],
             "vbmc_tile_counts": [vp, C.c_int32, C.POINTER(C.c_uint64)],
+            "vbmc_shell_search": [vp, C.POINTER(_Query), C.POINTER(_Options), vp, C.POINTER(_ShellOut), vp],
             "vbmc_autotune": [vp, C.c_char_p, C.POINTER(_Tuning)],
             "vbmc_fp8_accumulation_unit": [vp, C.POINTER(C.c_double)],
             "vbmc_pair_coverage": [vp, vp, vp, C.c_int32, C.POINTER(_CoverParams),
@@ -268,11 +282,13 @@ def _summary_dict(s: _Summary) -> dict:
 
 def verify_query(net: Net, res: Result, image, pixels, k: int, lo: int = 0, hi: int = 0,
                  precision="fp32", coverage: bool = True, bitmap: bool = True,
-                 stream: int | None = None) -> dict:
-    """vbmc_verify_query: host inputs, blocks until the result is final."""
+                 filter: int = 0, l2_max: int = 0, stream: int | None = None) -> dict:
+    """vbmc_verify_query: host inputs, blocks until the result is final. filter:
+    FILTER_L2 (with l2_max) and/or FILTER_SHELL."""
     img = np.ascontiguousarray(image, dtype=np.uint8)
     pix = np.ascontiguousarray(pixels, dtype=np.int32)
-    q = _Query(_ptr(img, C.c_uint8), len(pix), _ptr(pix, C.c_int32), int(k), int(lo), int(hi))
+    q = _Query(_ptr(img, C.c_uint8), len(pix), _ptr(pix, C.c_int32), int(k), int(lo), int(hi),
+               int(filter), int(l2_max))
     opt = _options(precision, coverage, bitmap)
     st = current_stream() if stream is None else stream
     _check(lib().vbmc_verify_query(net.h, C.byref(q), C.byref(opt), res.h, C.c_void_p(st)))
@@ -304,7 +320,8 @@ def verify_batch(net: Net, results: list, queries: list, precision="fp32",
         pix = np.ascontiguousarray(qd["pixels"], dtype=np.int32)
         keep += [img, pix]
         qs[i] = _Query(_ptr(img, C.c_uint8), len(pix), _ptr(pix, C.c_int32), int(qd["k"]),
-                       int(qd.get("lo", 0)), int(qd.get("hi", 0)))
+                       int(qd.get("lo", 0)), int(qd.get("hi", 0)), int(qd.get("filter", 0)),
+                       int(qd.get("l2_max", 0)))
     hs = (C.c_void_p * len(results))(*[r.h for r in results])
     opt = _options(precision, coverage, bitmap, graph, schedule)
     st = current_stream() if stream is None else stream
@@ -398,7 +415,7 @@ def set_tuning(net: Net, **fields) -> None:
 
 
 def search_query(net: Net, res: Result, image, pixels, k: int, order, precision="bf16",
-                 coverage: bool = False, bitmap: bool = False,
+                 coverage: bool = False, bitmap: bool = False, filter: int = 0, l2_max: int = 0,
                  stream: int | None = None) -> dict:
     """vbmc_search_query: check the len(order) contiguous tiles of the query's space in
     the given order and stop after the first tile holding a witness. Returns the
@@ -406,7 +423,8 @@ def search_query(net: Net, res: Result, image, pixels, k: int, order, precision=
     img = np.ascontiguousarray(image, dtype=np.uint8)
     pix = np.ascontiguousarray(pixels, dtype=np.int32)
     o = np.ascontiguousarray(order, dtype=np.int32)
-    q = _Query(_ptr(img, C.c_uint8), len(pix), _ptr(pix, C.c_int32), int(k), 0, 0)
+    q = _Query(_ptr(img, C.c_uint8), len(pix), _ptr(pix, C.c_int32), int(k), 0, 0, int(filter),
+               int(l2_max))
     opt = _options(precision, coverage, bitmap)
     out = _SearchOut()
     st = current_stream() if stream is None else stream
@@ -530,3 +548,22 @@ def pair_coverage(net: Net, images1, images2, g: float = 2.0, d: float = 1.0,
         _check(lib().vbmc_covered_fraction(net.h, layout, _ptr(m, C.c_uint32), C.byref(f)))
         out[name + "_fraction"] = f.value
     return out
+
+
+def shell_search(net: Net, res: Result, image, pixels, k: int, precision="bf16",
+                 coverage: bool = False, bitmap: bool = False, filter: int = 0, l2_max: int = 0,
+                 stream: int | None = None) -> dict:
+    """vbmc_shell_search: shells r = 0..k in order, stopping at the first one that
+    holds a witness; the record merged into the last shell's summary."""
+    img = np.ascontiguousarray(image, dtype=np.uint8)
+    pix = np.ascontiguousarray(pixels, dtype=np.int32)
+    q = _Query(_ptr(img, C.c_uint8), len(pix), _ptr(pix, C.c_int32), int(k), 0, 0, int(filter),
+               int(l2_max))
+    opt = _options(precision, coverage, bitmap)
+    out = _ShellOut()
+    st = current_stream() if stream is None else stream
+    _check(lib().vbmc_shell_search(net.h, C.byref(q), C.byref(opt), res.h, C.byref(out), C.c_void_p(st)))
+    d = result_summary(res)
+    d.update(radius=None if out.radius < 0 else out.radius, points_checked=int(out.points_checked),
+             ties_total=int(out.n_ties), ms_total=out.ms_device)
+    return d

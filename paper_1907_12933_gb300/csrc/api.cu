@@ -592,8 +592,11 @@ vbmc_status enqueue_passes(vbmc_net* net, QueryView* d_qs, const QueryView* hq, 
 }
 
 QueryView make_view(const vbmc_result* r, const uint8_t* d_image, const int* d_pix, int s, int k,
-                    uint64_t lo, uint64_t hi, uint64_t n, const vbmc_options& opt, int qid) {
+                    uint64_t lo, uint64_t hi, uint64_t n, const vbmc_options& opt, int qid,
+                    int filter = 0, long long l2max = 0) {
     QueryView q = r->hq;
+    q.filter = filter;
+    q.l2max = l2max;
     q.s = s;
     q.k = k;
     q.R = 2 * k + 1;
@@ -611,8 +614,8 @@ QueryView make_view(const vbmc_result* r, const uint8_t* d_image, const int* d_p
 // Enqueue the full pipeline for one query whose image/pixels are on the device.
 vbmc_status enqueue(vbmc_net* net, vbmc_result* r, const uint8_t* d_image, const int* d_pix, int s,
                     int k, uint64_t lo, uint64_t hi, uint64_t n, const vbmc_options& opt,
-                    cudaStream_t st) {
-    QueryView q = make_view(r, d_image, d_pix, s, k, lo, hi, n, opt, 0);
+                    cudaStream_t st, int filter = 0, long long l2max = 0) {
+    QueryView q = make_view(r, d_image, d_pix, s, k, lo, hi, n, opt, 0, filter, l2max);
     std::vector<unsigned long long> tp = tile_prefix(net->v, opt.precision, &q, 1);
     VB_CUDA(cudaMemcpyAsync(r->d_q, &q, sizeof(QueryView), cudaMemcpyHostToDevice, st));
     VB_CUDA(cudaMemcpyAsync(r->d_tp, tp.data(), sizeof(unsigned long long) * 2, cudaMemcpyHostToDevice, st));
@@ -640,7 +643,7 @@ void fill_summary(vbmc_result* r, const Counters& c, float ms, float ms_p, float
     std::memset(&s, 0, sizeof(s));
     s.D = c.D;
     s.base_margin = c.base_margin;
-    s.n_points = r->hi - r->lo;
+    s.n_points = c.n_points;  // points of [lo, hi) that pass the query's filter
     s.n_adversarial = c.n_adv;
     s.first_witness = c.first;
     s.n_ties = c.n_ties;
@@ -729,7 +732,10 @@ extern "C" vbmc_status vbmc_verify_query(vbmc_net* net, const vbmc_query* q, con
     if (q->s > 0)
         VB_CUDA(cudaMemcpyAsync(res->d_pix_in, q->pixels, sizeof(int32_t) * q->s,
                                 cudaMemcpyHostToDevice, stq));
-    st = enqueue(net, res, res->d_image, res->d_pix_in, q->s, q->k, q->lo, h, n, *opt, stq);
+    if ((q->filter & ~(VBMC_FILTER_L2 | VBMC_FILTER_SHELL)) || ((q->filter & VBMC_FILTER_L2) && q->l2_max < 0))
+        return fail(VBMC_ERR_ARG, "bad filter (VBMC_FILTER_L2 needs l2_max >= 0)");
+    st = enqueue(net, res, res->d_image, res->d_pix_in, q->s, q->k, q->lo, h, n, *opt, stq, q->filter,
+                 (long long)q->l2_max);
     if (st != VBMC_OK) return st;
     res->image.assign(q->image, q->image + H0);
     res->pixels.assign(q->pixels, q->pixels + q->s);
@@ -913,7 +919,9 @@ extern "C" vbmc_status vbmc_verify_batch(vbmc_net* net, const vbmc_query* querie
         std::memcpy(slot + ((H0 + 3) & ~3), q.pixels, sizeof(int32_t) * (size_t)q.s);
         const uint8_t* d_img = ar->d_stage + ar->stage_stride * (size_t)i;
         const int* d_pix = reinterpret_cast<const int*>(d_img + ((H0 + 3) & ~3));
-        hq[i] = make_view(r, d_img, d_pix, q.s, q.k, q.lo, h, n, *opt, i);
+        if ((q.filter & ~(VBMC_FILTER_L2 | VBMC_FILTER_SHELL)) || ((q.filter & VBMC_FILTER_L2) && q.l2_max < 0))
+            return fail(VBMC_ERR_ARG, "bad filter (VBMC_FILTER_L2 needs l2_max >= 0)");
+        hq[i] = make_view(r, d_img, d_pix, q.s, q.k, q.lo, h, n, *opt, i, q.filter, (long long)q.l2_max);
         nsp[i] = n;
     }
     std::vector<unsigned long long> tp = tile_prefix(v, opt->precision, hq.data(), nq);
@@ -1073,7 +1081,10 @@ extern "C" vbmc_status vbmc_search_query(vbmc_net* net, const vbmc_query* q, int
         VB_CUDA(cudaMemcpyAsync(res->d_pix_in, q->pixels, sizeof(int32_t) * q->s, cudaMemcpyHostToDevice, sq));
     const unsigned long long cap = std::max<uint64_t>(1, res->caps.queue_cap);
     // set-up once over the whole space: counters, cleared masks and bitmap, tables
-    QueryView qv = make_view(res, res->d_image, res->d_pix_in, q->s, q->k, 0, n, n, *opt, 0);
+    if ((q->filter & ~(VBMC_FILTER_L2 | VBMC_FILTER_SHELL)) || ((q->filter & VBMC_FILTER_L2) && q->l2_max < 0))
+        return fail(VBMC_ERR_ARG, "bad filter (VBMC_FILTER_L2 needs l2_max >= 0)");
+    QueryView qv = make_view(res, res->d_image, res->d_pix_in, q->s, q->k, 0, n, n, *opt, 0, q->filter,
+                             (long long)q->l2_max);
     std::vector<unsigned long long> tp = tile_prefix(net->v, opt->precision, &qv, 1);
     VB_CUDA(cudaMemcpyAsync(res->d_q, &qv, sizeof(QueryView), cudaMemcpyHostToDevice, sq));
     const cudaEvent_t ev_set[7] = {res->ev0,    res->ev_pro, res->ev_pro, res->ev_pro,
@@ -1112,6 +1123,7 @@ extern "C" vbmc_status vbmc_search_query(vbmc_net* net, const vbmc_query* q, int
             break;
         }
     }
+    if (qv.filter) so.points_checked = res->h_cnt->n_points;  // the passes counted what passed the filter
     if (!any_tile) {
         VB_CUDA(cudaEventRecord(res->ev1, sq));
         VB_CUDA(cudaMemcpyAsync(res->h_cnt, res->d_cnt, sizeof(Counters), cudaMemcpyDeviceToHost, sq));
@@ -1400,5 +1412,28 @@ extern "C" vbmc_status vbmc_fp8_accumulation_unit(vbmc_net* net, double* unit) {
     const vbmc_status st = wide_build(net->wide, net->v, net->hW, WIDE_E4M3);
     if (st != VBMC_OK) return fail(st, "FP8 set-up failed (self-test or weight preparation)");
     *unit = (double)net->wide.prec[WIDE_E4M3].acc_unit;
+    return VBMC_OK;
+}
+
+extern "C" vbmc_status vbmc_shell_search(vbmc_net* net, const vbmc_query* q, const vbmc_options* opt,
+                                         vbmc_result* res, vbmc_shell_out* out, void* stream) {
+    if (!net || !q || !opt || !res) return fail(VBMC_ERR_ARG, "null argument");
+    if (q->lo != 0 || q->hi != 0) return fail(VBMC_ERR_ARG, "a shell search covers whole shells: lo and hi must be 0");
+    vbmc_shell_out so{-1, 0, 0, 0.0};
+    for (int r = 0; r <= q->k; ++r) {
+        vbmc_query qr = *q;
+        qr.k = r;
+        qr.filter = q->filter | VBMC_FILTER_SHELL;
+        const vbmc_status st = vbmc_verify_query(net, &qr, opt, res, stream);
+        if (st != VBMC_OK) return st;
+        so.points_checked += res->sum.n_points;
+        so.n_ties += res->sum.n_ties;
+        so.ms_device += res->sum.ms_device;
+        if (res->sum.n_adversarial > 0) {
+            so.radius = r;
+            break;
+        }
+    }
+    if (out) *out = so;
     return VBMC_OK;
 }

@@ -78,8 +78,12 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
+enum { FILTER_L2 = 1, FILTER_SHELL = 2 };
+
 struct QueryView {
     int s, k, R, qid;
+    int filter;             // FILTER_L2 | FILTER_SHELL, 0: every point of the box
+    long long l2max;        // FILTER_L2: largest sum over the pixels of dv^2 (grey levels^2)
     unsigned long long n_points, lo, hi;  // space size and checked range
     unsigned long long ntiles;            // screen tiles of this query (time-to-verdict)
     const uint8_t* image;   // H_0 grey levels (device)
@@ -213,6 +217,27 @@ __device__ __forceinline__ void decode_digits(unsigned long long t, int s, int R
             t /= (unsigned long long)R;
         }
     }
+}
+
+// The point's digits pass the query's filter: the perturbed image within the
+// Euclidean ball sum_p dv_p^2 <= l2max (Eq. 9 on the grid, clipped steps), and
+// on the box's boundary max_p |d_p - k| = k (one shell of the k-shell order).
+__device__ __forceinline__ bool in_filter(const QueryView& Q, const int* d) {
+    if (!Q.filter) return true;
+    if (Q.filter & FILTER_L2) {
+        long long s2 = 0;
+        for (int p = 0; p < Q.s; ++p) {
+            const long long v = Q.dv[p * Q.R + d[p]];
+            s2 += v * v;
+        }
+        if (s2 > Q.l2max) return false;
+    }
+    if (Q.filter & FILTER_SHELL) {
+        bool on = Q.k == 0;
+        for (int p = 0; p < Q.s; ++p) on = on || d[p] == 0 || d[p] == Q.R - 1;
+        if (!on) return false;
+    }
+    return true;
 }
 
 }  // namespace vbmc

@@ -40,6 +40,7 @@ k_fp64(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__
     unsigned char* ti = fl + total;                                   // [total]
     __shared__ int nflip[kMaxL + 2], ntie[kMaxL + 2], only[kMaxL + 2];
     __shared__ int dstep[kMaxS];
+    __shared__ int skip;
 
     unsigned long long n;
     if (gather) {
@@ -65,7 +66,11 @@ k_fp64(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__
             int d[kMaxS];
             decode_digits(t, Q.s, Q.R, d);
             for (int p = 0; p < Q.s; ++p) dstep[p] = Q.dv[p * Q.R + d[p]];
+            skip = !gather && Q.filter && !in_filter(Q, d);  // outside the L2 ball / shell
+            if (!gather && Q.filter && !skip) atomicAdd(&Q.cnt->n_points, 1ull);
         }
+        __syncthreads();
+        if (skip) continue;
         if (threadIdx.x <= kMaxL + 1) {
             nflip[threadIdx.x] = 0;
             ntie[threadIdx.x] = 0;

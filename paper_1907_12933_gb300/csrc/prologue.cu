@@ -32,7 +32,7 @@ __global__ void k_pro_init(NetView net, QueryView* qs, int nq) {
         c->first = ~0ull;
         c->n_ties = 0;
         c->n_q[0] = c->n_q[1] = c->n_q[2] = c->n_q[3] = 0;
-        c->n_points = Q.hi - Q.lo;
+        c->n_points = Q.filter ? 0ull : Q.hi - Q.lo;  // with a filter the passes count
         c->err = ok ? 0u : DERR_PIXELS;
         c->D = 0;
         c->base_margin = 0.0;

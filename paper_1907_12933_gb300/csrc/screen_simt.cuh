@@ -261,9 +261,18 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
                 int d[kMaxS];
                 decode_digits(t, Q.s, Q.R, d);
                 for (int p = 0; p < Q.s; ++p) S.dig[m][p] = (unsigned char)d[p];
+                if (!gather && Q.filter && !in_filter(Q, d)) S.valid[m] = 0;  // L2 ball / shell
             }
         }
         __syncwarp();
+        if (!gather && lane == 0) {  // points that pass a filter are counted here
+            const QueryView& Q = qs[S.q[warp * PPW]];
+            if (Q.filter) {
+                int c = 0;
+                for (int r = 0; r < PPW; ++r) c += S.valid[warp * PPW + r];
+                if (c) atomicAdd(&Q.cnt->n_points, (unsigned long long)c);
+            }
+        }
 
         // ---- S2/S3: layer 1 from the delta tables
         {

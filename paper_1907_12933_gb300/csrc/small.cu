@@ -98,9 +98,16 @@ k_small(NetView net, const QueryView* __restrict__ qs, const unsigned long long*
         short flist[SM_MAXL + 1][SM_FCAP];
 #pragma unroll
         for (int l = 0; l <= SM_MAXL; ++l) fcnt[l] = 0;
+        int d[kMaxS];
         if (ok) {
-            int d[kMaxS];
             decode_digits(t, Q.s, Q.R, d);
+            if (!gather && Q.filter) ok = in_filter(Q, d);  // L2 ball / shell
+        }
+        if (!gather && Q.filter) {  // points that pass the filter are counted here
+            const unsigned vm = __ballot_sync(0xffffffffu, ok);
+            if (lane == 0 && vm) atomicAdd(&Q.cnt->n_points, (unsigned long long)__popc(vm));
+        }
+        if (ok) {
             const int H1 = net.dims[1];
             float h[SM_MAXW];
             float nsum = 0.f;

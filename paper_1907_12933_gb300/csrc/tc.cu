@@ -314,14 +314,19 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     t = base + gq * MROWS + r;
                     ok = t >= Q.lo && t < Q.hi;
                 }
+                int d[kMaxS];
+                decode_digits(ok ? t : 0, s, R, d);
+                if (ok && !gather && Q.filter) ok = in_filter(Q, d);  // L2 ball / shell
+                if (!gather && Q.filter) {  // points that pass the filter are counted here
+                    const unsigned vm = __ballot_sync(0xffffffffu, ok);
+                    if ((wtid & 31) == 0 && vm) atomicAdd(&Q.cnt->n_points, (unsigned long long)__popc(vm));
+                }
                 S.t[r] = t;
                 S.valid[r] = ok;
                 S.unc[r] = 0;
                 S.vst[r] = 0;
 #pragma unroll
                 for (int l = 0; l <= kTcMaxL; ++l) S.fcnt[r][l] = 0;
-                int d[kMaxS];
-                decode_digits(ok ? t : 0, s, R, d);
                 for (int p = 0; p < s; ++p) S.dig[r][p] = (unsigned char)d[p];
                 S.pidx[r] = -1;
             }

@@ -145,6 +145,18 @@ __global__ void __launch_bounds__(256) k_wide_l1(NetView net, const QueryView* q
     const int j0 = lane * per;
     int d[kMaxS];
     decode_digits(lo + i, Q.s, Q.R, d);
+    if (Q.filter && !in_filter(Q, d)) {  // outside the L2 ball / shell: a zero row, skipped later
+        uint32_t* row = reinterpret_cast<uint32_t*>(A_out + i * (unsigned long long)w.row_bytes);
+        for (int k = lane; k < w.row_bytes / 4; k += 32) row[k] = 0u;
+        if (lane == 0) {
+            const size_t at = (size_t)1 * w.chunk + i;
+            w.scale[at] = 1.f;
+            w.sN[at] = w.sR[at] = w.sE[at] = 0.f;
+            w.unc[i] = 2;
+        }
+        return;
+    }
+    if (Q.filter && lane == 0) atomicAdd(&Q.cnt->n_points, 1ull);  // points that pass are counted
     float du[32];
 #pragma unroll
     for (int e = 0; e < 32; ++e) du[e] = 0.f;
@@ -350,7 +362,7 @@ k_wide_gemm(const __grid_constant__ WGemmArgs G, NetView net, const QueryView* q
             const uint32_t buf = tl & 1;
             const int m = (int)(g / nb), n = (int)(g % nb);
             const unsigned long long i = (unsigned long long)m * W_BM + 32 * qd + lane;
-            const bool valid = i < G.count;
+            const bool valid = i < G.count && w.unc[i] != 2;  // 2: outside the query's filter
             float sin = 0.f, Nn = 0.f, Rr = 0.f, Ee = 0.f;
             if (valid) {
                 const size_t at = (size_t)(l - 1) * w.chunk + i;
@@ -494,6 +506,7 @@ __global__ void __launch_bounds__(256) k_wide_out(NetView net, const QueryView* 
             }
         }
         const unsigned long long t = lo + i;
+        if (w.unc[i] == 2) continue;  // outside the query's filter
         bool bad = w.unc[i] != 0;
         float y[kWideOut];
         float yD = 0.f;

@@ -60,7 +60,7 @@ struct WideWork {
     float* sN = nullptr;
     float* sR = nullptr;
     float* sE = nullptr;
-    unsigned char* unc = nullptr;  // [chunk]: some sign was not certain
+    unsigned char* unc = nullptr;  // [chunk]: 1 some sign was not certain, 2 outside the filter
     int* fcnt = nullptr;           // [kMaxL + 1][chunk]: certain sign changes per layer
     short* flist = nullptr;        // [kMaxL + 1][chunk][kWideFcap]
     std::vector<void*> owned;
