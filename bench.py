@@ -62,7 +62,20 @@ def parse():
                     help="tile-proposal workload: selected training queries (exact labels)")
     ap.add_argument("--test-queries", type=int, default=200,
                     help="tile-proposal workload: selected held-out queries")
+    ap.add_argument("--threshold", type=float, default=None,
+                    help="check the misclassified literal of Eq. 11 with this reference value V "
+                         "instead of the argmax property of Eq. 10")
+    ap.add_argument("--filter", default="none", choices=["none", "l2", "shell", "l2+shell"],
+                    help="restrict the checked points: the Euclidean ball of Eq. 9 on the grid "
+                         "(--l2-max) and/or the outer k-shell")
+    ap.add_argument("--l2-max", type=int, default=0,
+                    help="--filter l2: largest sum of squared grey-level changes")
+    ap.add_argument("--pairs", type=int, default=None,
+                    help="pair-coverage workload: number of image pairs (default: the workload's)")
     return ap.parse_args()
+
+
+FILTERS = {"none": 0, "l2": 1, "shell": 2, "l2+shell": 3}
 
 
 def rank_query(w, rank):
@@ -369,8 +382,109 @@ def main_proposal(a):
     prop.free()
 
 
+def main_pairs(a):
+    """Coverage over a dataset of image pairs (784-512-512-10 ReLU, 65,536 pairs of an
+    image and a noisy copy): one vbmc_pair_coverage call per step computes every
+    cover (sign change, SS, SV, DS, DV and their tie masks) ORed over all pairs.
+    value: pairs/s with the pairs resident on the device; e2e: through the host
+    API (pairs copied in, masks copied out, inside the timed region)."""
+    over = {"n_pairs": a.pairs} if a.pairs else {}
+    w = synth.workload(a.workload, **over)
+    net_d, cfg = w["net"], w["cfg"]
+    x1, x2 = w["pairs"]
+    n = x1.shape[0]
+    dims = cfg["dims"]
+    fma = sum(dims[l - 1] * dims[l] for l in range(1, len(dims)))
+    flops_pair = 2 * 2 * fma  # two FP64 forward passes per pair
+    if a.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        rate, cores, sample = oracle_pairs_rate(net_d, x1, x2, cfg, a.cpu_seconds * max(1, a.steps) / 10.0)
+        line = {"impl": "reference", "metric": "image pairs/sec (all covers)", "value": rate,
+                "unit": "pairs/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+                "ms_per_step": 1000.0 * n / rate, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": a.workload, "dims": dims, "pairs": n, "g": cfg["g"], "d": cfg["d"]},
+                "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample, "value": rate,
+                                 "unit": "pairs/s"},
+                "e2e": {"value": rate, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+    import torch
+    import paper_1907_12933_gb300 as vb
+    from paper_1907_12933_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    vnet = vb.Net(net_d)
+    da = torch.from_numpy(x1).cuda()
+    db = torch.from_numpy(x2).cuda()
+    masks = vb.pair_masks_device(vnet)
+    flush = torch.empty(256 * 2**20 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(a.warmup):
+        vb.pair_coverage_device(vnet, da, db, masks, cfg["g"], cfg["d"])
+    torch.cuda.synchronize()
+    clocks = Clocks()
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    for i in range(a.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        vb.pair_coverage_device(vnet, da, db, masks, cfg["g"], cfg["d"])
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop(torch.cuda.current_device())
+    ms = statistics.median([e0.elapsed_time(e1) for e0, e1 in ev])
+    e2e = []
+    for _ in range(max(1, min(a.steps, 5))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = vb.pair_coverage(vnet, x1, x2, cfg["g"], cfg["d"])
+        e2e.append(time.perf_counter() - t0)
+    fw, sw = vnet.mask_words()
+    pk, pk_kind = peaks()
+    ach = flops_pair * n / (ms / 1000.0) / 1e12
+    line = {"metric": "image pairs/sec (all covers)", "value": n / (ms / 1000.0), "unit": "pairs/s",
+            "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": a.workload, "dims": dims, "pairs": n, "noise": cfg["noise"],
+                       "g": cfg["g"], "d": cfg["d"], "l2": "flushed between timed steps (256 MB write)"},
+            "e2e": {"value": n / statistics.median(e2e), "unit": "pairs/s",
+                    "h2d_bytes_per_step": int(2 * x1.size), "d2h_bytes_per_step": int(4 * (6 * fw + 4 * sw))},
+            "gpu_launches": a.steps,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s", "frac": ach / 1.25,
+                         "traffic": None, "kernel": "k_pairs (two FP64 forward passes per pair)",
+                         "peak_kind": "nominal FP64 ALU", "flops_per_launch": flops_pair * n,
+                         "launch_ms": ms},
+            "covers": {k: out[k + "_fraction"] for k in ("ss", "sv", "ds", "dv")}}
+    if ck:
+        line["clocks"] = ck
+    if not a.no_cpu_baseline:
+        rate, cores, sample = oracle_pairs_rate(net_d, x1, x2, cfg, a.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": "pairs/s", "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    print(json.dumps(line))
+
+
+def oracle_pairs_rate(net, x1, x2, cfg, seconds):
+    """Oracle pairs/s on the first pairs of the workload (one host thread per
+    forward pass: the oracle's pair path is sequential)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.pairs_coverage(net, x1[:8], x2[:8], cfg["g"], cfg["d"])
+    dt = (time.perf_counter() - t0) / 8
+    m = int(min(x1.shape[0], max(8, seconds / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.pairs_coverage(net, x1[:m], x2[:m], cfg["g"], cfg["d"])
+    dt = time.perf_counter() - t0
+    return m / dt, 1, f"pairs [0, {m}) of {x1.shape[0]}, all covers"
+
+
 def main():
     a = parse()
+    if a.workload.startswith("pairs"):
+        return main_pairs(a)
     if "batch" in a.workload and a.impl == "ours":
         return main_batch(a)
     if a.workload.startswith("proposal") and a.impl == "ours":
@@ -427,10 +541,23 @@ def main():
         if world > 1:
             dist.barrier()
 
+    # a filter or the threshold literal needs the full query struct: those steps go
+    # through vbmc_verify_query (image and pixel list, H_0 + 4 s bytes, copied in
+    # on the stream inside the step)
+    plain = a.threshold is None and a.filter == "none"
+
+    def step():
+        if plain:
+            vb.verify_query_device(vnet, res, d_img, d_pix, k, precision=a.precision,
+                                   coverage=not a.no_coverage)
+        else:
+            vb.verify_query(vnet, res, q["image"], q["pixels"], k, precision=a.precision,
+                            coverage=not a.no_coverage, filter=FILTERS[a.filter], l2_max=a.l2_max,
+                            threshold=a.threshold, wait=False)
+
     # ---- device-resident steps (value)
     for _ in range(a.warmup):
-        vb.verify_query_device(vnet, res, d_img, d_pix, k, precision=a.precision,
-                               coverage=not a.no_coverage)
+        step()
         vb.result_summary(res)
     clocks = Clocks()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -443,8 +570,7 @@ def main():
     for i in range(a.steps):
         flush.zero_()
         ev[i][0].record(stream)
-        vb.verify_query_device(vnet, res, d_img, d_pix, k, precision=a.precision,
-                               coverage=not a.no_coverage)
+        step()
         ev[i][1].record(stream)
         sm = vb.result_summary(res)
         sums.append(sm)
@@ -458,7 +584,9 @@ def main():
     if world > 1:
         dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
     ms_max = float(t_local.item())
-    value = world * n_pts / (ms_max / 1000.0)
+    # points checked per step: all R^s, or those that pass the filter
+    n_chk = n_pts if plain or a.filter == "none" else int(sums[-1]["n_points"])
+    value = world * n_chk / (ms_max / 1000.0)
 
     # ---- end-to-end through the host API (copies inside the timed region)
     fw, sw = vnet.mask_words()
@@ -468,7 +596,8 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         vb.verify_query(vnet, res, q["image"], q["pixels"], k, precision=a.precision,
-                        coverage=not a.no_coverage)
+                        coverage=not a.no_coverage, filter=FILTERS[a.filter], l2_max=a.l2_max,
+                        threshold=a.threshold)
         vb.get_verdict_bitmap(res, n_pts)
         if not a.no_coverage:
             vb.get_coverage(res)
@@ -476,13 +605,13 @@ def main():
     e2e_local = torch.tensor([statistics.median(e2e_ms)], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(e2e_local, op=dist.ReduceOp.MAX)
-    e2e_value = world * n_pts / (float(e2e_local.item()) / 1000.0)
+    e2e_value = world * n_chk / (float(e2e_local.item()) / 1000.0)
 
     if rank == 0:
         last = sums[-1]
         pk, pk_kind = peaks()
         L = len(cfg["dims"]) - 1
-        roof = pass_rooflines(a.precision, cfg["dims"], s, n_pts, sums, pk, pk_kind)
+        roof = pass_rooflines(a.precision, cfg["dims"], s, n_chk, sums, pk, pk_kind)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -492,6 +621,12 @@ def main():
                 "config": {"workload": a.workload, "dims": cfg["dims"], "act": cfg["act"],
                            "s": s, "k": k, "points_per_query": n_pts, "precision": a.precision,
                            "coverage": not a.no_coverage,
+                           "property": "Eq. 10 (argmax)" if a.threshold is None
+                           else f"Eq. 11 (threshold literal, V = {a.threshold!r})",
+                           "filter": a.filter, "l2_max": a.l2_max if "l2" in a.filter else None,
+                           "points_checked": n_chk,
+                           "value_call": "vbmc_verify_query_device" if plain
+                           else "vbmc_verify_query (image and pixels copied in inside the step)",
                            "tuning": {key: tuning[key] for key in ("simt_range", "simt_range_ctas", "simt_gather",
                                                                    "simt_gather_ctas", "df_ctas", "from_cache")},
                            "queries": "one per rank (rank r: query r of the workload seed)",

@@ -109,8 +109,17 @@ typedef struct {
  *                      on the [0, 1] scale, l2_max = floor((255 b)^2))
  *   VBMC_FILTER_SHELL  the point lies on the box's boundary: some pixel is
  *                      moved by exactly k steps (one shell of the k-shell order)
- * Filtered-out points are not checked or counted (n_points counts the rest). */
+ * Filtered-out points are not checked or counted (n_points counts the rest).
+ * property selects what makes a point a counterexample:
+ *   VBMC_PROP_ARGMAX     Eq. 10: argmax of the outputs differs from the
+ *                        unperturbed image's class D (margin y_D - max_{i!=D}
+ *                        y_i < 0); tie when |margin| < 1e-9
+ *   VBMC_PROP_THRESHOLD  Eq. 11 with the reference value V = threshold:
+ *                        y_D < V and y_i > V for some i != D, i.e. the margin
+ *                        max(y_D - V, V - max_{i!=D} y_i) < 0; tie when
+ *                        |margin| < 1e-9. threshold must be finite. */
 enum { VBMC_FILTER_L2 = 1, VBMC_FILTER_SHELL = 2 };
+enum { VBMC_PROP_ARGMAX = 0, VBMC_PROP_THRESHOLD = 1 };
 
 typedef struct {
     const uint8_t *image;
@@ -120,6 +129,8 @@ typedef struct {
     uint64_t lo, hi;
     int32_t filter;
     int64_t l2_max;
+    int32_t property;  /* vbmc property enum above */
+    double threshold;  /* VBMC_PROP_THRESHOLD: the reference value V */
 } vbmc_query;
 
 enum { VBMC_SCHED_GIVEN = 0, VBMC_SCHED_SMALL_FIRST = 1 };
@@ -216,7 +227,8 @@ vbmc_status vbmc_verify_batch(vbmc_net *net, const vbmc_query *queries, int32_t 
 /* Waits for the result's last call and returns its summary. */
 vbmc_status vbmc_result_summary(vbmc_result *res, vbmc_summary *out);
 
-/* First (lexicographically smallest) counterexample of Eq. 10: its index,
+/* First (lexicographically smallest) counterexample of the query's property
+ * (Eq. 10, or Eq. 11): its index,
  * its s steps in [-k, k], the perturbed image (H_0 bytes) and its FP64
  * margin. Any output pointer may be NULL. With no witness, *index =
  * VBMC_NO_WITNESS and the other outputs are left untouched. */

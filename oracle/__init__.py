@@ -14,6 +14,8 @@ from .oracle import (  # noqa: F401
     layer_pair_fraction,
     ss_covered_fraction,
     space_size,
+    threshold_literal,
+    threshold_margin,
     digits,
     mask_words,
     TAU,

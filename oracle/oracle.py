@@ -45,7 +45,8 @@ class _Query(C.Structure):
                 ("ss_tie", C.POINTER(C.c_uint32)), ("ties", C.POINTER(C.c_uint64)),
                 ("ties_cap", C.c_uint64), ("D", C.c_int), ("base_margin", C.c_double),
                 ("n_points", C.c_uint64), ("n_adv", C.c_uint64), ("first_witness", C.c_uint64),
-                ("n_ties", C.c_uint64), ("filter", C.c_int), ("l2max", C.c_longlong)]
+                ("n_ties", C.c_uint64), ("filter", C.c_int), ("l2max", C.c_longlong),
+                ("property", C.c_int), ("V", C.c_double)]
 
 
 def configure(lib):
@@ -68,6 +69,11 @@ def configure(lib):
     lib.orc_ss_covered_fraction.argtypes = [C.c_int, C.POINTER(C.c_int),
                                             C.POINTER(C.c_uint32)]
     lib.orc_ss_covered_fraction.restype = C.c_double
+    lib.orc_threshold_literal.argtypes = [C.POINTER(C.c_double), C.c_int, C.c_int, C.c_double,
+                                          C.c_double]
+    lib.orc_threshold_literal.restype = C.c_int
+    lib.orc_threshold_margin.argtypes = [C.POINTER(C.c_double), C.c_int, C.c_int, C.c_double]
+    lib.orc_threshold_margin.restype = C.c_double
     lib.orc_space_size.argtypes = [C.c_int, C.c_int]
     lib.orc_space_size.restype = C.c_uint64
     lib.orc_digits.argtypes = [C.c_uint64, C.c_int, C.c_int, C.POINTER(C.c_int)]
@@ -142,6 +148,8 @@ def verify(net: dict, query: dict, lo: int = 0, hi: int = 0, coverage: bool = Tr
     q.lo, q.hi, q.tau = lo, hi, TAU
     q.filter = int(query.get("filter", 0))
     q.l2max = int(query.get("l2_max", 0))
+    q.property = int(query.get("property", 0))
+    q.V = float(query.get("threshold", 0.0))
     q.bitmap = _ptr(bm, C.c_uint32) if bitmap else None
     if coverage:
         q.flip, q.flip_tie, q.ss, q.ss_tie = [_ptr(m, C.c_uint32) for m in masks]
@@ -160,7 +168,8 @@ def verify(net: dict, query: dict, lo: int = 0, hi: int = 0, coverage: bool = Tr
 
 
 def eval_point(net: dict, query: dict, t: int) -> dict:
-    """FP64 activation potentials (all layers), class D, margin and verdict at point t."""
+    """FP64 activation potentials (all layers), class D, margin and verdict at point t
+    (Eq. 10, or Eq. 11 when query["property"] == 1)."""
     lib = _load()
     nh = _NetHandle(net)
     img = np.ascontiguousarray(query["image"], dtype=np.uint8)
@@ -170,7 +179,15 @@ def eval_point(net: dict, query: dict, t: int) -> dict:
     lib.orc_eval_point(C.byref(nh.c), _ptr(img, C.c_uint8), len(pix), _ptr(pix, C.c_int),
                        int(query["k"]), t, _ptr(u, C.c_double), C.byref(D), C.byref(m),
                        C.byref(adv))
-    return {"u": u, "D": D.value, "margin": m.value, "adversarial": bool(adv.value)}
+    out = {"u": u, "D": D.value, "margin": m.value, "adversarial": bool(adv.value)}
+    if int(query.get("property", 0)) == 1:  # Eq. 11 with V = query["threshold"]
+        HL = int(net["dims"][-1])
+        y = np.ascontiguousarray(u[-HL:])
+        V = float(query["threshold"])
+        lit = lib.orc_threshold_literal(_ptr(y, C.c_double), HL, D.value, V, TAU)
+        out.update(margin=lib.orc_threshold_margin(_ptr(y, C.c_double), HL, D.value, V),
+                   adversarial=lit == 1, tie=lit == 2)
+    return out
 
 
 def forward(net: dict, x) -> np.ndarray:
@@ -244,3 +261,17 @@ def pairs_coverage(net: dict, images1, images2, g: float, d: float, tau: float =
         for k, v in pair_covers(dims, u1, u2, g, d, tau).items():
             acc[k] |= v
     return acc
+
+
+def threshold_literal(y, D: int, V: float, tau: float = TAU) -> int:
+    """Eq. 11 on output vector y in three-valued logic: 1 true, 0 false, 2 tie."""
+    lib = _load()
+    a = np.ascontiguousarray(y, dtype=np.float64)
+    return int(lib.orc_threshold_literal(_ptr(a, C.c_double), len(a), int(D), float(V), tau))
+
+
+def threshold_margin(y, D: int, V: float) -> float:
+    """max(y_D - V, V - max_{i != D} y_i): negative iff Eq. 11 holds."""
+    lib = _load()
+    a = np.ascontiguousarray(y, dtype=np.float64)
+    return float(lib.orc_threshold_margin(_ptr(a, C.c_double), len(a), int(D), float(V)))

@@ -13,7 +13,9 @@
  *     output layer is left linear, so the class is the argmax of u_L
  *   - the safety property: the perturbed image must keep the class D of the
  *     unperturbed image (Eq. 10); a point is adversarial iff the argmax of
- *     its output differs from D, lowest index winning exact ties
+ *     its output differs from D, lowest index winning exact ties; or, on
+ *     request, the misclassified literal of Eq. 11 with a reference value V:
+ *     a point is adversarial iff y_D < V and y_i > V for some i != D
  *   - sign(u) = 1 if u >= 0 else 0, and the sign change sc between the
  *     unperturbed and the perturbed image for every non-input neuron
  *     (Sec. III-B, covering methods)
@@ -29,7 +31,8 @@
  * d means step d - k.
  *
  * Ties: a margin with |m| < 1e-9 is a tie (listed, not counted, its verdict
- * bit left clear). A neuron evaluation with |u| < 1e-9 (or whose unperturbed
+ * bit left clear); under Eq. 11, a verdict that rests on a comparison
+ * |y - V| < 1e-9 is a tie. A neuron evaluation with |u| < 1e-9 (or whose unperturbed
  * value has |u| < 1e-9) is a sign tie: its flip goes to the tie mask, and any
  * SS pair whose decision depends on it goes to the SS tie mask.
  */
@@ -74,6 +77,10 @@ typedef struct {
      * outside are neither checked nor counted. */
     int filter;
     long long l2max;
+    /* input: 0 the property of Eq. 10 (argmax), 1 the misclassified literal of
+     * Eq. 11 with reference value V */
+    int property;
+    double V;
 } orc_query;
 
 /* ---------------------------------------------------------------- basics */
@@ -181,6 +188,39 @@ double orc_margin(const double *y, int n, int D)
     for (int i = 0; i < n; i++)
         if (i != D && y[i] > m) m = y[i];
     return y[D] - m;
+}
+
+/* Eq. 11, the misclassified literal (n_D < V) and (n_i > V) for some i != D,
+ * evaluated in three-valued logic: each comparison of an output with V is
+ * undecided when |y - V| < tau. Returns 1 (true: the point is a
+ * counterexample), 0 (false) or 2 (the truth value rests on an undecided
+ * comparison: a tie). */
+int orc_threshold_literal(const double *y, int n, int D, double V, double tau)
+{
+    int lit_d;   /* n_D < V */
+    if (y[D] - V <= -tau) lit_d = 1;
+    else if (y[D] - V >= tau) lit_d = 0;
+    else lit_d = 2;
+    int any = 0; /* some i != D with n_i > V */
+    for (int i = 0; i < n; i++) {
+        if (i == D) continue;
+        if (y[i] - V >= tau) any = 1;
+        else if (y[i] - V > -tau && any == 0) any = 2;
+    }
+    if (lit_d == 0 || any == 0) return 0;
+    if (lit_d == 1 && any == 1) return 1;
+    return 2;
+}
+
+/* A signed distance of Eq. 11 from holding: max(y_D - V, V - max_{i != D} y_i),
+ * negative iff the literal holds. */
+double orc_threshold_margin(const double *y, int n, int D, double V)
+{
+    double m = -INFINITY;
+    for (int i = 0; i < n; i++)
+        if (i != D && y[i] > m) m = y[i];
+    double a = y[D] - V, b = V - m;
+    return a > b ? a : b;
 }
 
 static void set_bit(uint32_t *w, uint64_t b) { w[b >> 5] |= 1u << (b & 31); }
@@ -436,9 +476,16 @@ static void *orc_worker(void *arg)
         orc_point_image(net, q->image, q->s, q->pixels, q->k, t, x);
         orc_forward(net, x, u, h0, h1);
         const double *y = u + (total - HL);
-        double m = orc_margin(y, HL, w->D);
-        int adv = orc_argmax(y, HL) != w->D;
-        if (fabs(m) < q->tau) {
+        int adv, tie;
+        if (q->property == 1) {
+            int lit = orc_threshold_literal(y, HL, w->D, q->V, q->tau);
+            adv = lit == 1;
+            tie = lit == 2;
+        } else {
+            adv = orc_argmax(y, HL) != w->D;
+            tie = fabs(orc_margin(y, HL, w->D)) < q->tau;
+        }
+        if (tie) {
             if (w->ties_len == w->ties_cap) {
                 w->ties_cap = w->ties_cap ? 2 * w->ties_cap : 64;
                 w->ties = (uint64_t *)realloc(w->ties, sizeof(uint64_t) * w->ties_cap);
@@ -465,6 +512,7 @@ int orc_verify(const orc_net *net, orc_query *q, int nthreads)
 {
     int L = net->L, H0 = net->dims[0], HL = net->dims[L];
     if (L < 1 || HL < 2 || q->s < 0 || q->s > 64 || q->k < 0) return -1;
+    if (q->property != 0 && (q->property != 1 || !isfinite(q->V))) return -1;
     for (int p = 0; p < q->s; p++) {
         if (q->pixels[p] < 0 || q->pixels[p] >= H0) return -1;
         for (int r = 0; r < p; r++) if (q->pixels[r] == q->pixels[p]) return -1;
@@ -486,7 +534,8 @@ int orc_verify(const orc_net *net, orc_query *q, int nthreads)
     for (int j = 0; j < H0; j++) x[j] = (double)q->image[j] / 255.0;
     orc_forward(net, x, ub, h0, h1);
     q->D = orc_argmax(ub + (total - HL), HL);
-    q->base_margin = orc_margin(ub + (total - HL), HL, q->D);
+    q->base_margin = q->property == 1 ? orc_threshold_margin(ub + (total - HL), HL, q->D, q->V)
+                                      : orc_margin(ub + (total - HL), HL, q->D);
     free(x); free(h0); free(h1);
 
     if (nthreads < 1) nthreads = 1;

@@ -37,10 +37,20 @@ class _MlpDesc(C.Structure):
 class _Query(C.Structure):
     _fields_ = [("image", C.POINTER(C.c_uint8)), ("s", C.c_int32),
                 ("pixels", C.POINTER(C.c_int32)), ("k", C.c_int32), ("lo", C.c_uint64),
-                ("hi", C.c_uint64), ("filter", C.c_int32), ("l2_max", C.c_int64)]
+                ("hi", C.c_uint64), ("filter", C.c_int32), ("l2_max", C.c_int64),
+                ("property", C.c_int32), ("threshold", C.c_double)]
 
 
 FILTER_L2, FILTER_SHELL = 1, 2
+PROP_ARGMAX, PROP_THRESHOLD = 0, 1
+
+
+def _query(img, pix, k, lo=0, hi=0, filter=0, l2_max=0, threshold=None) -> _Query:
+    """vbmc_query over numpy buffers; threshold=None checks Eq. 10, a number V the
+    misclassified literal of Eq. 11 (y_D < V and y_i > V for some i != D)."""
+    prop = PROP_ARGMAX if threshold is None else PROP_THRESHOLD
+    return _Query(_ptr(img, C.c_uint8), len(pix), _ptr(pix, C.c_int32), int(k), int(lo), int(hi),
+                  int(filter), int(l2_max), prop, 0.0 if threshold is None else float(threshold))
 
 
 def l2_max_of(radius: float) -> int:
@@ -282,17 +292,18 @@ def _summary_dict(s: _Summary) -> dict:
 
 def verify_query(net: Net, res: Result, image, pixels, k: int, lo: int = 0, hi: int = 0,
                  precision="fp32", coverage: bool = True, bitmap: bool = True,
-                 filter: int = 0, l2_max: int = 0, stream: int | None = None) -> dict:
-    """vbmc_verify_query: host inputs, blocks until the result is final. filter:
-    FILTER_L2 (with l2_max) and/or FILTER_SHELL."""
+                 filter: int = 0, l2_max: int = 0, threshold: float | None = None,
+                 stream: int | None = None, wait: bool = True) -> dict | None:
+    """vbmc_verify_query: host inputs; with wait (default) blocks until the result
+    is final and returns its summary, else returns once the work is enqueued.
+    filter: FILTER_L2 (with l2_max) and/or FILTER_SHELL; threshold V: check Eq. 11."""
     img = np.ascontiguousarray(image, dtype=np.uint8)
     pix = np.ascontiguousarray(pixels, dtype=np.int32)
-    q = _Query(_ptr(img, C.c_uint8), len(pix), _ptr(pix, C.c_int32), int(k), int(lo), int(hi),
-               int(filter), int(l2_max))
+    q = _query(img, pix, k, lo, hi, filter, l2_max, threshold)
     opt = _options(precision, coverage, bitmap)
     st = current_stream() if stream is None else stream
     _check(lib().vbmc_verify_query(net.h, C.byref(q), C.byref(opt), res.h, C.c_void_p(st)))
-    return result_summary(res)
+    return result_summary(res) if wait else None
 
 
 def verify_query_device(net: Net, res: Result, d_image, d_pixels, k: int, lo: int = 0,
@@ -311,17 +322,17 @@ def verify_query_device(net: Net, res: Result, d_image, d_pixels, k: int, lo: in
 def verify_batch(net: Net, results: list, queries: list, precision="fp32",
                  coverage: bool = True, bitmap: bool = False, graph: bool = False,
                  schedule="given", stream: int | None = None) -> list:
-    """vbmc_verify_batch: queries are dicts with image, pixels, k (and optional lo, hi);
-    schedule 'given' or 'small_first' (tiles of smaller spaces first)."""
+    """vbmc_verify_batch: queries are dicts with image, pixels, k (and optional lo, hi,
+    filter, l2_max, threshold); schedule 'given' or 'small_first' (tiles of smaller
+    spaces first)."""
     keep = []
     qs = (_Query * len(queries))()
     for i, qd in enumerate(queries):
         img = np.ascontiguousarray(qd["image"], dtype=np.uint8)
         pix = np.ascontiguousarray(qd["pixels"], dtype=np.int32)
         keep += [img, pix]
-        qs[i] = _Query(_ptr(img, C.c_uint8), len(pix), _ptr(pix, C.c_int32), int(qd["k"]),
-                       int(qd.get("lo", 0)), int(qd.get("hi", 0)), int(qd.get("filter", 0)),
-                       int(qd.get("l2_max", 0)))
+        qs[i] = _query(img, pix, qd["k"], qd.get("lo", 0), qd.get("hi", 0), qd.get("filter", 0),
+                       qd.get("l2_max", 0), qd.get("threshold"))
     hs = (C.c_void_p * len(results))(*[r.h for r in results])
     opt = _options(precision, coverage, bitmap, graph, schedule)
     st = current_stream() if stream is None else stream
@@ -416,15 +427,14 @@ def set_tuning(net: Net, **fields) -> None:
 
 def search_query(net: Net, res: Result, image, pixels, k: int, order, precision="bf16",
                  coverage: bool = False, bitmap: bool = False, filter: int = 0, l2_max: int = 0,
-                 stream: int | None = None) -> dict:
+                 threshold: float | None = None, stream: int | None = None) -> dict:
     """vbmc_search_query: check the len(order) contiguous tiles of the query's space in
     the given order and stop after the first tile holding a witness. Returns the
     search record merged into the result summary."""
     img = np.ascontiguousarray(image, dtype=np.uint8)
     pix = np.ascontiguousarray(pixels, dtype=np.int32)
     o = np.ascontiguousarray(order, dtype=np.int32)
-    q = _Query(_ptr(img, C.c_uint8), len(pix), _ptr(pix, C.c_int32), int(k), 0, 0, int(filter),
-               int(l2_max))
+    q = _query(img, pix, k, 0, 0, filter, l2_max, threshold)
     opt = _options(precision, coverage, bitmap)
     out = _SearchOut()
     st = current_stream() if stream is None else stream
@@ -550,15 +560,34 @@ def pair_coverage(net: Net, images1, images2, g: float = 2.0, d: float = 1.0,
     return out
 
 
+def pair_masks_device(net: Net) -> dict:
+    """Zeroed device buffers (int32 tensors) for every mask of vbmc_pair_coverage."""
+    import torch
+    fw, sw = net.mask_words()
+    return {k: torch.zeros(max(1, fw if k in ("flip", "flip_tie", "ds", "ds_tie", "dv", "dv_tie") else sw),
+                           dtype=torch.int32, device="cuda") for k in PAIR_MASKS}
+
+
+def pair_coverage_device(net: Net, d_images1, d_images2, masks: dict, g: float = 2.0, d: float = 1.0,
+                         stream: int | None = None) -> None:
+    """vbmc_pair_coverage on device-resident pairs (uint8 CUDA tensors [n, H0]) into
+    the device masks of pair_masks_device; enqueues on `stream` and returns."""
+    n = int(d_images1.shape[0]) if d_images1.dim() > 1 else 0
+    pm = _PairMasks(*[masks[k].data_ptr() for k in PAIR_MASKS])
+    params = _CoverParams(float(g), float(d))
+    st = current_stream() if stream is None else stream
+    _check(lib().vbmc_pair_coverage(net.h, C.c_void_p(d_images1.data_ptr()), C.c_void_p(d_images2.data_ptr()),
+                                    n, C.byref(params), C.byref(pm), C.c_void_p(st)))
+
+
 def shell_search(net: Net, res: Result, image, pixels, k: int, precision="bf16",
                  coverage: bool = False, bitmap: bool = False, filter: int = 0, l2_max: int = 0,
-                 stream: int | None = None) -> dict:
+                 threshold: float | None = None, stream: int | None = None) -> dict:
     """vbmc_shell_search: shells r = 0..k in order, stopping at the first one that
     holds a witness; the record merged into the last shell's summary."""
     img = np.ascontiguousarray(image, dtype=np.uint8)
     pix = np.ascontiguousarray(pixels, dtype=np.int32)
-    q = _Query(_ptr(img, C.c_uint8), len(pix), _ptr(pix, C.c_int32), int(k), 0, 0, int(filter),
-               int(l2_max))
+    q = _query(img, pix, k, 0, 0, filter, l2_max, threshold)
     opt = _options(precision, coverage, bitmap)
     out = _ShellOut()
     st = current_stream() if stream is None else stream

@@ -591,12 +591,36 @@ vbmc_status enqueue_passes(vbmc_net* net, QueryView* d_qs, const QueryView* hq, 
     return VBMC_OK;
 }
 
+// Point filter and property of a query (the fields of vbmc_query beyond the box).
+struct QueryExtra {
+    int filter = 0;
+    long long l2max = 0;
+    int prop = PROP_ARGMAX;
+    double V = 0.0;
+};
+
+vbmc_status query_extra(const vbmc_query& q, QueryExtra* x) {
+    if ((q.filter & ~(VBMC_FILTER_L2 | VBMC_FILTER_SHELL)) || ((q.filter & VBMC_FILTER_L2) && q.l2_max < 0))
+        return fail(VBMC_ERR_ARG, "bad filter (VBMC_FILTER_L2 needs l2_max >= 0)");
+    if (q.property != VBMC_PROP_ARGMAX && q.property != VBMC_PROP_THRESHOLD)
+        return fail(VBMC_ERR_ARG, "bad property");
+    if (q.property == VBMC_PROP_THRESHOLD && !std::isfinite(q.threshold))
+        return fail(VBMC_ERR_ARG, "threshold must be finite");
+    x->filter = q.filter;
+    x->l2max = (long long)q.l2_max;
+    x->prop = q.property == VBMC_PROP_THRESHOLD ? PROP_THRESHOLD : PROP_ARGMAX;
+    x->V = x->prop == PROP_THRESHOLD ? q.threshold : 0.0;
+    return VBMC_OK;
+}
+
 QueryView make_view(const vbmc_result* r, const uint8_t* d_image, const int* d_pix, int s, int k,
                     uint64_t lo, uint64_t hi, uint64_t n, const vbmc_options& opt, int qid,
-                    int filter = 0, long long l2max = 0) {
+                    const QueryExtra& x = QueryExtra()) {
     QueryView q = r->hq;
-    q.filter = filter;
-    q.l2max = l2max;
+    q.filter = x.filter;
+    q.l2max = x.l2max;
+    q.prop = x.prop;
+    q.V = x.V;
     q.s = s;
     q.k = k;
     q.R = 2 * k + 1;
@@ -614,8 +638,8 @@ QueryView make_view(const vbmc_result* r, const uint8_t* d_image, const int* d_p
 // Enqueue the full pipeline for one query whose image/pixels are on the device.
 vbmc_status enqueue(vbmc_net* net, vbmc_result* r, const uint8_t* d_image, const int* d_pix, int s,
                     int k, uint64_t lo, uint64_t hi, uint64_t n, const vbmc_options& opt,
-                    cudaStream_t st, int filter = 0, long long l2max = 0) {
-    QueryView q = make_view(r, d_image, d_pix, s, k, lo, hi, n, opt, 0, filter, l2max);
+                    cudaStream_t st, const QueryExtra& x = QueryExtra()) {
+    QueryView q = make_view(r, d_image, d_pix, s, k, lo, hi, n, opt, 0, x);
     std::vector<unsigned long long> tp = tile_prefix(net->v, opt.precision, &q, 1);
     VB_CUDA(cudaMemcpyAsync(r->d_q, &q, sizeof(QueryView), cudaMemcpyHostToDevice, st));
     VB_CUDA(cudaMemcpyAsync(r->d_tp, tp.data(), sizeof(unsigned long long) * 2, cudaMemcpyHostToDevice, st));
@@ -732,10 +756,10 @@ extern "C" vbmc_status vbmc_verify_query(vbmc_net* net, const vbmc_query* q, con
     if (q->s > 0)
         VB_CUDA(cudaMemcpyAsync(res->d_pix_in, q->pixels, sizeof(int32_t) * q->s,
                                 cudaMemcpyHostToDevice, stq));
-    if ((q->filter & ~(VBMC_FILTER_L2 | VBMC_FILTER_SHELL)) || ((q->filter & VBMC_FILTER_L2) && q->l2_max < 0))
-        return fail(VBMC_ERR_ARG, "bad filter (VBMC_FILTER_L2 needs l2_max >= 0)");
-    st = enqueue(net, res, res->d_image, res->d_pix_in, q->s, q->k, q->lo, h, n, *opt, stq, q->filter,
-                 (long long)q->l2_max);
+    QueryExtra x;
+    st = query_extra(*q, &x);
+    if (st != VBMC_OK) return st;
+    st = enqueue(net, res, res->d_image, res->d_pix_in, q->s, q->k, q->lo, h, n, *opt, stq, x);
     if (st != VBMC_OK) return st;
     res->image.assign(q->image, q->image + H0);
     res->pixels.assign(q->pixels, q->pixels + q->s);
@@ -919,9 +943,10 @@ extern "C" vbmc_status vbmc_verify_batch(vbmc_net* net, const vbmc_query* querie
         std::memcpy(slot + ((H0 + 3) & ~3), q.pixels, sizeof(int32_t) * (size_t)q.s);
         const uint8_t* d_img = ar->d_stage + ar->stage_stride * (size_t)i;
         const int* d_pix = reinterpret_cast<const int*>(d_img + ((H0 + 3) & ~3));
-        if ((q.filter & ~(VBMC_FILTER_L2 | VBMC_FILTER_SHELL)) || ((q.filter & VBMC_FILTER_L2) && q.l2_max < 0))
-            return fail(VBMC_ERR_ARG, "bad filter (VBMC_FILTER_L2 needs l2_max >= 0)");
-        hq[i] = make_view(r, d_img, d_pix, q.s, q.k, q.lo, h, n, *opt, i, q.filter, (long long)q.l2_max);
+        QueryExtra x;
+        const vbmc_status xs = query_extra(q, &x);
+        if (xs != VBMC_OK) return xs;
+        hq[i] = make_view(r, d_img, d_pix, q.s, q.k, q.lo, h, n, *opt, i, x);
         nsp[i] = n;
     }
     std::vector<unsigned long long> tp = tile_prefix(v, opt->precision, hq.data(), nq);
@@ -1081,10 +1106,10 @@ extern "C" vbmc_status vbmc_search_query(vbmc_net* net, const vbmc_query* q, int
         VB_CUDA(cudaMemcpyAsync(res->d_pix_in, q->pixels, sizeof(int32_t) * q->s, cudaMemcpyHostToDevice, sq));
     const unsigned long long cap = std::max<uint64_t>(1, res->caps.queue_cap);
     // set-up once over the whole space: counters, cleared masks and bitmap, tables
-    if ((q->filter & ~(VBMC_FILTER_L2 | VBMC_FILTER_SHELL)) || ((q->filter & VBMC_FILTER_L2) && q->l2_max < 0))
-        return fail(VBMC_ERR_ARG, "bad filter (VBMC_FILTER_L2 needs l2_max >= 0)");
-    QueryView qv = make_view(res, res->d_image, res->d_pix_in, q->s, q->k, 0, n, n, *opt, 0, q->filter,
-                             (long long)q->l2_max);
+    QueryExtra x;
+    st = query_extra(*q, &x);
+    if (st != VBMC_OK) return st;
+    QueryView qv = make_view(res, res->d_image, res->d_pix_in, q->s, q->k, 0, n, n, *opt, 0, x);
     std::vector<unsigned long long> tp = tile_prefix(net->v, opt->precision, &qv, 1);
     VB_CUDA(cudaMemcpyAsync(res->d_q, &qv, sizeof(QueryView), cudaMemcpyHostToDevice, sq));
     const cudaEvent_t ev_set[7] = {res->ev0,    res->ev_pro, res->ev_pro, res->ev_pro,

@@ -79,11 +79,14 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 }
 
 enum { FILTER_L2 = 1, FILTER_SHELL = 2 };
+enum { PROP_ARGMAX = 0, PROP_THRESHOLD = 1 };
 
 struct QueryView {
     int s, k, R, qid;
     int filter;             // FILTER_L2 | FILTER_SHELL, 0: every point of the box
     long long l2max;        // FILTER_L2: largest sum over the pixels of dv^2 (grey levels^2)
+    int prop;               // PROP_ARGMAX (Eq. 10) or PROP_THRESHOLD (Eq. 11)
+    double V;               // PROP_THRESHOLD: the reference value V
     unsigned long long n_points, lo, hi;  // space size and checked range
     unsigned long long ntiles;            // screen tiles of this query (time-to-verdict)
     const uint8_t* image;   // H_0 grey levels (device)
@@ -217,6 +220,24 @@ __device__ __forceinline__ void decode_digits(unsigned long long t, int s, int R
             t /= (unsigned long long)R;
         }
     }
+}
+
+// Eq. 11 in a screen: the point is misclassified iff y_D < V and y_o > V for
+// some other output o. thr_side gives the side of V that output value y lies on
+// for certain: +1 above, -1 below, 0 undecided, where e bounds |y - exact| plus
+// the 2 tau tie slack; the 2^-22 (|y| + |V|) term covers the FP32 roundings of
+// V, of y and of y - V.
+__device__ __forceinline__ int thr_side(float y, float V, float e) {
+    const float t = __fmaf_ru(0x1p-22f, __fadd_ru(fabsf(y), fabsf(V)), e);
+    return y - V > t ? 1 : (V - y > t ? -1 : 0);
+}
+
+// Verdict from the sides: 0 certainly not misclassified (y_D above V, or every
+// other output below V), 1 certainly misclassified (y_D below V and some other
+// output above V), 2 undecided (a tighter pass decides).
+__device__ __forceinline__ int thr_verdict(bool d_above, bool d_below, bool other_above, bool others_below) {
+    if (d_above || others_below) return 0;
+    return d_below && other_above ? 1 : 2;
 }
 
 // The point's digits pass the query's filter: the perturbed image within the

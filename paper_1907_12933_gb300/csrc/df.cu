@@ -9,7 +9,7 @@
 // FMA, sums use TwoSum (Knuth), so a K-term dot product carries at most
 // (K + 2) 2^-46 sum_j |w_j||dh_j| <= (K + 2) 2^-46 ||W_i|| ||dh|| of error.
 // The error of the delta vector itself propagates with the spectral norm.
-// A sign (Sec. III-B) or the class (Eq. 10) is decided only when its value
+// A sign (Sec. III-B) or the class (Eq. 10, Eq. 11) is decided only when its value
 // clears the bound by 2 tau; if anything is left undecided the whole point
 // goes on to the FP64 pass and contributes nothing here.
 #include "dev.cuh"
@@ -189,7 +189,7 @@ k_df(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__ g
             }
             __syncthreads();
         }
-        // ---- verdict (Eq. 10) with the margin bound of each class pair: thread b
+        // ---- verdict (Eq. 10 with the margin bound of each class pair, or Eq. 11): thread b
         if (threadIdx.x < PB && valid[threadIdx.x] && !undecided[threadIdx.x]) {
             const int b = threadIdx.x;
             const QueryView& Q = qs[qpt[b]];
@@ -198,7 +198,22 @@ k_df(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__ g
             const int D = Q.cnt->D;
             const double cK = (net.dims[L - 1] + 2) * c46;
             bool unsafe = false, safe = true;
-            for (int o = 0; o < HL; ++o) {
+            if (Q.prop == PROP_THRESHOLD) {  // Eq. 11: per output ||W_o|| (cK N + E) + eub_o
+                const double V = Q.V;
+                bool da = false, db = false, oa = false, ob = true;
+                for (int o = 0; o < HL; ++o) {
+                    const double e = (double)net.rownorm[L][o] * (cK * N[b] + (L > 1 ? E[b] : 0.0)) +
+                                     Q.eub[offL + o] + 2.0 * kTau +
+                                     u52 * 2.0 * (fabs(y[o]) + fabs(Q.ub[offL + o]) + fabs(V));
+                    const int sd = y[o] - V > e ? 1 : (V - y[o] > e ? -1 : 0);
+                    if (o == D) { da = sd > 0; db = sd < 0; }
+                    else { oa = oa || sd > 0; ob = ob && sd < 0; }
+                }
+                const int vv = thr_verdict(da, db, oa, ob);
+                unsafe = vv == 1;
+                safe = vv == 0;
+            }
+            for (int o = 0; o < HL && Q.prop != PROP_THRESHOLD; ++o) {
                 if (o == D) continue;
                 const double diff = y[D] - y[o];
                 double eb = ((double)net.rownorm[L][D] + (double)net.rownorm[L][o]) * cK * N[b] +

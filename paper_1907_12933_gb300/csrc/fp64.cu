@@ -158,7 +158,11 @@ k_fp64(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__
                 if (y[i] > y[am]) am = i;
                 if (i != D && y[i] > mx) mx = y[i];
             }
-            const double m = y[D] - mx;
+            // Eq. 10: m = y_D - max_{i!=D} y_i; Eq. 11: m = max(y_D - V, V - max_{i!=D} y_i),
+            // negative iff y_D < V < some other output
+            const bool thr = Q.prop == PROP_THRESHOLD;
+            const double m = thr ? fmax(y[D] - Q.V, Q.V - mx) : y[D] - mx;
+            if (thr) am = m < 0.0 ? -1 : D;
             if (fabs(m) < kTau) {
                 unsigned long long k = atomicAdd(&Q.cnt->n_ties, 1ull);
                 if (k < Q.ties_cap) Q.ties[k] = t;
@@ -214,7 +218,7 @@ k_margin64(NetView net, const QueryView* __restrict__ qs, unsigned long long t, 
         double mx = -DBL_MAX;
         for (int i = 0; i < net.dims[L]; ++i)
             if (i != D && y[i] > mx) mx = y[i];
-        *out = y[D] - mx;
+        *out = Q.prop == PROP_THRESHOLD ? fmax(y[D] - Q.V, Q.V - mx) : y[D] - mx;
     }
 }
 

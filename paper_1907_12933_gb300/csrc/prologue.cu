@@ -174,7 +174,8 @@ __global__ void k_pro_finish(NetView net, QueryView* qs, int nq) {
         for (int i = 0; i < HL; ++i)
             if (i != D && y[i] > mx) mx = y[i];
         Q.cnt->D = D;
-        Q.cnt->base_margin = y[D] - mx;
+        // Eq. 10 margin, or max(y_D - V, V - max_{i!=D} y_i) for Eq. 11
+        Q.cnt->base_margin = Q.prop == PROP_THRESHOLD ? fmax(y[D] - Q.V, Q.V - mx) : y[D] - mx;
     }
     const double u24 = 0x1p-24;
     const int s = Q.s;

@@ -340,6 +340,24 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
                 const float yD = S.A[m][D];
                 const float rD = L > 1 ? rn[D] : 0.f;
                 const float dD = Q.dub[offL + D];
+                if (Q.prop == PROP_THRESHOLD) {  // Eq. 11: per output ||W_o|| (gamma N + E) + dub_o
+                    const float V = (float)Q.V;
+                    bool da = false, db = false, oa = false, ob = true;
+                    for (int o = lane; o < HL; o += 32) {
+                        const float ro = L > 1 ? rn[o] : 0.f;
+                        const float e = __fmaf_ru(ro, __fadd_ru(gN, Ep),
+                                                  __fadd_ru(Q.dub[offL + o], (float)(2.0 * kTau)));
+                        const int sd = thr_side(S.A[m][o], V, e);
+                        if (o == D) { da = sd > 0; db = sd < 0; }
+                        else { oa = oa || sd > 0; ob = ob && sd < 0; }
+                    }
+                    da = __any_sync(0xffffffffu, da);
+                    db = __any_sync(0xffffffffu, db);
+                    oa = __any_sync(0xffffffffu, oa);
+                    ob = __all_sync(0xffffffffu, ob);
+                    if (lane == 0) S.vstate[m] = thr_verdict(da, db, oa, ob);
+                    continue;
+                }
                 bool unsafe = false, safe = true;
                 for (int o = lane; o < HL; o += 32) {
                     if (o == D) continue;

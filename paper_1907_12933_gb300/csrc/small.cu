@@ -175,23 +175,38 @@ k_small(NetView net, const QueryView* __restrict__ qs, const unsigned long long*
                     Nn = __fmul_ru(gl, Nn);  // gamma N_{L-1}: dot-product rounding
                 }
             }
-            // verdict (Eq. 10); h holds the layer-L values (or layer 1 when L = 1)
+            // verdict (Eq. 10, or Eq. 11); h holds the layer-L values (or layer 1 when L = 1)
             const float gN = L > 1 ? Nn : 0.f, Ep = L > 1 ? Ee : 0.f;
             const float yD = h[D];
             const float rD = L > 1 ? S.rn[L][D] : 0.f;
             const float dD = S.dub[offL + D];
             bool unsafe = false, safe = true;
-            for (int o = 0; o < HL; ++o) {
-                if (o == D) continue;
-                const float yo = h[o];
-                const float diff = yD - yo;
-                const float ro = L > 1 ? S.rn[L][o] : 0.f;
-                const float pw = L > 1 ? net.pairw[D * HL + o] : 0.f;
-                float eb = __fmaf_ru(__fadd_ru(rD, ro), gN, __fadd_ru(__fadd_ru(dD, S.dub[offL + o]), (float)(2.0 * kTau)));
-                eb = __fmaf_ru(pw, Ep, eb);
-                eb = __fmaf_ru(0x1p-23f, __fadd_ru(__fadd_ru(fabsf(yD), fabsf(yo)), fabsf(diff)), eb);
-                if (diff < -eb) unsafe = true;
-                else if (!(diff > eb)) safe = false;
+            if (Q.prop == PROP_THRESHOLD) {  // Eq. 11: per output ||W_o|| (gamma N + E) + dub_o
+                const float V = (float)Q.V;
+                bool da = false, db = false, oa = false, ob = true;
+                for (int o = 0; o < HL; ++o) {
+                    const float ro = L > 1 ? S.rn[L][o] : 0.f;
+                    const float e = __fmaf_ru(ro, __fadd_ru(gN, Ep), __fadd_ru(S.dub[offL + o], (float)(2.0 * kTau)));
+                    const int sd = thr_side(h[o], V, e);
+                    if (o == D) { da = sd > 0; db = sd < 0; }
+                    else { oa = oa || sd > 0; ob = ob && sd < 0; }
+                }
+                const int v = thr_verdict(da, db, oa, ob);
+                unsafe = v == 1;
+                safe = v == 0;
+            } else {
+                for (int o = 0; o < HL; ++o) {
+                    if (o == D) continue;
+                    const float yo = h[o];
+                    const float diff = yD - yo;
+                    const float ro = L > 1 ? S.rn[L][o] : 0.f;
+                    const float pw = L > 1 ? net.pairw[D * HL + o] : 0.f;
+                    float eb = __fmaf_ru(__fadd_ru(rD, ro), gN, __fadd_ru(__fadd_ru(dD, S.dub[offL + o]), (float)(2.0 * kTau)));
+                    eb = __fmaf_ru(pw, Ep, eb);
+                    eb = __fmaf_ru(0x1p-23f, __fadd_ru(__fadd_ru(fabsf(yD), fabsf(yo)), fabsf(diff)), eb);
+                    if (diff < -eb) unsafe = true;
+                    else if (!(diff > eb)) safe = false;
+                }
             }
             vstate = unsafe ? 1 : (safe ? 0 : 2);
             if (Q.ss)

@@ -617,7 +617,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 tc::named_bar_sync(1, 256);
             }
 
-            // ---- output layer: margin, class, output signs
+            // ---- output layer: margin (Eq. 10) or threshold literal (Eq. 11), output signs
             {
                 const TcLayer& ly = P.ly[L];
                 tc::mbar_wait(bar(DFULL), dit & 1, abortp);
@@ -661,9 +661,25 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         const float dD = Q.dub[offL + D];
                         bool unsafe = false, safe = true;
                         const float* pr = P.pair + (size_t)D * HL * 5;
+                        if (Q.prop == PROP_THRESHOLD) {  // Eq. 11: per output a_o Pa + b_o Pb + dub_o
+                            const float V = (float)Q.V;
+                            bool da = false, db = false, oa = false, ob = true;
+#pragma unroll
+                            for (int o = 0; o < kTcMaxOut; ++o) {
+                                if (o >= HL) break;
+                                const float e = __fmaf_ru(av[o], Pa, __fmaf_ru(bv[o], Pb, __fadd_ru(Q.dub[offL + o],
+                                                                                              (float)(2.0 * kTau))));
+                                const int sd = thr_side(y[o], V, e);
+                                if (o == D) { da = sd > 0; db = sd < 0; }
+                                else { oa = oa || sd > 0; ob = ob && sd < 0; }
+                            }
+                            const int vv = thr_verdict(da, db, oa, ob);
+                            unsafe = vv == 1;
+                            safe = vv == 0;
+                        }
 #pragma unroll
                         for (int o = 0; o < kTcMaxOut; ++o) {
-                            if (o >= HL) break;
+                            if (Q.prop == PROP_THRESHOLD || o >= HL) break;
                             if (o == D) continue;
                             const float diff = yD - y[o];
                             const float* c5 = pr + o * 5;

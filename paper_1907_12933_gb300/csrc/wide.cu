@@ -14,7 +14,8 @@
 //                 l+1, sums of squares of dh_l and of its rounding residual
 //   k_wide_stats  per point: N_l, R_l, E_l of dh_l
 //   k_wide_out    one thread per point: output layer in FP32 from the rounded
-//                 operand, margin and class (Eq. 10), output signs, SS-Cover
+//                 operand, margin and class (Eq. 10) or the threshold literal
+//                 (Eq. 11), output signs, SS-Cover
 //                 (Sec. III-B); undecided points go to the recheck queue
 // then the chunk's undecided points run through the FP32, double-float and FP64
 // passes.
@@ -530,9 +531,26 @@ __global__ void __launch_bounds__(256) k_wide_out(NetView net, const QueryView* 
         }
         bool unsafe = false, safe = true;
         const float dD = Q.dub[offL + D];
+        if (Q.prop == PROP_THRESHOLD) {  // Eq. 11: per output ||W_o|| (R + E + gamma (N + R)) + dub_o
+            const float V = (float)Q.V;
+            bool da = false, db = false, oa = false, ob = true;
+#pragma unroll
+            for (int o = 0; o < kWideOut; ++o) {
+                if (o >= HL) continue;
+                const float wn = net.rownorm[L][o];
+                const float e = __fmaf_ru(wn, RE, __fmaf_ru(__fmul_ru(gam, wn), NR,
+                                                            __fadd_ru(Q.dub[offL + o], (float)(2.0 * kTau))));
+                const int sd = thr_side(y[o], V, e);
+                if (o == D) { da = sd > 0; db = sd < 0; }
+                else { oa = oa || sd > 0; ob = ob && sd < 0; }
+            }
+            const int vv = thr_verdict(da, db, oa, ob);
+            unsafe = vv == 1;
+            safe = vv == 0;
+        }
 #pragma unroll
         for (int o = 0; o < kWideOut; ++o) {
-            if (o >= HL || o == D) continue;
+            if (Q.prop == PROP_THRESHOLD || o >= HL || o == D) continue;
             const float diff = yD - y[o];
             float eb = __fmul_ru(net.pairw[D * HL + o], RE);
             eb = __fmaf_ru(__fmul_ru(gam, __fadd_ru(net.rownorm[L][D], net.rownorm[L][o])), NR, eb);

@@ -13,6 +13,7 @@ from .gen import (  # noqa: F401
     make_net,
     make_query,
     make_queries,
+    make_pairs,
     WORKLOADS,
     workload,
     proposal_candidates,

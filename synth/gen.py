@@ -122,7 +122,22 @@ WORKLOADS = {
     "proposal_mlp784x512x512_s6k7": dict(seed=1005, net_seed=1002, test_seed=1006,
                                          dims=[784, 512, 512, 10], act="relu", w_var=2.0,
                                          bias="zero", s=6, k=7, n_tiles=64),
+    # coverage over a dataset of image pairs (Sec. III-B): the 784-512-512-10 net
+    # (net_seed 1002); pair i is a random image and a noisy copy (every pixel
+    # moved by a uniform integer in [-noise, noise], clipped); covers with value
+    # ratio g and distance threshold d
+    "pairs_mlp784x512x512_n65536": dict(seed=1007, net_seed=1002, dims=[784, 512, 512, 10],
+                                        act="relu", w_var=2.0, bias="zero", n_pairs=65536,
+                                        noise=16, g=2.0, d=1.0),
 }
+
+
+def make_pairs(seed: int, n: int, h0: int, noise: int):
+    """n image pairs (uint8 [n, h0] each): uniform grey levels and a noisy copy."""
+    a = randint(seed, 30_000, n * h0, 0, 255).reshape(n, h0)
+    e = randint(seed, 30_001, n * h0, -noise, noise).reshape(n, h0)
+    b = np.clip(a + e, 0, 255)
+    return a.astype(np.uint8), b.astype(np.uint8)
 
 
 def workload(name: str, **override) -> dict:
@@ -132,7 +147,9 @@ def workload(name: str, **override) -> dict:
     net = make_net(cfg.get("net_seed", cfg["seed"]), cfg["dims"], cfg["act"], cfg["w_var"],
                    cfg["bias"])
     out = {"name": name, "net": net, "cfg": cfg}
-    if "nq" in cfg:
+    if "n_pairs" in cfg:
+        out["pairs"] = make_pairs(cfg["seed"], cfg["n_pairs"], cfg["dims"][0], cfg["noise"])
+    elif "nq" in cfg:
         out["queries"] = make_queries(cfg["seed"], cfg["nq"], cfg["dims"][0],
                                       cfg["s_range"], cfg["k_range"])
     else:

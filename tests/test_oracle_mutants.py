@@ -1,7 +1,8 @@
 """Plant mistakes in a copy of the oracle (on the CPU) and check that the pins
 catch each one: a dropped bias, a transposed weight index, a reversed digit
 order, a missing clip, "at least one" instead of "exactly one" in SS-Cover, a
-sign error in the sigmoid, and hidden layers left linear."""
+sign error in the sigmoid, hidden layers left linear, and in the literal of
+Eq. 11 a reversed comparison or a dropped tie band."""
 import ctypes
 import os
 import subprocess
@@ -11,6 +12,7 @@ import pytest
 import oracle
 from oracle import oracle as orc_mod
 import test_oracle_pins as pins
+import test_oracle_threshold as thr
 
 MUTANTS = {
     "dropped_bias": ("double u = acc + (double)b[i];", "double u = acc;"),
@@ -24,6 +26,8 @@ MUTANTS = {
     "sigmoid_sign": ("return 1.0 / (1.0 + exp(-u));", "return 1.0 / (1.0 + exp(u));"),
     "hidden_not_activated": ("out[i] = (l + 1 < net->L) ? orc_activation(net->act, u) : u;",
                              "out[i] = u;"),
+    "threshold_reversed": ("if (y[D] - V <= -tau) lit_d = 1;", "if (y[D] - V >= tau) lit_d = 1;"),
+    "threshold_no_tie_band": ("else if (y[i] - V > -tau && any == 0) any = 2;", ""),
 }
 
 PINS = [
@@ -36,6 +40,8 @@ PINS = [
     pins.test_affine_single_pixel_closed_form,
     lambda: pins.test_bruteforce_high_precision(*pins.BRUTE[0]),
     lambda: pins.test_bruteforce_high_precision(*pins.BRUTE[4]),
+    thr.test_literal_hand_cases,
+    lambda: thr.test_exact_bruteforce(23, 1.5),
 ]
 
 
