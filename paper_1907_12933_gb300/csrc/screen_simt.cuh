@@ -14,7 +14,12 @@
 //   N_l = ||dh_l||_2 as computed (rounded up), E_l = bound on ||dh_l - exact||_2
 //   X_l = gamma_{H_{l-1}} N_{l-1} + E_{l-1}
 //   |du_l,i - exact| <= ||W_l,i||_2 X_l              (dot-product error + propagated error)
-//   E_l = lambda ||W_l||_F X_l + kvec_l + u N_l      (lambda = 1 for ReLU, 1/4 for sigmoid)
+//   E_l = lambda (rho_l + sigma_l E_{l-1}) + kvec_l + u N_l
+//         (lambda = 1 for ReLU, 1/4 for sigmoid), where rho_l bounds the l2 norm
+//         of the layer's rounding errors: the a priori ||W_l||_F gamma N_{l-1},
+//         or the a posteriori bound from checkpointed partial sums (dense_layer),
+//         whichever is smaller; the output layer's per-output rounding is
+//         bounded the same way.
 // A neuron's sign is certain when |fl(ub) + du| exceeds that bound plus the
 // constant threshold (fp32 rounding of ub, 2 tau); the verdict is certain
 // when every margin difference exceeds the combined bound. Anything else
@@ -44,6 +49,7 @@ struct SimtSmem {
     int vstate[MT];
     float N[MT];
     float E[MT];
+    float rho[MT][32];  // output layer (width <= 32): rounding bound of each output
     int fcnt[MT][kMaxL + 1];
     short flist[MT][kMaxL + 1][FCAP];
     unsigned char dig[MT][kMaxS];
@@ -79,24 +85,49 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// Sums of non-negative fp32 terms with every addition rounded up: an upper bound.
+__device__ __forceinline__ float warp_sum_ru(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = __fadd_ru(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
 // One dense layer l >= 2 for the tile: du = W_l dh_{l-1} (FP32 FMA, sequential over
 // k), then the sign tests, the delta activation and the per-point error terms.
 // NQA = neuron slots per lane actually used (1 for narrow output layers).
+//
+// Rounding of the dot products, a priori: |err_i| <= gamma_K sum_j |W_ij x_j|.
+// A posteriori, from the partial sums: each FMA's rounding error is at most u
+// times its computed result s_k, so |err_i| <= u sum_k |s_k,i|. The sum is
+// kept at checkpoints every CKL = CKC * KC terms (segment starts g): within a
+// segment |s_k| <= (|s_g| + sum_{j in g} |t_j|) / (1 - CKL u), hence
+//   |err_i| <= u' CKL (V_i + ||W_i|| ||x||),  V_i = sum_g |s_g,i|,
+// u' = u / (1 - CKL u). Over the layer, ||V||_2 <= sqrt(G sum_g ||s_g||^2)
+// (Cauchy-Schwarz over the G segments), which each lane accumulates for its
+// neurons (one register per point); with one neuron per lane (narrow layers)
+// V_i itself is kept. Both bounds hold; the smaller one is used.
+constexpr int CKC = 2;                       // chunks per checkpoint segment
+constexpr float kUseg = 0x1.00002p-24f * (float)(CKC * KC);  // u' CKL, rounded up
+
 template <int PPW, int NQ, int NQA>
 __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView& net,
                                             const QueryView* __restrict__ qs, int l, int warp,
                                             int lane) {
     constexpr int HS = SimtSmem<PPW, NQ>::HS;
     constexpr int HW = 32 * NQA;  // columns of the weight chunk in use
+    constexpr bool PER_NEURON = NQA == 1;
     const int L = net.L;
     const int K = net.dims[l - 1], N = net.dims[l];
     const float* __restrict__ WT = net.WT[l];  // [K][N]
     const int nchunks = (K + KC - 1) / KC;
     float acc[PPW][NQA];
+    float chk[PPW];  // PER_NEURON: V_i of this lane's neuron; else sum_g ||s_g||^2 over this lane's neurons
 #pragma unroll
-    for (int r = 0; r < PPW; ++r)
+    for (int r = 0; r < PPW; ++r) {
+        chk[r] = 0.f;
 #pragma unroll
         for (int qq = 0; qq < NQA; ++qq) acc[r][qq] = 0.f;
+    }
 
     const bool vec = (N % 4) == 0;
     auto load_chunk = [&](int c, int buf) {
@@ -122,6 +153,17 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
         cp_async_wait0();
         __syncthreads();  // chunk c visible to all; chunk c-1's buffer free
         if (c + 1 < nchunks) load_chunk(c + 1, buf ^ 1);
+        if (c > 0 && c % CKC == 0) {  // checkpoint: the partial sums at k = c KC
+#pragma unroll
+            for (int r = 0; r < PPW; ++r) {
+                if (PER_NEURON) {
+                    chk[r] = __fadd_ru(chk[r], fabsf(acc[r][0]));
+                } else {
+#pragma unroll
+                    for (int qq = 0; qq < NQA; ++qq) chk[r] = __fmaf_ru(acc[r][qq], acc[r][qq], chk[r]);
+                }
+            }
+        }
 #pragma unroll
         for (int kk = 0; kk < KC; kk += 4) {
             float4 a4[PPW];
@@ -147,12 +189,15 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
     const float* rn = net.rownorm[l];
     const int off = net.noff[l];
     const float lf = net.lamfrob[l], gl = net.gam[l];
+    const float lam = net.act == ACT_SIGMOID ? 0.25f : 1.0f;
+    const float G = (float)((nchunks + CKC - 1) / CKC);
 #pragma unroll
     for (int r = 0; r < PPW; ++r) {
         const int m = warp * PPW + r;
         if (!S.valid[m]) continue;
         const QueryView& Q = qs[S.q[m]];
-        const float X = __fmaf_ru(gl, S.N[m], S.E[m]);
+        const float Nin = S.N[m], Ein = S.E[m];
+        const float X = __fmaf_ru(gl, Nin, Ein);
         float nsum = 0.f, usum = 0.f;
 #pragma unroll
         for (int qq = 0; qq < NQ; ++qq) {
@@ -162,7 +207,14 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
                 const float du = acc[r][qq < NQA ? qq : 0];
                 const float ub = Q.ub32[gi];
                 const float u = ub + du;
-                const float bound = __fmaf_ru(rn[n], X, Q.thr[gi]);
+                // |du - exact|: rounding (a priori, or a posteriori with one neuron per lane) + propagated
+                float bnd = __fmul_ru(rn[n], X);
+                if (PER_NEURON) {
+                    const float rho = __fmul_ru(kUseg, __fmaf_ru(rn[n], Nin, chk[r]));
+                    bnd = fminf(bnd, __fmaf_ru(rn[n], Ein, rho));
+                    if (l == L && n < 32) S.rho[m][n] = fminf(__fmul_ru(rn[n], __fmul_ru(gl, Nin)), rho);
+                }
+                const float bound = __fadd_ru(bnd, Q.thr[gi]);
                 if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound)) {
                     if (Q.flip) S.unc[m] = 1;  // signs matter only for coverage
                 } else if ((u >= 0.f) != (ub >= 0.f)) {
@@ -184,18 +236,24 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
         }
         nsum = warp_sum(nsum);
         usum = warp_sum(usum);
+        // ||V||_2 bound of this point's checkpoint sums
+        const float vv = PER_NEURON ? warp_sum_ru(__fmul_ru(chk[r], chk[r])) : __fmul_ru(G, warp_sum_ru(chk[r]));
         if (lane == 0) {
+            // rounding error vector of the layer, l2: min(a priori, a posteriori)
+            const float rpri = __fmul_ru(__fmul_ru(lf, gl), Nin);
+            const float rpost = __fmul_ru(lam, __fmul_ru(kUseg, __fmaf_ru(net.frob[l], Nin, __fsqrt_ru(vv))));
+            const float rl = fminf(rpri, rpost);
             if (l < L) {
                 const float Nl = norm_up(nsum);
-                // lambda (||W_l||_F gamma N_{l-1} + sigma_l E_{l-1}) + kvec_l
-                float El = __fmaf_ru(__fmul_ru(lf, gl), S.N[m], Q.kvec[l]);
-                El = __fmaf_ru(net.lamsig[l], S.E[m], El);
+                // lambda (rounding) + lambda sigma_l E_{l-1} + kvec_l + u N_l
+                float El = __fadd_ru(rl, Q.kvec[l]);
+                El = __fmaf_ru(net.lamsig[l], Ein, El);
                 El = __fmaf_ru(0x1p-24f, Nl, El);
                 if (net.act == ACT_SIGMOID) El = __fmaf_ru(0x1p-26f, norm_up(usum), El);
                 S.N[m] = Nl;
                 S.E[m] = El;
             } else {
-                S.N[m] = __fmul_ru(gl, S.N[m]);  // gamma N_{L-1}: dot-product rounding
+                S.N[m] = __fmul_ru(gl, Nin);  // gamma N_{L-1}: a priori dot-product rounding
             }
         }
     }
@@ -334,19 +392,21 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
                 if (!S.valid[m]) continue;
                 const QueryView& Q = qs[S.q[m]];
                 const int D = Q.cnt->D;
-                // per output: rounding ||W_o|| gamma N; shared error ||W_D - W_o|| E
+                // per output: rounding rho_o (a priori ||W_o|| gamma N, or the a posteriori
+                // bound of the output layer); shared error ||W_D - W_o|| E
                 const float gN = L > 1 ? S.N[m] : 0.f;
                 const float Ep = L > 1 ? S.E[m] : 0.f;
+                auto rho = [&](int o) { return L == 1 ? 0.f : HL <= 32 ? S.rho[m][o] : __fmul_ru(rn[o], gN); };
                 const float yD = S.A[m][D];
-                const float rD = L > 1 ? rn[D] : 0.f;
+                const float rhD = rho(D);
                 const float dD = Q.dub[offL + D];
-                if (Q.prop == PROP_THRESHOLD) {  // Eq. 11: per output ||W_o|| (gamma N + E) + dub_o
+                if (Q.prop == PROP_THRESHOLD) {  // Eq. 11: per output rho_o + ||W_o|| E + dub_o
                     const float V = (float)Q.V;
                     bool da = false, db = false, oa = false, ob = true;
                     for (int o = lane; o < HL; o += 32) {
                         const float ro = L > 1 ? rn[o] : 0.f;
-                        const float e = __fmaf_ru(ro, __fadd_ru(gN, Ep),
-                                                  __fadd_ru(Q.dub[offL + o], (float)(2.0 * kTau)));
+                        const float e = __fmaf_ru(ro, Ep, __fadd_ru(rho(o), __fadd_ru(Q.dub[offL + o],
+                                                                                      (float)(2.0 * kTau))));
                         const int sd = thr_side(S.A[m][o], V, e);
                         if (o == D) { da = sd > 0; db = sd < 0; }
                         else { oa = oa || sd > 0; ob = ob && sd < 0; }
@@ -363,9 +423,8 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
                     if (o == D) continue;
                     const float yo = S.A[m][o];
                     const float diff = yD - yo;
-                    const float ro = L > 1 ? rn[o] : 0.f;
                     const float pw = L > 1 ? net.pairw[D * HL + o] : 0.f;
-                    float eb = __fmaf_ru(__fadd_ru(rD, ro), gN,
+                    float eb = __fadd_ru(__fadd_ru(rhD, rho(o)),
                                          __fadd_ru(__fadd_ru(dD, Q.dub[offL + o]), (float)(2.0 * kTau)));
                     eb = __fmaf_ru(pw, Ep, eb);
                     eb = __fmaf_ru(0x1p-23f, __fadd_ru(__fadd_ru(fabsf(yD), fabsf(yo)), fabsf(diff)), eb);
