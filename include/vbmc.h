@@ -297,8 +297,9 @@ vbmc_status vbmc_covered_fraction(const vbmc_net *net, int32_t layout, const uin
                                   double *fraction);
 
 /* ---- Launch-shape autotuning. The FP32 pass (over index ranges, and over
- * queued points) comes in four variants that hold layers up to 32, 256, 512
- * and 1024 neurons with 128, 128, 64 and 32 points per tile; it and the
+ * queued points) comes in six variants that hold layers up to 32, 256, 512,
+ * 1024, 512 and 256 neurons with 128, 128, 64, 32, 32 and 64 points per
+ * tile (variant numbers 1..6); it and the
  * double-float pass also take a number of CTAs per SM. vbmc_autotune times
  * every variant that fits the net, at 1, 2 and 4 CTAs per SM, and the
  * double-float pass at 2, 4, 8 and 16 CTAs per SM, on a sample box of the

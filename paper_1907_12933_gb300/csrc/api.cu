@@ -1366,7 +1366,7 @@ extern "C" vbmc_status vbmc_autotune(vbmc_net* net, const char* cache_path, vbmc
     k_fill_queue<<<(unsigned)((n + 255) / 256), 256, 0, sq>>>(r->d_queue[1], n, 1);
     VB_CUDA(cudaMemcpyAsync(r->d_qcount + 1, qn.data(), sizeof(unsigned long long), cudaMemcpyHostToDevice, sq));
     float best_r = 1e30f, best_g = 1e30f;
-    for (int var = 1; var <= 4; ++var) {
+    for (int var = 1; var <= kSimtVariants; ++var) {
         if (v.hmax > simt_variant_width(var)) continue;
         const size_t sm = simt_variant_smem(var);
         for (int ctas = 1; ctas <= 4; ctas *= 2) {

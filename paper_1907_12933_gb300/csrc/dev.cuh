@@ -51,7 +51,7 @@ struct NetView {
     float frob[kMaxL + 1];            // ||W_l||_F (rounded up)
     const float* pairw;               // [H_L][H_L]: ||W_L,D - W_L,o||_2 (rounded up)
     // launch shapes (0: the built-in choice; set by vbmc_autotune)
-    int simt_var_range, simt_var_gather;    // FP32 pass variant, 1..4
+    int simt_var_range, simt_var_gather;    // FP32 pass variant, 1..6
     int simt_ctas_range, simt_ctas_gather;  // FP32 pass CTAs per SM
     int df_ctas;                            // double-float pass CTAs per SM
 };

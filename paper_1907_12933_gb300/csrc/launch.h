@@ -34,7 +34,8 @@ void launch_small(const NetView& net, const QueryView* d_qs, const unsigned long
                   unsigned long long n_tiles, const QEntry* gather, const unsigned long long* gc,
                   unsigned long long gcap, Queue out, int level, int n_sm, cudaStream_t st);
 
-// FP32 pass variants 1..4: widest layer held, points per tile, shared memory.
+// FP32 pass variants 1..kSimtVariants: widest layer held, points per tile, shared memory.
+constexpr int kSimtVariants = 6;
 int simt_variant_width(int var);
 int simt_variant_default(const NetView& net);
 int simt_variant_points(int var);

@@ -85,6 +85,15 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// Neuron held in accumulator slot qq of a lane. With 4 or more slots per lane the
+// lane holds groups of 4 consecutive neurons (128 g + 4 lane + e), so its weights
+// of one k come in with 16-byte shared-memory loads (a warp's load covers 128
+// contiguous bytes per phase: no bank conflicts); with one slot, neuron = lane.
+template <int NQA>
+__device__ __forceinline__ int slot_neuron(int lane, int qq) {
+    return NQA >= 4 ? 128 * (qq >> 2) + 4 * lane + (qq & 3) : lane + 32 * qq;
+}
+
 // Sums of non-negative fp32 terms with every addition rounded up: an upper bound.
 __device__ __forceinline__ float warp_sum_ru(float v) {
 #pragma unroll
@@ -173,8 +182,19 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
 #pragma unroll
             for (int k4 = 0; k4 < 4; ++k4) {
                 float wv[NQA];
+                if (NQA >= 4) {
 #pragma unroll
-                for (int qq = 0; qq < NQA; ++qq) wv[qq] = S.Wsm[buf][kk + k4][lane + 32 * qq];
+                    for (int g = 0; g < NQA / 4; ++g) {
+                        const float4 w4 = *reinterpret_cast<const float4*>(&S.Wsm[buf][kk + k4][128 * g + 4 * lane]);
+                        wv[4 * g] = w4.x;
+                        wv[4 * g + 1] = w4.y;
+                        wv[4 * g + 2] = w4.z;
+                        wv[4 * g + 3] = w4.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int qq = 0; qq < NQA; ++qq) wv[qq] = S.Wsm[buf][kk + k4][lane + 32 * qq];
+                }
 #pragma unroll
                 for (int r = 0; r < PPW; ++r) {
                     const float a = k4 == 0 ? a4[r].x : k4 == 1 ? a4[r].y : k4 == 2 ? a4[r].z : a4[r].w;
@@ -201,7 +221,7 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
         float nsum = 0.f, usum = 0.f;
 #pragma unroll
         for (int qq = 0; qq < NQ; ++qq) {
-            const int n = lane + 32 * qq;
+            const int n = qq < NQA ? slot_neuron<NQA>(lane, qq) : lane + 32 * qq;
             if (qq < NQA && n < N) {
                 const int gi = off + n;
                 const float du = acc[r][qq < NQA ? qq : 0];
@@ -260,8 +280,9 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
     __syncwarp();
 }
 
+// Tiles of at most 64 accumulators per thread are built for two CTAs per SM.
 template <int PPW, int NQ>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(THREADS, PPW * NQ <= 64 ? 2 : 1)
 k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
               const unsigned long long* __restrict__ tile_prefix, unsigned long long n_tiles,
               const QEntry* __restrict__ gather, const unsigned long long* __restrict__ gather_count,

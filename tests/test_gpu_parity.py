@@ -221,7 +221,7 @@ def test_autotune_cache_and_parity(vb, tmp_path):
     path = str(tmp_path / "tuning.jsonl")
     t1 = vb.autotune(vnet, path)
     assert t1["from_cache"] == 0 and t1["ms_range"] > 0 and t1["ms_df"] > 0
-    assert t1["simt_range"] in (2, 3, 4) and t1["simt_gather"] in (2, 3, 4)
+    assert t1["simt_range"] in (2, 3, 4, 5, 6) and t1["simt_gather"] in (2, 3, 4, 5, 6)
     assert t1["df_ctas"] in (2, 4, 8, 16)
     t2 = vb.autotune(vb.Net(net), path)
     assert t2["from_cache"] == 1
@@ -233,3 +233,30 @@ def test_autotune_cache_and_parity(vb, tmp_path):
         compare(run_gpu(vb, net, q, prec, vbnet=vnet), o, net, q)
     vb.set_tuning(vnet, simt_range=4, simt_range_ctas=1, simt_gather=4, simt_gather_ctas=2, df_ctas=3)
     compare(run_gpu(vb, net, q, "fp32", vbnet=vnet), o, net, q)
+
+
+WIDTHS = {1: 32, 2: 256, 3: 512, 4: 1024, 5: 512, 6: 256}
+
+
+@pytest.mark.parametrize("name,s,k", [("mlp784x256x256_relu_batch4096", 3, 8),
+                                      ("mlp784x512x512_relu_s6k7", 3, 12)])
+def test_every_simt_variant(vb, name, s, k):
+    """Each FP32-pass variant that holds the net (forced for ranges and for queued
+    points, at 1 and 2 CTAs per SM) gives the oracle's results."""
+    w = synth.workload(name, s=s, k=k) if "batch" not in name else None
+    if w is None:
+        w = synth.workload(name, nq=1, s_range=(s, s), k_range=(k, k))
+        net, q = w["net"], w["queries"][0]
+    else:
+        net, q = w["net"], w["query"]
+    o = oracle.verify(net, q)
+    vnet = vb.Net(net)
+    hmax = max(net["dims"][1:])
+    for var in range(1, 7):
+        if WIDTHS[var] < hmax:
+            continue
+        for ctas in (1, 2):
+            vb.set_tuning(vnet, simt_range=var, simt_range_ctas=ctas, simt_gather=var, simt_gather_ctas=ctas,
+                          df_ctas=4)
+            for prec in ("fp32", "bf16"):
+                compare(run_gpu(vb, net, q, prec, vbnet=vnet), o, net, q)
