@@ -44,7 +44,8 @@ namespace {
 
 constexpr int TC_THREADS = 320;
 constexpr int NA = 4;
-constexpr int NB = 7;
+constexpr int NB = 6;
+constexpr int kStageR = 16;  // layer-1 inner-digit tables are staged in shared memory for R <= kStageR
 constexpr int SLOT = 16384;
 constexpr int FCAP = 4;
 constexpr int PMAX = 4;
@@ -54,7 +55,7 @@ struct TcSmem {
     uint8_t A[NA][SLOT];
     uint8_t B[NB][SLOT];
     float souter[PMAX][512];
-    unsigned long long pref[PMAX];
+    unsigned char pdig[PMAX][kMaxS];  // digits of the outer prefix slots
     unsigned long long t[MROWS];
     int valid[MROWS];
     int pidx[MROWS];
@@ -68,6 +69,9 @@ struct TcSmem {
     int fcnt[MROWS][kTcMaxL + 1];
     short flist[MROWS][kTcMaxL + 1][FCAP];
     uint32_t cflip[256];   // sign changes seen by this CTA for query curq (flushed on change)
+    float4 cst4[8][32];    // per worker warp, the 32 columns it drains: (ub, a, b, thr)
+    float2 cst2[8][32];    //   and the delta-ReLU constants (c1, c2)
+    float tstage[2][2][kStageR][64];  // layer 1: tables of the two inner digits, one 64-column chunk, double-buffered
     int curq;
     int npref;
     int uniform_base;
@@ -75,6 +79,8 @@ struct TcSmem {
     uint32_t tmem_slot;
     int abort_flag;
 };
+
+static_assert(sizeof(TcSmem) + 1024 <= 227 * 1024, "tensor screen shared memory above the per-CTA limit");
 
 // bar indices
 __device__ __forceinline__ int BFULL(int i) { return i; }
@@ -87,6 +93,12 @@ constexpr int DRAINED = DFULL + 2;
 constexpr int FIN = DFULL + 3;
 
 __device__ __forceinline__ float norm_up(float s) { return __fsqrt_ru(__fmul_ru(s, 1.0002f)); }
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(tc::smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // Round two floats to a packed 16-bit pair (low half = first) and return the
 // rounded values as floats.
@@ -118,8 +130,9 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
      const unsigned long long* __restrict__ gcount, unsigned long long gcap, Queue out,
      int out_level) {
     extern __shared__ uint8_t smem_raw[];
-    TcSmem& S = *reinterpret_cast<TcSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                           ~uintptr_t(1023));
+    // 1024-byte aligned by pointer arithmetic on the shared array, so the compiler
+    // keeps every access in the shared address space
+    TcSmem& S = *reinterpret_cast<TcSmem*>(smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int L = P.L;
     volatile int* abortp = &S.abort_flag;
@@ -301,7 +314,20 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 if (wtid == 0) S.curq = q;
                 tc::named_bar_sync(1, 256);
             }
-            // ---- decode the tile's points
+            // ---- decode the tile's points. Range mode: the tile's indices are
+            // consecutive, so their outer prefixes t / R^ni (the digits above the ni
+            // inner ones) are consecutive integers from p0, that of the tile's first
+            // index in [lo, hi): row r uses prefix slot t / R^ni - p0 when below PMAX.
+            const bool pre = !gather && s > ni;
+            unsigned long long p0 = 0, np_need = 0;
+            if (pre) {
+                const unsigned long long t0 = base + gq * MROWS;
+                const unsigned long long ta = t0 > Q.lo ? t0 : Q.lo;
+                const unsigned long long tb = (t0 + MROWS < Q.hi ? t0 + MROWS : Q.hi) - 1;
+                p0 = ta / Rni;
+                np_need = tb / Rni - p0 + 1;
+            }
+            const int np = (int)(np_need < (unsigned long long)PMAX ? np_need : PMAX);
             if (wtid < MROWS) {
                 const int r = wtid;
                 unsigned long long t = 0;
@@ -328,48 +354,37 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
 #pragma unroll
                 for (int l = 0; l <= kTcMaxL; ++l) S.fcnt[r][l] = 0;
                 for (int p = 0; p < s; ++p) S.dig[r][p] = (unsigned char)d[p];
-                S.pidx[r] = -1;
-            }
-            tc::named_bar_sync(1, 256);
-            // outer-prefix partial sums of layer 1 (range mode: consecutive points)
-            if (wtid == 0) {
-                int np = 0;
-                if (!gather && s > ni) {
-                    for (int r = 0; r < MROWS; ++r) {
-                        if (!S.valid[r]) continue;
-                        const unsigned long long pv = S.t[r] / Rni;
-                        int k = 0;
-                        while (k < np && S.pref[k] != pv) ++k;
-                        if (k == np && np < PMAX) S.pref[np++] = pv;
-                        S.pidx[r] = k < np ? k : -1;
-                    }
+                int pi = -1;
+                if (pre && ok) {
+                    const unsigned long long k = t / Rni - p0;
+                    if (k < (unsigned long long)PMAX) pi = (int)k;
                 }
-                S.npref = np;
-            }
-            tc::named_bar_sync(1, 256);
-            if (wtid < MROWS) {
-                const int r = wtid;
+                S.pidx[r] = pi;
                 int4 ri;
-                ri.x = S.pidx[r];
-                ri.y = ni >= 2 ? ((s - 2) * R + S.dig[r][s - 2]) * H1 : 0;
-                ri.z = ni >= 1 ? ((s - 1) * R + S.dig[r][s - 1]) * H1 : 0;
-                ri.w = S.valid[r];
+                ri.x = pi;
+                ri.y = ni >= 2 ? ((s - 2) * R + d[s - 2]) * H1 : 0;
+                ri.z = ni >= 1 ? ((s - 1) * R + d[s - 1]) * H1 : 0;
+                // valid flag, and the two inner digits for the staged tables
+                ri.w = ok ? (1 | (ni >= 2 ? d[s - 2] << 8 : 0) | (ni >= 2 ? d[s - 1] << 16 : 0)) : 0;
                 S.rinfo[r] = ri;
+            } else if (wtid - MROWS < np) {  // digits of outer prefix slot k
+                const int k = wtid - MROWS;
+                int dd[kMaxS];
+                decode_digits(p0 + (unsigned long long)k, s - ni, R, dd);
+                for (int p = 0; p < s - ni; ++p) S.pdig[k][p] = (unsigned char)dd[p];
             }
             if (wtid == 0) {
-                int f = (!gather && ni == 2) ? 1 : 0;
-                for (int r = 0; r < MROWS && f; ++r)
-                    if (S.valid[r] && S.pidx[r] < 0) f = 0;
-                if (s == 2 && !gather) f = 1;  // no outer digits: the partial sum is 0
-                S.fast = f;
+                S.npref = np;
+                // fast layer-1 path: every valid row has its prefix slot (or s = 2: none needed)
+                S.fast = !gather && ((ni == 2 && s > 2 && np_need <= (unsigned long long)PMAX) || s == 2);
             }
+            tc::named_bar_sync(1, 256);
+            // outer-prefix partial sums of layer 1
             for (int k = 0; k < S.npref; ++k) {
-                int dd[kMaxS];
-                decode_digits(S.pref[k], s - ni, R, dd);
                 for (int j = wtid; j < H1; j += 256) {
                     float acc = 0.f;
                     for (int p = 0; p < s - ni; ++p)
-                        acc += __ldg(&Q.tab[((size_t)p * R + dd[p]) * H1 + j]);
+                        acc += __ldg(&Q.tab[((size_t)p * R + S.pdig[k][p]) * H1 + j]);
                     S.souter[k][j] = acc;
                 }
             }
@@ -384,10 +399,28 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 const int kch = H1 / 64;
                 const bool fast = S.fast;
                 const bool nosum = (s == 2);  // fast path without outer digits
+                // fast path with R <= kStageR: the tables of the two inner digits for a
+                // chunk's 64 columns go to shared memory one chunk ahead (cp.async)
+                const bool stage = fast && R <= kStageR;
+                auto stage_chunk = [&](int c, int buf) {
+                    for (int e = wtid; e < 2 * R * 16; e += 256) {
+                        const int tt = e / (R * 16), rem = e - tt * (R * 16), dgt = rem >> 4, u = rem & 15;
+                        cp_async16(&S.tstage[buf][tt][dgt][4 * u],
+                                   Q.tab + ((size_t)(s - 2 + tt) * R + dgt) * H1 + 64 * c + 4 * u);
+                    }
+                    cp_async_commit();
+                };
+                if (stage) stage_chunk(0, 0);
                 for (int c = 0; c < kch; ++c) {
                     const int a0 = ait % NA, a1 = (ait + 1) % NA;
                     tc::mbar_wait(bar(AEMPTY(a0)), ((ait / NA) & 1) ^ 1, abortp);
                     if (SPLIT) tc::mbar_wait(bar(AEMPTY(a1)), (((ait + 1) / NA) & 1) ^ 1, abortp);
+                    const int sbuf = c & 1;
+                    if (stage) {
+                        cp_async_wait_all();            // this thread's copies of chunk c
+                        tc::named_bar_sync(1, 256);     // everyone's; and chunk c-1's buffer is no longer read
+                        if (c + 1 < kch) stage_chunk(c + 1, sbuf ^ 1);
+                    }
                     const int j = 64 * c + 2 * lane;
                     const uint32_t pm = Q.cpos[32 + (j >> 5)], nm = Q.cneg[32 + (j >> 5)];
                     const bool pos0 = pm >> (j & 31) & 1, neg0 = nm >> (j & 31) & 1;
@@ -402,12 +435,26 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     const float th0 = cr0 ? Q.thr[j] : 0.f, th1 = cr1 ? Q.thr[j + 1] : 0.f;
                     const bool anyc = __any_sync(0xffffffffu, cr0 || cr1);
                     const uint32_t lanepart = (lane & 3) * 4;
+                    constexpr int RB = SPLIT ? 4 : 8;  // rows per batch (registers)
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const int r = wid * 16 + i;
+                    for (int i0 = 0; i0 < 16; i0 += RB) {
+                    // table sums of RB rows first (their loads overlap), then the rest
+                    float2 dus[RB];
+#pragma unroll
+                    for (int ii = 0; ii < RB; ++ii) {
+                        const int r = wid * 16 + i0 + ii;
                         const int4 ri = S.rinfo[r];
                         float2 du;
-                        if (fast) {
+                        if (stage) {
+                            du = nosum ? make_float2(0.f, 0.f)
+                                       : *reinterpret_cast<const float2*>(&S.souter[ri.x][j]);
+                            const float2 ta =
+                                *reinterpret_cast<const float2*>(&S.tstage[sbuf][0][(ri.w >> 8) & 0xff][2 * lane]);
+                            const float2 tb =
+                                *reinterpret_cast<const float2*>(&S.tstage[sbuf][1][(ri.w >> 16) & 0xff][2 * lane]);
+                            du.x = (du.x + ta.x) + tb.x;
+                            du.y = (du.y + ta.y) + tb.y;
+                        } else if (fast) {
                             du = nosum ? make_float2(0.f, 0.f)
                                        : *reinterpret_cast<const float2*>(&S.souter[ri.x][j]);
                             const float2 ta = __ldg(reinterpret_cast<const float2*>(&Q.tab[ri.y + j]));
@@ -431,6 +478,14 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                                 }
                             }
                         }
+                        dus[ii] = du;
+                    }
+#pragma unroll
+                    for (int ii = 0; ii < RB; ++ii) {
+                        const int i = i0 + ii;
+                        const int r = wid * 16 + i;
+                        const int4 ri = S.rinfo[r];
+                        const float2 du = dus[ii];
                         float dh0 = fmaxf(du.x + c10, c20);
                         float dh1 = fmaxf(du.y + c11, c21);
                         if (!ri.w) dh0 = dh1 = 0.f;
@@ -472,6 +527,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         nsum[i] = fmaf(dh0, dh0, fmaf(dh1, dh1, nsum[i]));
                         rsum[i] = fmaf(r0, r0, fmaf(r1, r1, rsum[i]));
                     }
+                    }  // i0
                     tc::fence_proxy_async();
                     __syncwarp();
                     if (lane == 0) {
@@ -528,27 +584,40 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     const uint32_t pm = Q.cpos[l * 32 + (n0 >> 5)], nm = Q.cneg[l * 32 + (n0 >> 5)];
                     const uint32_t cross = ~(pm | nm);
                     const bool rv = S.valid[r];
+                    {  // constants of the warp's 32 columns, one coalesced load each; the
+                       // delta-ReLU constants of the column classes: pos (0, -inf), neg (-inf, 0)
+                        const int nl = n0 + lane, gcol = off_l + nl;
+                        const bool crl = (cross >> lane) & 1u, negl = (nm >> lane) & 1u;
+                        float4 k4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                        float2 k2 = negl ? make_float2(-INFINITY, 0.f) : make_float2(0.f, -INFINITY);
+                        if (crl) {
+                            k4 = make_float4(Q.ub32[gcol], av[nl], bv[nl], Q.thr[gcol]);
+                            k2 = make_float2(Q.c1[gcol], Q.c2[gcol]);
+                        }
+                        S.cst4[wid][lane] = k4;
+                        S.cst2[wid][lane] = k2;
+                        __syncwarp();
+                    }
+                    const bool signs = rv && Q.flip != nullptr;  // signs matter only for coverage
 #pragma unroll
                     for (int i = 0; i < 32; ++i) {
-                        if (nm & (1u << i)) {
-                            v[i] = 0.f;
-                        } else if (cross & (1u << i)) {  // warp-uniform: column class
+                        const float du = v[i];
+                        if (signs && (cross & (1u << i))) {  // warp-uniform column class
+                            const float4 k4 = S.cst4[wid][i];
                             const int n = n0 + i, gi = off_l + n;
-                            const float du = v[i];
-                            const float ub = Q.ub32[gi];
-                            const float u = ub + du;
-                            const float bound = __fmaf_ru(av[n], Pa, __fmaf_ru(bv[n], Pb, Q.thr[gi]));
-                            if (rv && Q.flip) {  // signs matter only for coverage
-                                if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound)) S.unc[r] = 1;
-                                else if ((u >= 0.f) != (ub >= 0.f)) {
-                                    const int k = atomicAdd(&S.fcnt[r][l], 1);
-                                    if (k < FCAP) S.flist[r][l][k] = (short)n;
-                                    atomicOr(&S.cflip[gi >> 5], 1u << (gi & 31));
-                                }
+                            const float u = k4.x + du;
+                            const float bound = __fmaf_ru(k4.y, Pa, __fmaf_ru(k4.z, Pb, k4.w));
+                            if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound)) S.unc[r] = 1;
+                            else if ((u >= 0.f) != (k4.x >= 0.f)) {
+                                const int k = atomicAdd(&S.fcnt[r][l], 1);
+                                if (k < FCAP) S.flist[r][l][k] = (short)n;
+                                atomicOr(&S.cflip[gi >> 5], 1u << (gi & 31));
                             }
-                            v[i] = fmaxf(du + Q.c1[gi], Q.c2[gi]);
                         }
+                        const float2 k2 = S.cst2[wid][i];
+                        v[i] = fmaxf(du + k2.x, k2.y);
                     }
+                    __syncwarp();  // the staged constants are read before the next chunk overwrites them
                     if (!__all_sync(0xffffffffu, rv) && !rv) {
 #pragma unroll
                         for (int i = 0; i < 32; ++i) v[i] = 0.f;

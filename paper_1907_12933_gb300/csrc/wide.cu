@@ -256,7 +256,7 @@ k_wide_gemm(const __grid_constant__ WGemmArgs G, NetView net, const QueryView* q
     constexpr int EB = Elem<ET>::bytes;
     constexpr int KE = W_BKB / EB;  // elements per K chunk
     extern __shared__ uint8_t smem_raw[];
-    WSmem& S = *reinterpret_cast<WSmem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    WSmem& S = *reinterpret_cast<WSmem*>(smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     volatile int* abortp = &S.abort_flag;
     const int nb = G.N / W_BN, kch = G.K / KE;
@@ -591,7 +591,7 @@ __global__ void __launch_bounds__(128, 1)
 k_wide_selftest(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, float* out,
                 int* status) {
     extern __shared__ uint8_t smem_raw[];
-    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* base = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
     uint8_t* sa = base;
     uint8_t* sb = base + W_BM * W_BKB;
     __shared__ unsigned long long bars[2];
