@@ -19,7 +19,9 @@
 // Error bound of du_l,i (per point, all norms 2-norms, u_acc = 2^-22 per
 // accumulated product, Wq = rounded weights, Wr = W - Wq [- Wlo]):
 //   |err| <= a_i (R + E + rho Lo + u_acc n (N + R + Lo)) + b_i (N + E)
-// with a_i = ||Wq_i (+ Wlo_i)||, b_i = ||Wr_i||, N = ||dh_{l-1}||,
+// with n the number of nonzero entries of the point's operand row (a product
+// that is exactly zero adds nothing to the accumulator, so only the n others
+// can carry rounding), a_i = ||Wq_i (+ Wlo_i)||, b_i = ||Wr_i||, N = ||dh_{l-1}||,
 // R = ||dh_{l-1} - hi - lo|| (exact residual of the operand split),
 // Lo = ||lo||, E = bound on the error of dh_{l-1}. The error vector of a
 // whole layer propagates with spectral-norm bounds (sigma), the margin with
@@ -63,7 +65,8 @@ struct TcSmem {
     int fast;              // every valid row of the tile uses the fast path
     unsigned char dig[MROWS][kMaxS];
     float N[MROWS], R[MROWS], Lo[MROWS], E[MROWS];
-    float part[2][MROWS][3];
+    float nz[MROWS];       // nonzero entries of the point's operand row (products that can carry error)
+    float part[2][MROWS][4];
     int unc[MROWS];
     int vst[MROWS];
     int fcnt[MROWS][kTcMaxL + 1];
@@ -394,8 +397,12 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
             //      lanes over column pairs 2*lane, 2*lane+1 of each 64-column chunk)
             {
                 float nsum[16], rsum[16], lsum[16];
+                int nzc[16];  // nonzero operand entries per row (warp-uniform)
 #pragma unroll
-                for (int i = 0; i < 16; ++i) nsum[i] = rsum[i] = lsum[i] = 0.f;
+                for (int i = 0; i < 16; ++i) {
+                    nsum[i] = rsum[i] = lsum[i] = 0.f;
+                    nzc[i] = 0;
+                }
                 const int kch = H1 / 64;
                 const bool fast = S.fast;
                 const bool nosum = (s == 2);  // fast path without outer digits
@@ -526,6 +533,8 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         }
                         nsum[i] = fmaf(dh0, dh0, fmaf(dh1, dh1, nsum[i]));
                         rsum[i] = fmaf(r0, r0, fmaf(r1, r1, rsum[i]));
+                        nzc[i] += __popc(__ballot_sync(0xffffffffu, dh0 != 0.f)) +
+                                  __popc(__ballot_sync(0xffffffffu, dh1 != 0.f));
                     }
                     }  // i0
                     tc::fence_proxy_async();
@@ -552,6 +561,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         S.R[r] = norm_up(b);
                         S.Lo[r] = SPLIT ? norm_up(cc) : 0.f;
                         S.E[r] = __fmaf_ru(0x1p-24f, N, Q.kvec[1]);
+                        S.nz[r] = (float)nzc[i];
                     }
                 }
             }
@@ -565,7 +575,8 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 ++dit;
                 tc::tc_fence_after();
                 const float Nn = S.N[r], Rr = S.R[r], Ll = S.Lo[r], Ee = S.E[r];
-                const float uacc = uacc_base * (float)ly.K;
+                // accumulation: 2^-22 per product that can be nonzero (an exact zero adds nothing)
+                const float uacc = uacc_base * fminf(S.nz[r], (float)ly.K);
                 const float Pa = __fmaf_ru(uacc, __fadd_ru(__fadd_ru(Nn, Rr), __fmul_ru(2.f, Ll)),
                                            __fmaf_ru(SPLIT ? 0x1p-7f : 0.f, Ll, __fadd_ru(Rr, Ee)));
                 const float Pb = __fadd_ru(Nn, Ee);
@@ -573,6 +584,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 const float* bv = SPLIT ? ly.b3 : ly.b1;
                 const int off_l = net.noff[l];
                 float ns = 0.f, rs = 0.f, ls = 0.f;
+                int nzt = 0;
                 const int nch = ly.Npad / 64;
                 for (int c = 0; c < nch; ++c) {
                     const int a0 = ait % NA, a1 = (ait + 1) % NA;
@@ -616,6 +628,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         }
                         const float2 k2 = S.cst2[wid][i];
                         v[i] = fmaxf(du + k2.x, k2.y);
+                        nzt += v[i] != 0.f;
                     }
                     __syncwarp();  // the staged constants are read before the next chunk overwrites them
                     if (!__all_sync(0xffffffffu, rv) && !rv) {
@@ -659,6 +672,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 S.part[hf][r][0] = ns;
                 S.part[hf][r][1] = rs;
                 S.part[hf][r][2] = ls;
+                S.part[hf][r][3] = S.valid[r] ? (float)nzt : 0.f;
                 tc::tc_fence_before();
                 tc::named_bar_sync(1, 256);
                 if (hf == 0) {
@@ -678,6 +692,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     S.R[r] = Rn;
                     S.Lo[r] = Lo;
                     S.E[r] = El;
+                    S.nz[r] = S.part[0][r][3] + S.part[1][r][3];
                 }
                 if (l + 1 < L && P.ly[l + 1].Npad > 64) {
                     __syncwarp();
@@ -697,7 +712,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     tc::tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16), v);
                     if (S.valid[r]) {
                         const float Nn = S.N[r], Rr = S.R[r], Ll = S.Lo[r], Ee = S.E[r];
-                        const float uacc = uacc_base * (float)ly.K;
+                        const float uacc = uacc_base * fminf(S.nz[r], (float)ly.K);
                         const float Pa = __fmaf_ru(uacc, __fadd_ru(__fadd_ru(Nn, Rr), __fmul_ru(2.f, Ll)),
                                                    __fmaf_ru(SPLIT ? 0x1p-7f : 0.f, Ll, __fadd_ru(Rr, Ee)));
                         const float Pb = __fadd_ru(Nn, Ee);
