@@ -19,9 +19,9 @@
 // Error bound of du_l,i (per point, all norms 2-norms, u_acc = 2^-22 per
 // accumulated product, Wq = rounded weights, Wr = W - Wq [- Wlo]):
 //   |err| <= a_i (R + E + rho Lo + u_acc n (N + R + Lo)) + b_i (N + E)
-// with n the number of nonzero entries of the point's operand row (a product
-// that is exactly zero adds nothing to the accumulator, so only the n others
-// can carry rounding), a_i = ||Wq_i (+ Wlo_i)||, b_i = ||Wr_i||, N = ||dh_{l-1}||,
+// with n the number of operand columns that can be nonzero, i.e. not of the
+// column class "neg" (zero at every point of the box: a product that is exactly
+// zero adds nothing to the accumulator, so only the n others can carry rounding), a_i = ||Wq_i (+ Wlo_i)||, b_i = ||Wr_i||, N = ||dh_{l-1}||,
 // R = ||dh_{l-1} - hi - lo|| (exact residual of the operand split),
 // Lo = ||lo||, E = bound on the error of dh_{l-1}. The error vector of a
 // whole layer propagates with spectral-norm bounds (sigma), the margin with
@@ -65,8 +65,8 @@ struct TcSmem {
     int fast;              // every valid row of the tile uses the fast path
     unsigned char dig[MROWS][kMaxS];
     float N[MROWS], R[MROWS], Lo[MROWS], E[MROWS];
-    float nz[MROWS];       // nonzero entries of the point's operand row (products that can carry error)
-    float part[2][MROWS][4];
+    float nzl[kTcMaxL + 1];  // layer l: columns not in the class "neg" (the others are 0 at every point)
+    float part[2][MROWS][3];
     int unc[MROWS];
     int vst[MROWS];
     int fcnt[MROWS][kTcMaxL + 1];
@@ -315,6 +315,11 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         }
                 tc::named_bar_sync(1, 256);
                 if (wtid == 0) S.curq = q;
+                if (wtid >= 1 && wtid < L) {  // operand entries that can be nonzero, per hidden layer
+                    int c = 0;
+                    for (int w = 0; w < (net.dims[wtid] + 31) / 32; ++w) c += __popc(~Q.cneg[wtid * 32 + w]);
+                    S.nzl[wtid] = (float)min(c, net.dims[wtid]);
+                }
                 tc::named_bar_sync(1, 256);
             }
             // ---- decode the tile's points. Range mode: the tile's indices are
@@ -331,6 +336,10 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 np_need = tb / Rni - p0 + 1;
             }
             const int np = (int)(np_need < (unsigned long long)PMAX ? np_need : PMAX);
+            // fast layer-1 path: every valid row has its prefix slot (or s = 2: none needed);
+            // with R <= kStageR its inner-digit tables come from shared memory
+            const bool fast_t = !gather && ((ni == 2 && s > 2 && np_need <= (unsigned long long)PMAX) || s == 2);
+            const bool stage_t = fast_t && R <= kStageR;
             if (wtid < MROWS) {
                 const int r = wtid;
                 unsigned long long t = 0;
@@ -363,12 +372,18 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     if (k < (unsigned long long)PMAX) pi = (int)k;
                 }
                 S.pidx[r] = pi;
+                // float offsets: the prefix slot's row of souter, and the rows of the two
+                // inner-digit tables (staged chunk, or the global tables)
                 int4 ri;
-                ri.x = pi;
-                ri.y = ni >= 2 ? ((s - 2) * R + d[s - 2]) * H1 : 0;
-                ri.z = ni >= 1 ? ((s - 1) * R + d[s - 1]) * H1 : 0;
-                // valid flag, and the two inner digits for the staged tables
-                ri.w = ok ? (1 | (ni >= 2 ? d[s - 2] << 8 : 0) | (ni >= 2 ? d[s - 1] << 16 : 0)) : 0;
+                ri.x = (pi >= 0 ? pi : 0) * 512;
+                if (stage_t) {
+                    ri.y = d[s - 2] * 64;
+                    ri.z = (kStageR + d[s - 1]) * 64;
+                } else {
+                    ri.y = ni >= 2 ? ((s - 2) * R + d[s - 2]) * H1 : 0;
+                    ri.z = ni >= 1 ? ((s - 1) * R + d[s - 1]) * H1 : 0;
+                }
+                ri.w = ok;
                 S.rinfo[r] = ri;
             } else if (wtid - MROWS < np) {  // digits of outer prefix slot k
                 const int k = wtid - MROWS;
@@ -378,8 +393,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
             }
             if (wtid == 0) {
                 S.npref = np;
-                // fast layer-1 path: every valid row has its prefix slot (or s = 2: none needed)
-                S.fast = !gather && ((ni == 2 && s > 2 && np_need <= (unsigned long long)PMAX) || s == 2);
+                S.fast = fast_t;
             }
             tc::named_bar_sync(1, 256);
             // outer-prefix partial sums of layer 1
@@ -397,12 +411,8 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
             //      lanes over column pairs 2*lane, 2*lane+1 of each 64-column chunk)
             {
                 float nsum[16], rsum[16], lsum[16];
-                int nzc[16];  // nonzero operand entries per row (warp-uniform)
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    nsum[i] = rsum[i] = lsum[i] = 0.f;
-                    nzc[i] = 0;
-                }
+                for (int i = 0; i < 16; ++i) nsum[i] = rsum[i] = lsum[i] = 0.f;
                 const int kch = H1 / 64;
                 const bool fast = S.fast;
                 const bool nosum = (s == 2);  // fast path without outer digits
@@ -447,23 +457,25 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     for (int i0 = 0; i0 < 16; i0 += RB) {
                     // table sums of RB rows first (their loads overlap), then the rest
                     float2 dus[RB];
+                    unsigned vbits = 0;  // valid rows of the batch (the compute loop stores to
+                                         // shared memory, so it reloads nothing)
 #pragma unroll
                     for (int ii = 0; ii < RB; ++ii) {
                         const int r = wid * 16 + i0 + ii;
                         const int4 ri = S.rinfo[r];
+                        if (ri.w) vbits |= 1u << ii;
                         float2 du;
                         if (stage) {
                             du = nosum ? make_float2(0.f, 0.f)
-                                       : *reinterpret_cast<const float2*>(&S.souter[ri.x][j]);
-                            const float2 ta =
-                                *reinterpret_cast<const float2*>(&S.tstage[sbuf][0][(ri.w >> 8) & 0xff][2 * lane]);
-                            const float2 tb =
-                                *reinterpret_cast<const float2*>(&S.tstage[sbuf][1][(ri.w >> 16) & 0xff][2 * lane]);
+                                       : *reinterpret_cast<const float2*>(&S.souter[0][0] + ri.x + j);
+                            const float* ts = &S.tstage[sbuf][0][0][2 * lane];
+                            const float2 ta = *reinterpret_cast<const float2*>(ts + ri.y);
+                            const float2 tb = *reinterpret_cast<const float2*>(ts + ri.z);
                             du.x = (du.x + ta.x) + tb.x;
                             du.y = (du.y + ta.y) + tb.y;
                         } else if (fast) {
                             du = nosum ? make_float2(0.f, 0.f)
-                                       : *reinterpret_cast<const float2*>(&S.souter[ri.x][j]);
+                                       : *reinterpret_cast<const float2*>(&S.souter[0][0] + ri.x + j);
                             const float2 ta = __ldg(reinterpret_cast<const float2*>(&Q.tab[ri.y + j]));
                             const float2 tb = __ldg(reinterpret_cast<const float2*>(&Q.tab[ri.z + j]));
                             du.x = (du.x + ta.x) + tb.x;
@@ -491,12 +503,12 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     for (int ii = 0; ii < RB; ++ii) {
                         const int i = i0 + ii;
                         const int r = wid * 16 + i;
-                        const int4 ri = S.rinfo[r];
+                        const bool rw = (vbits >> ii) & 1u;
                         const float2 du = dus[ii];
                         float dh0 = fmaxf(du.x + c10, c20);
                         float dh1 = fmaxf(du.y + c11, c21);
-                        if (!ri.w) dh0 = dh1 = 0.f;
-                        if (anyc && ri.w && Q.flip) {  // signs matter only for coverage
+                        if (!rw) dh0 = dh1 = 0.f;
+                        if (anyc && rw && Q.flip) {  // signs matter only for coverage
                             if (cr0) {
                                 const float u = ub0 + du.x;
                                 if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > th0)) S.unc[r] = 1;
@@ -533,8 +545,6 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         }
                         nsum[i] = fmaf(dh0, dh0, fmaf(dh1, dh1, nsum[i]));
                         rsum[i] = fmaf(r0, r0, fmaf(r1, r1, rsum[i]));
-                        nzc[i] += __popc(__ballot_sync(0xffffffffu, dh0 != 0.f)) +
-                                  __popc(__ballot_sync(0xffffffffu, dh1 != 0.f));
                     }
                     }  // i0
                     tc::fence_proxy_async();
@@ -561,7 +571,6 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         S.R[r] = norm_up(b);
                         S.Lo[r] = SPLIT ? norm_up(cc) : 0.f;
                         S.E[r] = __fmaf_ru(0x1p-24f, N, Q.kvec[1]);
-                        S.nz[r] = (float)nzc[i];
                     }
                 }
             }
@@ -576,7 +585,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 tc::tc_fence_after();
                 const float Nn = S.N[r], Rr = S.R[r], Ll = S.Lo[r], Ee = S.E[r];
                 // accumulation: 2^-22 per product that can be nonzero (an exact zero adds nothing)
-                const float uacc = uacc_base * fminf(S.nz[r], (float)ly.K);
+                const float uacc = uacc_base * fminf(S.nzl[l - 1], (float)ly.K);
                 const float Pa = __fmaf_ru(uacc, __fadd_ru(__fadd_ru(Nn, Rr), __fmul_ru(2.f, Ll)),
                                            __fmaf_ru(SPLIT ? 0x1p-7f : 0.f, Ll, __fadd_ru(Rr, Ee)));
                 const float Pb = __fadd_ru(Nn, Ee);
@@ -584,7 +593,6 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 const float* bv = SPLIT ? ly.b3 : ly.b1;
                 const int off_l = net.noff[l];
                 float ns = 0.f, rs = 0.f, ls = 0.f;
-                int nzt = 0;
                 const int nch = ly.Npad / 64;
                 for (int c = 0; c < nch; ++c) {
                     const int a0 = ait % NA, a1 = (ait + 1) % NA;
@@ -610,25 +618,28 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         S.cst2[wid][lane] = k2;
                         __syncwarp();
                     }
-                    const bool signs = rv && Q.flip != nullptr;  // signs matter only for coverage
+                    if (cross && rv && Q.flip != nullptr) {  // signs matter only for coverage
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
-                        const float du = v[i];
-                        if (signs && (cross & (1u << i))) {  // warp-uniform column class
-                            const float4 k4 = S.cst4[wid][i];
-                            const int n = n0 + i, gi = off_l + n;
-                            const float u = k4.x + du;
-                            const float bound = __fmaf_ru(k4.y, Pa, __fmaf_ru(k4.z, Pb, k4.w));
-                            if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound)) S.unc[r] = 1;
-                            else if ((u >= 0.f) != (k4.x >= 0.f)) {
-                                const int k = atomicAdd(&S.fcnt[r][l], 1);
-                                if (k < FCAP) S.flist[r][l][k] = (short)n;
-                                atomicOr(&S.cflip[gi >> 5], 1u << (gi & 31));
+                        for (int i = 0; i < 32; ++i) {
+                            if (cross & (1u << i)) {  // warp-uniform column class
+                                const float4 k4 = S.cst4[wid][i];
+                                const int n = n0 + i, gi = off_l + n;
+                                const float u = k4.x + v[i];
+                                const float bound = __fmaf_ru(k4.y, Pa, __fmaf_ru(k4.z, Pb, k4.w));
+                                if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound)) S.unc[r] = 1;
+                                else if ((u >= 0.f) != (k4.x >= 0.f)) {
+                                    const int k = atomicAdd(&S.fcnt[r][l], 1);
+                                    if (k < FCAP) S.flist[r][l][k] = (short)n;
+                                    atomicOr(&S.cflip[gi >> 5], 1u << (gi & 31));
+                                }
                             }
                         }
+                    }
+                    // delta ReLU; no stores in this loop, so its loads pipeline
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
                         const float2 k2 = S.cst2[wid][i];
-                        v[i] = fmaxf(du + k2.x, k2.y);
-                        nzt += v[i] != 0.f;
+                        v[i] = fmaxf(v[i] + k2.x, k2.y);
                     }
                     __syncwarp();  // the staged constants are read before the next chunk overwrites them
                     if (!__all_sync(0xffffffffu, rv) && !rv) {
@@ -672,7 +683,6 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 S.part[hf][r][0] = ns;
                 S.part[hf][r][1] = rs;
                 S.part[hf][r][2] = ls;
-                S.part[hf][r][3] = S.valid[r] ? (float)nzt : 0.f;
                 tc::tc_fence_before();
                 tc::named_bar_sync(1, 256);
                 if (hf == 0) {
@@ -692,7 +702,6 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     S.R[r] = Rn;
                     S.Lo[r] = Lo;
                     S.E[r] = El;
-                    S.nz[r] = S.part[0][r][3] + S.part[1][r][3];
                 }
                 if (l + 1 < L && P.ly[l + 1].Npad > 64) {
                     __syncwarp();
@@ -712,7 +721,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     tc::tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16), v);
                     if (S.valid[r]) {
                         const float Nn = S.N[r], Rr = S.R[r], Ll = S.Lo[r], Ee = S.E[r];
-                        const float uacc = uacc_base * fminf(S.nz[r], (float)ly.K);
+                        const float uacc = uacc_base * fminf(S.nzl[L - 1], (float)ly.K);
                         const float Pa = __fmaf_ru(uacc, __fadd_ru(__fadd_ru(Nn, Rr), __fmul_ru(2.f, Ll)),
                                                    __fmaf_ru(SPLIT ? 0x1p-7f : 0.f, Ll, __fadd_ru(Rr, Ee)));
                         const float Pb = __fadd_ru(Nn, Ee);
