@@ -125,10 +125,19 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
     constexpr int HS = SimtSmem<PPW, NQ>::HS;
     constexpr int HW = 32 * NQA;  // columns of the weight chunk in use
     constexpr bool PER_NEURON = NQA == 1;
+    // a narrow layer's weight chunks take more rows of k in the same buffer
+    // (fewer chunks, fewer barriers): KCL rows of WSL floats
+    constexpr int WSL = HW + 4;
+    // (a power of two, so that the chunks tile the operand rows of HS floats)
+    constexpr int KFIT = (KC * SimtSmem<PPW, NQ>::WS) / WSL;
+    constexpr int KCL = !PER_NEURON ? KC : KFIT >= 64 ? 64 : KFIT >= 32 ? 32 : KFIT >= 16 ? 16 : KC;
+    static_assert(2 * KCL * WSL <= 2 * KC * SimtSmem<PPW, NQ>::WS, "weight chunk view exceeds its buffer");
+    static_assert(HS % KCL == 0, "weight chunks must tile the operand rows");
     const int L = net.L;
     const int K = net.dims[l - 1], N = net.dims[l];
     const float* __restrict__ WT = net.WT[l];  // [K][N]
-    const int nchunks = (K + KC - 1) / KC;
+    const int nchunks = (K + KCL - 1) / KCL;
+    float* const Wb = &S.Wsm[0][0][0];
     float acc[PPW][NQA];
     float chk[PPW];  // PER_NEURON: V_i of this lane's neuron; else sum_g ||s_g||^2 over this lane's neurons
 #pragma unroll
@@ -140,17 +149,18 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
 
     const bool vec = (N % 4) == 0;
     auto load_chunk = [&](int c, int buf) {
+        float* const dst = Wb + buf * (KCL * WSL);
         if (vec) {
-            for (int e = threadIdx.x; e < KC * (HW / 4); e += THREADS) {
-                const int kk = e / (HW / 4), n = (e % (HW / 4)) * 4, k = c * KC + kk;
+            for (int e = threadIdx.x; e < KCL * (HW / 4); e += THREADS) {
+                const int kk = e / (HW / 4), n = (e % (HW / 4)) * 4, k = c * KCL + kk;
                 const bool ok = k < K && n < N;
-                cp_async16(&S.Wsm[buf][kk][n], ok ? (const void*)&WT[(size_t)k * N + n] : (const void*)WT, ok);
+                cp_async16(dst + kk * WSL + n, ok ? (const void*)&WT[(size_t)k * N + n] : (const void*)WT, ok);
             }
         } else {
-            for (int e = threadIdx.x; e < KC * HW; e += THREADS) {
-                const int kk = e / HW, n = e % HW, k = c * KC + kk;
+            for (int e = threadIdx.x; e < KCL * HW; e += THREADS) {
+                const int kk = e / HW, n = e % HW, k = c * KCL + kk;
                 const bool ok = k < K && n < N;
-                cp_async4(&S.Wsm[buf][kk][n], ok ? (const void*)&WT[(size_t)k * N + n] : (const void*)WT, ok);
+                cp_async4(dst + kk * WSL + n, ok ? (const void*)&WT[(size_t)k * N + n] : (const void*)WT, ok);
             }
         }
         cp_async_commit();
@@ -162,30 +172,32 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
         cp_async_wait0();
         __syncthreads();  // chunk c visible to all; chunk c-1's buffer free
         if (c + 1 < nchunks) load_chunk(c + 1, buf ^ 1);
-        if (c > 0 && c % CKC == 0) {  // checkpoint: the partial sums at k = c KC
+        const float* const wc = Wb + buf * (KCL * WSL);
 #pragma unroll
-            for (int r = 0; r < PPW; ++r) {
-                if (PER_NEURON) {
-                    chk[r] = __fadd_ru(chk[r], fabsf(acc[r][0]));
-                } else {
+        for (int kk = 0; kk < KCL; kk += 4) {
+            const int k0 = c * KCL + kk;
+            if (k0 > 0 && k0 % (CKC * KC) == 0) {  // checkpoint: the partial sums at k = k0
 #pragma unroll
-                    for (int qq = 0; qq < NQA; ++qq) chk[r] = __fmaf_ru(acc[r][qq], acc[r][qq], chk[r]);
+                for (int r = 0; r < PPW; ++r) {
+                    if (PER_NEURON) {
+                        chk[r] = __fadd_ru(chk[r], fabsf(acc[r][0]));
+                    } else {
+#pragma unroll
+                        for (int qq = 0; qq < NQA; ++qq) chk[r] = __fmaf_ru(acc[r][qq], acc[r][qq], chk[r]);
+                    }
                 }
             }
-        }
-#pragma unroll
-        for (int kk = 0; kk < KC; kk += 4) {
             float4 a4[PPW];
 #pragma unroll
             for (int r = 0; r < PPW; ++r)
-                a4[r] = *reinterpret_cast<const float4*>(&S.A[warp * PPW + r][c * KC + kk]);
+                a4[r] = *reinterpret_cast<const float4*>(&S.A[warp * PPW + r][k0]);
 #pragma unroll
             for (int k4 = 0; k4 < 4; ++k4) {
                 float wv[NQA];
                 if (NQA >= 4) {
 #pragma unroll
                     for (int g = 0; g < NQA / 4; ++g) {
-                        const float4 w4 = *reinterpret_cast<const float4*>(&S.Wsm[buf][kk + k4][128 * g + 4 * lane]);
+                        const float4 w4 = *reinterpret_cast<const float4*>(wc + (kk + k4) * WSL + 128 * g + 4 * lane);
                         wv[4 * g] = w4.x;
                         wv[4 * g + 1] = w4.y;
                         wv[4 * g + 2] = w4.z;
@@ -193,7 +205,7 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
                     }
                 } else {
 #pragma unroll
-                    for (int qq = 0; qq < NQA; ++qq) wv[qq] = S.Wsm[buf][kk + k4][lane + 32 * qq];
+                    for (int qq = 0; qq < NQA; ++qq) wv[qq] = wc[(kk + k4) * WSL + lane + 32 * qq];
                 }
 #pragma unroll
                 for (int r = 0; r < PPW; ++r) {
@@ -210,7 +222,7 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
     const int off = net.noff[l];
     const float lf = net.lamfrob[l], gl = net.gam[l];
     const float lam = net.act == ACT_SIGMOID ? 0.25f : 1.0f;
-    const float G = (float)((nchunks + CKC - 1) / CKC);
+    const float G = (float)((nchunks * KCL + CKC * KC - 1) / (CKC * KC));  // checkpoint segments
 #pragma unroll
     for (int r = 0; r < PPW; ++r) {
         const int m = warp * PPW + r;
@@ -219,31 +231,29 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
         const float Nin = S.N[m], Ein = S.E[m];
         const float X = __fmaf_ru(gl, Nin, Ein);
         float nsum = 0.f, usum = 0.f;
+        uint32_t uncb = 0u, flipb = 0u;  // per slot: uncertain sign, certain change (handled after)
 #pragma unroll
         for (int qq = 0; qq < NQ; ++qq) {
             const int n = qq < NQA ? slot_neuron<NQA>(lane, qq) : lane + 32 * qq;
             if (qq < NQA && n < N) {
                 const int gi = off + n;
                 const float du = acc[r][qq < NQA ? qq : 0];
-                const float ub = Q.ub32[gi];
+                const float ub = __ldg(&Q.ub32[gi]);
                 const float u = ub + du;
+                const float rnn = __ldg(&rn[n]);
                 // |du - exact|: rounding (a priori, or a posteriori with one neuron per lane) + propagated
-                float bnd = __fmul_ru(rn[n], X);
+                float bnd = __fmul_ru(rnn, X);
                 if (PER_NEURON) {
-                    const float rho = __fmul_ru(kUseg, __fmaf_ru(rn[n], Nin, chk[r]));
-                    bnd = fminf(bnd, __fmaf_ru(rn[n], Ein, rho));
-                    if (l == L && n < 32) S.rho[m][n] = fminf(__fmul_ru(rn[n], __fmul_ru(gl, Nin)), rho);
+                    const float rho = __fmul_ru(kUseg, __fmaf_ru(rnn, Nin, chk[r]));
+                    bnd = fminf(bnd, __fmaf_ru(rnn, Ein, rho));
+                    if (l == L && n < 32) S.rho[m][n] = fminf(__fmul_ru(rnn, __fmul_ru(gl, Nin)), rho);
                 }
-                const float bound = __fadd_ru(bnd, Q.thr[gi]);
-                if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound)) {
-                    if (Q.flip) S.unc[m] = 1;  // signs matter only for coverage
-                } else if ((u >= 0.f) != (ub >= 0.f)) {
-                    int idx = atomicAdd(&S.fcnt[m][l], 1);
-                    if (idx < FCAP) S.flist[m][l][idx] = (short)n;
-                    if (Q.flip) set_bit_once(Q.flip, gi);
-                }
+                const float bound = __fadd_ru(bnd, __ldg(&Q.thr[gi]));
+                const bool cert = __fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound;
+                uncb |= (uint32_t)!cert << qq;
+                flipb |= (uint32_t)(cert && ((u >= 0.f) != (ub >= 0.f))) << qq;
                 if (l < L) {
-                    const float dh = act_delta(net.act, du, u, Q.c1[gi], Q.c2[gi]);
+                    const float dh = act_delta(net.act, du, u, __ldg(&Q.c1[gi]), __ldg(&Q.c2[gi]));
                     nsum = fmaf(dh, dh, nsum);
                     usum = fmaf(u, u, usum);
                     S.A[m][n] = dh;
@@ -253,6 +263,15 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
             } else if (l < L && n < HS) {
                 S.A[m][n] = 0.f;
             }
+        }
+        if (uncb && Q.flip) S.unc[m] = 1;  // signs matter only for coverage
+        while (flipb) {
+            const int qq = __ffs(flipb) - 1;
+            flipb &= flipb - 1u;
+            const int n = qq < NQA ? slot_neuron<NQA>(lane, qq) : lane + 32 * qq;
+            const int idx = atomicAdd(&S.fcnt[m][l], 1);
+            if (idx < FCAP) S.flist[m][l][idx] = (short)n;
+            if (Q.flip) set_bit_once(Q.flip, off + n);
         }
         nsum = warp_sum(nsum);
         usum = warp_sum(usum);
@@ -362,31 +381,47 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
                 const QueryView& Q = qs[S.q[m]];
                 const int R = Q.R, s = Q.s;
                 const float* tab = Q.tab;
-                int offs[kMaxS];
-                for (int p = 0; p < s; ++p) offs[p] = (p * R + S.dig[m][p]) * H1;
+                // du_j = sum_p tab[p][d_p][j], p in order; the loads of one p are
+                // independent, so each p costs one memory latency for all NQ slots
+                float dus[NQ];
+#pragma unroll
+                for (int qq = 0; qq < NQ; ++qq) dus[qq] = 0.f;
+                for (int p = 0; p < s; ++p) {
+                    const float* tp = tab + (size_t)(p * R + S.dig[m][p]) * H1;
+#pragma unroll
+                    for (int qq = 0; qq < NQ; ++qq) {
+                        const int j = lane + 32 * qq;
+                        if (j < H1) dus[qq] += __ldg(&tp[j]);
+                    }
+                }
+                // branch-free over the slots (their loads pipeline); uncertain signs
+                // and certain changes are collected as bits and handled after
                 float nsum = 0.f;
+                uint32_t uncb = 0u, flipb = 0u;
 #pragma unroll
                 for (int qq = 0; qq < NQ; ++qq) {
                     const int j = lane + 32 * qq;
                     float dh = 0.f;
                     if (j < H1) {
-                        float du = 0.f;
-                        for (int p = 0; p < s; ++p) du += __ldg(&tab[offs[p] + j]);
-                        const float ub = Q.ub32[j];
+                        const float du = dus[qq];
+                        const float ub = __ldg(&Q.ub32[j]);
                         const float u = ub + du;
-                        const float thr = Q.thr[j];
-                        if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > thr)) {
-                            if (Q.flip) S.unc[m] = 1;  // signs matter only for coverage
-                        } else if ((u >= 0.f) != (ub >= 0.f)) {
-                            int idx = atomicAdd(&S.fcnt[m][1], 1);
-                            if (idx < FCAP) S.flist[m][1][idx] = (short)j;
-                            if (Q.flip) set_bit_once(Q.flip, j);
-                        }
-                        if (L > 1) dh = act_delta(net.act, du, u, Q.c1[j], Q.c2[j]);
+                        const bool cert = __fmul_rd(fabsf(u), 1.f - 0x1p-22f) > __ldg(&Q.thr[j]);
+                        uncb |= (uint32_t)!cert << qq;
+                        flipb |= (uint32_t)(cert && ((u >= 0.f) != (ub >= 0.f))) << qq;
+                        if (L > 1) dh = act_delta(net.act, du, u, __ldg(&Q.c1[j]), __ldg(&Q.c2[j]));
                         else dh = u;
                         nsum = fmaf(dh, dh, nsum);
                     }
                     S.A[m][j] = dh;
+                }
+                if (uncb && Q.flip) S.unc[m] = 1;  // signs matter only for coverage
+                while (flipb) {
+                    const int j = lane + 32 * (__ffs(flipb) - 1);
+                    flipb &= flipb - 1u;
+                    const int idx = atomicAdd(&S.fcnt[m][1], 1);
+                    if (idx < FCAP) S.flist[m][1][idx] = (short)j;
+                    if (Q.flip) set_bit_once(Q.flip, j);
                 }
                 nsum = warp_sum(nsum);
                 if (lane == 0) {
