@@ -88,7 +88,7 @@ k_df(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__ g
         __syncthreads();
         double N[PB], E[PB];
         // ---- layer 1 in FP64; its signs are decided here
-        const int H0 = net.dims[0], H1 = net.dims[1];
+        const int H1 = net.dims[1];
         for (int b = 0; b < PB; ++b) {
             double nsq = 0.0, esq = 0.0;
             if (valid[b]) {
@@ -97,8 +97,9 @@ k_df(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__ g
                     const double ub = Q.ub[j];
                     double a = ub, mag = fabs(ub);
                     for (int p = 0; p < Q.s; ++p) {
+                        // W_1[j][pix] from the transposed copy: threads over j read contiguously
                         const double term =
-                            (double)net.W[1][(size_t)j * H0 + Q.pix[p]] * ((double)dstep[b][p] / 255.0);
+                            (double)net.WT[1][(size_t)Q.pix[p] * H1 + j] * ((double)dstep[b][p] / 255.0);
                         a += term;
                         mag += fabs(term);
                     }

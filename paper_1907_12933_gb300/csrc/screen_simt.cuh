@@ -386,6 +386,7 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
                 float dus[NQ];
 #pragma unroll
                 for (int qq = 0; qq < NQ; ++qq) dus[qq] = 0.f;
+#pragma unroll 2
                 for (int p = 0; p < s; ++p) {
                     const float* tp = tab + (size_t)(p * R + S.dig[m][p]) * H1;
 #pragma unroll
