@@ -78,6 +78,22 @@ def parse():
 FILTERS = {"none": 0, "l2": 1, "shell": 2, "l2+shell": 3}
 
 
+def job_throughput(ms_local: float, points_local: int, world: int, device=None) -> tuple[float, int, float]:
+    """Whole-job figures of a step over all ranks: the slowest rank's time (max),
+    the points all ranks checked (sum) and points per second. Each rank works on
+    its own query, so nothing else crosses ranks."""
+    if world <= 1:
+        return ms_local, points_local, points_local / (ms_local / 1000.0)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    n = torch.tensor([points_local], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    ms_max, n_all = float(t.item()), int(n.item())
+    return ms_max, n_all, n_all / (ms_max / 1000.0)
+
+
 def rank_query(w, rank):
     cfg = w["cfg"]
     if rank == 0:
@@ -580,13 +596,9 @@ def main():
     ck = clocks.stop(torch.cuda.current_device())
     step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
     ms = sum(step_ms) / len(step_ms)
-    t_local = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms_max = float(t_local.item())
     # points checked per step: all R^s, or those that pass the filter
     n_chk = n_pts if plain or a.filter == "none" else int(sums[-1]["n_points"])
-    value = world * n_chk / (ms_max / 1000.0)
+    ms_max, n_all, value = job_throughput(ms, n_chk, world, dev)
 
     # ---- end-to-end through the host API (copies inside the timed region)
     fw, sw = vnet.mask_words()
@@ -602,10 +614,7 @@ def main():
         if not a.no_coverage:
             vb.get_coverage(res)
         e2e_ms.append(1000.0 * (time.perf_counter() - t0))
-    e2e_local = torch.tensor([statistics.median(e2e_ms)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_local, op=dist.ReduceOp.MAX)
-    e2e_value = world * n_chk / (float(e2e_local.item()) / 1000.0)
+    _, _, e2e_value = job_throughput(statistics.median(e2e_ms), n_chk, world, dev)
 
     if rank == 0:
         last = sums[-1]
@@ -624,7 +633,7 @@ def main():
                            "property": "Eq. 10 (argmax)" if a.threshold is None
                            else f"Eq. 11 (threshold literal, V = {a.threshold!r})",
                            "filter": a.filter, "l2_max": a.l2_max if "l2" in a.filter else None,
-                           "points_checked": n_chk,
+                           "points_checked": n_chk, "points_checked_all_ranks": n_all,
                            "value_call": "vbmc_verify_query_device" if plain
                            else "vbmc_verify_query (image and pixels copied in inside the step)",
                            "tuning": {key: tuning[key] for key in ("simt_range", "simt_range_ctas", "simt_gather",
