@@ -290,6 +290,18 @@ vbmc_status vbmc_pair_coverage(const vbmc_net *net, const uint8_t *d_images1, co
                                int32_t n_pairs, const vbmc_cover_params *params,
                                const vbmc_pair_masks *out, void *stream);
 
+/* The same covers over the enumeration: the pairs (x, x_t) of the query's
+ * unperturbed image x and each point x_t of [lo, hi) (hi = 0: the whole box)
+ * that passes the query's filter, in FP64 (x_t's layer 1 incrementally from
+ * x's potentials, layers 2..L in full), with the definitions and tie masks of
+ * vbmc_pair_coverage; flip and SS equal the masks of vbmc_verify_query for
+ * the same points. The query's property is ignored. Uses res for staging (its
+ * verify result is discarded). *n_points (may be NULL) receives the points
+ * checked. Blocks until done. */
+vbmc_status vbmc_enum_coverage(vbmc_net *net, const vbmc_query *query, const vbmc_cover_params *params,
+                               const vbmc_pair_masks *out, vbmc_result *res, uint64_t *n_points,
+                               void *stream);
+
 /* Eq. 3-6: fraction of non-input neurons that belong to at least one covered
  * pair of a host mask in pair layout (SS, SV) or layer layout (DS, DV). */
 enum { VBMC_LAYOUT_PAIRS = 0, VBMC_LAYOUT_LAYER = 1 };

@@ -158,6 +158,8 @@ def lib():
             "vbmc_pair_coverage": [vp, vp, vp, C.c_int32, C.POINTER(_CoverParams),
                                    C.POINTER(_PairMasks), vp],
             "vbmc_covered_fraction": [vp, C.c_int32, C.POINTER(C.c_uint32), C.POINTER(C.c_double)],
+            "vbmc_enum_coverage": [vp, C.POINTER(_Query), C.POINTER(_CoverParams), C.POINTER(_PairMasks), vp,
+                                   C.POINTER(C.c_uint64), vp],
             "vbmc_set_tuning": [vp, C.POINTER(_Tuning)],
             "vbmc_proposal_create": [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
                                      C.c_uint64, C.POINTER(vp)],
@@ -557,6 +559,42 @@ def pair_coverage(net: Net, images1, images2, g: float = 2.0, d: float = 1.0,
         f = C.c_double()
         _check(lib().vbmc_covered_fraction(net.h, layout, _ptr(m, C.c_uint32), C.byref(f)))
         out[name + "_fraction"] = f.value
+    return out
+
+
+def _masks_out(net: Net, dev: dict) -> dict:
+    """Host copies of device masks and the Eq. 3-6 fractions of SS, SV, DS, DV."""
+    import torch
+    torch.cuda.synchronize()
+    fw, sw = net.mask_words()
+    words = {k: (fw if k in ("flip", "flip_tie", "ds", "ds_tie", "dv", "dv_tie") else sw) for k in PAIR_MASKS}
+    out = {k: dev[k].cpu().numpy().view(np.uint32)[:words[k]] for k in PAIR_MASKS}
+    for name, layout in (("ss", 0), ("sv", 0), ("ds", 1), ("dv", 1)):
+        m = np.ascontiguousarray(out[name]) if len(out[name]) else np.zeros(1, np.uint32)
+        f = C.c_double()
+        _check(lib().vbmc_covered_fraction(net.h, layout, _ptr(m, C.c_uint32), C.byref(f)))
+        out[name + "_fraction"] = f.value
+    return out
+
+
+def enum_coverage(net: Net, res: Result, image, pixels, k: int, g: float = 2.0, d: float = 1.0,
+                  lo: int = 0, hi: int = 0, filter: int = 0, l2_max: int = 0,
+                  stream: int | None = None) -> dict:
+    """vbmc_enum_coverage: every cover (flip, SS, SV, DS, DV and their tie masks) over
+    the pairs (unperturbed image, point) of the query's box, FP64; the masks, the
+    Eq. 3-6 fractions and the number of points checked."""
+    img = np.ascontiguousarray(image, dtype=np.uint8)
+    pix = np.ascontiguousarray(pixels, dtype=np.int32)
+    q = _query(img, pix, k, lo, hi, filter, l2_max)
+    dev = pair_masks_device(net)
+    masks = _PairMasks(*[dev[kk].data_ptr() for kk in PAIR_MASKS])
+    params = _CoverParams(float(g), float(d))
+    npts = C.c_uint64()
+    st = current_stream() if stream is None else stream
+    _check(lib().vbmc_enum_coverage(net.h, C.byref(q), C.byref(params), C.byref(masks), res.h, C.byref(npts),
+                                    C.c_void_p(st)))
+    out = _masks_out(net, dev)
+    out["n_points"] = int(npts.value)
     return out
 
 

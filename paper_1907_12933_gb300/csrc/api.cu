@@ -1072,6 +1072,52 @@ extern "C" vbmc_status vbmc_verify_batch(vbmc_net* net, const vbmc_query* querie
     return result;
 }
 
+namespace vbmc {
+vbmc_status launch_enum_pairs(const NetView& v, const QueryView& q, const vbmc_cover_params* params,
+                              const vbmc_pair_masks* out, unsigned long long* d_npoints, cudaStream_t st);
+}
+
+extern "C" vbmc_status vbmc_enum_coverage(vbmc_net* net, const vbmc_query* q, const vbmc_cover_params* params,
+                                          const vbmc_pair_masks* out, vbmc_result* res, uint64_t* n_points,
+                                          void* stream) {
+    if (!net || !q || !params || !out || !res || !q->image || (!q->pixels && q->s > 0))
+        return fail(VBMC_ERR_ARG, "null argument");
+    if (res->net != net) return fail(VBMC_ERR_ARG, "result belongs to another net");
+    if (res->pending) {
+        vbmc_status st = finish(res);
+        if (st != VBMC_OK) return st;
+    }
+    uint64_t n, h;
+    vbmc_status st = check_query_shape(res, q->s, q->k, q->lo, q->hi, nullptr, &n, &h);
+    if (st != VBMC_OK) return st;
+    const int H0 = net->v.dims[0];
+    for (int p = 0; p < q->s; ++p) {
+        if (q->pixels[p] < 0 || q->pixels[p] >= H0) return fail(VBMC_ERR_ARG, "pixel index out of range");
+        for (int r = 0; r < p; ++r)
+            if (q->pixels[r] == q->pixels[p]) return fail(VBMC_ERR_ARG, "duplicate pixel index");
+    }
+    QueryExtra x;
+    st = query_extra(*q, &x);
+    if (st != VBMC_OK) return st;
+    cudaStream_t sq = (cudaStream_t)stream;
+    VB_CUDA(cudaMemcpyAsync(res->d_image, q->image, H0, cudaMemcpyHostToDevice, sq));
+    if (q->s > 0)
+        VB_CUDA(cudaMemcpyAsync(res->d_pix_in, q->pixels, sizeof(int32_t) * q->s, cudaMemcpyHostToDevice, sq));
+    vbmc_options none{};
+    const QueryView qv = make_view(res, res->d_image, res->d_pix_in, q->s, q->k, q->lo, h, n, none, 0, x);
+    // the result's point counter carries the count; its verify state is gone
+    res->have_result = false;
+    unsigned long long* dn = &res->d_cnt->n_points;
+    VB_CUDA(cudaMemsetAsync(dn, 0, sizeof(unsigned long long), sq));
+    st = launch_enum_pairs(net->v, qv, params, out, dn, sq);
+    if (st != VBMC_OK) return st;
+    unsigned long long hn = 0;
+    VB_CUDA(cudaMemcpyAsync(&hn, dn, sizeof(hn), cudaMemcpyDeviceToHost, sq));
+    VB_CUDA(cudaStreamSynchronize(sq));
+    if (n_points) *n_points = hn;
+    return VBMC_OK;
+}
+
 extern "C" vbmc_status vbmc_search_query(vbmc_net* net, const vbmc_query* q, int32_t n_tiles,
                                          const int32_t* order, const vbmc_options* opt, vbmc_result* res,
                                          vbmc_search_out* out, void* stream) {
