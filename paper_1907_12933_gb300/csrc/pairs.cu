@@ -188,13 +188,18 @@ __global__ void __launch_bounds__(TP) k_enum_pairs(NetView net, QueryView Q, dou
         if (threadIdx.x == 0) {
             int dg[kMaxS];
             decode_digits(t, Q.s, Q.R, dg);
-            pass = !Q.filter || in_filter(Q, dg);
+            long long s2 = 0;
+            bool shell = Q.k == 0;
             for (int p = 0; p < Q.s; ++p) {
                 const int v0 = Q.image[Q.pix_in[p]];
                 int v1 = v0 + dg[p] - Q.k;
                 v1 = v1 < 0 ? 0 : (v1 > 255 ? 255 : v1);
                 dv[p] = v1 - v0;
+                s2 += (long long)dv[p] * dv[p];
+                shell = shell || dg[p] == 0 || dg[p] == Q.R - 1;
             }
+            // the query's filter (the Euclidean ball of Eq. 9 on the grid, a k-shell)
+            pass = (!(Q.filter & FILTER_L2) || s2 <= Q.l2max) && (!(Q.filter & FILTER_SHELL) || shell);
         }
         __syncthreads();
         if (!pass) {
