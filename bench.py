@@ -72,6 +72,11 @@ def parse():
                     help="--filter l2: largest sum of squared grey-level changes")
     ap.add_argument("--pairs", type=int, default=None,
                     help="pair-coverage workload: number of image pairs (default: the workload's)")
+    ap.add_argument("--enum-covers", action="store_true",
+                    help="every cover (SS, SV, DS, DV, sign changes) over the pairs (unperturbed image, "
+                         "point) of the workload's box, FP64 (vbmc_enum_coverage)")
+    ap.add_argument("--cover-g", type=float, default=2.0, help="value-change ratio g of the covers")
+    ap.add_argument("--cover-d", type=float, default=1.0, help="distance-change bound d of the covers")
     return ap.parse_args()
 
 
@@ -482,6 +487,102 @@ def main_pairs(a):
     print(json.dumps(line))
 
 
+def main_enum_covers(a):
+    """Covers over the enumeration: one vbmc_enum_coverage call per step over the
+    workload's query (its box, or --s/--k), every cover in FP64. value: points/s."""
+    over = {key: val for key, val in (("s", a.s), ("k", a.k)) if val is not None}
+    w = synth.workload(a.workload, **over)
+    net_d, cfg, q = w["net"], w["cfg"], w["query"]
+    s, k = len(q["pixels"]), q["k"]
+    n_pts = (2 * k + 1) ** s
+    dims = cfg["dims"]
+    flops = 2 * sum(dims[l - 1] * dims[l] for l in range(2, len(dims))) + 2 * s * dims[1]
+    if a.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        rate, cores, sample = oracle_enum_rate(net_d, q, a)
+        print(json.dumps({"impl": "reference", "metric": "points/sec (all covers over the enumeration)",
+                          "value": rate, "unit": "points/s", "n_gpus": a.gpus, "steps": a.steps,
+                          "warmup": a.warmup, "ms_per_step": 1000.0 * n_pts / rate, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": a.workload, "dims": dims, "s": s, "k": k, "g": a.cover_g,
+                                     "d": a.cover_d},
+                          "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample, "value": rate,
+                                           "unit": "points/s"},
+                          "e2e": {"value": rate, "unit": "points/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return
+    import torch
+    import paper_1907_12933_gb300 as vb
+    from paper_1907_12933_gb300 import build
+    build.build()
+    torch.cuda.set_device(0)
+    vnet = vb.Net(net_d)
+    res = vb.Result(vnet, max_points=0, max_s=s, max_k=k)
+    for _ in range(a.warmup):
+        vb.enum_coverage(vnet, res, q["image"], q["pixels"], k, a.cover_g, a.cover_d)
+    clocks = Clocks()
+    clocks.start()
+    times = []
+    for _ in range(a.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = vb.enum_coverage(vnet, res, q["image"], q["pixels"], k, a.cover_g, a.cover_d)
+        times.append(time.perf_counter() - t0)
+    ck = clocks.stop(torch.cuda.current_device())
+    ms = 1000.0 * statistics.median(times)
+    ach = flops * n_pts / (ms / 1000.0) / 1e12
+    fw, sw = vnet.mask_words()
+    line = {"metric": "points/sec (all covers over the enumeration)", "value": n_pts / (ms / 1000.0),
+            "unit": "points/s", "n_gpus": 1, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": a.workload, "dims": dims, "s": s, "k": k, "points": n_pts, "g": a.cover_g,
+                       "d": a.cover_d, "timing": "host clock around the blocking call (masks copied back)"},
+            "e2e": {"value": n_pts / (ms / 1000.0), "unit": "points/s", "h2d_bytes_per_step": dims[0] + 4 * s,
+                    "d2h_bytes_per_step": int(4 * (6 * fw + 4 * sw))},
+            "gpu_launches": a.steps,
+            "roofline": {"bound": "alu", "achieved": ach, "peak": 1.25, "unit": "TFLOP/s", "frac": ach / 1.25,
+                         "traffic": None, "kernel": "k_enum_pairs (FP64 forward of each point)",
+                         "peak_kind": "nominal FP64 ALU", "flops_per_launch": flops * n_pts, "launch_ms": ms},
+            "covers": {key: out[key + "_fraction"] for key in ("ss", "sv", "ds", "dv")}}
+    if ck:
+        line["clocks"] = ck
+    if not a.no_cpu_baseline:
+        rate, cores, sample = oracle_enum_rate(net_d, q, a)
+        line["cpu_baseline"] = {"value": rate, "unit": "points/s", "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    print(json.dumps(line))
+
+
+def oracle_enum_rate(net, q, a):
+    """Oracle points/s of the enumeration covers on the box's first points (one host
+    thread: the oracle's pair path is sequential)."""
+    import oracle
+    oracle.build()
+    s, k = len(q["pixels"]), q["k"]
+    n = (2 * k + 1) ** s
+    img = np.asarray(q["image"], np.int64)
+
+    def pairs(lo, hi):
+        xs = []
+        for t in range(lo, hi):
+            x = img.copy()
+            for p, d in zip(q["pixels"], oracle.digits(t, s, k)):
+                x[p] = min(255, max(0, x[p] + d - k))
+            xs.append(x.astype(np.uint8))
+        return np.repeat(img.astype(np.uint8)[None], hi - lo, 0), np.array(xs)
+
+    x1, x2 = pairs(0, min(n, 8))
+    t0 = time.perf_counter()
+    oracle.pairs_coverage(net, x1, x2, a.cover_g, a.cover_d)
+    dt = (time.perf_counter() - t0) / len(x1)
+    m = int(min(n, max(8, a.cpu_seconds / max(dt, 1e-6))))
+    x1, x2 = pairs(0, m)
+    t0 = time.perf_counter()
+    oracle.pairs_coverage(net, x1, x2, a.cover_g, a.cover_d)
+    return m / (time.perf_counter() - t0), 1, f"points [0, {m}) of {n}, all covers"
+
+
 def oracle_pairs_rate(net, x1, x2, cfg, seconds):
     """Oracle pairs/s on the first pairs of the workload (one host thread per
     forward pass: the oracle's pair path is sequential)."""
@@ -501,6 +602,8 @@ def main():
     a = parse()
     if a.workload.startswith("pairs"):
         return main_pairs(a)
+    if a.enum_covers:
+        return main_enum_covers(a)
     if "batch" in a.workload and a.impl == "ours":
         return main_batch(a)
     if a.workload.startswith("proposal") and a.impl == "ours":
