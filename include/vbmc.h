@@ -302,6 +302,20 @@ vbmc_status vbmc_enum_coverage(vbmc_net *net, const vbmc_query *query, const vbm
                                const vbmc_pair_masks *out, vbmc_result *res, uint64_t *n_points,
                                void *stream);
 
+/* Diagnostic of the wide-layer tensor path (FP8 E4M3, or BF16/FP16 on nets the
+ * fused screen does not hold): verifies points [0, n_points) of the query at
+ * that precision (coverage off) and returns, for each hidden layer l = 1..L-1
+ * and point i, the layer's operand as the tensor cores consume it (the
+ * rounded dh_l = h_l(point) - h_l(unperturbed), dequantized with the point's
+ * scale) in vals[((l-1) n_points + i) H_max + j] (H_max = widest layer), and
+ * in nre[((l-1) n_points + i) 3 + {0, 1, 2}] the path's N_l = ||dh_l||, R_l =
+ * ||dh_l - operand|| and its proven bound E_l on ||dh_l - exact||, all rounded
+ * up; so ||operand - exact dh_l|| <= R_l + E_l. Host output buffers. Allocates
+ * and frees device scratch; n_points must not exceed the path's chunk of
+ * points (2^20 by default). Blocks until done; res holds the verification. */
+vbmc_status vbmc_wide_trace(vbmc_net *net, const vbmc_query *query, int32_t precision, int32_t n_points,
+                            float *vals, float *nre, vbmc_result *res, void *stream);
+
 /* Eq. 3-6: fraction of non-input neurons that belong to at least one covered
  * pair of a host mask in pair layout (SS, SV) or layer layout (DS, DV). */
 enum { VBMC_LAYOUT_PAIRS = 0, VBMC_LAYOUT_LAYER = 1 };

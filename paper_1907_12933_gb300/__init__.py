@@ -158,6 +158,8 @@ def lib():
             "vbmc_pair_coverage": [vp, vp, vp, C.c_int32, C.POINTER(_CoverParams),
                                    C.POINTER(_PairMasks), vp],
             "vbmc_covered_fraction": [vp, C.c_int32, C.POINTER(C.c_uint32), C.POINTER(C.c_double)],
+            "vbmc_wide_trace": [vp, C.POINTER(_Query), C.c_int32, C.c_int32, C.POINTER(C.c_float),
+                                C.POINTER(C.c_float), vp, vp],
             "vbmc_enum_coverage": [vp, C.POINTER(_Query), C.POINTER(_CoverParams), C.POINTER(_PairMasks), vp,
                                    C.POINTER(C.c_uint64), vp],
             "vbmc_set_tuning": [vp, C.POINTER(_Tuning)],
@@ -596,6 +598,24 @@ def enum_coverage(net: Net, res: Result, image, pixels, k: int, g: float = 2.0, 
     out = _masks_out(net, dev)
     out["n_points"] = int(npts.value)
     return out
+
+
+def wide_trace(net: Net, res: Result, image, pixels, k: int, precision: str, n_points: int,
+               stream: int | None = None) -> tuple:
+    """vbmc_wide_trace: per hidden layer the operand rows the wide-layer tensor path
+    consumed for points 0..n_points-1 (float32 [L-1, n, H_max]) and their N, R, E
+    ([L-1, n, 3]): ||operand - exact dh_l|| <= R + E."""
+    img = np.ascontiguousarray(image, dtype=np.uint8)
+    pix = np.ascontiguousarray(pixels, dtype=np.int32)
+    q = _query(img, pix, k)
+    L, hmax = len(net.dims) - 1, max(net.dims[1:])
+    vals = np.zeros((L - 1, n_points, hmax), dtype=np.float32)
+    nre = np.zeros((L - 1, n_points, 3), dtype=np.float32)
+    p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    st = current_stream() if stream is None else stream
+    _check(lib().vbmc_wide_trace(net.h, C.byref(q), p, int(n_points), _ptr(vals, C.c_float), _ptr(nre, C.c_float),
+                                 res.h, C.c_void_p(st)))
+    return vals, nre
 
 
 def pair_masks_device(net: Net) -> dict:

@@ -1118,6 +1118,46 @@ extern "C" vbmc_status vbmc_enum_coverage(vbmc_net* net, const vbmc_query* q, co
     return VBMC_OK;
 }
 
+extern "C" vbmc_status vbmc_wide_trace(vbmc_net* net, const vbmc_query* q, int32_t precision, int32_t n_points,
+                                       float* vals, float* nre, vbmc_result* res, void* stream) {
+    if (!net || !q || !res || !vals || !nre) return fail(VBMC_ERR_ARG, "null argument");
+    const NetView& v = net->v;
+    const bool wide = wide_type(precision) >= 0 && wide_supported(v) &&
+                      (precision == VBMC_PREC_FP8 || !tc_supported(v, precision));
+    if (!wide) return fail(VBMC_ERR_UNSUPPORTED, "this net and precision do not take the wide-layer path");
+    const uint64_t n = space_size(q->s, q->k);
+    if (n_points < 1 || (uint64_t)n_points > n) return fail(VBMC_ERR_ARG, "n_points outside [1, R^s]");
+    const size_t nv = (size_t)(v.L - 1) * n_points * v.hmax, nn = (size_t)(v.L - 1) * n_points * 3;
+    float *dvals = nullptr, *dnre = nullptr;
+    if (cudaMalloc(&dvals, sizeof(float) * nv) != cudaSuccess || cudaMalloc(&dnre, sizeof(float) * nn) != cudaSuccess) {
+        cudaFree(dvals);
+        return fail(VBMC_ERR_OOM, "trace buffers");
+    }
+    cudaMemset(dvals, 0, sizeof(float) * nv);
+    cudaMemset(dnre, 0, sizeof(float) * nn);
+    WideTrace t;
+    t.vals = dvals;
+    t.nre = dnre;
+    t.n = n_points;
+    t.hmax = v.hmax;
+    wide_set_trace(&t);
+    vbmc_query qq = *q;
+    qq.lo = 0;
+    qq.hi = (uint64_t)n_points;
+    vbmc_options o{};
+    o.precision = precision;
+    vbmc_status st = vbmc_verify_query(net, &qq, &o, res, stream);
+    if (st == VBMC_OK) st = finish(res);
+    wide_set_trace(nullptr);
+    if (st == VBMC_OK &&
+        (cudaMemcpy(vals, dvals, sizeof(float) * nv, cudaMemcpyDeviceToHost) != cudaSuccess ||
+         cudaMemcpy(nre, dnre, sizeof(float) * nn, cudaMemcpyDeviceToHost) != cudaSuccess))
+        st = fail(VBMC_ERR_CUDA, "trace copy");
+    cudaFree(dvals);
+    cudaFree(dnre);
+    return st;
+}
+
 extern "C" vbmc_status vbmc_search_query(vbmc_net* net, const vbmc_query* q, int32_t n_tiles,
                                          const int32_t* order, const vbmc_options* opt, vbmc_result* res,
                                          vbmc_search_out* out, void* stream) {

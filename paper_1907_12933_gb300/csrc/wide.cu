@@ -584,6 +584,30 @@ __global__ void __launch_bounds__(256) k_wide_out(NetView net, const QueryView* 
 
 __global__ void k_wide_work_done(const QueryView* qs) { work_done(qs[0].cnt, 1); }
 
+// Diagnostic copy of the operand rows of dh_m (m = 1..L-1) for points 0..n-1.
+template <int ET>
+__global__ void k_wide_trace(const uint8_t* A, WDev w, int m, int H, WideTrace t) {
+    constexpr int EB = Elem<ET>::bytes;
+    const int i = blockIdx.x;
+    if (i >= t.n) return;
+    const size_t at = (size_t)m * w.chunk + i;
+    const float sc = w.scale[at];
+    const uint8_t* row = A + (size_t)i * w.row_bytes;
+    float* out = t.vals + ((size_t)(m - 1) * t.n + i) * t.hmax;
+    for (int j = threadIdx.x; j < H; j += blockDim.x) {
+        const uint32_t bits = EB == 1 ? (uint32_t)row[j] : (uint32_t)reinterpret_cast<const uint16_t*>(row)[j];
+        out[j] = Elem<ET>::value(bits) * sc;
+    }
+    if (threadIdx.x == 0) {
+        float* o = t.nre + ((size_t)(m - 1) * t.n + i) * 3;
+        o[0] = w.sN[at];
+        o[1] = w.sR[at];
+        o[2] = w.sE[at];
+    }
+}
+
+const WideTrace* g_trace = nullptr;
+
 // ------------------------------------------------------------------ E4M3 self-test
 
 // One 128 x 256 x 128 E4M3 product through the same TMA, descriptor and MMA path.
@@ -804,13 +828,15 @@ done:
 template <int ET>
 void launch_chunk(const WidePrec& P, int type, WideWork& w, const WDev& dv, const NetView& v, QueryView* d_q,
                   unsigned long long c0, unsigned long long count, unsigned int* err, Queue q32, int n_sm,
-                  cudaStream_t st) {
+                  cudaStream_t st, const WideTrace* trace) {
     const int L = v.L;
     const size_t gemm_smem = sizeof(WSmem) + 1024;
     cudaFuncSetAttribute(k_wide_gemm<ET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gemm_smem);
     const size_t out_smem = sizeof(float) * (size_t)v.dims[L] * v.dims[L - 1];
     cudaFuncSetAttribute(k_wide_out<ET>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)out_smem);
     k_wide_l1<ET><<<(unsigned)((count + 7) / 8), 256, 0, st>>>(v, d_q, c0, count, w.A[0], dv);
+    if (trace && count >= (unsigned long long)trace->n)
+        k_wide_trace<ET><<<trace->n, 256, 0, st>>>(w.A[0], dv, 1, v.dims[1], *trace);
     for (int l = 2; l < L; ++l) {
         const WideLayer& ly = P.ly[l];
         WGemmArgs G;
@@ -832,12 +858,16 @@ void launch_chunk(const WidePrec& P, int type, WideWork& w, const WDev& dv, cons
         k_wide_gemm<ET><<<grid, W_THREADS, gemm_smem, st>>>(G, v, d_q, dv);
         k_wide_stats<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(dv, count, l, ly.sq, ly.sd, ly.fq,
                                                                      (float)ly.K * P.acc_unit, d_q);
+        if (trace && count >= (unsigned long long)trace->n)
+            k_wide_trace<ET><<<trace->n, 256, 0, st>>>(w.A[(l + 1) % 2], dv, l, ly.N, *trace);
     }
     k_wide_out<ET><<<(unsigned)std::min<unsigned long long>((count + 255) / 256, (unsigned long long)n_sm * 8), 256,
                      out_smem, st>>>(v, d_q, c0, count, w.A[L % 2], dv, q32, 1);
 }
 
 }  // namespace
+
+void wide_set_trace(const WideTrace* t) { g_trace = t; }
 
 int wide_type(int precision) {
     if (precision == VBMC_PREC_FP8) return WIDE_E4M3;
@@ -1021,9 +1051,10 @@ vbmc_status wide_run(const WideNet& wn, int type, WideWork& w, const NetView& v,
         cudaMemsetAsync(w.unc, 0, count, st);
         cudaMemsetAsync(w.fcnt, 0, sizeof(int) * (size_t)(kMaxL + 1) * w.chunk, st);
         const WidePrec& P = wn.prec[type];
-        if (type == WIDE_E4M3) launch_chunk<WIDE_E4M3>(P, type, w, dv, v, d_q, c0, count, err, q32, n_sm, st);
-        else if (type == WIDE_BF16) launch_chunk<WIDE_BF16>(P, type, w, dv, v, d_q, c0, count, err, q32, n_sm, st);
-        else launch_chunk<WIDE_FP16>(P, type, w, dv, v, d_q, c0, count, err, q32, n_sm, st);
+        const WideTrace* tr = c0 == lo ? g_trace : nullptr;
+        if (type == WIDE_E4M3) launch_chunk<WIDE_E4M3>(P, type, w, dv, v, d_q, c0, count, err, q32, n_sm, st, tr);
+        else if (type == WIDE_BF16) launch_chunk<WIDE_BF16>(P, type, w, dv, v, d_q, c0, count, err, q32, n_sm, st, tr);
+        else launch_chunk<WIDE_FP16>(P, type, w, dv, v, d_q, c0, count, err, q32, n_sm, st, tr);
         // this chunk's undecided points: FP32, double-float, FP64 passes
         launch_screen_simt(v, d_q, 1, nullptr, 0, d_queue[1], d_qcount + 1, cap, qdf, 2, n_sm, st);
         launch_df(v, d_q, d_queue[2], d_qcount + 2, cap, q64, 3, n_sm, st);

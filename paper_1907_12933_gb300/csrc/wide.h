@@ -74,6 +74,18 @@ void wide_free(WideNet& wn);
 vbmc_status wide_work_alloc(WideWork& w, const NetView& v);
 void wide_work_free(WideWork& w);
 
+// Diagnostic: while set, the first chunk of a wide-path run copies each hidden
+// layer's operand rows (dequantized: the value times the point's scale) for its
+// first n points into vals [(L-1)][n][hmax], and N, R, E of dh_l into nre
+// [(L-1)][n][3] (device buffers).
+struct WideTrace {
+    float* vals = nullptr;
+    float* nre = nullptr;
+    int n = 0;
+    int hmax = 0;
+};
+void wide_set_trace(const WideTrace* t);
+
 // Screen [lo, hi) of query d_q[0] chunk by chunk. Each chunk's undecided points
 // go through the FP32 (queue level 1), double-float (2) and FP64 (3) passes
 // before the next chunk starts; the queue counters are reset per chunk.
