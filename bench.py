@@ -172,6 +172,21 @@ class Clocks:
 
 # ------------------------------------------------------------ roofline inputs
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each pass
+# of the timed step, from one ncu capture of this configuration on a GB300
+# (profiles/traffic_mlp784x512x512_s6k7_bf16.md; ncu replays each kernel from a
+# cold L2, so queue entries that a normal step keeps in L2 count as DRAM reads).
+# Keyed by (workload, precision, coverage, s, k); other configurations report null.
+PROFILED_TRAFFIC = {
+    ("mlp784x512x512_relu_s6k7", "bf16", True, 6, 7): {
+        "screen (first pass over every point)": 2175488 + 419584,
+        "split tensor pass": 51521536 + 51456,
+        "FP32 pass": 24272384 + 10240,
+        "double-float pass": 2820096 + 101888,
+    },
+}
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -204,7 +219,7 @@ def launches_per_step(precision, L, batch=False, n_points=0):
     return pro + (6 if batch else 7)
 
 
-def pass_rooflines(precision, dims, s, n_pts, sums, pk, pk_kind):
+def pass_rooflines(precision, dims, s, n_pts, sums, pk, pk_kind, traffic=None):
     """Roofline of each pass of a verify call (CUDA-event times from the library,
     medians over the timed steps) and, at the top level, the pass that took
     longest. Algorithmic work: 2 sum_{l>=2} H_{l-1} H_l + s H_1 FLOP per point
@@ -235,10 +250,11 @@ def pass_rooflines(precision, dims, s, n_pts, sums, pk, pk_kind):
             continue
         ach = flops / (ms / 1000.0) / 1e12
         passes.append({"kernel": name, "launch_ms": ms, "flops_per_launch": flops, "bound": bound,
-                       "achieved": ach, "peak": peak, "peak_kind": kind, "frac": ach / peak})
+                       "achieved": ach, "peak": peak, "peak_kind": kind, "frac": ach / peak,
+                       "traffic": (traffic or {}).get(name)})
     top = max(passes, key=lambda x: x["launch_ms"])
     roof = {"bound": top["bound"], "achieved": top["achieved"], "peak": top["peak"], "unit": "TFLOP/s",
-            "frac": top["frac"], "traffic": None, "kernel": top["kernel"], "peak_kind": top["peak_kind"],
+            "frac": top["frac"], "traffic": top["traffic"], "kernel": top["kernel"], "peak_kind": top["peak_kind"],
             "flops_per_launch": top["flops_per_launch"], "launch_ms": top["launch_ms"], "passes": passes}
     return roof
 
@@ -723,7 +739,9 @@ def main():
         last = sums[-1]
         pk, pk_kind = peaks()
         L = len(cfg["dims"]) - 1
-        roof = pass_rooflines(a.precision, cfg["dims"], s, n_chk, sums, pk, pk_kind)
+        traffic = PROFILED_TRAFFIC.get((a.workload, a.precision, not a.no_coverage, s, k)) \
+            if plain else None
+        roof = pass_rooflines(a.precision, cfg["dims"], s, n_chk, sums, pk, pk_kind, traffic)
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
