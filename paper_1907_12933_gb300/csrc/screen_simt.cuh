@@ -2,7 +2,7 @@
 //
 // A CTA owns a tile of MT points (8 warps x PPW points). For each point:
 //   S1  decode t into s digits (first pixel most significant)
-//   S2  layer 1 incrementally: du_j = sum_p tab[p][d_p][j]            (Eq. 1)
+//   S2  layer 1 incrementally: du_j = sum_p W_1[j][pix_p] dv_p / 255   (Eq. 1)
 //   S3  sign test and delta activation dh = act(ub + du) - act(ub)    (Eq. 2, sign)
 //   S4  layers 2..L in FP32 on the deltas: du_l = W_l dh_{l-1}, weight
 //       chunks staged in shared memory, 128 accumulators per thread
@@ -53,6 +53,7 @@ struct SimtSmem {
     int fcnt[MT][kMaxL + 1];
     short flist[MT][kMaxL + 1][FCAP];
     unsigned char dig[MT][kMaxS];
+    float cpx[MT][kMaxS];  // per point and pixel: fl(dv_p / 255), the pixel's input change
 };
 
 __device__ __forceinline__ float warp_sum(float v) {
@@ -307,7 +308,7 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
               const QEntry* __restrict__ gather, const unsigned long long* __restrict__ gather_count,
               unsigned long long gather_cap, Queue out, int out_level) {
     using Sm = SimtSmem<PPW, NQ>;
-    constexpr int MT = Sm::MT, HS = Sm::HS;
+    constexpr int MT = Sm::MT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Sm& S = *reinterpret_cast<Sm*>(smem_raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -358,7 +359,10 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
                 const QueryView& Q = qs[q];
                 int d[kMaxS];
                 decode_digits(t, Q.s, Q.R, d);
-                for (int p = 0; p < Q.s; ++p) S.dig[m][p] = (unsigned char)d[p];
+                for (int p = 0; p < Q.s; ++p) {
+                    S.dig[m][p] = (unsigned char)d[p];
+                    S.cpx[m][p] = __fdiv_rn((float)Q.dv[p * Q.R + d[p]], 255.f);
+                }
                 if (!gather && Q.filter && !in_filter(Q, d)) S.valid[m] = 0;  // L2 ball / shell
             }
         }
@@ -379,20 +383,22 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
                 const int m = warp * PPW + r;
                 if (!S.valid[m]) continue;
                 const QueryView& Q = qs[S.q[m]];
-                const int R = Q.R, s = Q.s;
-                const float* tab = Q.tab;
-                // du_j = sum_p tab[p][d_p][j], p in order; the loads of one p are
-                // independent, so each p costs one memory latency for all NQ slots
+                const int s = Q.s;
+                // du_j = sum_p fl(W_1[j][pix_p] * fl(dv_p / 255)), p in order (Eq. 1 on the
+                // s changed pixels): the s weight rows of the query's pixels are shared by
+                // all points and stay in L1. Per term at most 2u |t_p| from the exact
+                // product, plus the FP32 sum: inside the table-sum bound e1 of the prologue.
                 float dus[NQ];
 #pragma unroll
                 for (int qq = 0; qq < NQ; ++qq) dus[qq] = 0.f;
-#pragma unroll 2
+                const float* __restrict__ W1T = net.WT[1];  // [H_0][H_1]
                 for (int p = 0; p < s; ++p) {
-                    const float* tp = tab + (size_t)(p * R + S.dig[m][p]) * H1;
+                    const float* wr = W1T + (size_t)Q.pix_in[p] * H1;
+                    const float c = S.cpx[m][p];
 #pragma unroll
                     for (int qq = 0; qq < NQ; ++qq) {
                         const int j = lane + 32 * qq;
-                        if (j < H1) dus[qq] += __ldg(&tp[j]);
+                        if (j < H1) dus[qq] += __fmul_rn(__ldg(&wr[j]), c);
                     }
                 }
                 // branch-free over the slots (their loads pipeline); uncertain signs
