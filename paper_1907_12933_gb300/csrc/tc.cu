@@ -63,7 +63,7 @@ struct TcSmem {
     int pidx[MROWS];
     int4 rinfo[MROWS];     // layer-1 fast path: {prefix slot, inner table offsets a, b, valid}
     int fast;              // every valid row of the tile uses the fast path
-    unsigned char dig[MROWS][kMaxS];
+    int pixs[kMaxS];       // the query's pixel indices
     float N[MROWS], R[MROWS], Lo[MROWS], E[MROWS];
     float nzl[kTcMaxL + 1];  // layer l: columns not in the class "neg" (the others are 0 at every point)
     float part[2][MROWS][3];
@@ -74,7 +74,12 @@ struct TcSmem {
     uint32_t cflip[256];   // sign changes seen by this CTA for query curq (flushed on change)
     float4 cst4[8][32];    // per worker warp, the 32 columns it drains: (ub, a, b, thr)
     float2 cst2[8][32];    //   and the delta-ReLU constants (c1, c2)
-    float tstage[2][2][kStageR][64];  // layer 1: tables of the two inner digits, one 64-column chunk, double-buffered
+    union {
+        // fast layer-1 path: tables of the two inner digits, one 64-column chunk, double-buffered
+        float tstage[2][2][kStageR][64];
+        // other tiles: per row and pixel fl(dv_p / 255), the pixel's input change
+        float cpx[MROWS][kMaxS];
+    };
     int curq;
     int npref;
     int uniform_base;
@@ -365,7 +370,8 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 S.vst[r] = 0;
 #pragma unroll
                 for (int l = 0; l <= kTcMaxL; ++l) S.fcnt[r][l] = 0;
-                for (int p = 0; p < s; ++p) S.dig[r][p] = (unsigned char)d[p];
+                if (!fast_t)  // rows of the general layer-1 path: each pixel's input change
+                    for (int p = 0; p < s; ++p) S.cpx[r][p] = __fdiv_rn((float)Q.dv[p * R + d[p]], 255.f);
                 int pi = -1;
                 if (pre && ok) {
                     const unsigned long long k = t / Rni - p0;
@@ -385,6 +391,8 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 }
                 ri.w = ok;
                 S.rinfo[r] = ri;
+            } else if (wtid >= MROWS + 64 && wtid - (MROWS + 64) < s) {
+                S.pixs[wtid - (MROWS + 64)] = Q.pix_in[wtid - (MROWS + 64)];
             } else if (wtid - MROWS < np) {  // digits of outer prefix slot k
                 const int k = wtid - MROWS;
                 int dd[kMaxS];
@@ -459,45 +467,55 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     float2 dus[RB];
                     unsigned vbits = 0;  // valid rows of the batch (the compute loop stores to
                                          // shared memory, so it reloads nothing)
+                    if (fast) {
 #pragma unroll
-                    for (int ii = 0; ii < RB; ++ii) {
-                        const int r = wid * 16 + i0 + ii;
-                        const int4 ri = S.rinfo[r];
-                        if (ri.w) vbits |= 1u << ii;
-                        float2 du;
-                        if (stage) {
-                            du = nosum ? make_float2(0.f, 0.f)
-                                       : *reinterpret_cast<const float2*>(&S.souter[0][0] + ri.x + j);
-                            const float* ts = &S.tstage[sbuf][0][0][2 * lane];
-                            const float2 ta = *reinterpret_cast<const float2*>(ts + ri.y);
-                            const float2 tb = *reinterpret_cast<const float2*>(ts + ri.z);
+                        for (int ii = 0; ii < RB; ++ii) {
+                            const int r = wid * 16 + i0 + ii;
+                            const int4 ri = S.rinfo[r];
+                            if (ri.w) vbits |= 1u << ii;
+                            float2 du = nosum ? make_float2(0.f, 0.f)
+                                              : *reinterpret_cast<const float2*>(&S.souter[0][0] + ri.x + j);
+                            float2 ta, tb;
+                            if (stage) {
+                                const float* ts = &S.tstage[sbuf][0][0][2 * lane];
+                                ta = *reinterpret_cast<const float2*>(ts + ri.y);
+                                tb = *reinterpret_cast<const float2*>(ts + ri.z);
+                            } else {
+                                ta = __ldg(reinterpret_cast<const float2*>(&Q.tab[ri.y + j]));
+                                tb = __ldg(reinterpret_cast<const float2*>(&Q.tab[ri.z + j]));
+                            }
                             du.x = (du.x + ta.x) + tb.x;
                             du.y = (du.y + ta.y) + tb.y;
-                        } else if (fast) {
-                            du = nosum ? make_float2(0.f, 0.f)
-                                       : *reinterpret_cast<const float2*>(&S.souter[0][0] + ri.x + j);
-                            const float2 ta = __ldg(reinterpret_cast<const float2*>(&Q.tab[ri.y + j]));
-                            const float2 tb = __ldg(reinterpret_cast<const float2*>(&Q.tab[ri.z + j]));
-                            du.x = (du.x + ta.x) + tb.x;
-                            du.y = (du.y + ta.y) + tb.y;
-                        } else {
-                            du = make_float2(0.f, 0.f);
-                            if (ri.w) {
-                                const int pi = S.pidx[r];
-                                int p0 = 0;
-                                if (pi >= 0) {
-                                    du = *reinterpret_cast<const float2*>(&S.souter[pi][j]);
-                                    p0 = s - ni;
-                                }
-                                for (int p = p0; p < s; ++p) {
-                                    const float2 tv = __ldg(reinterpret_cast<const float2*>(
-                                        &Q.tab[((size_t)p * R + S.dig[r][p]) * H1 + j]));
-                                    du.x += tv.x;
-                                    du.y += tv.y;
-                                }
+                            dus[ii] = du;
+                        }
+                    } else {
+                        // general path: a row's outer-prefix sum when it has a slot, then
+                        // W_1[j][pix_p] * fl(dv_p / 255) for its remaining pixels in order.
+                        // The weight pair of pixel p is the same for every row: one load
+                        // per pixel serves the batch. Per term at most 2u |t_p| from the
+                        // exact product: inside the prologue's table-sum bound e1.
+                        int pfrom[RB];
+#pragma unroll
+                        for (int ii = 0; ii < RB; ++ii) {
+                            const int r = wid * 16 + i0 + ii;
+                            const int4 ri = S.rinfo[r];
+                            if (ri.w) vbits |= 1u << ii;
+                            const int pi = S.pidx[r];
+                            dus[ii] = (ri.w && pi >= 0) ? *reinterpret_cast<const float2*>(&S.souter[pi][j])
+                                                        : make_float2(0.f, 0.f);
+                            pfrom[ii] = !ri.w ? s : (pi >= 0 ? s - ni : 0);
+                        }
+                        for (int p = 0; p < s; ++p) {
+                            const float2 w2 =
+                                __ldg(reinterpret_cast<const float2*>(&net.WT[1][(size_t)S.pixs[p] * H1 + j]));
+#pragma unroll
+                            for (int ii = 0; ii < RB; ++ii) {
+                                if (p < pfrom[ii]) continue;
+                                const float c = S.cpx[wid * 16 + i0 + ii][p];
+                                dus[ii].x += __fmul_rn(w2.x, c);
+                                dus[ii].y += __fmul_rn(w2.y, c);
                             }
                         }
-                        dus[ii] = du;
                     }
 #pragma unroll
                     for (int ii = 0; ii < RB; ++ii) {
