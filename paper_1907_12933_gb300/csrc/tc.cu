@@ -637,20 +637,27 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         __syncwarp();
                     }
                     if (cross && rv && Q.flip != nullptr) {  // signs matter only for coverage
+                        // no stores in the loop (its loads pipeline): uncertain signs and
+                        // certain changes as bits, handled after
+                        uint32_t uncb = 0u, flb = 0u;
 #pragma unroll
                         for (int i = 0; i < 32; ++i) {
                             if (cross & (1u << i)) {  // warp-uniform column class
                                 const float4 k4 = S.cst4[wid][i];
-                                const int n = n0 + i, gi = off_l + n;
                                 const float u = k4.x + v[i];
                                 const float bound = __fmaf_ru(k4.y, Pa, __fmaf_ru(k4.z, Pb, k4.w));
-                                if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound)) S.unc[r] = 1;
-                                else if ((u >= 0.f) != (k4.x >= 0.f)) {
-                                    const int k = atomicAdd(&S.fcnt[r][l], 1);
-                                    if (k < FCAP) S.flist[r][l][k] = (short)n;
-                                    atomicOr(&S.cflip[gi >> 5], 1u << (gi & 31));
-                                }
+                                const bool cert = __fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound;
+                                uncb |= (uint32_t)!cert << i;
+                                flb |= (uint32_t)(cert && ((u >= 0.f) != (k4.x >= 0.f))) << i;
                             }
+                        }
+                        if (uncb) S.unc[r] = 1;
+                        while (flb) {
+                            const int n = n0 + __ffs(flb) - 1, gi = off_l + n;
+                            flb &= flb - 1u;
+                            const int k = atomicAdd(&S.fcnt[r][l], 1);
+                            if (k < FCAP) S.flist[r][l][k] = (short)n;
+                            atomicOr(&S.cflip[gi >> 5], 1u << (gi & 31));
                         }
                     }
                     // delta ReLU; no stores in this loop, so its loads pipeline
