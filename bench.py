@@ -179,10 +179,10 @@ class Clocks:
 # Keyed by (workload, precision, coverage, s, k); other configurations report null.
 PROFILED_TRAFFIC = {
     ("mlp784x512x512_relu_s6k7", "bf16", True, 6, 7): {
-        "screen (first pass over every point)": 2175488 + 419584,
-        "split tensor pass": 51521536 + 51456,
-        "FP32 pass": 22734920,  # from the section capture of the current kernel (DRAM rate x duration)
-        "double-float pass": 2820096 + 101888,
+        "screen (first pass over every point)": 2518528 + 278016,
+        "split tensor pass": 50960896 + 45824,
+        "FP32 pass": 23342848 + 9216,
+        "double-float pass": 2638592 + 104960,
     },
 }
 
