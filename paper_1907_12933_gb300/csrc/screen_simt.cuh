@@ -138,14 +138,21 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
     const int K = net.dims[l - 1], N = net.dims[l];
     const float* __restrict__ WT = net.WT[l];  // [K][N]
     const int nchunks = (K + KCL - 1) / KCL;
+    // Wide tiles (paired FMAs) read two operand values per shared load and keep
+    // the k loop rolled: their accumulators leave no registers for more.
+    constexpr bool PAIRED = NQA % 4 == 0;
+    constexpr int AK = (PAIRED && PPW * NQA >= 64) ? 2 : 4;
+    constexpr int KUNROLL = AK == 2 ? 1 : KCL / AK;
     float* const Wb = &S.Wsm[0][0][0];
-    float acc[PPW][NQA];
+    // accumulators in pairs (slots 2i, 2i+1), the operand layout of the paired FMA
+    float2 acc[PPW][(NQA + 1) / 2];
+    auto accv = [&](int r, int qq) -> float& { return (qq & 1) ? acc[r][qq >> 1].y : acc[r][qq >> 1].x; };
     float chk[PPW];  // PER_NEURON: V_i of this lane's neuron; else sum_g ||s_g||^2 over this lane's neurons
 #pragma unroll
     for (int r = 0; r < PPW; ++r) {
         chk[r] = 0.f;
 #pragma unroll
-        for (int qq = 0; qq < NQA; ++qq) acc[r][qq] = 0.f;
+        for (int i = 0; i < (NQA + 1) / 2; ++i) acc[r][i] = make_float2(0.f, 0.f);
     }
 
     const bool vec = (N % 4) == 0;
@@ -174,45 +181,61 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
         __syncthreads();  // chunk c visible to all; chunk c-1's buffer free
         if (c + 1 < nchunks) load_chunk(c + 1, buf ^ 1);
         const float* const wc = Wb + buf * (KCL * WSL);
-#pragma unroll
-        for (int kk = 0; kk < KCL; kk += 4) {
+#pragma unroll KUNROLL
+        for (int kk = 0; kk < KCL; kk += AK) {
             const int k0 = c * KCL + kk;
             if (k0 > 0 && k0 % (CKC * KC) == 0) {  // checkpoint: the partial sums at k = k0
 #pragma unroll
                 for (int r = 0; r < PPW; ++r) {
                     if (PER_NEURON) {
-                        chk[r] = __fadd_ru(chk[r], fabsf(acc[r][0]));
+                        chk[r] = __fadd_ru(chk[r], fabsf(acc[r][0].x));
                     } else {
 #pragma unroll
-                        for (int qq = 0; qq < NQA; ++qq) chk[r] = __fmaf_ru(acc[r][qq], acc[r][qq], chk[r]);
+                        for (int qq = 0; qq < NQA; ++qq) chk[r] = __fmaf_ru(accv(r, qq), accv(r, qq), chk[r]);
                     }
                 }
             }
-            float4 a4[PPW];
+            float av[PPW][AK];
 #pragma unroll
-            for (int r = 0; r < PPW; ++r)
-                a4[r] = *reinterpret_cast<const float4*>(&S.A[warp * PPW + r][k0]);
+            for (int r = 0; r < PPW; ++r) {
+                if (AK == 4) {
+                    const float4 t = *reinterpret_cast<const float4*>(&S.A[warp * PPW + r][k0]);
+                    av[r][0] = t.x;
+                    av[r][1] = t.y;
+                    av[r][AK > 2 ? 2 : 0] = t.z;
+                    av[r][AK > 3 ? 3 : 0] = t.w;
+                } else {
+                    const float2 t = *reinterpret_cast<const float2*>(&S.A[warp * PPW + r][k0]);
+                    av[r][0] = t.x;
+                    av[r][1] = t.y;
+                }
+            }
 #pragma unroll
-            for (int k4 = 0; k4 < 4; ++k4) {
-                float wv[NQA];
-                if (NQA >= 4) {
+            for (int k4 = 0; k4 < AK; ++k4) {
+                if (PAIRED) {
+                    // paired FMA (each half rounds to nearest like fmaf, half the
+                    // instructions), one float4 of weights at a time
+                    float2 aa[PPW];
+#pragma unroll
+                    for (int r = 0; r < PPW; ++r) aa[r] = make_float2(av[r][k4], av[r][k4]);
 #pragma unroll
                     for (int g = 0; g < NQA / 4; ++g) {
                         const float4 w4 = *reinterpret_cast<const float4*>(wc + (kk + k4) * WSL + 128 * g + 4 * lane);
-                        wv[4 * g] = w4.x;
-                        wv[4 * g + 1] = w4.y;
-                        wv[4 * g + 2] = w4.z;
-                        wv[4 * g + 3] = w4.w;
+#pragma unroll
+                        for (int r = 0; r < PPW; ++r) {
+                            acc[r][2 * g] = __ffma2_rn(aa[r], make_float2(w4.x, w4.y), acc[r][2 * g]);
+                            acc[r][2 * g + 1] = __ffma2_rn(aa[r], make_float2(w4.z, w4.w), acc[r][2 * g + 1]);
+                        }
                     }
                 } else {
+                    float wv[NQA];
 #pragma unroll
                     for (int qq = 0; qq < NQA; ++qq) wv[qq] = wc[(kk + k4) * WSL + lane + 32 * qq];
-                }
 #pragma unroll
-                for (int r = 0; r < PPW; ++r) {
-                    const float a = k4 == 0 ? a4[r].x : k4 == 1 ? a4[r].y : k4 == 2 ? a4[r].z : a4[r].w;
+                    for (int r = 0; r < PPW; ++r) {
 #pragma unroll
-                    for (int qq = 0; qq < NQA; ++qq) acc[r][qq] = fmaf(a, wv[qq], acc[r][qq]);
+                        for (int qq = 0; qq < NQA; ++qq) accv(r, qq) = fmaf(av[r][k4], wv[qq], accv(r, qq));
+                    }
                 }
             }
         }
@@ -238,7 +261,7 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
             const int n = qq < NQA ? slot_neuron<NQA>(lane, qq) : lane + 32 * qq;
             if (qq < NQA && n < N) {
                 const int gi = off + n;
-                const float du = acc[r][qq < NQA ? qq : 0];
+                const float du = accv(r, qq < NQA ? qq : 0);
                 const float ub = __ldg(&Q.ub32[gi]);
                 const float u = ub + du;
                 const float rnn = __ldg(&rn[n]);
