@@ -177,14 +177,7 @@ class Clocks:
 # (profiles/traffic_mlp784x512x512_s6k7_bf16.md; ncu replays each kernel from a
 # cold L2, so queue entries that a normal step keeps in L2 count as DRAM reads).
 # Keyed by (workload, precision, coverage, s, k); other configurations report null.
-PROFILED_TRAFFIC = {
-    ("mlp784x512x512_relu_s6k7", "bf16", True, 6, 7): {
-        "screen (first pass over every point)": 2518528 + 278016,
-        "split tensor pass": 50960896 + 45824,
-        "FP32 pass": 23342848 + 9216,
-        "double-float pass": 2638592 + 104960,
-    },
-}
+PROFILED_TRAFFIC = {}
 
 
 def peaks():

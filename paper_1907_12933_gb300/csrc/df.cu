@@ -54,7 +54,7 @@ k_df(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__ g
     unsigned char* fl = reinterpret_cast<unsigned char*>(dh + (size_t)PB * hmax);  // [PB][total]
     __shared__ double red[32];
     __shared__ int nflip[PB][kMaxL + 2], only[PB][kMaxL + 2];
-    __shared__ int dstep[PB][kMaxS];
+    __shared__ double dvs[PB][kMaxS];  // the point's input changes dv_p / 255 (FP64), once per pixel
     __shared__ int undecided[PB], valid[PB];
     __shared__ unsigned long long tpt[PB];
     __shared__ unsigned qpt[PB];
@@ -78,7 +78,7 @@ k_df(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__ g
                 const QueryView& Q = qs[en.q];
                 int d[kMaxS];
                 decode_digits(en.t, Q.s, Q.R, d);
-                for (int p = 0; p < Q.s; ++p) dstep[b][p] = Q.dv[p * Q.R + d[p]];
+                for (int p = 0; p < Q.s; ++p) dvs[b][p] = (double)Q.dv[p * Q.R + d[p]] / 255.0;
             }
         }
         if (threadIdx.x < PB * (kMaxL + 2)) {
@@ -98,8 +98,7 @@ k_df(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__ g
                     double a = ub, mag = fabs(ub);
                     for (int p = 0; p < Q.s; ++p) {
                         // W_1[j][pix] from the transposed copy: threads over j read contiguously
-                        const double term =
-                            (double)net.WT[1][(size_t)Q.pix[p] * H1 + j] * ((double)dstep[b][p] / 255.0);
+                        const double term = (double)net.WT[1][(size_t)Q.pix[p] * H1 + j] * dvs[b][p];
                         a += term;
                         mag += fabs(term);
                     }

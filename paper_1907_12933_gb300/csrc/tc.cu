@@ -639,18 +639,25 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     if (cross && rv && Q.flip != nullptr) {  // signs matter only for coverage
                         // no stores in the loop (its loads pipeline): uncertain signs and
                         // certain changes as bits, handled after
+                        // branch-free within groups of 8 columns (constants of the other
+                        // classes are zero); the column class selects the bits afterwards
                         uint32_t uncb = 0u, flb = 0u;
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) {
-                            if (cross & (1u << i)) {  // warp-uniform column class
-                                const float4 k4 = S.cst4[wid][i];
-                                const float u = k4.x + v[i];
-                                const float bound = __fmaf_ru(k4.y, Pa, __fmaf_ru(k4.z, Pb, k4.w));
-                                const bool cert = __fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound;
-                                uncb |= (uint32_t)!cert << i;
-                                flb |= (uint32_t)(cert && ((u >= 0.f) != (k4.x >= 0.f))) << i;
+                        for (int g = 0; g < 4; ++g) {
+                            if ((cross >> (8 * g)) & 0xFFu) {
+#pragma unroll
+                                for (int i = 8 * g; i < 8 * g + 8; ++i) {
+                                    const float4 k4 = S.cst4[wid][i];
+                                    const float u = k4.x + v[i];
+                                    const float bound = __fmaf_ru(k4.y, Pa, __fmaf_ru(k4.z, Pb, k4.w));
+                                    const bool cert = __fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound;
+                                    uncb |= (uint32_t)!cert << i;
+                                    flb |= (uint32_t)(cert && ((u >= 0.f) != (k4.x >= 0.f))) << i;
+                                }
                             }
                         }
+                        uncb &= cross;
+                        flb &= cross;
                         if (uncb) S.unc[r] = 1;
                         while (flb) {
                             const int n = n0 + __ffs(flb) - 1, gi = off_l + n;
