@@ -133,6 +133,9 @@ k_df(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__ g
                 float S[PB], sl[PB];
 #pragma unroll
                 for (int b = 0; b < PB; ++b) S[b] = sl[b] = 0.f;
+                // unrolled so that the weight loads of several j are in flight (each
+                // point's sum still runs in order of j)
+#pragma unroll 4
                 for (int j = 0; j < K; ++j) {
                     const float w = WT[(size_t)j * Nn + i];
 #pragma unroll
