@@ -177,7 +177,14 @@ class Clocks:
 # (profiles/traffic_mlp784x512x512_s6k7_bf16.md; ncu replays each kernel from a
 # cold L2, so queue entries that a normal step keeps in L2 count as DRAM reads).
 # Keyed by (workload, precision, coverage, s, k); other configurations report null.
-PROFILED_TRAFFIC = {}
+PROFILED_TRAFFIC = {
+    ("mlp784x512x512_relu_s6k7", "bf16", True, 6, 7): {
+        "screen (first pass over every point)": 2261760 + 302848,
+        "split tensor pass": 51234304 + 26368,
+        "FP32 pass": 23104000 + 5632,
+        "double-float pass": 2907648 + 103680,
+    },
+}
 
 
 def peaks():
