@@ -7,11 +7,19 @@ already in device memory (vbmc_verify_query_device, CUDA events on the
 launching stream); `e2e` through vbmc_verify_query with host buffers plus the
 device-to-host copies of the verdict bitmap and coverage masks.
 
-Multi-GPU: each rank verifies its own query of the same net (independent
-problems, no collective on the data path): weak scaling.
+The same step on the plain FP32 GPU path (no tensor cores) is timed in the same
+run for the tensor precisions: `fp32_path` and the ratio `vs_fp32_path`, with a
+check that both paths give identical results.
 
---impl reference times the FP64 CPU oracle (the slow reference program) on a
-bounded sample of the same workload on the host cores.
+Multi-GPU (--partition): `range` (the default) splits the query's index space
+into contiguous slices, one per rank, and merges the slices' results in one
+exchange step (paper_1907_12933_gb300.partition: sums, min, bitwise or, joined
+tie lists): strong scaling. `queries` gives each rank its own query of the same
+net (independent problems, no collective on the data path): weak scaling.
+
+--impl reference times the FP64 CPU oracle (the slow reference program) on
+bounded samples of the same workload on the host cores: each step checks one
+contiguous sample of the query, and the line reports those steps' own times.
 """
 from __future__ import annotations
 
@@ -77,6 +85,11 @@ def parse():
                          "point) of the workload's box, FP64 (vbmc_enum_coverage)")
     ap.add_argument("--cover-g", type=float, default=2.0, help="value-change ratio g of the covers")
     ap.add_argument("--cover-d", type=float, default=1.0, help="distance-change bound d of the covers")
+    ap.add_argument("--partition", default="range", choices=["range", "queries"],
+                    help="several GPUs: split one query's index space across the ranks and merge "
+                         "(range), or give each rank its own query (queries)")
+    ap.add_argument("--no-fp32-arm", action="store_true",
+                    help="skip timing the plain FP32 GPU path next to a tensor precision")
     return ap.parse_args()
 
 
@@ -124,6 +137,35 @@ def oracle_rate(net, q, seconds):
     oracle.verify(net, q, lo=lo, hi=lo + m, bitmap=False)
     dt = time.perf_counter() - t0
     return m / dt, cores, f"points [{lo}, {lo + m}) of query 0 ({m} of {n}), coverage on"
+
+
+def oracle_steps(net, q, steps, warmup, seconds_total):
+    """The reference arm: `warmup` untimed and `steps` timed steps of the FP64
+    oracle on all host cores, each step one contiguous sample of the query
+    (coverage on), sized so the timed steps take about seconds_total together.
+    Returns (points/s, ms per step, points per step, cores, sample text)."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    n = oracle.space_size(len(q["pixels"]), q["k"])
+    probe = min(n, 64 * cores)
+    for _ in range(max(1, warmup)):
+        t0 = time.perf_counter()
+        oracle.verify(net, q, lo=0, hi=probe, bitmap=False)
+        dt = time.perf_counter() - t0
+    per_step = seconds_total / max(1, steps)
+    m = int(min(n, max(probe, probe * per_step / max(dt, 1e-6))))
+    times, los = [], []
+    for i in range(steps):
+        lo = ((n - m) * (2 * i + 1)) // (2 * steps)  # samples spread over the space
+        t0 = time.perf_counter()
+        oracle.verify(net, q, lo=lo, hi=lo + m, bitmap=False)
+        times.append(time.perf_counter() - t0)
+        los.append(lo)
+    rate = steps * m / sum(times)
+    sample = (f"{steps} steps of {m} contiguous points of query 0 ({n} points), first at "
+              f"{los[0]}, last at {los[-1]}, coverage on")
+    return rate, 1000.0 * sum(times) / steps, m, cores, sample
 
 
 # ------------------------------------------------------------------- clocks
@@ -223,7 +265,9 @@ def pass_rooflines(precision, dims, s, n_pts, sums, pk, pk_kind, traffic=None):
     """Roofline of each pass of a verify call (CUDA-event times from the library,
     medians over the timed steps) and, at the top level, the pass that took
     longest. Algorithmic work: 2 sum_{l>=2} H_{l-1} H_l + s H_1 FLOP per point
-    that the pass evaluates (the split tensor pass: three products). Peaks: the
+    that the pass evaluates, one evaluation per point in every pass (the split
+    tensor pass issues three products per layer; that hardware work is reported
+    beside it as hardware_flops_per_launch, not counted as the method's). Peaks: the
     measured BF16 tensor peak (FP16 the same, E4M3 twice: nominal ratios); the
     FP32 ALU peak 152 SM x 128 lanes x 2 FLOP x sm_max_mhz; double-float costs
     11 FP32 instructions per multiply-add, so its peak is the FP32 one x 2/11;
@@ -239,7 +283,7 @@ def pass_rooflines(precision, dims, s, n_pts, sums, pk, pk_kind, traffic=None):
     first = {"fp64": ("alu", 1.25, "nominal FP64 ALU"), "fp32": ("alu", alu, "derived FP32 ALU")}.get(
         precision, ("tensor", tensor, tkind))
     rows = [("screen (first pass over every point)", med([x["ms_screen"] for x in sums]), fpp * n_pts) + first,
-            ("split tensor pass", med([x["ms_pass"][0] for x in sums]), 3 * fpp * nq[0], "tensor", tensor, tkind),
+            ("split tensor pass", med([x["ms_pass"][0] for x in sums]), fpp * nq[0], "tensor", tensor, tkind),
             ("FP32 pass", med([x["ms_pass"][1] for x in sums]), fpp * nq[1], "alu", alu, "derived FP32 ALU"),
             ("double-float pass", med([x["ms_pass"][2] for x in sums]), fpp * nq[2], "alu", alu * 2 / 11,
              "derived FP32 ALU x 2/11"),
@@ -252,6 +296,8 @@ def pass_rooflines(precision, dims, s, n_pts, sums, pk, pk_kind, traffic=None):
         passes.append({"kernel": name, "launch_ms": ms, "flops_per_launch": flops, "bound": bound,
                        "achieved": ach, "peak": peak, "peak_kind": kind, "frac": ach / peak,
                        "traffic": (traffic or {}).get(name)})
+        if name == "split tensor pass":
+            passes[-1]["hardware_flops_per_launch"] = 3 * flops
     top = max(passes, key=lambda x: x["launch_ms"])
     roof = {"bound": top["bound"], "achieved": top["achieved"], "peak": top["peak"], "unit": "TFLOP/s",
             "frac": top["frac"], "traffic": top["traffic"], "kernel": top["kernel"], "peak_kind": top["peak_kind"],
@@ -636,13 +682,15 @@ def main():
     if a.impl == "reference":
         if rank != 0:
             return
-        rate, cores, sample = oracle_rate(net_d, q, a.cpu_seconds * max(1, a.steps) / 10.0)
+        rate, ms_step, m, cores, sample = oracle_steps(net_d, q, a.steps, a.warmup,
+                                                       a.cpu_seconds * max(1, a.steps) / 10.0)
         line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT,
                 "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
-                "ms_per_step": 1000.0 * n_pts / rate, "higher_is_better": True,
+                "ms_per_step": ms_step, "points_per_step": m, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": a.workload, "dims": cfg["dims"], "s": s, "k": k,
-                           "points_per_query": n_pts, "parallelism": "host threads"},
+                           "points_per_query": n_pts, "parallelism": "host threads",
+                           "step": "one bounded contiguous sample of the query (points_per_step)"},
                 "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample,
                                  "value": rate, "unit": UNIT},
                 "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -658,9 +706,16 @@ def main():
     else:
         torch.cuda.set_device(0)
     import paper_1907_12933_gb300 as vb
-    from paper_1907_12933_gb300 import build
+    from paper_1907_12933_gb300 import build, partition
     build.build()
 
+    # range partition: every rank takes a contiguous slice of the same query
+    split = world > 1 and a.partition == "range"
+    if split:
+        q = w["query"]
+        lo, hi = partition.rank_range(n_pts, rank, world)
+    else:
+        lo, hi = 0, n_pts
     dev = torch.device("cuda")
     stream = torch.cuda.current_stream()
     vnet = vb.Net(net_d)
@@ -681,43 +736,89 @@ def main():
     # on the stream inside the step)
     plain = a.threshold is None and a.filter == "none"
 
-    def step():
+    def step(precision):
         if plain:
-            vb.verify_query_device(vnet, res, d_img, d_pix, k, precision=a.precision,
+            vb.verify_query_device(vnet, res, d_img, d_pix, k, lo=lo, hi=hi, precision=precision,
                                    coverage=not a.no_coverage)
         else:
-            vb.verify_query(vnet, res, q["image"], q["pixels"], k, precision=a.precision,
+            vb.verify_query(vnet, res, q["image"], q["pixels"], k, lo=lo, hi=hi, precision=precision,
                             coverage=not a.no_coverage, filter=FILTERS[a.filter], l2_max=a.l2_max,
                             threshold=a.threshold, wait=False)
 
+    def partial():
+        """This rank's result of its slice, for the exchange step."""
+        sm = vb.result_summary(res)
+        out = {"n_points": sm["n_points"], "n_adv": sm["n_adversarial"], "n_ties": sm["n_ties"],
+               "first_witness": sm["first_witness"], "D": sm["D"], "base_margin": sm["base_margin"],
+               "bitmap": vb.get_verdict_bitmap(res, n_pts), "ties": vb.get_ties(res)}
+        if not a.no_coverage:
+            out.update({key: val for key, val in vb.get_coverage(res).items()
+                        if key in ("flip", "flip_tie", "ss", "ss_tie")})
+        return out
+
+    def timed_steps(precision, steps):
+        """CUDA-event time of each step on the launching stream (L2 flushed between
+        steps), the summaries, and for a split query the exchange step's time."""
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        sums, merge_ms, merged = [], [], None
+        barrier()
+        torch.cuda.synchronize()
+        for i in range(steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step(precision)
+            ev[i][1].record(stream)
+            sums.append(vb.result_summary(res))
+            if split:
+                t0 = time.perf_counter()
+                merged = partition.merge_partials(partial(), device=dev)
+                merge_ms.append(1000.0 * (time.perf_counter() - t0))
+        torch.cuda.synchronize()
+        barrier()
+        step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+        return step_ms, sums, merge_ms, merged
+
     # ---- device-resident steps (value)
     for _ in range(a.warmup):
-        step()
+        step(a.precision)
         vb.result_summary(res)
     clocks = Clocks()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(a.steps)]
-    screen_ms, sums = [], []
-    barrier()
-    torch.cuda.synchronize()
     clocks.start()
     t_wall = time.perf_counter()
-    for i in range(a.steps):
-        flush.zero_()
-        ev[i][0].record(stream)
-        step()
-        ev[i][1].record(stream)
-        sm = vb.result_summary(res)
-        sums.append(sm)
-    torch.cuda.synchronize()
-    barrier()
+    step_ms, sums, merge_ms, merged = timed_steps(a.precision, a.steps)
     wall = time.perf_counter() - t_wall
     ck = clocks.stop(torch.cuda.current_device())
-    step_ms = [e0.elapsed_time(e1) for e0, e1 in ev]
     ms = sum(step_ms) / len(step_ms)
-    # points checked per step: all R^s, or those that pass the filter
-    n_chk = n_pts if plain or a.filter == "none" else int(sums[-1]["n_points"])
+    if split:  # the exchange step is part of a step of a split query
+        ms += statistics.median(merge_ms)
+    # points checked per step by this rank: its slice, or those that pass the filter
+    n_chk = hi - lo if plain or a.filter == "none" else int(sums[-1]["n_points"])
     ms_max, n_all, value = job_throughput(ms, n_chk, world, dev)
+
+    # ---- the plain FP32 GPU path on the same query, same timing (the metric's
+    # comparison arm); its results must be identical
+    fp32_arm = None
+    if a.precision in ("bf16", "fp16", "fp8") and not a.no_fp32_arm:
+        ref_cov = None if a.no_coverage else vb.get_coverage(res)
+        ref_bm = vb.get_verdict_bitmap(res, n_pts)
+        step("fp32")
+        vb.result_summary(res)
+        k32 = max(3, min(a.steps, 5))
+        ms32, sums32, merge32, _ = timed_steps("fp32", k32)
+        m32 = sum(ms32) / len(ms32) + (statistics.median(merge32) if split else 0.0)
+        ms32_max, _, value32 = job_throughput(m32, n_chk, world, dev)
+        a0, b0 = sums[-1], sums32[-1]
+        same = all(a0[f] == b0[f] for f in ("n_adversarial", "first_witness", "n_ties", "D", "n_points"))
+        same = same and np.array_equal(vb.get_verdict_bitmap(res, n_pts), ref_bm)
+        if ref_cov is not None:
+            cov32 = vb.get_coverage(res)
+            same = same and all(np.array_equal(cov32[f], ref_cov[f]) for f in ("flip", "flip_tie", "ss", "ss_tie"))
+        fp32_arm = {"value": value32, "unit": UNIT, "ms_per_step": ms32_max, "steps": k32,
+                    "call": "vbmc_verify_query_device, precision fp32 (no tensor cores)",
+                    "identical_results": bool(same),
+                    "ms_pass": dict(zip(("split", "fp32", "double_float", "fp64"), b0["ms_pass"])),
+                    "ms_screen": b0["ms_screen"], "n_recheck": b0["n_recheck"]}
 
     # ---- end-to-end through the host API (copies inside the timed region)
     fw, sw = vnet.mask_words()
@@ -726,12 +827,15 @@ def main():
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        vb.verify_query(vnet, res, q["image"], q["pixels"], k, precision=a.precision,
+        vb.verify_query(vnet, res, q["image"], q["pixels"], k, lo=lo, hi=hi, precision=a.precision,
                         coverage=not a.no_coverage, filter=FILTERS[a.filter], l2_max=a.l2_max,
                         threshold=a.threshold)
-        vb.get_verdict_bitmap(res, n_pts)
-        if not a.no_coverage:
-            vb.get_coverage(res)
+        if split:
+            partition.merge_partials(partial(), device=dev)
+        else:
+            vb.get_verdict_bitmap(res, n_pts)
+            if not a.no_coverage:
+                vb.get_coverage(res)
         e2e_ms.append(1000.0 * (time.perf_counter() - t0))
     _, _, e2e_value = job_throughput(statistics.median(e2e_ms), n_chk, world, dev)
 
@@ -740,11 +844,21 @@ def main():
         pk, pk_kind = peaks()
         L = len(cfg["dims"]) - 1
         traffic = PROFILED_TRAFFIC.get((a.workload, a.precision, not a.no_coverage, s, k)) \
-            if plain else None
+            if plain and not split else None
         roof = pass_rooflines(a.precision, cfg["dims"], s, n_chk, sums, pk, pk_kind, traffic)
+        verdict = {"verdict": last["verdict"], "n_adversarial": last["n_adversarial"],
+                   "first_witness": last["first_witness"], "n_ties": last["n_ties"],
+                   "n_recheck": last["n_recheck"], "ms_prologue": last["ms_prologue"],
+                   "ms_screen": last["ms_screen"], "ms_recheck": last["ms_recheck"],
+                   "ms_pass": dict(zip(("split", "fp32", "double_float", "fp64"), last["ms_pass"]))}
+        if split:  # the whole query's result after the exchange step
+            verdict.update({"verdict": partition.merged_verdict(merged), "n_adversarial": merged["n_adv"],
+                            "first_witness": merged["first_witness"], "n_ties": merged["n_ties"],
+                            "rank0_slice": [lo, hi], "ms_exchange": statistics.median(merge_ms)})
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "higher_is_better": True, "scaling": "strong" if split else "weak",
+                "vs_baseline": None,
                 "dtype": {"fp64": "f64", "fp32": "f32", "bf16": "bf16", "fp16": "f16",
                           "fp8": "e4m3"}[a.precision],
                 "data": "synthetic",
@@ -759,20 +873,22 @@ def main():
                            else "vbmc_verify_query (image and pixels copied in inside the step)",
                            "tuning": {key: tuning[key] for key in ("simt_range", "simt_range_ctas", "simt_gather",
                                                                    "simt_gather_ctas", "df_ctas", "from_cache")},
-                           "queries": "one per rank (rank r: query r of the workload seed)",
+                           "queries": ("one query split into contiguous slices, one per rank, merged "
+                                       "by one exchange step") if split
+                           else "one per rank (rank r: query r of the workload seed)",
                            "l2": "flushed between timed steps (256 MB write)",
-                           "parallelism": f"dp{world}" if world > 1 else "single GPU"},
+                           "parallelism": (f"range split over {world} ranks" if split else f"dp{world}")
+                           if world > 1 else "single GPU"},
                 "e2e": {"value": e2e_value, "unit": UNIT,
                         "h2d_bytes_per_step": int(cfg["dims"][0] + 4 * s),
                         "d2h_bytes_per_step": int(4 * ((n_pts + 31) // 32) + 8 * fw + 8 * sw + 128)},
                 "gpu_launches": a.steps * launches_per_step(a.precision, L, n_points=n_pts),
                 "roofline": roof,
-                "verdict": {"verdict": last["verdict"], "n_adversarial": last["n_adversarial"],
-                            "first_witness": last["first_witness"], "n_ties": last["n_ties"],
-                            "n_recheck": last["n_recheck"], "ms_prologue": last["ms_prologue"],
-                            "ms_screen": last["ms_screen"], "ms_recheck": last["ms_recheck"],
-                            "ms_pass": dict(zip(("split", "fp32", "double_float", "fp64"), last["ms_pass"]))},
+                "verdict": verdict,
                 "wall_s": wall}
+        if fp32_arm:
+            line["fp32_path"] = fp32_arm
+            line["vs_fp32_path"] = value / fp32_arm["value"]
         if ck:
             line["clocks"] = ck
         if world == 1 and not a.no_cpu_baseline:

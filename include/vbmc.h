@@ -34,8 +34,11 @@
  *     until the matching *_free. get_* calls copy into caller buffers.
  *   - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
  *     All device work of a call is ordered on it.
- *   - Memory: device memory is allocated only by vbmc_net_create and
- *     vbmc_result_create; verify calls allocate nothing.
+ *   - Memory: device memory is allocated by vbmc_net_create,
+ *     vbmc_net_prepare, vbmc_result_create(_batch), vbmc_autotune, the proposal
+ *     calls and the diagnostic vbmc_wide_trace. A verify call allocates
+ *     nothing, except that the first call at a tensor precision on a net that
+ *     was not prepared for it builds that precision's weight copies.
  *   - Errors found on the device (an invalid pixel list passed by device
  *     pointer, a full recheck queue) are latched in the result and returned
  *     by the next call that reads it.
@@ -156,6 +159,14 @@ typedef struct {
     int32_t max_k;       /* <= VBMC_MAX_K                                  */
     uint32_t ties_cap;   /* tie indices kept (all are counted)             */
     uint64_t queue_cap;  /* points that may wait for a tighter recheck     */
+    int64_t wide_chunk;  /* nets with the wide-layer tensor path (ReLU,
+                          * hidden widths a multiple of 256 up to 1024):
+                          * points per chunk of its workspace, allocated
+                          * here (about 4 x widest hidden layer + 250
+                          * bytes per point). 0: min(2^20, (2 max_k + 1)
+                          * ^ max_s); -1: none, and FP8 or wide BF16/FP16
+                          * verify calls on this result fail with
+                          * VBMC_ERR_STATE. Rounded up to 128.          */
 } vbmc_caps;
 
 typedef struct {
@@ -187,6 +198,13 @@ typedef struct vbmc_result vbmc_result;
  * first input (Sec. III-C), to the device. Computes the weight norms the
  * screens' error bounds use. Allocates device memory; not for the timed path. */
 vbmc_status vbmc_net_create(const vbmc_mlp_desc *desc, vbmc_net **out);
+
+/* Build the net's operands for a tensor precision now (BF16/FP16: the fused
+ * screen's or the wide-layer path's rounded weights, their norms, and the
+ * accumulator self-test; FP8: the E4M3 weights, scales and self-test), so that
+ * no later verify call allocates. FP32 and FP64 need nothing (VBMC_OK).
+ * VBMC_ERR_UNSUPPORTED when the net has no tensor path at that precision. */
+vbmc_status vbmc_net_prepare(vbmc_net *net, int32_t precision);
 vbmc_status vbmc_net_free(vbmc_net *net);
 
 /* Allocate a reusable result workspace for queries on `net` within `caps`. */
@@ -214,7 +232,7 @@ vbmc_status vbmc_verify_query_device(vbmc_net *net, const uint8_t *d_image, int3
                                      const int32_t *d_pixels, int32_t k, uint64_t lo, uint64_t hi,
                                      const vbmc_options *opt, vbmc_result *res, void *stream);
 
-/* Many queries against one net: with results from one vbmc_result_create_batch
+/* checkNN (Sec. III-C) for many queries against one net: with results from one vbmc_result_create_batch
  * call (in order), every query's points go to one persistent launch per pass
  * (tiles never span queries; rechecked points of all queries share the
  * queues), optionally captured as one CUDA graph (opt->graph). Other result
@@ -355,6 +373,20 @@ vbmc_status vbmc_set_tuning(vbmc_net *net, const vbmc_tuning *t);
  * first use. */
 vbmc_status vbmc_fp8_accumulation_unit(vbmc_net *net, double *unit);
 
+/* Accumulation error per product that the BF16 / FP16 screens' bounds use on
+ * this device (precision VBMC_PREC_BF16 or VBMC_PREC_FP16), relative to the sum
+ * of |products| of a dot product. The PTX ISA does not state how the kind::f16
+ * MMA rounds its partial sums, so a set-up self-test measures it on the
+ * screens' own operand layout (K = 256 over four chunks): integer tiles that
+ * must come back exact (else VBMC_ERR_UNSUPPORTED), probe sums that need 17 to
+ * 24 significand bits, and random operands checked against the model
+ * K u sum |products|. *unit = 2^-22 (the FP32 model) when the probes are exact
+ * and every output lies within the model at that unit, 2^-13 when only the
+ * looser model holds. *worst (may be NULL) = the largest observed
+ * |error| / (K sum |products|) over the test tile. Does not need the net's
+ * weights; the result is kept per device and type. */
+vbmc_status vbmc_tc_accumulation_unit(vbmc_net *net, int32_t precision, double *unit, double *worst);
+
 /* ---- k-shell order: the shells r = 0, 1, ..., k (points whose largest step
  * is exactly r, checked as the box of radius r restricted to its boundary)
  * one after another, stopping after the first shell that holds a point
@@ -401,9 +433,11 @@ vbmc_status vbmc_search_query(vbmc_net *net, const vbmc_query *query, int32_t n_
                               const int32_t *order, const vbmc_options *opt, vbmc_result *res,
                               vbmc_search_out *out, void *stream);
 
-/* Adversarial points per tile (n_tiles tiles as above) from the verdict bitmap
- * of the result's last call, which must have covered the whole space with the
- * bitmap on. counts: n_tiles uint64 in host memory. */
+/* Adversarial points per tile (n_tiles tiles as above, at most
+ * VBMC_MAX_TILES) from the verdict bitmap of the result's last call, which must
+ * have covered the whole space with the bitmap on. counts: n_tiles uint64 in
+ * host memory; the device counters are the result's own (no allocation). */
+#define VBMC_MAX_TILES 1024
 vbmc_status vbmc_tile_counts(vbmc_result *res, int32_t n_tiles, uint64_t *counts);
 
 /* ---- Learned tile proposal: a 3-layer MLP (F -> H1 -> H2 -> T, ReLU hidden
@@ -481,12 +515,20 @@ vbmc_status vbmc_proposal_set_params(vbmc_proposal *p, int32_t layer, const floa
  * call's end. */
 #define VBMC_NOALLOC_MAX_NEURONS 4096
 #define VBMC_NOALLOC_MAX_SR 4096
+#define VBMC_NOALLOC_BAD_PIXELS 1u /* flags in the high word of counters[3] */
+#define VBMC_NOALLOC_TIES_CUT 4u
 
 typedef struct {
     uint64_t *counters;      /* [4]: adversarial count, first witness (UINT64_MAX: none),
                                 tie count, and class D of the unperturbed image in the
-                                low 32 bits with device error flags in the high 32 bits
-                                (nonzero: the pixel list was invalid)                  */
+                                low 32 bits with flags in the high 32 bits:
+                                VBMC_NOALLOC_BAD_PIXELS  the pixel list was invalid (not
+                                                         distinct or out of range): no
+                                                         other output is meaningful
+                                VBMC_NOALLOC_TIES_CUT    more ties than ties_cap (or
+                                                         ties == NULL): the count is
+                                                         exact, the list holds the first
+                                                         ties_cap found               */
     uint32_t *flip, *flip_tie, *ss, *ss_tie; /* coverage masks: all four, or all NULL   */
     uint32_t *bitmap;        /* verdict bits (bit t), or NULL                           */
     uint64_t bitmap_bits;    /* capacity of `bitmap` in bits                            */

@@ -68,7 +68,7 @@ SCHEDULES = {"given": 0, "small_first": 1}
 
 class _Caps(C.Structure):
     _fields_ = [("max_points", C.c_uint64), ("max_s", C.c_int32), ("max_k", C.c_int32),
-                ("ties_cap", C.c_uint32), ("queue_cap", C.c_uint64)]
+                ("ties_cap", C.c_uint32), ("queue_cap", C.c_uint64), ("wide_chunk", C.c_int64)]
 
 
 class _Summary(C.Structure):
@@ -130,6 +130,7 @@ def lib():
         sig = {
             "vbmc_net_create": [C.POINTER(_MlpDesc), C.POINTER(vp)],
             "vbmc_net_free": [vp],
+            "vbmc_net_prepare": [vp, C.c_int32],
             "vbmc_result_create": [vp, C.POINTER(_Caps), C.POINTER(vp)],
             "vbmc_result_free": [vp],
             "vbmc_result_create_batch": [vp, C.POINTER(_Caps), C.c_int32, C.POINTER(vp)],
@@ -155,6 +156,7 @@ def lib():
             "vbmc_shell_search": [vp, C.POINTER(_Query), C.POINTER(_Options), vp, C.POINTER(_ShellOut), vp],
             "vbmc_autotune": [vp, C.c_char_p, C.POINTER(_Tuning)],
             "vbmc_fp8_accumulation_unit": [vp, C.POINTER(C.c_double)],
+            "vbmc_tc_accumulation_unit": [vp, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)],
             "vbmc_pair_coverage": [vp, vp, vp, C.c_int32, C.POINTER(_CoverParams),
                                    C.POINTER(_PairMasks), vp],
             "vbmc_covered_fraction": [vp, C.c_int32, C.POINTER(C.c_uint32), C.POINTER(C.c_double)],
@@ -245,8 +247,8 @@ class Result:
     """vbmc_result_create / vbmc_result_free: a reusable workspace."""
 
     def __init__(self, net: Net, max_points: int = 0, max_s: int = MAX_S, max_k: int = 32,
-                 ties_cap: int = 1 << 16, queue_cap: int = 1 << 22):
-        caps = _Caps(max_points, max_s, max_k, ties_cap, queue_cap)
+                 ties_cap: int = 1 << 16, queue_cap: int = 1 << 22, wide_chunk: int = 0):
+        caps = _Caps(max_points, max_s, max_k, ties_cap, queue_cap, wide_chunk)
         h = C.c_void_p()
         _check(lib().vbmc_result_create(net.h, C.byref(caps), C.byref(h)))
         self.h = h
@@ -265,9 +267,10 @@ class Result:
 
 
 def result_create_batch(net: Net, nq: int, max_points: int = 0, max_s: int = MAX_S,
-                        max_k: int = 32, ties_cap: int = 1 << 12, queue_cap: int = 1 << 24) -> list:
+                        max_k: int = 32, ties_cap: int = 1 << 12, queue_cap: int = 1 << 24,
+                        wide_chunk: int = 0) -> list:
     """vbmc_result_create_batch: nq workspaces that vbmc_verify_batch serves together."""
-    caps = _Caps(max_points, max_s, max_k, ties_cap, queue_cap)
+    caps = _Caps(max_points, max_s, max_k, ties_cap, queue_cap, wide_chunk)
     hs = (C.c_void_p * nq)()
     _check(lib().vbmc_result_create_batch(net.h, C.byref(caps), nq, hs))
     out = []
@@ -412,6 +415,18 @@ def fp8_accumulation_unit(net: Net) -> float:
     u = C.c_double()
     _check(lib().vbmc_fp8_accumulation_unit(net.h, C.byref(u)))
     return u.value
+
+
+def net_prepare(net: Net, precision: str) -> None:
+    """vbmc_net_prepare: build a tensor precision's operands now (no later allocation)."""
+    _check(lib().vbmc_net_prepare(net.h, PRECISIONS[precision]))
+
+
+def tc_accumulation_unit(net: Net, precision: str = "bf16") -> tuple[float, float]:
+    """vbmc_tc_accumulation_unit: (unit, worst) of the kind::f16 accumulator self-test."""
+    u, w = C.c_double(), C.c_double()
+    _check(lib().vbmc_tc_accumulation_unit(net.h, PRECISIONS[precision], C.byref(u), C.byref(w)))
+    return u.value, w.value
 
 
 def autotune(net: Net, cache_path: str | None = None) -> dict:

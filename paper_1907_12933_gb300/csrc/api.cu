@@ -114,7 +114,8 @@ struct vbmc_result {
     unsigned long long* d_qcount = nullptr;  // 4 queue counters
     QEntry* d_queue[4] = {nullptr, nullptr, nullptr, nullptr};
     double* d_margin = nullptr;
-    WideWork ww{};  // chunk workspace of the wide-layer path (allocated on first use)
+    WideWork ww{};  // chunk workspace of the wide-layer path (caps.wide_chunk; allocated at creation)
+    unsigned long long* d_tiles = nullptr;  // VBMC_MAX_TILES counters of vbmc_tile_counts
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_pro = nullptr, ev_scr = nullptr;
     cudaEvent_t ev_split = nullptr, ev_f32 = nullptr, ev_df = nullptr;  // after each recheck pass
     cudaStream_t last_stream = nullptr;
@@ -341,6 +342,7 @@ vbmc_status create_result(const vbmc_net* net, const vbmc_caps* caps, BatchArena
     if (arena) qc = std::min<uint64_t>(qc, 1u << 16);
     r->caps.queue_cap = qc;
     for (int i = 0; i < 4; ++i) A(&r->d_queue[i], (size_t)qc);
+    A(&r->d_tiles, (size_t)VBMC_MAX_TILES);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&r->h_cnt, sizeof(Counters));
     if (e == cudaSuccess) e = cudaEventCreate(&r->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&r->ev1);
@@ -352,6 +354,20 @@ vbmc_status create_result(const vbmc_net* net, const vbmc_caps* caps, BatchArena
     if (e != cudaSuccess) {
         vbmc_result_free(r);
         return fail(VBMC_ERR_OOM, std::string("result_create: ") + cudaGetErrorString(e));
+    }
+    // the wide-layer tensor path's chunk workspace: sized here so that verify
+    // calls allocate nothing (batch members: only when asked for explicitly)
+    if (wide_supported(v) && caps->wide_chunk >= 0 && !(arena && caps->wide_chunk == 0)) {
+        unsigned long long chunk = (unsigned long long)caps->wide_chunk;
+        if (chunk == 0) {
+            const uint64_t box = space_size(caps->max_s, caps->max_k);
+            chunk = (box == 0 || box > (1ull << 20)) ? (1ull << 20) : box;
+        }
+        const vbmc_status ws = wide_work_alloc(r->ww, v, chunk);
+        if (ws != VBMC_OK) {
+            vbmc_result_free(r);
+            return fail(ws, "result_create: wide-layer workspace (lower caps.wide_chunk, or -1 for none)");
+        }
     }
     q.cnt = r->d_cnt;
     q.bitmap_bits = caps->max_points;
@@ -515,8 +531,9 @@ vbmc_status enqueue_passes(vbmc_net* net, QueryView* d_qs, const QueryView* hq, 
                         "a multiple of 256 up to 1024, at most 32 outputs)");
         vbmc_status fs = wide_build(net->wide, v, net->hW, wtype);
         if (fs != VBMC_OK) return fail(fs, "wide-layer tensor set-up failed (self-test or weight preparation)");
-        fs = wide_work_alloc(*ww, v);
-        if (fs != VBMC_OK) return fail(fs, "wide-layer chunk workspace allocation failed");
+        if (!ww->chunk)
+            return fail(VBMC_ERR_STATE, "the result has no wide-layer workspace (created with caps.wide_chunk = -1, "
+                                        "or as a batch member without one)");
     }
     VB_CUDA(cudaMemsetAsync(d_qcount, 0, sizeof(unsigned long long) * 4, st));
     VB_CUDA(record(ev[0]));
@@ -1273,15 +1290,14 @@ extern "C" vbmc_status vbmc_tile_counts(vbmc_result* res, int32_t n_tiles, uint6
     if (!res->opt.bitmap) return fail(VBMC_ERR_STATE, "bitmap was off for the last call");
     if (res->lo != 0 || res->hi != res->n_space)
         return fail(VBMC_ERR_STATE, "the last call did not cover the whole space");
-    unsigned long long* d = nullptr;
-    VB_CUDA(cudaMalloc(&d, sizeof(unsigned long long) * n_tiles));
+    if (n_tiles > VBMC_MAX_TILES) return fail(VBMC_ERR_ARG, "n_tiles above VBMC_MAX_TILES");
+    unsigned long long* d = res->d_tiles;
     launch_tile_counts(res->hq.bitmap, res->n_space, n_tiles, d, res->last_stream);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(counts, d, sizeof(unsigned long long) * n_tiles, cudaMemcpyDeviceToHost,
                             res->last_stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(res->last_stream);
-    cudaFree(d);
     if (e != cudaSuccess) return fail(VBMC_ERR_CUDA, cudaGetErrorString(e));
     return VBMC_OK;
 }
@@ -1523,6 +1539,33 @@ extern "C" vbmc_status vbmc_fp8_accumulation_unit(vbmc_net* net, double* unit) {
     const vbmc_status st = wide_build(net->wide, net->v, net->hW, WIDE_E4M3);
     if (st != VBMC_OK) return fail(st, "FP8 set-up failed (self-test or weight preparation)");
     *unit = (double)net->wide.prec[WIDE_E4M3].acc_unit;
+    return VBMC_OK;
+}
+
+extern "C" vbmc_status vbmc_net_prepare(vbmc_net* net, int32_t precision) {
+    if (!net) return fail(VBMC_ERR_ARG, "null argument");
+    if (precision < 0 || precision > VBMC_PREC_FP8) return fail(VBMC_ERR_ARG, "bad precision");
+    if (precision == VBMC_PREC_FP64 || precision == VBMC_PREC_FP32) return VBMC_OK;
+    const NetView& v = net->v;
+    if ((precision == VBMC_PREC_BF16 || precision == VBMC_PREC_FP16) && tc_supported(v, precision)) {
+        const vbmc_status st = tc_build(net->tc, v, net->hW, net->hb, precision);
+        return st == VBMC_OK ? VBMC_OK : fail(st, "tensor-core set-up failed");
+    }
+    if (!wide_supported(v)) return fail(VBMC_ERR_UNSUPPORTED, "no tensor-core path for this net and precision");
+    const vbmc_status st = wide_build(net->wide, v, net->hW, wide_type(precision));
+    return st == VBMC_OK ? VBMC_OK : fail(st, "wide-layer tensor set-up failed (self-test or weight preparation)");
+}
+
+extern "C" vbmc_status vbmc_tc_accumulation_unit(vbmc_net* net, int32_t precision, double* unit, double* worst) {
+    if (!net || !unit) return fail(VBMC_ERR_ARG, "null argument");
+    if (precision != VBMC_PREC_BF16 && precision != VBMC_PREC_FP16)
+        return fail(VBMC_ERR_ARG, "precision must be VBMC_PREC_BF16 or VBMC_PREC_FP16");
+    float u = 0.f;
+    double w = 0.0;
+    const vbmc_status st = tc_f16_selftest(precision == VBMC_PREC_BF16, &u, &w);
+    if (st != VBMC_OK) return fail(st, "kind::f16 accumulator self-test failed or found no usable unit");
+    *unit = (double)u;
+    if (worst) *worst = w;
     return VBMC_OK;
 }
 

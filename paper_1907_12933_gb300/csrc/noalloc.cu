@@ -76,6 +76,10 @@ __global__ void k_na_class(NetView net, QueryView* qs) {
     Q.cnt->base_margin = y[D] - mx;
 }
 
+// Write the query view into the scratch array. The view travels as a kernel
+// argument (by value), so no host buffer has to outlive the call.
+__global__ void k_na_set(const QueryView q, QueryView* d_q) { *d_q = q; }
+
 // Copy the counters the caller asked for into its buffer.
 __global__ void k_na_out(const QueryView* qs, unsigned long long* out) {
     const Counters* c = qs[0].cnt;
@@ -159,9 +163,12 @@ extern "C" vbmc_status vbmc_verify_range_fp64_noalloc(const vbmc_net* net, const
     q.ties = reinterpret_cast<unsigned long long*>(out->ties);
     q.ties_cap = out->ties_cap;
     QueryView* d_q = reinterpret_cast<QueryView*>(base + Ly.qv);
-    // the caller's result buffers start from zero on every call
-    cudaError_t e = cudaMemcpyAsync(d_q, &q, sizeof(QueryView), cudaMemcpyHostToDevice, st);
+    // coverage needs all four masks; with any missing none is written
     const bool cov = out->flip && out->flip_tie && out->ss && out->ss_tie;
+    if (!cov) q.flip = q.flip_tie = q.ss = q.ss_tie = nullptr;
+    k_na_set<<<1, 1, 0, st>>>(q, d_q);
+    // the caller's result buffers start from zero on every call
+    cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && cov) e = cudaMemsetAsync(out->flip, 0, 4ull * v.flip_words, st);
     if (e == cudaSuccess && cov) e = cudaMemsetAsync(out->flip_tie, 0, 4ull * v.flip_words, st);
     if (e == cudaSuccess && cov) e = cudaMemsetAsync(out->ss, 0, 4ull * v.ss_words, st);
@@ -169,13 +176,6 @@ extern "C" vbmc_status vbmc_verify_range_fp64_noalloc(const vbmc_net* net, const
     if (e == cudaSuccess && out->bitmap && hi > 0)
         e = cudaMemsetAsync(out->bitmap, 0, 4ull * ((hi + 31) / 32), st);
     if (e != cudaSuccess) return set_error(VBMC_ERR_CUDA, cudaGetErrorString(e));
-    if (!cov) {
-        // coverage needs all four masks; with any missing none is written
-        QueryView q2 = q;
-        q2.flip = q2.flip_tie = q2.ss = q2.ss_tie = nullptr;
-        if (cudaMemcpyAsync(d_q, &q2, sizeof(QueryView), cudaMemcpyHostToDevice, st) != cudaSuccess)
-            return set_error(VBMC_ERR_CUDA, "copy of the query view failed");
-    }
     // k_pro_init resets the counters in the scratch and validates the pixels
     launch_pro_init(v, d_q, 1, st);
     for (int l = 1; l <= v.L; ++l) launch_pro_layer(v, d_q, 1, l, st);

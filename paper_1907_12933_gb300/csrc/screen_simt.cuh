@@ -416,7 +416,7 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
                 for (int qq = 0; qq < NQ; ++qq) dus[qq] = 0.f;
                 const float* __restrict__ W1T = net.WT[1];  // [H_0][H_1]
                 for (int p = 0; p < s; ++p) {
-                    const float* wr = W1T + (size_t)Q.pix_in[p] * H1;
+                    const float* wr = W1T + (size_t)Q.pix[p] * H1;  // validated by the prologue
                     const float c = S.cpx[m][p];
 #pragma unroll
                     for (int qq = 0; qq < NQ; ++qq) {

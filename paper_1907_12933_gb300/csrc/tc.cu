@@ -38,6 +38,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 namespace vbmc {
@@ -290,7 +291,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
         const int hf = wid >> 2;             // column half in the drain phases
         const int H0 = net.dims[0], H1 = net.dims[1];
         uint32_t ait = 0, dit = 0;
-        const float uacc_base = 0x1p-22f * (SPLIT ? 3.f : 1.f);
+        const float uacc_base = P.acc_unit * (SPLIT ? 3.f : 1.f);  // measured by tc_f16_selftest
         (void)H0;
         for (unsigned long long g = blockIdx.x; g < ntiles; g += gridDim.x) {
             if (*abortp) break;
@@ -392,7 +393,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 ri.w = ok;
                 S.rinfo[r] = ri;
             } else if (wtid >= MROWS + 64 && wtid - (MROWS + 64) < s) {
-                S.pixs[wtid - (MROWS + 64)] = Q.pix_in[wtid - (MROWS + 64)];
+                S.pixs[wtid - (MROWS + 64)] = Q.pix[wtid - (MROWS + 64)];  // validated by the prologue
             } else if (wtid - MROWS < np) {  // digits of outer prefix slot k
                 const int k = wtid - MROWS;
                 int dd[kMaxS];
@@ -933,7 +934,7 @@ __global__ void k_classes_tc(const __grid_constant__ TcParams P, NetView net, Qu
         const int K = ly.K, N = ly.N;
         const double Rmax = uq * Nmax + sqrt((double)K) * 0x1p-25;
         const double Lmax = uq * Nmax;
-        const double u1 = K * 0x1p-22, u3 = 3.0 * K * 0x1p-22;
+        const double u1 = K * (double)P.acc_unit, u3 = 3.0 * K * (double)P.acc_unit;
         const double Pa1 = Rmax + Emax + u1 * (Nmax + Rmax);
         const double Pa3 = Rmax + Emax + 0x1p-7 * Lmax + u3 * (Nmax + Rmax + 2.0 * Lmax);
         const double Pb = Nmax + Emax;
@@ -967,6 +968,78 @@ __global__ void k_classes_tc(const __grid_constant__ TcParams P, NetView net, Qu
     }
 }
 
+// ------------------------------------------------ kind::f16 accumulator probe
+//
+// One 128 x 128 tile with K = 256 (four 64-column chunks, the tensor screen's
+// K-major 128-byte-swizzle layout) through TMA, tcgen05.mma kind::f16 and
+// tcgen05.ld, exactly as the screen issues them. The host compares every output
+// with its exact value (see tc_f16_selftest).
+constexpr int ST_DIM = 128, ST_KCH = 4;
+
+__global__ void __launch_bounds__(128, 1)
+k_tc_selftest(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int bf,
+              float* out, int* status) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* base = smem_raw + ((1024u - (tc::smem_u32(smem_raw) & 1023u)) & 1023u);
+    uint8_t* sa = base;                            // ST_KCH chunks of 128 rows x 128 bytes
+    uint8_t* sb = base + ST_KCH * ST_DIM * 128;
+    __shared__ unsigned long long bars[2];
+    __shared__ uint32_t slot;
+    __shared__ int abort_flag;
+    const int warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(tc::smem_u32(&bars[0]), 1);
+        tc::mbar_init(tc::smem_u32(&bars[1]), 1);
+        abort_flag = 0;
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tc::smem_u32(&slot), ST_DIM);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = slot;
+    if (threadIdx.x == 0) {
+        tc::mbar_expect_tx(tc::smem_u32(&bars[0]), (uint32_t)(2 * ST_KCH * ST_DIM * 128));
+        for (int c = 0; c < ST_KCH; ++c) {
+            tc::tma_load_2d(tc::smem_u32(sa + c * ST_DIM * 128), &ta, 64 * c, 0, tc::smem_u32(&bars[0]));
+            tc::tma_load_2d(tc::smem_u32(sb + c * ST_DIM * 128), &tb, 64 * c, 0, tc::smem_u32(&bars[0]));
+        }
+        bool ok = tc::mbar_wait(tc::smem_u32(&bars[0]), 0, &abort_flag);
+        if (ok) {
+            tc::tc_fence_after();
+            const uint32_t idesc = tc::idesc_f16(ST_DIM, ST_DIM, bf != 0);
+            for (int c = 0; c < ST_KCH; ++c)
+                for (int ks = 0; ks < 4; ++ks)
+                    tc::mma_f16(tmem, tc::desc_sw128(tc::smem_u32(sa + c * ST_DIM * 128) + ks * 32),
+                                tc::desc_sw128(tc::smem_u32(sb + c * ST_DIM * 128) + ks * 32), idesc,
+                                (c | ks) != 0);
+        }
+        // the commit also covers the case where nothing was issued
+        tc::mma_commit(tc::smem_u32(&bars[1]));
+        if (!tc::mbar_wait(tc::smem_u32(&bars[1]), 0, &abort_flag)) ok = false;
+        if (!ok) atomicExch(status, 2);
+    }
+    __syncthreads();
+    tc::tc_fence_after();
+    if (!abort_flag) {
+        const int lane = threadIdx.x & 31;
+        for (int c = 0; c < ST_DIM; c += 32) {
+            float v[32];
+            tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
+            for (int e = 0; e < 32; ++e) out[(size_t)(32 * warp + lane) * ST_DIM + c + e] = v[e];
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, ST_DIM);
+    }
+}
+
 // ------------------------------------------------------- host-side set-up
 
 float up_f(double x) {
@@ -982,6 +1055,182 @@ float q16(float x) {
 }
 
 }  // namespace
+
+// The kind::f16 accumulator self-test (BF16 or FP16 operands, FP32 accumulate).
+// The screens' bounds take the accumulation error of a K-term MMA dot product
+// as at most K u sum_k |a_k b_k| with u = 2^-22 (an FP32 accumulator, whatever
+// the order of its additions). The PTX ISA does not specify how the MMA rounds
+// its partial sums, so the unit is measured here on the operand layout the
+// screen uses, K = 256 over four K chunks:
+//   - rows and columns 0..95: integers in [-2, 2]; products and sums are exact
+//     in any accumulator, so a wrong value means a wrong layout (unsupported);
+//   - five probe outputs whose exact sums need 17 to 24 significand bits (one
+//     large product and 255 small ones of the same or the opposite sign, the
+//     large one first or in the third chunk): exact in an FP32 accumulator,
+//     so a short accumulator or one that truncates the small terms fails them;
+//   - every other output (random operands m 2^e, 8-bit m, |value| in [2^-14, 4), random
+//     signs, against the integer and probe rows and columns) must lie within
+//     the model K 2^-22 sum |products| of its FP64 value.
+// *unit = 2^-22 when all of these hold; 2^-13 when only the integers are exact
+// and every output lies within K 2^-13 sum |products|; otherwise the screens are
+// unsupported on this device. *worst = the largest |error| / (K sum |products|)
+// seen over the tile (0 when every output is exact). The result is kept per
+// device and operand type.
+vbmc_status tc_f16_selftest(bool bf, float* unit, double* worst) {
+    static std::mutex mu;
+    static int done[64][2] = {};
+    static float units[64][2];
+    static double worsts[64][2];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return VBMC_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(mu);
+    const int ti = bf ? 0 : 1;
+    if (done[dev][ti]) {
+        *unit = units[dev][ti];
+        if (worst) *worst = worsts[dev][ti];
+        return VBMC_OK;
+    }
+    constexpr int Kt = 64 * ST_KCH;
+    std::vector<uint16_t> ha((size_t)ST_DIM * Kt), hb((size_t)ST_DIM * Kt);
+    std::vector<double> va(ha.size()), vb(hb.size());
+    auto bits = [&](double x) -> uint16_t {
+        const float f = (float)x;
+        if (bf) {
+            __nv_bfloat16 h = __float2bfloat16_rn(f);
+            return *reinterpret_cast<uint16_t*>(&h);
+        }
+        __half h = __float2half_rn(f);
+        return *reinterpret_cast<uint16_t*>(&h);
+    };
+    auto put = [&](std::vector<uint16_t>& h, std::vector<double>& v, int r, int k, double x) {
+        h[(size_t)r * Kt + k] = bits(x);
+        v[(size_t)r * Kt + k] = x;  // every value below is exact in both formats
+    };
+    uint64_t z = 0x243F6A8885A308D3ull;  // SplitMix64 stream for the random operands
+    auto rnd = [&]() {
+        z += 0x9E3779B97F4A7C15ull;
+        uint64_t x = z;
+        x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+        x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+        return x ^ (x >> 31);
+    };
+    auto random_value = [&]() {
+        const uint64_t r = rnd();
+        const double m = (double)(128 + (r & 127));      // 8 significand bits
+        const int e = (int)((r >> 8) % 16) - 21;          // m 2^e in [2^-14, 2^2): normal in FP16
+        return ((r >> 20) & 1 ? -1.0 : 1.0) * std::ldexp(m, e);
+    };
+    for (int r = 0; r < ST_DIM; ++r)
+        for (int k = 0; k < Kt; ++k) {
+            if (r < 96) {
+                put(ha, va, r, k, (double)((int)((r * 7 + k * 3 + 1) % 5) - 2));
+                put(hb, vb, r, k, (double)((int)((r * 11 + k * 5 + 2) % 5) - 2));
+            } else {
+                put(ha, va, r, k, random_value());
+                put(hb, vb, r, k, random_value());
+            }
+        }
+    // probe rows r of A and B: products p_0 = a0 b0 at position k0, and 255 small
+    // products q = as bs; the exact sums fit 24 significand bits
+    struct Probe { int r, k0; double a0, b0, as, bs; };
+    const Probe probes[5] = {
+        {127, 0, 1.0, 1.0, 0x1p-12, 0x1p-11},      // 1 + 255 2^-23
+        {126, 0, 16.0, 16.0, 0x1p-8, 0x1p-7},      // 256 + 255 2^-15
+        {125, 0, -1.0, 1.0, 0x1p-12, 0x1p-11},     // -1 + 255 2^-23
+        {124, 128, 1.0, 1.0, 0x1p-12, 0x1p-11},    // 128 2^-23, then 1, then 127 2^-23
+        {123, 0, 4.0, 2.0, 0x1p-10, 0x1p-11},      // 8 + 255 2^-21
+    };
+    for (const Probe& p : probes)
+        for (int k = 0; k < Kt; ++k) {
+            put(ha, va, p.r, k, k == p.k0 ? p.a0 : p.as);
+            put(hb, vb, p.r, k, k == p.k0 ? p.b0 : p.bs);
+        }
+    void *da = nullptr, *db = nullptr;
+    float* dout = nullptr;
+    int* dst = nullptr;
+    vbmc_status res = VBMC_ERR_CUDA;
+    std::vector<float> got((size_t)ST_DIM * ST_DIM);
+    int status = 0;
+    PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    cudaDriverEntryPointQueryResult qr;
+    CUtensorMap ta, tb;
+    const CUtensorMapDataType dt = bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    cuuint64_t gdim[2] = {(cuuint64_t)Kt, (cuuint64_t)ST_DIM};
+    cuuint64_t gstr[1] = {(cuuint64_t)Kt * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)ST_DIM};
+    cuuint32_t estr[2] = {1, 1};
+    const size_t smem = (size_t)2 * ST_KCH * ST_DIM * 128 + 1024;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&encode, 12000, cudaEnableDefault,
+                                         &qr) != cudaSuccess || !encode)
+        goto done;
+    if (cudaMalloc(&da, 2 * ha.size()) != cudaSuccess || cudaMalloc(&db, 2 * hb.size()) != cudaSuccess ||
+        cudaMalloc(&dout, sizeof(float) * got.size()) != cudaSuccess || cudaMalloc(&dst, sizeof(int)) != cudaSuccess)
+        goto done;
+    if (cudaMemcpy(da, ha.data(), 2 * ha.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(db, hb.data(), 2 * hb.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(dst, 0, sizeof(int)) != cudaSuccess)
+        goto done;
+    if (encode(&ta, dt, 2, da, gdim, gstr, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+        encode(&tb, dt, 2, db, gdim, gstr, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        goto done;
+    cudaFuncSetAttribute(k_tc_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_tc_selftest<<<1, 128, smem>>>(ta, tb, bf ? 1 : 0, dout, dst);
+    if (cudaDeviceSynchronize() != cudaSuccess) goto done;
+    if (cudaMemcpy(got.data(), dout, sizeof(float) * got.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&status, dst, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        goto done;
+    if (status != 0) {
+        res = VBMC_ERR_DEVICE;
+        goto done;
+    }
+    {
+        bool layout_ok = true, probes_exact = true;
+        double w = 0.0;
+        for (int r = 0; r < ST_DIM; ++r)
+            for (int n = 0; n < ST_DIM; ++n) {
+                double ex = 0.0, mag = 0.0;
+                for (int k = 0; k < Kt; ++k) {
+                    const double p = va[(size_t)r * Kt + k] * vb[(size_t)n * Kt + k];
+                    ex += p;  // products of 8- and 11-bit values: exact, sums within FP64
+                    mag += std::fabs(p);
+                }
+                const double g = (double)got[(size_t)r * ST_DIM + n];
+                const double err = std::fabs(g - ex);
+                if (r < 96 && n < 96) {
+                    if (err != 0.0) layout_ok = false;
+                    continue;
+                }
+                if (r == n && r >= 123 && err != 0.0) probes_exact = false;
+                if (mag > 0.0) w = std::max(w, err / ((double)Kt * mag));
+                else if (err != 0.0) w = INFINITY;
+            }
+        if (!layout_ok) {
+            res = VBMC_ERR_UNSUPPORTED;
+            goto done;
+        }
+        float u = 0.f;
+        if (probes_exact && w <= 0x1p-22) u = 0x1p-22f;
+        else if (w <= 0x1p-13) u = 0x1p-13f;
+        if (u == 0.f) {
+            res = VBMC_ERR_UNSUPPORTED;
+            goto done;
+        }
+        units[dev][ti] = u;
+        worsts[dev][ti] = w;
+        done[dev][ti] = 1;
+        *unit = u;
+        if (worst) *worst = w;
+        res = VBMC_OK;
+    }
+done:
+    cudaFree(da);
+    cudaFree(db);
+    cudaFree(dout);
+    cudaFree(dst);
+    return res;
+}
 
 bool tc_supported(const NetView& v, int precision) {
     if (precision != VBMC_PREC_BF16 && precision != VBMC_PREC_FP16) return false;
@@ -1009,6 +1258,10 @@ static vbmc_status build_prec(TcNet& tc, const NetView& v, const std::vector<std
     (void)cudaGetLastError();  // start from a clean error state
     P.L = v.L;
     P.bf16 = BF ? 1 : 0;
+    {
+        const vbmc_status ss = tc_f16_selftest(BF, &P.acc_unit, nullptr);
+        if (ss != VBMC_OK) return ss;
+    }
     PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     cudaDriverEntryPointQueryResult qr;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", (void**)&encode, 12000,

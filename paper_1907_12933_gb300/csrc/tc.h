@@ -31,6 +31,7 @@ struct TcParams {
     const float* pair;             // [H_L][H_L][5]: output-layer pair constants
     int L;
     int bf16;                      // 1: bf16 operands, 0: fp16
+    float acc_unit;                // MMA accumulation error per product (tc_f16_selftest)
 };
 
 struct TcPrec {
@@ -45,6 +46,9 @@ struct TcNet {
 };
 
 bool tc_supported(const NetView& v, int precision);
+// Measures the kind::f16 MMA accumulation unit on this device (see tc.cu):
+// 2^-22 (the FP32 model) or 2^-13; VBMC_ERR_UNSUPPORTED when neither holds.
+vbmc_status tc_f16_selftest(bool bf16, float* unit, double* worst);
 vbmc_status tc_build(TcNet& tc, const NetView& v, const std::vector<std::vector<float>>& W,
                      const std::vector<std::vector<float>>& b, int precision);
 void tc_free(TcNet& tc);

@@ -32,6 +32,7 @@
 #include "launch.h"
 #include "tc_ptx.cuh"
 #include "wide.h"
+#include "tc.h"
 
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -897,7 +898,11 @@ vbmc_status wide_build(WideNet& wn, const NetView& v, const std::vector<std::vec
         if (st != VBMC_OK) return st;
         P.acc_unit = fp32_acc ? kWideAccFp32 : kWideAccShort;
     } else {
-        P.acc_unit = kWideAccFp32;
+        // BF16 / FP16: the kind::f16 accumulator probe of the fused screen
+        float u = 0.f;
+        const vbmc_status st = tc_f16_selftest(type == WIDE_BF16, &u, nullptr);
+        if (st != VBMC_OK) return st;
+        P.acc_unit = u;
     }
     const int eb = type == WIDE_E4M3 ? 1 : 2;
     for (int l = 2; l < v.L; ++l) {
@@ -973,13 +978,9 @@ void wide_free(WideNet& wn) {
     for (auto& p : wn.prec) p.ready = false;
 }
 
-vbmc_status wide_work_alloc(WideWork& w, const NetView& v) {
+vbmc_status wide_work_alloc(WideWork& w, const NetView& v, unsigned long long chunk) {
     if (w.chunk) return VBMC_OK;
-    unsigned long long chunk = W_CHUNK;
-    if (const char* env = std::getenv("VBMC_WIDE_CHUNK")) {
-        const unsigned long long c = std::strtoull(env, nullptr, 10);
-        if (c >= 128) chunk = c;
-    }
+    if (chunk == 0) chunk = W_CHUNK;
     chunk = (chunk + 127) & ~127ull;
     int kmax = 0;
     for (int l = 1; l < v.L; ++l) kmax = std::max(kmax, v.dims[l]);

@@ -15,7 +15,8 @@ enum { WIDE_E4M3 = 0, WIDE_BF16 = 1, WIDE_FP16 = 2, WIDE_NTYPES = 3 };
 constexpr int kWideFcap = 4;  // sign changes kept per point and layer (SS-Cover needs one)
 constexpr int kWideOut = 32;  // classes (output width) the path supports
 // Accumulation error per product of the tensor-core MMA, relative to sum
-// |products|. The 16-bit kinds take the FP32 model 2^-22. FP8 tensor-core
+// |products|. The 16-bit kinds take the unit their set-up probe measures
+// (tc_f16_selftest: 2^-22, the FP32 model, when exact). FP8 tensor-core
 // accumulators have been reported to keep fewer bits than FP32 on earlier
 // parts: the E4M3 set-up self-test adds probe sums whose exact values need 18
 // to 23 significand bits, and the bound takes 2^-22 only when the MMA returns
@@ -71,7 +72,8 @@ int wide_type(int precision);
 bool wide_supported(const NetView& v);
 vbmc_status wide_build(WideNet& wn, const NetView& v, const std::vector<std::vector<float>>& W, int type);
 void wide_free(WideNet& wn);
-vbmc_status wide_work_alloc(WideWork& w, const NetView& v);
+// Workspace for chunks of `chunk` points (0: the default 2^20), rounded up to 128.
+vbmc_status wide_work_alloc(WideWork& w, const NetView& v, unsigned long long chunk);
 void wide_work_free(WideWork& w);
 
 // Diagnostic: while set, the first chunk of a wide-path run copies each hidden

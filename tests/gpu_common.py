@@ -6,12 +6,12 @@ import oracle
 
 
 def run_gpu(vb, net_dict, q, precision, lo=0, hi=0, coverage=True, bitmap=True, queue_cap=None,
-            vbnet=None):
+            vbnet=None, wide_chunk=0):
     s, k = len(q["pixels"]), int(q["k"])
     n = oracle.space_size(s, k)
     net = vbnet or vb.Net(net_dict)
     res = vb.Result(net, max_points=n if bitmap else 0, max_s=max(1, s), max_k=max(1, k),
-                    ties_cap=1 << 16, queue_cap=queue_cap or max(4096, n))
+                    ties_cap=1 << 16, queue_cap=queue_cap or max(4096, n), wide_chunk=wide_chunk)
     summ = vb.verify_query(net, res, q["image"], q["pixels"], k, lo=lo, hi=hi,
                            precision=precision, coverage=coverage, bitmap=bitmap)
     out = {"summary": summ, "n": n}

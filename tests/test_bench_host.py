@@ -33,7 +33,7 @@ def test_pass_rooflines_bf16():
     alu = 152 * 128 * 2 * 2000.0e6 / 1e12  # 77.824 TFLOP/s
     exp = {
         "screen (first pass over every point)": (fpp * n, 20.0, 2000.0),
-        "split tensor pass": (3 * fpp * 3_000_000, 10.0, 2000.0),
+        "split tensor pass": (fpp * 3_000_000, 10.0, 2000.0),
         "FP32 pass": (fpp * 1_000_000, 25.0, alu),
         "double-float pass": (fpp * 40_000, 5.0, alu * 2 / 11),
         "FP64 pass": (fpp * 50, 0.5, 1.25),
@@ -44,6 +44,10 @@ def test_pass_rooflines_bf16():
         assert p["achieved"] == pytest.approx(flops / (ms / 1e3) / 1e12)
         assert p["peak"] == pytest.approx(peak)
         assert p["frac"] == pytest.approx(p["achieved"] / peak)
+    # the split pass: one evaluation per point is the method's work; its three
+    # products per layer are reported as hardware work beside it
+    assert by["split tensor pass"]["hardware_flops_per_launch"] == 3 * fpp * 3_000_000
+    assert "hardware_flops_per_launch" not in by["FP32 pass"]
     assert by["screen (first pass over every point)"]["traffic"] == 1000
     assert by["FP32 pass"]["traffic"] == 7 and by["split tensor pass"]["traffic"] is None
     # the top-level fields are those of the longest pass (the FP32 pass here)
@@ -99,3 +103,16 @@ def test_profiled_traffic_is_keyed_by_the_bench_configuration():
         assert set(per_pass) <= {"screen (first pass over every point)", "split tensor pass", "FP32 pass",
                                  "double-float pass", "FP64 pass"}
         assert all(isinstance(v, int) and v > 0 for v in per_pass.values())
+
+
+def test_reference_arm_times_each_step_on_its_own_sample(monkeypatch):
+    """--impl reference: K timed steps, each one contiguous sample of the query;
+    ms_per_step is those steps' mean time and the rate counts only their points."""
+    import synth
+    w = synth.workload("mlp25_sigmoid_s5k8", s=3, k=4)
+    rate, ms_step, m, cores, sample = bench.oracle_steps(w["net"], w["query"], steps=3, warmup=1,
+                                                        seconds_total=0.3)
+    n = 9 ** 3
+    assert 1 <= m <= n and cores >= 1
+    assert rate == pytest.approx(m / (ms_step / 1e3), rel=1e-9)
+    assert sample.startswith(f"3 steps of {m} contiguous points")

@@ -25,6 +25,21 @@ def vb():
     return m
 
 
+@pytest.mark.parametrize("prec", TC)
+def test_kind_f16_accumulation_unit(vb, prec):
+    """The set-up probe of the kind::f16 MMA (integer tiles, probe sums needing up
+    to 24 significand bits, random operands against the model) picks the unit the
+    screens' bounds use. On a GB300 the probe sums come back exact and every
+    random output lies within the FP32 model, so the unit is 2^-22."""
+    w = synth.workload("mlp784x512x512_relu_s6k7", s=1, k=1)
+    vnet = vb.Net(w["net"])
+    u, worst = vb.tc_accumulation_unit(vnet, prec)
+    print(prec, "accumulation unit", u, "worst |err| / (K sum|p|)", worst)
+    assert u == 2.0 ** -22, (u, worst)
+    assert 0.0 <= worst <= u
+    vnet.free()
+
+
 def active_tc_case(seed=142, k=25):
     """16-64-64-8 ReLU, three pixels: sign changes in every layer, SS pairs and
     adversarial points (seed 142 picked for that); 132,651 points."""

@@ -4,7 +4,6 @@ fused 16-bit screen does not fit, against the FP64 oracle through the C ABI:
 small boxes element by element, several chunks with ragged tails, a net whose
 signs change (coverage and SS-Cover), agreement with the FP32 path, and the
 full-size 784-1024-1024-1024-10 workload on sampled points."""
-import os
 
 import numpy as np
 import pytest
@@ -26,16 +25,9 @@ def vb():
     return m
 
 
-@pytest.fixture
-def small_chunks():
-    """FP8 chunk of 384 points (three 128-point tiles): many chunks, ragged tails."""
-    old = os.environ.get("VBMC_WIDE_CHUNK")
-    os.environ["VBMC_WIDE_CHUNK"] = "384"
-    yield
-    if old is None:
-        del os.environ["VBMC_WIDE_CHUNK"]
-    else:
-        os.environ["VBMC_WIDE_CHUNK"] = old
+# chunks of 384 points (three 128-point tiles; caps.wide_chunk of the result):
+# many chunks, ragged tails
+SMALL_CHUNK = 384
 
 
 def test_accumulation_model(vb):
@@ -68,18 +60,18 @@ def test_config3_small_box(vb, prec):
 
 
 @pytest.mark.parametrize("prec", WIDE)
-def test_config3_many_chunks(vb, small_chunks, prec):
+def test_config3_many_chunks(vb, prec):
     """s = 3, k = 6 (2197 points in chunks of 384) and a sub-range that starts
     and ends inside chunks."""
     w = synth.workload("mlp784x1024x3_relu_s5k15", s=3, k=6)
     net, q = w["net"], w["query"]
-    compare(run_gpu(vb, net, q, prec), oracle.verify(net, q), net, q)
-    g = run_gpu(vb, net, q, prec, lo=100, hi=2000)
+    compare(run_gpu(vb, net, q, prec, wide_chunk=SMALL_CHUNK), oracle.verify(net, q), net, q)
+    g = run_gpu(vb, net, q, prec, lo=100, hi=2000, wide_chunk=SMALL_CHUNK)
     compare(g, oracle.verify(net, q, lo=100, hi=2000), net, q)
 
 
 @pytest.mark.parametrize("prec", WIDE)
-def test_active_net_coverage(vb, small_chunks, prec):
+def test_active_net_coverage(vb, prec):
     """32-256-512-256-6 ReLU net (seed 94: the smallest base margin of seeds
     70..109), 3 pixels moved by up to 40 grey levels (531,441 points): sign
     changes, SS-Cover pairs and 104,011 adversarial points."""
@@ -87,7 +79,7 @@ def test_active_net_coverage(vb, small_chunks, prec):
     q = synth.make_query(94, 0, 32, 3, 40)
     o = oracle.verify(net, q)
     assert o["flip"].any() and o["ss"].any() and o["n_adv"] > 0
-    g = run_gpu(vb, net, q, prec)
+    g = run_gpu(vb, net, q, prec, wide_chunk=SMALL_CHUNK)
     compare(g, o, net, q)
 
 
