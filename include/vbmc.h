@@ -383,9 +383,11 @@ vbmc_status vbmc_fp8_accumulation_unit(vbmc_net *net, double *unit);
  * K u sum |products|. *unit = 2^-22 (the FP32 model) when the probes are exact
  * and every output lies within the model at that unit, 2^-13 when only the
  * looser model holds. *worst (may be NULL) = the largest observed
- * |error| / (K sum |products|) over the test tile. Does not need the net's
- * weights; the result is kept per device and type. */
-vbmc_status vbmc_tc_accumulation_unit(vbmc_net *net, int32_t precision, double *unit, double *worst);
+ * |error| / (K sum |products|) over the test tile; *probes_failed (may be
+ * NULL) = bit i set when probe i did not come back exact. Does not need the
+ * net's weights; the result is kept per device and type. */
+vbmc_status vbmc_tc_accumulation_unit(vbmc_net *net, int32_t precision, double *unit, double *worst,
+                                      int32_t *probes_failed);
 
 /* ---- k-shell order: the shells r = 0, 1, ..., k (points whose largest step
  * is exactly r, checked as the box of radius r restricted to its boundary)

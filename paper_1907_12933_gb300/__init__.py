@@ -156,7 +156,8 @@ def lib():
             "vbmc_shell_search": [vp, C.POINTER(_Query), C.POINTER(_Options), vp, C.POINTER(_ShellOut), vp],
             "vbmc_autotune": [vp, C.c_char_p, C.POINTER(_Tuning)],
             "vbmc_fp8_accumulation_unit": [vp, C.POINTER(C.c_double)],
-            "vbmc_tc_accumulation_unit": [vp, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+            "vbmc_tc_accumulation_unit": [vp, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                          C.POINTER(C.c_int32)],
             "vbmc_pair_coverage": [vp, vp, vp, C.c_int32, C.POINTER(_CoverParams),
                                    C.POINTER(_PairMasks), vp],
             "vbmc_covered_fraction": [vp, C.c_int32, C.POINTER(C.c_uint32), C.POINTER(C.c_double)],
@@ -422,11 +423,13 @@ def net_prepare(net: Net, precision: str) -> None:
     _check(lib().vbmc_net_prepare(net.h, PRECISIONS[precision]))
 
 
-def tc_accumulation_unit(net: Net, precision: str = "bf16") -> tuple[float, float]:
-    """vbmc_tc_accumulation_unit: (unit, worst) of the kind::f16 accumulator self-test."""
-    u, w = C.c_double(), C.c_double()
-    _check(lib().vbmc_tc_accumulation_unit(net.h, PRECISIONS[precision], C.byref(u), C.byref(w)))
-    return u.value, w.value
+def tc_accumulation_unit(net: Net, precision: str = "bf16") -> tuple[float, float, int]:
+    """vbmc_tc_accumulation_unit: (unit, worst, probes_failed) of the kind::f16
+    accumulator self-test."""
+    u, w, f = C.c_double(), C.c_double(), C.c_int32()
+    _check(lib().vbmc_tc_accumulation_unit(net.h, PRECISIONS[precision], C.byref(u), C.byref(w),
+                                           C.byref(f)))
+    return u.value, w.value, f.value
 
 
 def autotune(net: Net, cache_path: str | None = None) -> dict:

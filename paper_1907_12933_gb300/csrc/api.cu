@@ -116,6 +116,8 @@ struct vbmc_result {
     double* d_margin = nullptr;
     WideWork ww{};  // chunk workspace of the wide-layer path (caps.wide_chunk; allocated at creation)
     unsigned long long* d_tiles = nullptr;  // VBMC_MAX_TILES counters of vbmc_tile_counts
+    TcQueryWork tw{};  // compacted operands of the fused tensor screen (single-query calls)
+    bool have_tw = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_pro = nullptr, ev_scr = nullptr;
     cudaEvent_t ev_split = nullptr, ev_f32 = nullptr, ev_df = nullptr;  // after each recheck pass
     cudaStream_t last_stream = nullptr;
@@ -343,6 +345,14 @@ vbmc_status create_result(const vbmc_net* net, const vbmc_caps* caps, BatchArena
     r->caps.queue_cap = qc;
     for (int i = 0; i < 4; ++i) A(&r->d_queue[i], (size_t)qc);
     A(&r->d_tiles, (size_t)VBMC_MAX_TILES);
+    // compacted columns of the fused tensor screen (calls with one query)
+    const bool fused = !arena && (tc_supported(v, VBMC_PREC_BF16) || tc_supported(v, VBMC_PREC_FP16));
+    if (fused) {
+        A(&q.perm, T);
+        A(&q.kc, (size_t)2 * (kMaxL + 1));
+        A(&q.tabc, (size_t)S * RM * v.dims[1]);
+        A(&q.w1c, (size_t)kMaxS * v.dims[1]);
+    }
     if (e == cudaSuccess) e = cudaMallocHost((void**)&r->h_cnt, sizeof(Counters));
     if (e == cudaSuccess) e = cudaEventCreate(&r->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&r->ev1);
@@ -354,6 +364,14 @@ vbmc_status create_result(const vbmc_net* net, const vbmc_caps* caps, BatchArena
     if (e != cudaSuccess) {
         vbmc_result_free(r);
         return fail(VBMC_ERR_OOM, std::string("result_create: ") + cudaGetErrorString(e));
+    }
+    if (fused) {
+        const vbmc_status ts = tc_query_work_alloc(r->tw, v);
+        if (ts != VBMC_OK) {
+            vbmc_result_free(r);
+            return fail(ts, "result_create: compacted tensor-screen weights");
+        }
+        r->have_tw = true;
     }
     // the wide-layer tensor path's chunk workspace: sized here so that verify
     // calls allocate nothing (batch members: only when asked for explicitly)
@@ -440,6 +458,7 @@ extern "C" vbmc_status vbmc_result_free(vbmc_result* r) {
     if (r->pending && r->last_stream) cudaStreamSynchronize(r->last_stream);
     for (void* p : r->owned) cudaFree(p);
     wide_work_free(r->ww);
+    tc_query_work_free(r->tw);
     arena_release(r->arena);
     if (r->h_cnt) cudaFreeHost(r->h_cnt);
     if (r->ev0) cudaEventDestroy(r->ev0);
@@ -506,7 +525,8 @@ vbmc_status enqueue_passes(vbmc_net* net, QueryView* d_qs, const QueryView* hq, 
                            unsigned long long* d_qcount, QEntry* const* d_queue,
                            unsigned long long cap, const cudaEvent_t* ev, const vbmc_options& opt,
                            cudaStream_t st, bool capturing = false, int stages = STAGE_ALL,
-                           WideWork* ww = nullptr) {
+                           WideWork* ww = nullptr, TcQueryWork* tw = nullptr) {
+    if (nq != 1) tw = nullptr;  // compacted columns are per query: single-query calls only
     const NetView& v = net->v;
     // inside a stream capture an event record must be an explicit graph node
     const unsigned evflag = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
@@ -544,7 +564,7 @@ vbmc_status enqueue_passes(vbmc_net* net, QueryView* d_qs, const QueryView* hq, 
             return fail(VBMC_ERR_UNSUPPORTED, "tensor-core screen does not support this net/precision");
         vbmc_status sst = tc_build(net->tc, v, net->hW, net->hb, opt.precision);
         if (sst != VBMC_OK) return fail(sst, "tensor-core set-up failed");
-        if (stages & STAGE_SETUP) tc_launch_query_setup(net->tc, v, d_qs, nq, opt.precision, st);
+        if (stages & STAGE_SETUP) tc_launch_query_setup(net->tc, v, d_qs, nq, opt.precision, st, tw);
     }
     if (!(stages & STAGE_PASSES)) return VBMC_OK;
     // queue levels: 0 tensor split pass, 1 FP32 pass, 2 double-float pass, 3 FP64 pass
@@ -582,12 +602,12 @@ vbmc_status enqueue_passes(vbmc_net* net, QueryView* d_qs, const QueryView* hq, 
         } else {
             // one query: screen -> split tensor pass -> FP32; many: screen -> FP32 directly
             vbmc_status sst = tc_launch_screen(net->tc, v, d_qs, nq, d_tp, ntiles, opt.precision,
-                                   nq == 1 ? qsplit : q32, nq == 1 ? 0 : 1, net->n_sm, st);
+                                   nq == 1 ? qsplit : q32, nq == 1 ? 0 : 1, net->n_sm, st, tw);
             if (sst != VBMC_OK) return fail(sst, "tensor-core screen launch failed");
             VB_CUDA(record(ev[2]));
             if (nq == 1) {
                 sst = tc_launch_gather(net->tc, v, d_qs, d_queue[0], d_qcount + 0, cap, opt.precision,
-                                       q32, net->n_sm, st);
+                                       q32, net->n_sm, st, tw);
                 if (sst != VBMC_OK) return fail(sst, "tensor-core split pass launch failed");
             }
             VB_CUDA(record(ev[4]));
@@ -663,7 +683,7 @@ vbmc_status enqueue(vbmc_net* net, vbmc_result* r, const uint8_t* d_image, const
     const cudaEvent_t ev[7] = {r->ev0, r->ev_pro, r->ev_scr, r->ev1, r->ev_split, r->ev_f32, r->ev_df};
     vbmc_status sst = enqueue_passes(net, r->d_q, &q, 1, r->d_tp, tp[1], r->d_qcount, r->d_queue,
                                      std::max<uint64_t>(1, r->caps.queue_cap), ev, opt, st, false, STAGE_ALL,
-                                     &r->ww);
+                                     &r->ww, r->have_tw ? &r->tw : nullptr);
     if (sst != VBMC_OK) return sst;
     VB_CUDA(cudaMemcpyAsync(r->h_cnt, r->d_cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
     r->last_stream = st;
@@ -1218,7 +1238,7 @@ extern "C" vbmc_status vbmc_search_query(vbmc_net* net, const vbmc_query* q, int
     const cudaEvent_t ev_set[7] = {res->ev0,    res->ev_pro, res->ev_pro, res->ev_pro,
                                    res->ev_pro, res->ev_pro, res->ev_pro};
     st = enqueue_passes(net, res->d_q, &qv, 1, res->d_tp, tp[1], res->d_qcount, res->d_queue, cap, ev_set,
-                        *opt, sq, false, STAGE_SETUP, &res->ww);
+                        *opt, sq, false, STAGE_SETUP, &res->ww, res->have_tw ? &res->tw : nullptr);
     if (st != VBMC_OK) return st;
     const cudaEvent_t ev_tile[7] = {res->ev_scr, res->ev_scr, res->ev_scr, res->ev1,
                                     res->ev_scr, res->ev_scr, res->ev_scr};
@@ -1238,7 +1258,7 @@ extern "C" vbmc_status vbmc_search_query(vbmc_net* net, const vbmc_query* q, int
         VB_CUDA(cudaMemcpyAsync(res->d_tp, tp.data(), sizeof(unsigned long long) * 2, cudaMemcpyHostToDevice,
                                 sq));
         st = enqueue_passes(net, res->d_q, &qv, 1, res->d_tp, tp[1], res->d_qcount, res->d_queue, cap, ev_tile,
-                            *opt, sq, false, STAGE_PASSES, &res->ww);
+                            *opt, sq, false, STAGE_PASSES, &res->ww, res->have_tw ? &res->tw : nullptr);
         if (st != VBMC_OK) return st;
         any_tile = true;
         VB_CUDA(cudaMemcpyAsync(res->h_cnt, res->d_cnt, sizeof(Counters), cudaMemcpyDeviceToHost, sq));
@@ -1556,16 +1576,19 @@ extern "C" vbmc_status vbmc_net_prepare(vbmc_net* net, int32_t precision) {
     return st == VBMC_OK ? VBMC_OK : fail(st, "wide-layer tensor set-up failed (self-test or weight preparation)");
 }
 
-extern "C" vbmc_status vbmc_tc_accumulation_unit(vbmc_net* net, int32_t precision, double* unit, double* worst) {
+extern "C" vbmc_status vbmc_tc_accumulation_unit(vbmc_net* net, int32_t precision, double* unit, double* worst,
+                                                  int32_t* probes_failed) {
     if (!net || !unit) return fail(VBMC_ERR_ARG, "null argument");
     if (precision != VBMC_PREC_BF16 && precision != VBMC_PREC_FP16)
         return fail(VBMC_ERR_ARG, "precision must be VBMC_PREC_BF16 or VBMC_PREC_FP16");
     float u = 0.f;
     double w = 0.0;
-    const vbmc_status st = tc_f16_selftest(precision == VBMC_PREC_BF16, &u, &w);
+    int pf = 0;
+    const vbmc_status st = tc_f16_selftest(precision == VBMC_PREC_BF16, &u, &w, &pf);
     if (st != VBMC_OK) return fail(st, "kind::f16 accumulator self-test failed or found no usable unit");
     *unit = (double)u;
     if (worst) *worst = w;
+    if (probes_failed) *probes_failed = pf;
     return VBMC_OK;
 }
 

@@ -106,6 +106,15 @@ struct QueryView {
     float* kvec;            // [kMaxL+1] per-layer constant error-norm terms
     uint32_t* cpos;         // [kMaxL+1][32] tensor screen: columns whose sign never changes
     uint32_t* cneg;         //   (pos: output change = input change; neg: output stays 0)
+    // Compacted columns of the tensor screen (one query per call): the neurons of
+    // hidden layer l that are not of the class "neg" come first, in order, so
+    // the dense layers run over them only (a "neg" neuron's change is 0 at every
+    // point of the box, so dropping it changes no product).
+    int compact;            // 1: the screen reads the compacted operands below
+    int* perm;              // [total]: layer l at noff[l]: compacted position -> neuron
+    int* kc;                // [kMaxL+1]: layer l's compacted width, a multiple of 64
+    float* tabc;            // [s][R][H_1]: tab in compacted column order
+    float* w1c;             // [kMaxS][H_1]: W_1[perm_1[j']][pix_p], compacted order
     Counters* cnt;
     uint32_t* bitmap;       // verdict bits (nullptr: off)
     unsigned long long bitmap_bits;

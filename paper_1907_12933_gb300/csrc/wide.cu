@@ -900,7 +900,7 @@ vbmc_status wide_build(WideNet& wn, const NetView& v, const std::vector<std::vec
     } else {
         // BF16 / FP16: the kind::f16 accumulator probe of the fused screen
         float u = 0.f;
-        const vbmc_status st = tc_f16_selftest(type == WIDE_BF16, &u, nullptr);
+        const vbmc_status st = tc_f16_selftest(type == WIDE_BF16, &u, nullptr, nullptr);
         if (st != VBMC_OK) return st;
         P.acc_unit = u;
     }

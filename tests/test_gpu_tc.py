@@ -33,9 +33,9 @@ def test_kind_f16_accumulation_unit(vb, prec):
     random output lies within the FP32 model, so the unit is 2^-22."""
     w = synth.workload("mlp784x512x512_relu_s6k7", s=1, k=1)
     vnet = vb.Net(w["net"])
-    u, worst = vb.tc_accumulation_unit(vnet, prec)
-    print(prec, "accumulation unit", u, "worst |err| / (K sum|p|)", worst)
-    assert u == 2.0 ** -22, (u, worst)
+    u, worst, failed = vb.tc_accumulation_unit(vnet, prec)
+    print(prec, "accumulation unit", u, "worst |err| / (K sum|p|)", worst, "probes failed", bin(failed))
+    assert failed == 0 and u == 2.0 ** -22, (u, worst, bin(failed))
     assert 0.0 <= worst <= u
     vnet.free()
 
