@@ -352,6 +352,7 @@ vbmc_status create_result(const vbmc_net* net, const vbmc_caps* caps, BatchArena
         A(&q.kc, (size_t)2 * (kMaxL + 1));
         A(&q.tabc, (size_t)S * RM * v.dims[1]);
         A(&q.w1c, (size_t)kMaxS * v.dims[1]);
+        for (int l = 2; l <= v.L; ++l) A(&q.wtc[l], (size_t)v.dims[l - 1] * v.dims[l]);
     }
     if (e == cudaSuccess) e = cudaMallocHost((void**)&r->h_cnt, sizeof(Counters));
     if (e == cudaSuccess) e = cudaEventCreate(&r->ev0);

@@ -110,11 +110,14 @@ struct QueryView {
     // hidden layer l that are not of the class "neg" come first, in order, so
     // the dense layers run over them only (a "neg" neuron's change is 0 at every
     // point of the box, so dropping it changes no product).
-    int compact;            // 1: the screen reads the compacted operands below
+    int compact;            // 1: the set-up of this call built the compacted operands below
+                            //    (the tensor screen, and the FP32 pass of the same call, read them)
     int* perm;              // [total]: layer l at noff[l]: compacted position -> neuron
     int* kc;                // [kMaxL+1]: layer l's compacted width, a multiple of 64
     float* tabc;            // [s][R][H_1]: tab in compacted column order
     float* w1c;             // [kMaxS][H_1]: W_1[perm_1[j']][pix_p], compacted order
+    float* wtc[kMaxL + 1];  // l >= 2: W_l^T [H_{l-1}][H_l], rows and columns compacted
+                            // (the output layer keeps its columns)
     Counters* cnt;
     uint32_t* bitmap;       // verdict bits (nullptr: off)
     unsigned long long bitmap_bits;

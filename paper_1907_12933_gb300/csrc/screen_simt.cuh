@@ -122,7 +122,7 @@ constexpr float kUseg = 0x1.00002p-24f * (float)(CKC * KC);  // u' CKL, rounded 
 template <int PPW, int NQ, int NQA>
 __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView& net,
                                             const QueryView* __restrict__ qs, int l, int warp,
-                                            int lane) {
+                                            int lane, bool cmp) {
     constexpr int HS = SimtSmem<PPW, NQ>::HS;
     constexpr int HW = 32 * NQA;  // columns of the weight chunk in use
     constexpr bool PER_NEURON = NQA == 1;
@@ -135,8 +135,14 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
     static_assert(2 * KCL * WSL <= 2 * KC * SimtSmem<PPW, NQ>::WS, "weight chunk view exceeds its buffer");
     static_assert(HS % KCL == 0, "weight chunks must tile the operand rows");
     const int L = net.L;
-    const int K = net.dims[l - 1], N = net.dims[l];
-    const float* __restrict__ WT = net.WT[l];  // [K][N]
+    // compacted (one query whose set-up kept the non-"neg" neurons, see tc.cu):
+    // K and N count the kept positions of layers l-1 and l (the output layer keeps
+    // its neurons); W_l^T comes from the query's compacted copy, rows of NS floats
+    const int NS = net.dims[l];
+    const int K = cmp ? qs[0].kc[l - 1] : net.dims[l - 1];
+    const int N = (cmp && l < L) ? qs[0].kc[l] : NS;
+    const int cntN = (cmp && l < L) ? qs[0].kc[kMaxL + 1 + l] : NS;  // kept neurons
+    const float* __restrict__ WT = cmp ? qs[0].wtc[l] : net.WT[l];  // [K][NS]
     const int nchunks = (K + KCL - 1) / KCL;
     // Wide tiles (paired FMAs) read two operand values per shared load and keep
     // the k loop rolled: their accumulators leave no registers for more.
@@ -155,20 +161,20 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
         for (int i = 0; i < (NQA + 1) / 2; ++i) acc[r][i] = make_float2(0.f, 0.f);
     }
 
-    const bool vec = (N % 4) == 0;
+    const bool vec = (N % 4) == 0 && (NS % 4) == 0;
     auto load_chunk = [&](int c, int buf) {
         float* const dst = Wb + buf * (KCL * WSL);
         if (vec) {
             for (int e = threadIdx.x; e < KCL * (HW / 4); e += THREADS) {
                 const int kk = e / (HW / 4), n = (e % (HW / 4)) * 4, k = c * KCL + kk;
                 const bool ok = k < K && n < N;
-                cp_async16(dst + kk * WSL + n, ok ? (const void*)&WT[(size_t)k * N + n] : (const void*)WT, ok);
+                cp_async16(dst + kk * WSL + n, ok ? (const void*)&WT[(size_t)k * NS + n] : (const void*)WT, ok);
             }
         } else {
             for (int e = threadIdx.x; e < KCL * HW; e += THREADS) {
                 const int kk = e / HW, n = e % HW, k = c * KCL + kk;
                 const bool ok = k < K && n < N;
-                cp_async4(dst + kk * WSL + n, ok ? (const void*)&WT[(size_t)k * N + n] : (const void*)WT, ok);
+                cp_async4(dst + kk * WSL + n, ok ? (const void*)&WT[(size_t)k * NS + n] : (const void*)WT, ok);
             }
         }
         cp_async_commit();
@@ -258,19 +264,23 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
         uint32_t uncb = 0u, flipb = 0u;  // per slot: uncertain sign, certain change (handled after)
 #pragma unroll
         for (int qq = 0; qq < NQ; ++qq) {
-            const int n = qq < NQA ? slot_neuron<NQA>(lane, qq) : lane + 32 * qq;
-            if (qq < NQA && n < N) {
-                const int gi = off + n;
+            const int n = qq < NQA ? slot_neuron<NQA>(lane, qq) : lane + 32 * qq;  // position
+            // neuron at position n; -1: a padding position (output change 0)
+            const int no = (cmp && l < L) ? (n < cntN ? Q.perm[off + n] : -1) : n;
+            if (qq < NQA && n < N && no < 0) {
+                S.A[m][n] = 0.f;
+            } else if (qq < NQA && n < N) {
+                const int gi = off + no;
                 const float du = accv(r, qq < NQA ? qq : 0);
                 const float ub = __ldg(&Q.ub32[gi]);
                 const float u = ub + du;
-                const float rnn = __ldg(&rn[n]);
+                const float rnn = __ldg(&rn[no]);
                 // |du - exact|: rounding (a priori, or a posteriori with one neuron per lane) + propagated
                 float bnd = __fmul_ru(rnn, X);
                 if (PER_NEURON) {
                     const float rho = __fmul_ru(kUseg, __fmaf_ru(rnn, Nin, chk[r]));
                     bnd = fminf(bnd, __fmaf_ru(rnn, Ein, rho));
-                    if (l == L && n < 32) S.rho[m][n] = fminf(__fmul_ru(rnn, __fmul_ru(gl, Nin)), rho);
+                    if (l == L && no < 32) S.rho[m][no] = fminf(__fmul_ru(rnn, __fmul_ru(gl, Nin)), rho);
                 }
                 const float bound = __fadd_ru(bnd, __ldg(&Q.thr[gi]));
                 const bool cert = __fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound;
@@ -292,7 +302,8 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
         while (flipb) {
             const int qq = __ffs(flipb) - 1;
             flipb &= flipb - 1u;
-            const int n = qq < NQA ? slot_neuron<NQA>(lane, qq) : lane + 32 * qq;
+            const int np = qq < NQA ? slot_neuron<NQA>(lane, qq) : lane + 32 * qq;
+            const int n = (cmp && l < L) ? Q.perm[off + np] : np;  // neuron
             const int idx = atomicAdd(&S.fcnt[m][l], 1);
             if (idx < FCAP) S.flist[m][l][idx] = (short)n;
             if (Q.flip) set_bit_once(Q.flip, off + n);
@@ -337,6 +348,8 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int L = net.L;
 
+    // compacted columns: one query whose set-up built them (tensor-screen calls)
+    const bool cmp = nq == 1 && qs[0].compact;
     unsigned long long tiles = n_tiles;
     unsigned long long gcount = 0;
     if (gather) {
@@ -402,6 +415,8 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
         // ---- S2/S3: layer 1 from the delta tables
         {
             const int H1 = net.dims[1];
+            const int W1 = cmp ? qs[0].kc[1] : H1;               // positions computed
+            const int cnt1 = cmp ? qs[0].kc[kMaxL + 2] : H1;     // kept neurons
             for (int r = 0; r < PPW; ++r) {
                 const int m = warp * PPW + r;
                 if (!S.valid[m]) continue;
@@ -416,12 +431,13 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
                 for (int qq = 0; qq < NQ; ++qq) dus[qq] = 0.f;
                 const float* __restrict__ W1T = net.WT[1];  // [H_0][H_1]
                 for (int p = 0; p < s; ++p) {
-                    const float* wr = W1T + (size_t)Q.pix[p] * H1;  // validated by the prologue
+                    // validated by the prologue; compacted: the query's row of W_1 weights
+                    const float* wr = cmp ? Q.w1c + (size_t)p * H1 : W1T + (size_t)Q.pix[p] * H1;
                     const float c = S.cpx[m][p];
 #pragma unroll
                     for (int qq = 0; qq < NQ; ++qq) {
                         const int j = lane + 32 * qq;
-                        if (j < H1) dus[qq] += __fmul_rn(__ldg(&wr[j]), c);
+                        if (j < W1) dus[qq] += __fmul_rn(__ldg(&wr[j]), c);
                     }
                 }
                 // branch-free over the slots (their loads pipeline); uncertain signs
@@ -430,16 +446,17 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
                 uint32_t uncb = 0u, flipb = 0u;
 #pragma unroll
                 for (int qq = 0; qq < NQ; ++qq) {
-                    const int j = lane + 32 * qq;
+                    const int j = lane + 32 * qq;                       // position
+                    const int jo = cmp ? (j < cnt1 ? Q.perm[j] : -1) : j;  // neuron (-1: padding)
                     float dh = 0.f;
-                    if (j < H1) {
+                    if (j < W1 && jo >= 0) {
                         const float du = dus[qq];
-                        const float ub = __ldg(&Q.ub32[j]);
+                        const float ub = __ldg(&Q.ub32[jo]);
                         const float u = ub + du;
-                        const bool cert = __fmul_rd(fabsf(u), 1.f - 0x1p-22f) > __ldg(&Q.thr[j]);
+                        const bool cert = __fmul_rd(fabsf(u), 1.f - 0x1p-22f) > __ldg(&Q.thr[jo]);
                         uncb |= (uint32_t)!cert << qq;
                         flipb |= (uint32_t)(cert && ((u >= 0.f) != (ub >= 0.f))) << qq;
-                        if (L > 1) dh = act_delta(net.act, du, u, __ldg(&Q.c1[j]), __ldg(&Q.c2[j]));
+                        if (L > 1) dh = act_delta(net.act, du, u, __ldg(&Q.c1[jo]), __ldg(&Q.c2[jo]));
                         else dh = u;
                         nsum = fmaf(dh, dh, nsum);
                     }
@@ -447,7 +464,8 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
                 }
                 if (uncb && Q.flip) S.unc[m] = 1;  // signs matter only for coverage
                 while (flipb) {
-                    const int j = lane + 32 * (__ffs(flipb) - 1);
+                    const int jp = lane + 32 * (__ffs(flipb) - 1);
+                    const int j = cmp ? Q.perm[jp] : jp;
                     flipb &= flipb - 1u;
                     const int idx = atomicAdd(&S.fcnt[m][1], 1);
                     if (idx < FCAP) S.flist[m][1][idx] = (short)j;
@@ -465,8 +483,8 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
 
         // ---- S4: dense layers on the deltas
         for (int l = 2; l <= L; ++l) {
-            if (net.dims[l] > 32) dense_layer<PPW, NQ, NQ>(S, net, qs, l, warp, lane);
-            else dense_layer<PPW, NQ, 1>(S, net, qs, l, warp, lane);
+            if (net.dims[l] > 32) dense_layer<PPW, NQ, NQ>(S, net, qs, l, warp, lane, cmp);
+            else dense_layer<PPW, NQ, 1>(S, net, qs, l, warp, lane, cmp);
         }
 
         // ---- S5: verdict (layer L values are in A[m][0..H_L))

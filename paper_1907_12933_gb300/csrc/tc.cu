@@ -1023,6 +1023,7 @@ __global__ void __launch_bounds__(512) k_compact_perm(const __grid_constant__ Tc
         if (keep) Q.perm[net.noff[l] + before + __popc(m & ((1u << lane) - 1u))] = t;
         if (t >= total && t < kcl) Q.perm[net.noff[l] + t] = 0;  // padding ("neg" by position)
         if (t == 0) {
+            Q.compact = 1;
             Q.kc[l] = kcl;
             Q.kc[kMaxL + 1 + l] = total;
             if (l == 1) {
@@ -1077,6 +1078,18 @@ __global__ void k_compact_gather(const __grid_constant__ TcParams P, NetView net
             }
             dq[(size_t)r * K + k] = a;
             dl[(size_t)r * K + k] = b;
+        }
+    }
+    // the FP32 transposed copy for the FP32 pass: wtc[l][k'][n'] (row stride N)
+    const int N = ly.N;
+    const int ncols = out ? N : Q.kc[l];
+    const int ncnt = out ? N : Q.kc[kMaxL + 1 + l];
+    float* wt = Q.wtc[l];
+    for (int k = blockIdx.x; k < kin; k += gridDim.x) {
+        const int ko = k < cin ? Q.perm[net.noff[l - 1] + k] : -1;
+        for (int n = threadIdx.x; n < ncols; n += blockDim.x) {
+            const int no = n < ncnt ? (out ? n : Q.perm[net.noff[l] + n]) : -1;
+            wt[(size_t)k * N + n] = (ko >= 0 && no >= 0) ? net.WT[l][(size_t)ko * N + no] : 0.f;
         }
     }
 }
