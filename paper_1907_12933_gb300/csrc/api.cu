@@ -604,12 +604,15 @@ vbmc_status enqueue_passes(vbmc_net* net, QueryView* d_qs, const QueryView* hq, 
             // one query: screen -> split tensor pass -> FP32; many: screen -> FP32 directly
             vbmc_status sst = tc_launch_screen(net->tc, v, d_qs, nq, d_tp, ntiles, opt.precision,
                                    nq == 1 ? qsplit : q32, nq == 1 ? 0 : 1, net->n_sm, st, tw);
-            if (sst != VBMC_OK) return fail(sst, "tensor-core screen launch failed");
+            if (sst != VBMC_OK)
+                return fail(sst, std::string("tensor-core screen launch failed: ") + cudaGetErrorString(cudaGetLastError()));
             VB_CUDA(record(ev[2]));
             if (nq == 1) {
                 sst = tc_launch_gather(net->tc, v, d_qs, d_queue[0], d_qcount + 0, cap, opt.precision,
                                        q32, net->n_sm, st, tw);
-                if (sst != VBMC_OK) return fail(sst, "tensor-core split pass launch failed");
+                if (sst != VBMC_OK)
+                    return fail(sst, std::string("tensor-core split pass launch failed: ") +
+                                         cudaGetErrorString(cudaGetLastError()));
             }
             VB_CUDA(record(ev[4]));
             launch_screen_simt(v, d_qs, nq, nullptr, 0, d_queue[1], d_qcount + 1, cap, qdf, 2,

@@ -5,7 +5,7 @@
 //   warp 0      TMA producer: weight tiles [slice x 64] of W_l (K-major,
 //               128-byte swizzle) into a ring of NB 16 KB slots
 //   warp 1      TMEM owner (512 columns) and MMA issuer (one thread)
-//   warps 2..9  workers: build the layer-2 operand (incremental layer 1,
+//   warps 2..17 workers: build the layer-2 operand (incremental layer 1,
 //               Eq. 1, from the delta tables), drain each layer's
 //               accumulator from TMEM, apply ReLU in delta form, quantise to
 //               16-bit into the next layer's operand ring (NA 16 KB slots of
@@ -45,7 +45,12 @@ namespace vbmc {
 
 namespace {
 
-constexpr int TC_THREADS = 320;
+constexpr int NW = 16;                   // worker warps
+constexpr int NWT = 32 * NW;             // worker threads
+constexpr int TC_THREADS = 64 + NWT;     // + TMA producer warp + MMA warp
+constexpr int RPW = 128 / NW;            // layer-1 rows per worker warp
+constexpr int CQ = NW / 4;               // worker warps per TMEM lane quarter
+constexpr int CW = 64 / CQ;              // drain: columns of a 64-column chunk per warp
 constexpr int NA = 4;
 constexpr int NB = 6;
 constexpr int kStageR = 16;  // layer-1 inner-digit tables are staged in shared memory for R <= kStageR
@@ -67,14 +72,14 @@ struct TcSmem {
     int pixs[kMaxS];       // the query's pixel indices
     float N[MROWS], R[MROWS], Lo[MROWS], E[MROWS];
     float nzl[kTcMaxL + 1];  // layer l: columns not in the class "neg" (the others are 0 at every point)
-    float part[2][MROWS][3];
+    float part[CQ][MROWS][3];
     int unc[MROWS];
     int vst[MROWS];
     int fcnt[MROWS][kTcMaxL + 1];
     short flist[MROWS][kTcMaxL + 1][FCAP];
     uint32_t cflip[256];   // sign changes seen by this CTA for query curq (flushed on change)
-    float4 cst4[8][32];    // per worker warp, the 32 columns it drains: (ub, a, b, thr)
-    float2 cst2[8][32];    //   and the delta-ReLU constants (c1, c2)
+    float4 cst4[NW][CW];   // per worker warp, the CW columns it drains: (ub, a, b, thr)
+    float2 cst2[NW][CW];   //   and the delta-ReLU constants (c1, c2)
     union {
         // fast layer-1 path: tables of the two inner digits, one 64-column chunk, double-buffered
         float tstage[2][2][kStageR][64];
@@ -168,12 +173,12 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
             tc::mbar_init(bar(BEMPTY(i)), 1);
         }
         for (int i = 0; i < NA; ++i) {
-            tc::mbar_init(bar(AFULL(i)), 8);
+            tc::mbar_init(bar(AFULL(i)), NW);
             tc::mbar_init(bar(AEMPTY(i)), 1);
         }
         tc::mbar_init(bar(DFULL), 1);
-        tc::mbar_init(bar(TFREE), 8);
-        tc::mbar_init(bar(DRAINED), 8);
+        tc::mbar_init(bar(TFREE), NW);
+        tc::mbar_init(bar(DRAINED), NW);
         tc::mbar_init(bar(FIN), 1);
         S.abort_flag = 0;
         S.curq = -1;
@@ -298,10 +303,10 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
         }
     } else {
         // -------------------------------------------------------------- workers
-        const int wid = warp - 2;            // 0..7
-        const int wtid = threadIdx.x - 64;   // 0..255
+        const int wid = warp - 2;            // 0..NW-1
+        const int wtid = threadIdx.x - 64;   // 0..NWT-1
         const int qd = warp & 3;             // TMEM lane quarter
-        const int hf = wid >> 2;             // column half in the drain phases
+        const int hf = wid >> 2;             // column part (of CQ) in the drain phases
         const int H0 = net.dims[0], H1 = net.dims[1];
         uint32_t ait = 0, dit = 0;
         const float uacc_base = P.acc_unit * (SPLIT ? 3.f : 1.f);  // measured by tc_f16_selftest
@@ -328,19 +333,19 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
             if (q != S.curq) {  // this CTA's sign changes belong to the previous query
                 const int cq = S.curq;
                 if (cq >= 0)
-                    for (int w = wtid; w < net.flip_words && w < 256; w += 256)
+                    for (int w = wtid; w < net.flip_words && w < 256; w += NWT)
                         if (S.cflip[w]) {
                             if (qs[cq].flip) atomicOr(&qs[cq].flip[w], S.cflip[w]);
                             S.cflip[w] = 0u;
                         }
-                tc::named_bar_sync(1, 256);
+                tc::named_bar_sync(1, NWT);
                 if (wtid == 0) S.curq = q;
                 if (wtid >= 1 && wtid < L) {  // operand entries that can be nonzero, per hidden layer
                     int c = 0;
                     for (int w = 0; w < (net.dims[wtid] + 31) / 32; ++w) c += __popc(~Q.cneg[wtid * 32 + w]);
                     S.nzl[wtid] = (float)min(c, net.dims[wtid]);
                 }
-                tc::named_bar_sync(1, 256);
+                tc::named_bar_sync(1, NWT);
             }
             // ---- decode the tile's points. Range mode: the tile's indices are
             // consecutive, so their outer prefixes t / R^ni (the digits above the ni
@@ -418,7 +423,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 S.npref = np;
                 S.fast = fast_t;
             }
-            tc::named_bar_sync(1, 256);
+            tc::named_bar_sync(1, NWT);
             // layer-1 tables (compacted: column j' holds neuron perm_1[j']) and the
             // number of columns the dense layer 2 reads
             const float* __restrict__ tabq = cmp ? Q.tabc : Q.tab;
@@ -426,21 +431,21 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
             const int cnt1 = cmp ? Q.kc[kMaxL + 2] : H1;  // non-"neg" layer-1 neurons (compacted)
             // outer-prefix partial sums of layer 1
             for (int k = 0; k < S.npref; ++k) {
-                for (int j = wtid; j < W1cols; j += 256) {
+                for (int j = wtid; j < W1cols; j += NWT) {
                     float acc = 0.f;
                     for (int p = 0; p < s - ni; ++p)
                         acc += __ldg(&tabq[((size_t)p * R + S.pdig[k][p]) * H1 + j]);
                     S.souter[k][j] = acc;
                 }
             }
-            tc::named_bar_sync(1, 256);
+            tc::named_bar_sync(1, NWT);
 
-            // ---- W1: layer-1 deltas -> operand of layer 2 (rows wid*16 .. +15,
+            // ---- W1: layer-1 deltas -> operand of layer 2 (rows wid*RPW .. +RPW-1,
             //      lanes over column pairs 2*lane, 2*lane+1 of each 64-column chunk)
             {
-                float nsum[16], rsum[16], lsum[16];
+                float nsum[RPW], rsum[RPW], lsum[RPW];
 #pragma unroll
-                for (int i = 0; i < 16; ++i) nsum[i] = rsum[i] = lsum[i] = 0.f;
+                for (int i = 0; i < RPW; ++i) nsum[i] = rsum[i] = lsum[i] = 0.f;
                 const int kch = S.kch[2];
                 const bool fast = S.fast;
                 const bool nosum = (s == 2);  // fast path without outer digits
@@ -448,7 +453,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 // chunk's 64 columns go to shared memory one chunk ahead (cp.async)
                 const bool stage = fast && R <= kStageR;
                 auto stage_chunk = [&](int c, int buf) {
-                    for (int e = wtid; e < 2 * R * 16; e += 256) {
+                    for (int e = wtid; e < 2 * R * 16; e += NWT) {
                         const int tt = e / (R * 16), rem = e - tt * (R * 16), dgt = rem >> 4, u = rem & 15;
                         cp_async16(&S.tstage[buf][tt][dgt][4 * u],
                                    tabq + ((size_t)(s - 2 + tt) * R + dgt) * H1 + 64 * c + 4 * u);
@@ -463,7 +468,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     const int sbuf = c & 1;
                     if (stage) {
                         cp_async_wait_all();            // this thread's copies of chunk c
-                        tc::named_bar_sync(1, 256);     // everyone's; and chunk c-1's buffer is no longer read
+                        tc::named_bar_sync(1, NWT);     // everyone's; and chunk c-1's buffer is no longer read
                         if (c + 1 < kch) stage_chunk(c + 1, sbuf ^ 1);
                     }
                     const int j = 64 * c + 2 * lane;  // column (compacted: position) of this lane
@@ -482,9 +487,9 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     const float th0 = cr0 ? Q.thr[jo0] : 0.f, th1 = cr1 ? Q.thr[jo1] : 0.f;
                     const bool anyc = __any_sync(0xffffffffu, cr0 || cr1);
                     const uint32_t lanepart = (lane & 3) * 4;
-                    constexpr int RB = SPLIT ? 4 : 8;  // rows per batch (registers)
+                    constexpr int RB = SPLIT ? (RPW < 4 ? RPW : 4) : (RPW < 8 ? RPW : 8);  // rows per batch
 #pragma unroll
-                    for (int i0 = 0; i0 < 16; i0 += RB) {
+                    for (int i0 = 0; i0 < RPW; i0 += RB) {
                     // table sums of RB rows first (their loads overlap), then the rest
                     float2 dus[RB];
                     unsigned vbits = 0;  // valid rows of the batch (the compute loop stores to
@@ -492,7 +497,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     if (fast) {
 #pragma unroll
                         for (int ii = 0; ii < RB; ++ii) {
-                            const int r = wid * 16 + i0 + ii;
+                            const int r = wid * RPW + i0 + ii;
                             const int4 ri = S.rinfo[r];
                             if (ri.w) vbits |= 1u << ii;
                             float2 du = nosum ? make_float2(0.f, 0.f)
@@ -519,7 +524,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         int pfrom[RB];
 #pragma unroll
                         for (int ii = 0; ii < RB; ++ii) {
-                            const int r = wid * 16 + i0 + ii;
+                            const int r = wid * RPW + i0 + ii;
                             const int4 ri = S.rinfo[r];
                             if (ri.w) vbits |= 1u << ii;
                             const int pi = S.pidx[r];
@@ -533,7 +538,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
 #pragma unroll
                             for (int ii = 0; ii < RB; ++ii) {
                                 if (p < pfrom[ii]) continue;
-                                const float c = S.cpx[wid * 16 + i0 + ii][p];
+                                const float c = S.cpx[wid * RPW + i0 + ii][p];
                                 dus[ii].x += __fmul_rn(w2.x, c);
                                 dus[ii].y += __fmul_rn(w2.y, c);
                             }
@@ -542,7 +547,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
 #pragma unroll
                     for (int ii = 0; ii < RB; ++ii) {
                         const int i = i0 + ii;
-                        const int r = wid * 16 + i;
+                        const int r = wid * RPW + i;
                         const bool rw = (vbits >> ii) & 1u;
                         const float2 du = dus[ii];
                         float dh0 = fmaxf(du.x + c10, c20);
@@ -571,8 +576,9 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         float q0, q1;
                         const uint32_t w = pack2<BF>(dh0, dh1, q0, q1);
                         float r0 = dh0 - q0, r1 = dh1 - q1;
-                        // r & 7 == i & 7 (wid * 16 is a multiple of 8): swizzle known per i
-                        const uint32_t off = (uint32_t)((wid * 2 + (i >> 3)) * 1024 + (i & 7) * 128) +
+                        // r & 7 == i & 7 (wid * RPW is a multiple of 8): swizzle known per i
+                        static_assert(RPW % 8 == 0, "rows of a warp start at a swizzle atom");
+                        const uint32_t off = (uint32_t)((wid * (RPW / 8) + (i >> 3)) * 1024 + (i & 7) * 128) +
                                              ((((uint32_t)lane >> 2) ^ (uint32_t)(i & 7)) << 4) + lanepart;
                         *reinterpret_cast<uint32_t*>(&S.A[a0][off]) = w;
                         if (SPLIT) {
@@ -596,7 +602,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     ait += SPLIT ? 2 : 1;
                 }
 #pragma unroll
-                for (int i = 0; i < 16; ++i) {
+                for (int i = 0; i < RPW; ++i) {
                     float a = nsum[i], b = rsum[i], cc = lsum[i];
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
@@ -605,7 +611,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         if (SPLIT) cc += __shfl_xor_sync(0xffffffffu, cc, o);
                     }
                     if (lane == i) {
-                        const int r = wid * 16 + i;
+                        const int r = wid * RPW + i;
                         const float N = norm_up(a);
                         S.N[r] = N;
                         S.R[r] = norm_up(b);
@@ -614,7 +620,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     }
                 }
             }
-            tc::named_bar_sync(1, 256);
+            tc::named_bar_sync(1, NWT);
 
             // ---- hidden layers: drain D_l, write the operand of layer l+1
             const int r = 32 * qd + lane;
@@ -639,18 +645,20 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     const int a0 = ait % NA, a1 = (ait + 1) % NA;
                     tc::mbar_wait(bar(AEMPTY(a0)), ((ait / NA) & 1) ^ 1, abortp);
                     if (SPLIT) tc::mbar_wait(bar(AEMPTY(a1)), (((ait + 1) / NA) & 1) ^ 1, abortp);
-                    const int n0 = 64 * c + 32 * hf;
-                    float v[32];
-                    tc::tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)n0, v);
-                    // the class of each of the warp's 32 columns (lane = column); compacted:
-                    // position nl holds neuron perm_l[nl], positions past the count are "neg"
-                    const int nl = n0 + lane;
+                    const int n0 = 64 * c + CW * hf;
+                    float v[CW];
+                    tc::tmem_ld<CW>(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)n0, v);
+                    // the class of each of the warp's CW columns (lane i < CW: column n0 + i);
+                    // compacted: position nl holds neuron perm_l[nl], positions past the
+                    // count are "neg"
+                    const bool cl = lane < CW;
+                    const int nl = n0 + (cl ? lane : 0);
                     const int nlo = cmp ? Q.perm[off_l + nl] : nl, gcol = off_l + nlo;
                     const bool negl = cmp ? nl >= cntl : (Q.cneg[l * 32 + (nlo >> 5)] >> (nlo & 31)) & 1u;
                     const bool posl = !negl && ((Q.cpos[l * 32 + (nlo >> 5)] >> (nlo & 31)) & 1u);
-                    const uint32_t cross = __ballot_sync(0xffffffffu, !posl && !negl);
+                    const uint32_t cross = __ballot_sync(0xffffffffu, cl && !posl && !negl);
                     const bool rv = S.valid[r];
-                    {  // constants of the warp's 32 columns, one coalesced load each; the
+                    {  // constants of the warp's columns, one coalesced load each; the
                        // delta-ReLU constants of the column classes: pos (0, -inf), neg (-inf, 0)
                         const bool crl = (cross >> lane) & 1u;
                         float4 k4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -659,8 +667,10 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                             k4 = make_float4(Q.ub32[gcol], av[nlo], bv[nlo], Q.thr[gcol]);
                             k2 = make_float2(Q.c1[gcol], Q.c2[gcol]);
                         }
-                        S.cst4[wid][lane] = k4;
-                        S.cst2[wid][lane] = k2;
+                        if (cl) {
+                            S.cst4[wid][lane] = k4;
+                            S.cst2[wid][lane] = k2;
+                        }
                         __syncwarp();
                     }
                     if (cross && rv && Q.flip != nullptr) {  // signs matter only for coverage
@@ -670,7 +680,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         // classes are zero); the column class selects the bits afterwards
                         uint32_t uncb = 0u, flb = 0u;
 #pragma unroll
-                        for (int g = 0; g < 4; ++g) {
+                        for (int g = 0; g < CW / 8; ++g) {
                             if ((cross >> (8 * g)) & 0xFFu) {
 #pragma unroll
                                 for (int i = 8 * g; i < 8 * g + 8; ++i) {
@@ -697,18 +707,18 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     }
                     // delta ReLU; no stores in this loop, so its loads pipeline
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) {
+                    for (int i = 0; i < CW; ++i) {
                         const float2 k2 = S.cst2[wid][i];
                         v[i] = fmaxf(v[i] + k2.x, k2.y);
                     }
                     __syncwarp();  // the staged constants are read before the next chunk overwrites them
                     if (!__all_sync(0xffffffffu, rv) && !rv) {
 #pragma unroll
-                        for (int i = 0; i < 32; ++i) v[i] = 0.f;
+                        for (int i = 0; i < CW; ++i) v[i] = 0.f;
                     }
-                    uint32_t wq[16], wl[16];
+                    uint32_t wq[CW / 2], wl[CW / 2];
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
+                    for (int i = 0; i < CW / 2; ++i) {
                         float q0, q1;
                         wq[i] = pack2<BF>(v[2 * i], v[2 * i + 1], q0, q1);
                         float r0 = v[2 * i] - q0, r1 = v[2 * i + 1] - q1;
@@ -723,8 +733,8 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         rs = fmaf(r0, r0, fmaf(r1, r1, rs));
                     }
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const uint32_t o = sw_off(r, hf * 4 + k);
+                    for (int k = 0; k < CW / 8; ++k) {  // 16-byte units of the row's CW columns
+                        const uint32_t o = sw_off(r, hf * (CW / 8) + k);
                         *reinterpret_cast<uint4*>(&S.A[a0][o]) =
                             make_uint4(wq[4 * k], wq[4 * k + 1], wq[4 * k + 2], wq[4 * k + 3]);
                         if (SPLIT)
@@ -744,11 +754,18 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 S.part[hf][r][1] = rs;
                 S.part[hf][r][2] = ls;
                 tc::tc_fence_before();
-                tc::named_bar_sync(1, 256);
+                tc::named_bar_sync(1, NWT);
                 if (hf == 0) {
-                    const float N = norm_up(S.part[0][r][0] + S.part[1][r][0]);
-                    const float Rn = norm_up(S.part[0][r][1] + S.part[1][r][1]);
-                    const float Lo = norm_up(S.part[0][r][2] + S.part[1][r][2]);
+                    float n2 = 0.f, r2 = 0.f, l2 = 0.f;
+#pragma unroll
+                    for (int h = 0; h < CQ; ++h) {
+                        n2 += S.part[h][r][0];
+                        r2 += S.part[h][r][1];
+                        l2 += S.part[h][r][2];
+                    }
+                    const float N = norm_up(n2);
+                    const float Rn = norm_up(r2);
+                    const float Lo = norm_up(l2);
                     // ||err(du_l)|| <= sA R + sB N + (sA + sB) E + sL Lo + uacc fq (N + R + 2 Lo)
                     const float sA = SPLIT ? ly.sa : ly.sq, sB = SPLIT ? ly.sd3 : ly.sd1;
                     float El = __fmul_ru(sA, Rr);
@@ -767,7 +784,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(bar(DRAINED));
                 }
-                tc::named_bar_sync(1, 256);
+                tc::named_bar_sync(1, NWT);
             }
 
             // ---- output layer: margin (Eq. 10) or threshold literal (Eq. 11), output signs
@@ -853,7 +870,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 tc::tc_fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(bar(TFREE));
-                tc::named_bar_sync(1, 256);
+                tc::named_bar_sync(1, NWT);
                 // ---- per-point results
                 if (hf == 0) {
                     const bool rv = S.valid[r];
@@ -886,7 +903,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         }
                     }
                 }
-                tc::named_bar_sync(1, 256);
+                tc::named_bar_sync(1, NWT);
                 // time to verdict: a screen tile done, or this tile's queued points resolved
                 if (wtid == 0) work_done(Q.cnt, gather ? (g * MROWS + MROWS <= gn ? MROWS : gn - g * MROWS) : 1);
             }
@@ -1652,7 +1669,7 @@ vbmc_status tc_launch_screen(TcNet& tc, const NetView& v, const QueryView* d_q, 
     const TcParams& P = (qw && nq == 1) ? Pc : tc.prec[bf ? 0 : 1].p;
     if (bf) launch_k<false, true>(P, v, d_q, nq, d_tile_prefix, ntiles, nullptr, nullptr, 0, out, out_level, n_sm, st);
     else launch_k<false, false>(P, v, d_q, nq, d_tile_prefix, ntiles, nullptr, nullptr, 0, out, out_level, n_sm, st);
-    return cudaGetLastError() == cudaSuccess ? VBMC_OK : VBMC_ERR_CUDA;
+    return cudaPeekAtLastError() == cudaSuccess ? VBMC_OK : VBMC_ERR_CUDA;  // the caller reports the error
 }
 
 vbmc_status tc_launch_gather(TcNet& tc, const NetView& v, const QueryView* d_q, const QEntry* in,
@@ -1664,7 +1681,7 @@ vbmc_status tc_launch_gather(TcNet& tc, const NetView& v, const QueryView* d_q, 
     const TcParams& P = qw ? Pc : tc.prec[bf ? 0 : 1].p;
     if (bf) launch_k<true, true>(P, v, d_q, 1, nullptr, 0, in, in_count, cap, out, 1, n_sm, st);
     else launch_k<true, false>(P, v, d_q, 1, nullptr, 0, in, in_count, cap, out, 1, n_sm, st);
-    return cudaGetLastError() == cudaSuccess ? VBMC_OK : VBMC_ERR_CUDA;
+    return cudaPeekAtLastError() == cudaSuccess ? VBMC_OK : VBMC_ERR_CUDA;  // the caller reports the error
 }
 
 int tc_tile_points() { return MROWS; }
