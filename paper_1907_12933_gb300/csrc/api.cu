@@ -346,8 +346,11 @@ vbmc_status create_result(const vbmc_net* net, const vbmc_caps* caps, BatchArena
     for (int i = 0; i < 4; ++i) A(&r->d_queue[i], (size_t)qc);
     A(&r->d_tiles, (size_t)VBMC_MAX_TILES);
     // compacted columns of the fused tensor screen (calls with one query)
-    const bool fused = !arena && (tc_supported(v, VBMC_PREC_BF16) || tc_supported(v, VBMC_PREC_FP16));
+    const bool tcnet = tc_supported(v, VBMC_PREC_BF16) || tc_supported(v, VBMC_PREC_FP16);
+    const bool fused = !arena && tcnet;
+    if (tcnet) A(&q.kcol, 2 * T);
     if (fused) {
+        A(&q.kcolc, 2 * T);
         A(&q.perm, T);
         A(&q.kc, (size_t)2 * (kMaxL + 1));
         A(&q.tabc, (size_t)S * RM * v.dims[1]);

@@ -118,6 +118,13 @@ struct QueryView {
     float* w1c;             // [kMaxS][H_1]: W_1[perm_1[j']][pix_p], compacted order
     float* wtc[kMaxL + 1];  // l >= 2: W_l^T [H_{l-1}][H_l], rows and columns compacted
                             // (the output layer keeps its columns)
+    // Column constants of the tensor screen per hidden neuron, two float4 each:
+    // (fl(ub), ||Wq_i||, ||W_i - Wq_i||, ||W_i - Wq_i - Wlo_i||) and (thr, c1, c2,
+    // class), with the delta-ReLU constants of the class folded in (pos: 0, -inf;
+    // neg: -inf, 0) and class 0 pos, 1 neg, 2 cross. kcol in neuron order,
+    // kcolc in compacted order (padding positions "neg").
+    float4* kcol;           // [total][2]
+    float4* kcolc;          // [total][2]
     Counters* cnt;
     uint32_t* bitmap;       // verdict bits (nullptr: off)
     unsigned long long bitmap_bits;

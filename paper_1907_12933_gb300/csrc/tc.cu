@@ -104,6 +104,13 @@ __device__ __forceinline__ int BFULL(int i) { return i; }
 __device__ __forceinline__ int BEMPTY(int i) { return NB + i; }
 __device__ __forceinline__ int AFULL(int i) { return 2 * NB + i; }
 __device__ __forceinline__ int AEMPTY(int i) { return 2 * NB + NA + i; }
+// verdict flag bits of a point, ORed by the warps that share its outputs:
+// Eq. 10: some margin pair certainly negative / some pair undecided;
+// Eq. 11: y_D certainly above / below V, some other output certainly above V,
+// some other output not certainly below V
+enum : int {
+    VF_UNSAFE = 1, VF_UNDECIDED = 2, VF_D_ABOVE = 4, VF_D_BELOW = 8, VF_O_ABOVE = 16, VF_O_NOT_BELOW = 32
+};
 constexpr int DFULL = 2 * NB + 2 * NA;
 constexpr int TFREE = DFULL + 1;
 constexpr int DRAINED = DFULL + 2;
@@ -428,7 +435,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
             // number of columns the dense layer 2 reads
             const float* __restrict__ tabq = cmp ? Q.tabc : Q.tab;
             const int W1cols = 64 * S.kch[2];
-            const int cnt1 = cmp ? Q.kc[kMaxL + 2] : H1;  // non-"neg" layer-1 neurons (compacted)
+
             // outer-prefix partial sums of layer 1
             for (int k = 0; k < S.npref; ++k) {
                 for (int j = wtid; j < W1cols; j += NWT) {
@@ -472,19 +479,15 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         if (c + 1 < kch) stage_chunk(c + 1, sbuf ^ 1);
                     }
                     const int j = 64 * c + 2 * lane;  // column (compacted: position) of this lane
-                    const int jo0 = cmp ? Q.perm[j] : j, jo1 = cmp ? Q.perm[j + 1] : j + 1;  // neurons
-                    const bool neg0 = cmp ? j >= cnt1 : (Q.cneg[32 + (jo0 >> 5)] >> (jo0 & 31)) & 1;
-                    const bool neg1 = cmp ? j + 1 >= cnt1 : (Q.cneg[32 + (jo1 >> 5)] >> (jo1 & 31)) & 1;
-                    const bool pos0 = !neg0 && ((Q.cpos[32 + (jo0 >> 5)] >> (jo0 & 31)) & 1);
-                    const bool pos1 = !neg1 && ((Q.cpos[32 + (jo1 >> 5)] >> (jo1 & 31)) & 1);
-                    const bool cr0 = !pos0 && !neg0, cr1 = !pos1 && !neg1;
+                    // the columns' constants, one coalesced load each (class folded in);
                     // dh = max(du + c1, c2) covers all classes: pos (0, -inf), neg (-inf, 0)
-                    const float c10 = cr0 ? Q.c1[jo0] : (pos0 ? 0.f : -INFINITY);
-                    const float c20 = cr0 ? Q.c2[jo0] : (pos0 ? -INFINITY : 0.f);
-                    const float c11 = cr1 ? Q.c1[jo1] : (pos1 ? 0.f : -INFINITY);
-                    const float c21 = cr1 ? Q.c2[jo1] : (pos1 ? -INFINITY : 0.f);
-                    const float ub0 = cr0 ? Q.ub32[jo0] : 0.f, ub1 = cr1 ? Q.ub32[jo1] : 0.f;
-                    const float th0 = cr0 ? Q.thr[jo0] : 0.f, th1 = cr1 ? Q.thr[jo1] : 0.f;
+                    const float4* __restrict__ kcl = cmp ? Q.kcolc : Q.kcol;
+                    const float4 kA0 = kcl[2 * j], kB0 = kcl[2 * j + 1];
+                    const float4 kA1 = kcl[2 * j + 2], kB1 = kcl[2 * j + 3];
+                    const bool cr0 = kB0.w == 2.f, cr1 = kB1.w == 2.f;
+                    const float c10 = kB0.y, c20 = kB0.z, c11 = kB1.y, c21 = kB1.z;
+                    const float ub0 = cr0 ? kA0.x : 0.f, ub1 = cr1 ? kA1.x : 0.f;
+                    const float th0 = cr0 ? kB0.x : 0.f, th1 = cr1 ? kB1.x : 0.f;
                     const bool anyc = __any_sync(0xffffffffu, cr0 || cr1);
                     const uint32_t lanepart = (lane & 3) * 4;
                     constexpr int RB = SPLIT ? (RPW < 4 ? RPW : 4) : (RPW < 8 ? RPW : 8);  // rows per batch
@@ -559,6 +562,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                                 if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > th0)) S.unc[r] = 1;
                                 else if ((u >= 0.f) != (ub0 >= 0.f)) {
                                     const int k = atomicAdd(&S.fcnt[r][1], 1);
+                                    const int jo0 = cmp ? Q.perm[j] : j;  // the neuron
                                     if (k < FCAP) S.flist[r][1][k] = (short)jo0;
                                     atomicOr(&S.cflip[jo0 >> 5], 1u << (jo0 & 31));
                                 }
@@ -568,6 +572,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                                 if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > th1)) S.unc[r] = 1;
                                 else if ((u >= 0.f) != (ub1 >= 0.f)) {
                                     const int k = atomicAdd(&S.fcnt[r][1], 1);
+                                    const int jo1 = cmp ? Q.perm[j + 1] : j + 1;  // the neuron
                                     if (k < FCAP) S.flist[r][1][k] = (short)jo1;
                                     atomicOr(&S.cflip[jo1 >> 5], 1u << (jo1 & 31));
                                 }
@@ -635,12 +640,9 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 const float Pa = __fmaf_ru(uacc, __fadd_ru(__fadd_ru(Nn, Rr), __fmul_ru(2.f, Ll)),
                                            __fmaf_ru(SPLIT ? 0x1p-7f : 0.f, Ll, __fadd_ru(Rr, Ee)));
                 const float Pb = __fadd_ru(Nn, Ee);
-                const float* av = ly.a;
-                const float* bv = SPLIT ? ly.b3 : ly.b1;
                 const int off_l = net.noff[l];
                 float ns = 0.f, rs = 0.f, ls = 0.f;
                 const int nch = S.np[l] / 64;
-                const int cntl = cmp ? Q.kc[kMaxL + 1 + l] : ly.N;  // non-"neg" neurons of layer l
                 for (int c = 0; c < nch; ++c) {
                     const int a0 = ait % NA, a1 = (ait + 1) % NA;
                     tc::mbar_wait(bar(AEMPTY(a0)), ((ait / NA) & 1) ^ 1, abortp);
@@ -653,20 +655,16 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     // count are "neg"
                     const bool cl = lane < CW;
                     const int nl = n0 + (cl ? lane : 0);
-                    const int nlo = cmp ? Q.perm[off_l + nl] : nl, gcol = off_l + nlo;
-                    const bool negl = cmp ? nl >= cntl : (Q.cneg[l * 32 + (nlo >> 5)] >> (nlo & 31)) & 1u;
-                    const bool posl = !negl && ((Q.cpos[l * 32 + (nlo >> 5)] >> (nlo & 31)) & 1u);
-                    const uint32_t cross = __ballot_sync(0xffffffffu, cl && !posl && !negl);
+                    const float4* __restrict__ kcl = (cmp ? Q.kcolc : Q.kcol) + 2 * (off_l + nl);
+                    const float4 kA = kcl[0], kB = kcl[1];  // this column's constants
+                    const uint32_t cross = __ballot_sync(0xffffffffu, cl && kB.w == 2.f);
                     const bool rv = S.valid[r];
                     {  // constants of the warp's columns, one coalesced load each; the
                        // delta-ReLU constants of the column classes: pos (0, -inf), neg (-inf, 0)
                         const bool crl = (cross >> lane) & 1u;
-                        float4 k4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                        float2 k2 = negl ? make_float2(-INFINITY, 0.f) : make_float2(0.f, -INFINITY);
-                        if (crl) {
-                            k4 = make_float4(Q.ub32[gcol], av[nlo], bv[nlo], Q.thr[gcol]);
-                            k2 = make_float2(Q.c1[gcol], Q.c2[gcol]);
-                        }
+                        const float4 k4 = crl ? make_float4(kA.x, kA.y, SPLIT ? kA.w : kA.z, kB.x)
+                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+                        const float2 k2 = make_float2(kB.y, kB.z);
                         if (cl) {
                             S.cst4[wid][lane] = k4;
                             S.cst2[wid][lane] = k2;
@@ -793,7 +791,10 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 tc::mbar_wait(bar(DFULL), dit & 1, abortp);
                 ++dit;
                 tc::tc_fence_after();
-                if (hf == 0) {
+                // the CQ warps of a TMEM lane quarter share the outputs: warp hf takes
+                // outputs o = hf, hf + CQ, ...; their verdict parts meet in S.vst[r]
+                // as flag bits (see VF_* below)
+                {
                     float v[32];
                     tc::tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16), v);
                     if (S.valid[r]) {
@@ -806,16 +807,26 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         const float* bv = SPLIT ? ly.b3 : ly.b1;
                         const int HL = ly.N, offL = net.noff[L];
                         const int D = Q.cnt->D;
-                        float y[kTcMaxOut];
+                        float vD = 0.f;  // v[D] by selection (v stays in registers)
 #pragma unroll
-                        for (int o = 0; o < kTcMaxOut; ++o) y[o] = 0.f;
+                        for (int o = 0; o < kTcMaxOut; ++o)
+                            if (o == D) vD = v[o];
+                        const float yD = Q.ub32[offL + D] + vD;
+                        const float dD = Q.dub[offL + D];
+                        const float* pr = P.pair + (size_t)D * HL * 5;
+                        const bool thr = Q.prop == PROP_THRESHOLD;
                         bool unc = false;
+                        int f = 0;
 #pragma unroll
-                        for (int o = 0; o < kTcMaxOut; ++o) {
+                        for (int o0 = 0; o0 < kTcMaxOut; o0 += CQ) {
+                            const int o = o0 + hf;
                             if (o >= HL) break;
+                            float vo = 0.f;  // v[o] by selection (v stays in registers)
+#pragma unroll
+                            for (int h = 0; h < CQ; ++h)
+                                if (h == hf && o0 + h < kTcMaxOut) vo = v[o0 + h];
                             const float ub = Q.ub32[offL + o];
-                            const float u = ub + v[o];
-                            y[o] = u;
+                            const float u = ub + vo;
                             const float bound = __fmaf_ru(av[o], Pa, __fmaf_ru(bv[o], Pb, Q.thr[offL + o]));
                             if (!(__fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound)) unc = Q.flip != nullptr;
                             else if ((u >= 0.f) != (ub >= 0.f)) {
@@ -823,47 +834,27 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                                 if (k < FCAP) S.flist[r][L][k] = (short)o;
                                 atomicOr(&S.cflip[(offL + o) >> 5], 1u << ((offL + o) & 31));
                             }
-                        }
-                        float yD = 0.f;
-#pragma unroll
-                        for (int o = 0; o < kTcMaxOut; ++o)
-                            if (o == D) yD = y[o];
-                        const float dD = Q.dub[offL + D];
-                        bool unsafe = false, safe = true;
-                        const float* pr = P.pair + (size_t)D * HL * 5;
-                        if (Q.prop == PROP_THRESHOLD) {  // Eq. 11: per output a_o Pa + b_o Pb + dub_o
-                            const float V = (float)Q.V;
-                            bool da = false, db = false, oa = false, ob = true;
-#pragma unroll
-                            for (int o = 0; o < kTcMaxOut; ++o) {
-                                if (o >= HL) break;
+                            if (thr) {  // Eq. 11: per output a_o Pa + b_o Pb + dub_o
                                 const float e = __fmaf_ru(av[o], Pa, __fmaf_ru(bv[o], Pb, __fadd_ru(Q.dub[offL + o],
                                                                                               (float)(2.0 * kTau))));
-                                const int sd = thr_side(y[o], V, e);
-                                if (o == D) { da = sd > 0; db = sd < 0; }
-                                else { oa = oa || sd > 0; ob = ob && sd < 0; }
+                                const int sd = thr_side(u, (float)Q.V, e);
+                                if (o == D) f |= (sd > 0 ? VF_D_ABOVE : 0) | (sd < 0 ? VF_D_BELOW : 0);
+                                else f |= (sd > 0 ? VF_O_ABOVE : 0) | (sd < 0 ? 0 : VF_O_NOT_BELOW);
+                            } else if (o != D) {  // Eq. 10: margin pair (D, o)
+                                const float diff = yD - u;
+                                const float* c5 = pr + o * 5;
+                                float eb = __fmul_ru(c5[0], __fadd_ru(Rr, 0.f));
+                                eb = __fmaf_ru(c5[1], Nn, eb);
+                                eb = __fmaf_ru(c5[2], Ee, eb);
+                                if (SPLIT) eb = __fmaf_ru(c5[3], Ll, eb);
+                                eb = __fmaf_ru(__fmul_ru(uacc, c5[4]), __fadd_ru(__fadd_ru(Nn, Rr), __fmul_ru(2.f, Ll)), eb);
+                                eb = __fadd_ru(eb, __fadd_ru(__fadd_ru(dD, Q.dub[offL + o]), (float)(2.0 * kTau)));
+                                eb = __fmaf_ru(0x1p-23f, __fadd_ru(__fadd_ru(fabsf(yD), fabsf(u)), fabsf(diff)), eb);
+                                if (diff < -eb) f |= VF_UNSAFE;
+                                else if (!(diff > eb)) f |= VF_UNDECIDED;
                             }
-                            const int vv = thr_verdict(da, db, oa, ob);
-                            unsafe = vv == 1;
-                            safe = vv == 0;
                         }
-#pragma unroll
-                        for (int o = 0; o < kTcMaxOut; ++o) {
-                            if (Q.prop == PROP_THRESHOLD || o >= HL) break;
-                            if (o == D) continue;
-                            const float diff = yD - y[o];
-                            const float* c5 = pr + o * 5;
-                            float eb = __fmul_ru(c5[0], __fadd_ru(Rr, 0.f));
-                            eb = __fmaf_ru(c5[1], Nn, eb);
-                            eb = __fmaf_ru(c5[2], Ee, eb);
-                            if (SPLIT) eb = __fmaf_ru(c5[3], Ll, eb);
-                            eb = __fmaf_ru(__fmul_ru(uacc, c5[4]), __fadd_ru(__fadd_ru(Nn, Rr), __fmul_ru(2.f, Ll)), eb);
-                            eb = __fadd_ru(eb, __fadd_ru(__fadd_ru(dD, Q.dub[offL + o]), (float)(2.0 * kTau)));
-                            eb = __fmaf_ru(0x1p-23f, __fadd_ru(__fadd_ru(fabsf(yD), fabsf(y[o])), fabsf(diff)), eb);
-                            if (diff < -eb) unsafe = true;
-                            else if (!(diff > eb)) safe = false;
-                        }
-                        S.vst[r] = unsafe ? 1 : (safe ? 0 : 2);
+                        if (f) atomicOr(&S.vst[r], f);
                         if (unc) S.unc[r] = 1;
                     }
                 }
@@ -874,13 +865,18 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 // ---- per-point results
                 if (hf == 0) {
                     const bool rv = S.valid[r];
-                    bool bad = rv && (S.unc[r] || S.vst[r] == 2);
+                    const int vf = S.vst[r];
+                    const int vv = Q.prop == PROP_THRESHOLD
+                                       ? thr_verdict(vf & VF_D_ABOVE, vf & VF_D_BELOW, vf & VF_O_ABOVE,
+                                                     !(vf & VF_O_NOT_BELOW))
+                                       : ((vf & VF_UNSAFE) ? 1 : ((vf & VF_UNDECIDED) ? 2 : 0));
+                    bool bad = rv && (S.unc[r] || vv == 2);
                     if (rv && !bad && Q.ss)
                         for (int l = 1; l < L; ++l)
                             if (S.fcnt[r][l] == 1 && S.fcnt[r][l + 1] > FCAP) bad = true;
                     const unsigned long long t = S.t[r];
                     queue_push_warp(out, bad, t, (unsigned)q, Q.cnt, out_level);
-                    const bool adv = rv && !bad && S.vst[r] == 1;
+                    const bool adv = rv && !bad && vv == 1;
                     if (!gather) {
                         const unsigned m = __ballot_sync(0xffffffffu, adv);
                         if (m && lane == 0) {
@@ -956,6 +952,12 @@ __global__ void k_classes_tc(const __grid_constant__ TcParams P, NetView net, Qu
         const bool cross = !(fabs(ub) > (b1 + (double)Q.thr[j]) * (1.0 + 1e-6) + 4.0 * kTau);
         if (!cross) atomicOr(ub >= 0.0 ? &Q.cpos[32 + (j >> 5)] : &Q.cneg[32 + (j >> 5)], 1u << (j & 31));
         Bh[j] = (!cross && ub < 0.0) ? 0.0 : b1;
+        if (Q.kcol) {
+            const int cls = cross ? 2 : (ub >= 0.0 ? 0 : 1);
+            Q.kcol[2 * j] = make_float4(Q.ub32[j], 0.f, 0.f, 0.f);
+            Q.kcol[2 * j + 1] = make_float4(Q.thr[j], cls == 2 ? Q.c1[j] : (cls == 0 ? 0.f : -INFINITY),
+                                            cls == 2 ? Q.c2[j] : (cls == 0 ? -INFINITY : 0.f), (float)cls);
+        }
         part += Bh[j] * Bh[j];
     }
     // block reduction helper
@@ -997,6 +999,12 @@ __global__ void k_classes_tc(const __grid_constant__ TcParams P, NetView net, Qu
             if (!cross)
                 atomicOr(ub >= 0.0 ? &Q.cpos[l * 32 + (i >> 5)] : &Q.cneg[l * 32 + (i >> 5)], 1u << (i & 31));
             Bn[i] = (!cross && ub < 0.0) ? 0.0 : B;
+            if (Q.kcol) {
+                const int cls = cross ? 2 : (ub >= 0.0 ? 0 : 1);
+                Q.kcol[2 * gi] = make_float4(Q.ub32[gi], ly.a[i], ly.b1[i], ly.b3[i]);
+                Q.kcol[2 * gi + 1] = make_float4(Q.thr[gi], cls == 2 ? Q.c1[gi] : (cls == 0 ? 0.f : -INFINITY),
+                                                 cls == 2 ? Q.c2[gi] : (cls == 0 ? -INFINITY : 0.f), (float)cls);
+            }
             part2 += Bn[i] * Bn[i];
         }
         __syncthreads();
@@ -1037,8 +1045,17 @@ __global__ void __launch_bounds__(512) k_compact_perm(const __grid_constant__ Tc
             total += wsum[w];
         }
         const int kcl = max(64, (total + 63) & ~63);
-        if (keep) Q.perm[net.noff[l] + before + __popc(m & ((1u << lane) - 1u))] = t;
-        if (t >= total && t < kcl) Q.perm[net.noff[l] + t] = 0;  // padding ("neg" by position)
+        if (keep) {
+            const int pos = before + __popc(m & ((1u << lane) - 1u));
+            Q.perm[net.noff[l] + pos] = t;
+            Q.kcolc[2 * (net.noff[l] + pos)] = Q.kcol[2 * (net.noff[l] + t)];
+            Q.kcolc[2 * (net.noff[l] + pos) + 1] = Q.kcol[2 * (net.noff[l] + t) + 1];
+        }
+        if (t >= total && t < kcl) {  // padding: "neg" by position
+            Q.perm[net.noff[l] + t] = 0;
+            Q.kcolc[2 * (net.noff[l] + t)] = make_float4(0.f, 0.f, 0.f, 0.f);
+            Q.kcolc[2 * (net.noff[l] + t) + 1] = make_float4(0.f, -INFINITY, 0.f, 1.f);
+        }
         if (t == 0) {
             Q.compact = 1;
             Q.kc[l] = kcl;
