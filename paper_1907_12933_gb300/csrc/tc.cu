@@ -52,16 +52,17 @@ constexpr int RPW = 128 / NW;            // layer-1 rows per worker warp
 constexpr int CQ = NW / 4;               // worker warps per TMEM lane quarter
 constexpr int CW = 64 / CQ;              // drain: columns of a 64-column chunk per warp
 constexpr int NA = 4;
-constexpr int NB = 6;
+constexpr int NB = 8;
 constexpr int kStageR = 16;  // layer-1 inner-digit tables are staged in shared memory for R <= kStageR
-constexpr int SLOT = 16384;
+constexpr int SLOT = 16384;             // operand slot: 128 rows x 64 K (16-bit)
+constexpr int SLOTB = 8192;              // weight slot: 64 rows (one N slice) x 64 K
 constexpr int FCAP = 4;
 constexpr int PMAX = 4;
 constexpr int MROWS = 128;
 
 struct TcSmem {
     uint8_t A[NA][SLOT];
-    uint8_t B[NB][SLOT];
+    uint8_t B[NB][SLOTB];
     float souter[PMAX][512];
     unsigned char pdig[PMAX][kMaxS];  // digits of the outer prefix slots
     unsigned long long t[MROWS];
@@ -78,8 +79,12 @@ struct TcSmem {
     int fcnt[MROWS][kTcMaxL + 1];
     short flist[MROWS][kTcMaxL + 1][FCAP];
     uint32_t cflip[256];   // sign changes seen by this CTA for query curq (flushed on change)
-    float4 cst4[NW][CW];   // per worker warp, the CW columns it drains: (ub, a, b, thr)
-    float2 cst2[NW][CW];   //   and the delta-ReLU constants (c1, c2)
+    // column constants of the layer in work, staged once per tile and layer from
+    // the query's kcol arrays; thr' > 0 marks the class "cross" (ub', thr' are 0
+    // for the other classes, whose signs are certain)
+    float4 k1s[512];       // layer 1: (c1, c2, ub', thr')
+    float4 kd4[512];       // drained layer: (ub', ||Wq_i||, ||W_i - Wq_i (- Wlo_i)||, thr')
+    float2 kd2[512];       //   and (c1, c2)
     union {
         // fast layer-1 path: tables of the two inner digits, one 64-column chunk, double-buffered
         float tstage[2][2][kStageR][64];
@@ -430,6 +435,14 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 S.npref = np;
                 S.fast = fast_t;
             }
+            {   // the query's layer-1 column constants, for the build below
+                const float4* __restrict__ kcl = cmp ? Q.kcolc : Q.kcol;
+                for (int e = wtid; e < 64 * S.kch[2]; e += NWT) {
+                    const float4 kA = kcl[2 * e], kB = kcl[2 * e + 1];
+                    const bool cr = kB.w == 2.f;
+                    S.k1s[e] = make_float4(kB.y, kB.z, cr ? kA.x : 0.f, cr ? kB.x : 0.f);
+                }
+            }
             tc::named_bar_sync(1, NWT);
             // layer-1 tables (compacted: column j' holds neuron perm_1[j']) and the
             // number of columns the dense layer 2 reads
@@ -479,15 +492,12 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         if (c + 1 < kch) stage_chunk(c + 1, sbuf ^ 1);
                     }
                     const int j = 64 * c + 2 * lane;  // column (compacted: position) of this lane
-                    // the columns' constants, one coalesced load each (class folded in);
+                    // the columns' constants (staged for the tile, class folded in);
                     // dh = max(du + c1, c2) covers all classes: pos (0, -inf), neg (-inf, 0)
-                    const float4* __restrict__ kcl = cmp ? Q.kcolc : Q.kcol;
-                    const float4 kA0 = kcl[2 * j], kB0 = kcl[2 * j + 1];
-                    const float4 kA1 = kcl[2 * j + 2], kB1 = kcl[2 * j + 3];
-                    const bool cr0 = kB0.w == 2.f, cr1 = kB1.w == 2.f;
-                    const float c10 = kB0.y, c20 = kB0.z, c11 = kB1.y, c21 = kB1.z;
-                    const float ub0 = cr0 ? kA0.x : 0.f, ub1 = cr1 ? kA1.x : 0.f;
-                    const float th0 = cr0 ? kB0.x : 0.f, th1 = cr1 ? kB1.x : 0.f;
+                    const float4 k0 = S.k1s[j], k1 = S.k1s[j + 1];
+                    const bool cr0 = k0.w > 0.f, cr1 = k1.w > 0.f;
+                    const float c10 = k0.x, c20 = k0.y, c11 = k1.x, c21 = k1.y;
+                    const float ub0 = k0.z, ub1 = k1.z, th0 = k0.w, th1 = k1.w;
                     const bool anyc = __any_sync(0xffffffffu, cr0 || cr1);
                     const uint32_t lanepart = (lane & 3) * 4;
                     constexpr int RB = SPLIT ? (RPW < 4 ? RPW : 4) : (RPW < 8 ? RPW : 8);  // rows per batch
@@ -606,6 +616,9 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     }
                     ait += SPLIT ? 2 : 1;
                 }
+                // row sums over the warp (every lane ends with the totals), then lane i
+                // bounds row i's norms: the square roots run in parallel over the lanes
+                float tn = 0.f, tr = 0.f, tl = 0.f;
 #pragma unroll
                 for (int i = 0; i < RPW; ++i) {
                     float a = nsum[i], b = rsum[i], cc = lsum[i];
@@ -616,13 +629,18 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         if (SPLIT) cc += __shfl_xor_sync(0xffffffffu, cc, o);
                     }
                     if (lane == i) {
-                        const int r = wid * RPW + i;
-                        const float N = norm_up(a);
-                        S.N[r] = N;
-                        S.R[r] = norm_up(b);
-                        S.Lo[r] = SPLIT ? norm_up(cc) : 0.f;
-                        S.E[r] = __fmaf_ru(0x1p-24f, N, Q.kvec[1]);
+                        tn = a;
+                        tr = b;
+                        tl = cc;
                     }
+                }
+                if (lane < RPW) {
+                    const int r = wid * RPW + lane;
+                    const float N = norm_up(tn);
+                    S.N[r] = N;
+                    S.R[r] = norm_up(tr);
+                    S.Lo[r] = SPLIT ? norm_up(tl) : 0.f;
+                    S.E[r] = __fmaf_ru(0x1p-24f, N, Q.kvec[1]);
                 }
             }
             tc::named_bar_sync(1, NWT);
@@ -631,9 +649,21 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
             const int r = 32 * qd + lane;
             for (int l = 2; l < L; ++l) {
                 const TcLayer& ly = P.ly[l];
+                {   // this layer's column constants (the previous readers passed a barrier);
+                    // their loads overlap the wait for the layer's MMAs
+                    const float4* __restrict__ kcl = (cmp ? Q.kcolc : Q.kcol) + 2 * net.noff[l];
+                    for (int e = wtid; e < S.np[l]; e += NWT) {
+                        const float4 kA = kcl[2 * e], kB = kcl[2 * e + 1];
+                        const bool cr = kB.w == 2.f;
+                        S.kd4[e] = cr ? make_float4(kA.x, kA.y, SPLIT ? kA.w : kA.z, kB.x)
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+                        S.kd2[e] = make_float2(kB.y, kB.z);
+                    }
+                }
                 tc::mbar_wait(bar(DFULL), dit & 1, abortp);
                 ++dit;
                 tc::tc_fence_after();
+                tc::named_bar_sync(1, NWT);  // the staged constants are visible
                 const float Nn = S.N[r], Rr = S.R[r], Ll = S.Lo[r], Ee = S.E[r];
                 // accumulation: 2^-22 per product that can be nonzero (an exact zero adds nothing)
                 const float uacc = uacc_base * fminf(S.nzl[l - 1], (float)ly.K);
@@ -655,22 +685,9 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     // count are "neg"
                     const bool cl = lane < CW;
                     const int nl = n0 + (cl ? lane : 0);
-                    const float4* __restrict__ kcl = (cmp ? Q.kcolc : Q.kcol) + 2 * (off_l + nl);
-                    const float4 kA = kcl[0], kB = kcl[1];  // this column's constants
-                    const uint32_t cross = __ballot_sync(0xffffffffu, cl && kB.w == 2.f);
+                    // the class "cross" of the warp's columns (thr' > 0; staged constants)
+                    const uint32_t cross = __ballot_sync(0xffffffffu, cl && S.kd4[nl].w > 0.f);
                     const bool rv = S.valid[r];
-                    {  // constants of the warp's columns, one coalesced load each; the
-                       // delta-ReLU constants of the column classes: pos (0, -inf), neg (-inf, 0)
-                        const bool crl = (cross >> lane) & 1u;
-                        const float4 k4 = crl ? make_float4(kA.x, kA.y, SPLIT ? kA.w : kA.z, kB.x)
-                                              : make_float4(0.f, 0.f, 0.f, 0.f);
-                        const float2 k2 = make_float2(kB.y, kB.z);
-                        if (cl) {
-                            S.cst4[wid][lane] = k4;
-                            S.cst2[wid][lane] = k2;
-                        }
-                        __syncwarp();
-                    }
                     if (cross && rv && Q.flip != nullptr) {  // signs matter only for coverage
                         // no stores in the loop (its loads pipeline): uncertain signs and
                         // certain changes as bits, handled after
@@ -682,7 +699,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                             if ((cross >> (8 * g)) & 0xFFu) {
 #pragma unroll
                                 for (int i = 8 * g; i < 8 * g + 8; ++i) {
-                                    const float4 k4 = S.cst4[wid][i];
+                                    const float4 k4 = S.kd4[n0 + i];
                                     const float u = k4.x + v[i];
                                     const float bound = __fmaf_ru(k4.y, Pa, __fmaf_ru(k4.z, Pb, k4.w));
                                     const bool cert = __fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound;
@@ -706,7 +723,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     // delta ReLU; no stores in this loop, so its loads pipeline
 #pragma unroll
                     for (int i = 0; i < CW; ++i) {
-                        const float2 k2 = S.cst2[wid][i];
+                        const float2 k2 = S.kd2[n0 + i];
                         v[i] = fmaxf(v[i] + k2.x, k2.y);
                     }
                     __syncwarp();  // the staged constants are read before the next chunk overwrites them
@@ -1443,7 +1460,7 @@ static vbmc_status build_prec(TcNet& tc, const NetView& v, const std::vector<std
         ly.K = K;
         ly.N = N;
         ly.Npad = Npad;
-        ly.slice = std::min(Npad, 128);
+        ly.slice = std::min(Npad, 64);  // one 8 KB weight slot per N slice
         ly.nslice = Npad / ly.slice;
         ly.kch = K / 64;
         std::vector<T> hq((size_t)Npad * K), hlo((size_t)Npad * K);
