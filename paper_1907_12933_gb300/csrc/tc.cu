@@ -69,6 +69,9 @@ struct TcSmem {
     int valid[MROWS];
     int pidx[MROWS];
     int4 rinfo[MROWS];     // layer-1 fast path: {prefix slot, inner table offsets a, b, valid}
+    int4 winfo[NW];        // pair path: per worker warp {souter offset, digit s-2, digit s-1 of its
+                           // first row, first row of the next (prefix, digit s-2) pair (RPW: none)}
+    int2 winfo2[NW];       //   and that next pair's {souter offset, digit s-2}
     int fast;              // every valid row of the tile uses the fast path
     int pixs[kMaxS];       // the query's pixel indices
     float N[MROWS], R[MROWS], Lo[MROWS], E[MROWS];
@@ -390,7 +393,24 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     ok = t >= Q.lo && t < Q.hi;
                 }
                 int d[kMaxS];
-                decode_digits(ok ? t : 0, s, R, d);
+                const bool quick = fast_t && !Q.filter;  // only the two inner digits and the prefix
+                unsigned long long tq = 0;               // t / R^ni (quick decode)
+                if (quick) {
+                    const unsigned long long tt = t;  // range mode: every row has its index
+                    unsigned rr;
+                    if (tt < 0xFFFFFFFFull && Rni < 0xFFFFFFFFull) {
+                        const unsigned t32 = (unsigned)tt, r2 = (unsigned)Rni, q32 = t32 / r2;
+                        tq = q32;
+                        rr = t32 - q32 * r2;
+                    } else {
+                        tq = tt / Rni;
+                        rr = (unsigned)(tt - tq * Rni);
+                    }
+                    d[s - 2] = (int)(rr / (unsigned)R);
+                    d[s - 1] = (int)(rr - (unsigned)d[s - 2] * (unsigned)R);
+                } else {
+                    decode_digits(ok ? t : 0, s, R, d);
+                }
                 if (ok && !gather && Q.filter) ok = in_filter(Q, d);  // L2 ball / shell
                 if (!gather && Q.filter) {  // points that pass the filter are counted here
                     const unsigned vm = __ballot_sync(0xffffffffu, ok);
@@ -406,7 +426,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     for (int p = 0; p < s; ++p) S.cpx[r][p] = __fdiv_rn((float)Q.dv[p * R + d[p]], 255.f);
                 int pi = -1;
                 if (pre && ok) {
-                    const unsigned long long k = t / Rni - p0;
+                    const unsigned long long k = (quick ? tq : t / Rni) - p0;
                     if (k < (unsigned long long)PMAX) pi = (int)k;
                 }
                 S.pidx[r] = pi;
@@ -423,6 +443,26 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 }
                 ri.w = ok;
                 S.rinfo[r] = ri;
+                if (quick && stage_t && R >= RPW && (r % RPW) == 0) {
+                    // the warp's RPW consecutive rows: digit s-1 runs up from its first row's
+                    // and wraps at most once (R >= RPW), moving to the next (prefix, digit
+                    // s-2) pair. Slots from the first row's true prefix offset (it may lie
+                    // before lo: then every row of its pair does); rows outside [lo, hi)
+                    // are masked off by their validity, so their slots are only clamped
+                    const int d4 = d[s - 2], d5 = d[s - 1];
+                    const int wrap = R - d5;  // first row of the next pair
+                    const long long ka = pre ? (long long)tq - (long long)p0 : 0;
+                    long long kb = ka;
+                    int d4_b = d4 + 1;
+                    if (d4_b == R) {
+                        d4_b = 0;
+                        kb = ka + 1;
+                    }
+                    const int sa = (int)(ka < 0 ? 0 : (ka >= PMAX ? PMAX - 1 : ka));
+                    const int sb = (int)(kb < 0 ? 0 : (kb >= PMAX ? PMAX - 1 : kb));
+                    S.winfo[r / RPW] = make_int4(sa * 512, d4, d5, wrap < RPW ? wrap : RPW);
+                    S.winfo2[r / RPW] = make_int2(sb * 512, d4_b);
+                }
             } else if (wtid >= MROWS + 64 && wtid - (MROWS + 64) < s) {
                 S.pixs[wtid - (MROWS + 64)] = Q.pix[wtid - (MROWS + 64)];  // validated by the prologue
             } else if (wtid - MROWS < np) {  // digits of outer prefix slot k
@@ -472,6 +512,8 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 // fast path with R <= kStageR: the tables of the two inner digits for a
                 // chunk's 64 columns go to shared memory one chunk ahead (cp.async)
                 const bool stage = fast && R <= kStageR;
+                const bool pairs = stage && R >= RPW && !Q.filter;  // see winfo
+                const unsigned wvalid = __ballot_sync(0xffffffffu, lane < RPW && S.valid[wid * RPW + lane]);
                 auto stage_chunk = [&](int c, int buf) {
                     for (int e = wtid; e < 2 * R * 16; e += NWT) {
                         const int tt = e / (R * 16), rem = e - tt * (R * 16), dgt = rem >> 4, u = rem & 15;
@@ -507,7 +549,37 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     float2 dus[RB];
                     unsigned vbits = 0;  // valid rows of the batch (the compute loop stores to
                                          // shared memory, so it reloads nothing)
-                    if (fast) {
+                    if (pairs) {
+                        // the warp's rows share at most two (prefix, digit s-2) pairs: their
+                        // sums souter + table(s-2) once per lane, then + table(s-1) per row,
+                        // in the order of the per-row path
+                        const int4 wa = S.winfo[wid];
+                        const float* ts = &S.tstage[sbuf][0][0][2 * lane];
+                        float2 s1a = nosum ? make_float2(0.f, 0.f)
+                                           : *reinterpret_cast<const float2*>(&S.souter[0][0] + wa.x + j);
+                        const float2 taa = *reinterpret_cast<const float2*>(ts + wa.y * 64);
+                        s1a.x = s1a.x + taa.x;
+                        s1a.y = s1a.y + taa.y;
+                        float2 s1b = s1a;
+                        if (wa.w < RPW) {  // warp-uniform
+                            const int2 wb = S.winfo2[wid];
+                            s1b = nosum ? make_float2(0.f, 0.f)
+                                        : *reinterpret_cast<const float2*>(&S.souter[0][0] + wb.x + j);
+                            const float2 tab_ = *reinterpret_cast<const float2*>(ts + wb.y * 64);
+                            s1b.x = s1b.x + tab_.x;
+                            s1b.y = s1b.y + tab_.y;
+                        }
+                        vbits = (wvalid >> i0) & ((1u << RB) - 1u);
+#pragma unroll
+                        for (int ii = 0; ii < RB; ++ii) {
+                            const int i = i0 + ii;
+                            const bool second = i >= wa.w;
+                            const int d5 = wa.z + i - (second ? R : 0);
+                            const float2 tb = *reinterpret_cast<const float2*>(ts + (kStageR + d5) * 64);
+                            const float2 s1 = second ? s1b : s1a;
+                            dus[ii] = make_float2(s1.x + tb.x, s1.y + tb.y);
+                        }
+                    } else if (fast) {
 #pragma unroll
                         for (int ii = 0; ii < RB; ++ii) {
                             const int r = wid * RPW + i0 + ii;
@@ -879,8 +951,10 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(bar(TFREE));
                 tc::named_bar_sync(1, NWT);
-                // ---- per-point results
-                if (hf == 0) {
+                // ---- per-point results: the warps of a lane quarter split the three
+                // independent parts (queue, verdict counts and bitmap, SS-Cover bits)
+                static_assert(CQ >= 3, "the results need three warps per lane quarter");
+                if (hf < 3) {
                     const bool rv = S.valid[r];
                     const int vf = S.vst[r];
                     const int vv = Q.prop == PROP_THRESHOLD
@@ -892,19 +966,19 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         for (int l = 1; l < L; ++l)
                             if (S.fcnt[r][l] == 1 && S.fcnt[r][l + 1] > FCAP) bad = true;
                     const unsigned long long t = S.t[r];
-                    queue_push_warp(out, bad, t, (unsigned)q, Q.cnt, out_level);
                     const bool adv = rv && !bad && vv == 1;
-                    if (!gather) {
+                    if (hf == 0) {
+                        queue_push_warp(out, bad, t, (unsigned)q, Q.cnt, out_level);
+                    } else if (hf == 1 && !gather) {
                         const unsigned m = __ballot_sync(0xffffffffu, adv);
                         if (m && lane == 0) {
                             atomicAdd(&Q.cnt->n_adv, (unsigned long long)__popc(m));
                             atomicMin(&Q.cnt->first, t + (unsigned)(__ffs(m) - 1));
                             if (Q.bitmap && t < Q.bitmap_bits) atomicOr(&Q.bitmap[t >> 5], m);
                         }
-                    } else if (adv) {
+                    } else if (hf == 1 && adv) {
                         record_adversarial(Q, t);
-                    }
-                    if (rv && !bad && Q.ss) {
+                    } else if (hf == 2 && rv && !bad && Q.ss) {
                         for (int l = 1; l < L; ++l) {
                             if (S.fcnt[r][l] != 1) continue;  // SS needs exactly one change
                             const int j = S.flist[r][l][0];
