@@ -52,10 +52,10 @@ constexpr int RPW = 128 / NW;            // layer-1 rows per worker warp
 constexpr int CQ = NW / 4;               // worker warps per TMEM lane quarter
 constexpr int CW = 64 / CQ;              // drain: columns of a 64-column chunk per warp
 constexpr int NA = 4;
-constexpr int NB = 8;
+constexpr int NB = 4;
 constexpr int kStageR = 16;  // layer-1 inner-digit tables are staged in shared memory for R <= kStageR
 constexpr int SLOT = 16384;             // operand slot: 128 rows x 64 K (16-bit)
-constexpr int SLOTB = 8192;              // weight slot: 64 rows (one N slice) x 64 K
+constexpr int SLOTB = 16384;             // weight slot: 128 rows (one N slice) x 64 K
 constexpr int FCAP = 4;
 constexpr int PMAX = 4;
 constexpr int MROWS = 128;
@@ -205,7 +205,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
             const int Nc = P.compact && l < L ? qs[0].kc[l] : ly.Npad;
             S.kch[l] = Kc / 64;
             S.np[l] = Nc;
-            S.nsl[l] = Nc / ly.slice;
+            S.nsl[l] = (Nc + ly.slice - 1) / ly.slice;  // the last slice may be narrower
         }
         tc::fence_mbar_init();
     }
@@ -269,7 +269,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         ++drit;
                         tc::tc_fence_after();
                     }
-                    const uint32_t idesc = tc::idesc_f16(128, ly.slice, BF);
+                    // N of each slice: ly.slice, the last one what is left (a multiple of 64)
                     for (int kc = 0; kc < S.kch[l] && ok; ++kc) {
                         const int a0 = ait % NA, a1 = (ait + 1) % NA;
                         if (!tc::mbar_wait(bar(AFULL(a0)), (ait / NA) & 1, abortp)) { ok = false; break; }
@@ -289,6 +289,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                             tc::tc_fence_after();
                             const uint32_t bb0 = tc::smem_u32(S.B[b0]), bb1 = tc::smem_u32(S.B[b1]);
                             const uint32_t d = tmem + (uint32_t)(s * ly.slice);
+                            const uint32_t idesc = tc::idesc_f16(128, min(ly.slice, S.np[l] - s * ly.slice), BF);
 #pragma unroll
                             for (int ks = 0; ks < 4; ++ks) {
                                 const uint64_t ad = tc::desc_sw128(ab0 + ks * 32);
@@ -1534,7 +1535,7 @@ static vbmc_status build_prec(TcNet& tc, const NetView& v, const std::vector<std
         ly.K = K;
         ly.N = N;
         ly.Npad = Npad;
-        ly.slice = std::min(Npad, 64);  // one 8 KB weight slot per N slice
+        ly.slice = std::min(Npad, 128);  // one 16 KB weight slot per N slice
         ly.nslice = Npad / ly.slice;
         ly.kch = K / 64;
         std::vector<T> hq((size_t)Npad * K), hlo((size_t)Npad * K);
@@ -1716,7 +1717,7 @@ void tc_launch_query_setup(TcNet& tc, const NetView& v, QueryView* d_q, int nq, 
 namespace {
 
 // Kernel parameters of a compacted call: the net's, with the weight maps of
-// the query's own copies and 64-row slices for the hidden layers.
+// the query's own copies and 128-row slices for the hidden layers.
 bool compact_params(const TcParams& P, const NetView& v, TcQueryWork& qw, int pi, TcParams& out) {
     if (!qw.maps[pi]) {
         PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -1727,7 +1728,7 @@ bool compact_params(const TcParams& P, const NetView& v, TcQueryWork& qw, int pi
         const CUtensorMapDataType dt = pi == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
         for (int l = 2; l <= v.L; ++l) {
             const TcLayer& ly = P.ly[l];
-            const int slice = l == v.L ? ly.slice : 64;
+            const int slice = l == v.L ? ly.slice : 128;
             cuuint64_t gdim[2] = {(cuuint64_t)ly.K, (cuuint64_t)ly.Npad};
             cuuint64_t gstr[1] = {(cuuint64_t)ly.K * 2};
             cuuint32_t box[2] = {64, (cuuint32_t)slice};
@@ -1747,7 +1748,7 @@ bool compact_params(const TcParams& P, const NetView& v, TcQueryWork& qw, int pi
     for (int l = 2; l <= v.L; ++l) {
         out.tq[l] = qw.tq[pi][l];
         out.tlo[l] = qw.tlo[pi][l];
-        if (l < v.L) out.ly[l].slice = 64;
+        if (l < v.L) out.ly[l].slice = 128;
     }
     return true;
 }

@@ -35,7 +35,7 @@ struct TcParams {
     int bf16;                      // 1: bf16 operands, 0: fp16
     float acc_unit;                // MMA accumulation error per product (tc_f16_selftest)
     int compact;                   // 1: per-query compacted columns (tq/tlo then map the
-                                   // query's own weight copies; hidden layers in 64-row slices)
+                                   // query's own weight copies; hidden layers in 128-row slices)
 };
 
 // Per-result workspace of the compacted screen: the query's copies of Wq_l and
