@@ -51,9 +51,11 @@ constexpr int TC_THREADS = 64 + NWT;     // + TMA producer warp + MMA warp
 constexpr int RPW = 128 / NW;            // layer-1 rows per worker warp
 constexpr int CQ = NW / 4;               // worker warps per TMEM lane quarter
 constexpr int CW = 64 / CQ;              // drain: columns of a 64-column chunk per warp
+constexpr int kPfx0 = 160;               // decode phase: worker threads from here sum the prefixes
 constexpr int NA = 4;
 constexpr int NB = 4;
 constexpr int kStageR = 16;  // layer-1 inner-digit tables are staged in shared memory for R <= kStageR
+constexpr int kStageAll = 4; // with at most this many 64-column chunks, all of them at the tile's start
 constexpr int SLOT = 16384;             // operand slot: 128 rows x 64 K (16-bit)
 constexpr int SLOTB = 16384;             // weight slot: 128 rows (one N slice) x 64 K
 constexpr int FCAP = 4;
@@ -64,7 +66,6 @@ struct TcSmem {
     uint8_t A[NA][SLOT];
     uint8_t B[NB][SLOTB];
     float souter[PMAX][512];
-    unsigned char pdig[PMAX][kMaxS];  // digits of the outer prefix slots
     unsigned long long t[MROWS];
     int valid[MROWS];
     int pidx[MROWS];
@@ -90,7 +91,7 @@ struct TcSmem {
     float2 kd2[512];       //   and (c1, c2)
     union {
         // fast layer-1 path: tables of the two inner digits, one 64-column chunk, double-buffered
-        float tstage[2][2][kStageR][64];
+        float tstage[kStageAll][2][kStageR][64];
         // other tiles: per row and pixel fl(dv_p / 255), the pixel's input change
         float cpx[MROWS][kMaxS];
     };
@@ -373,14 +374,34 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 const unsigned long long t0 = base + gq * MROWS;
                 const unsigned long long ta = t0 > Q.lo ? t0 : Q.lo;
                 const unsigned long long tb = (t0 + MROWS < Q.hi ? t0 + MROWS : Q.hi) - 1;
-                p0 = ta / Rni;
-                np_need = tb / Rni - p0 + 1;
+                if (tb < 0xFFFFFFFFull && Rni < 0xFFFFFFFFull) {  // 32-bit division when it fits
+                    p0 = (unsigned)ta / (unsigned)Rni;
+                    np_need = (unsigned)tb / (unsigned)Rni - p0 + 1;
+                } else {
+                    p0 = ta / Rni;
+                    np_need = tb / Rni - p0 + 1;
+                }
             }
             const int np = (int)(np_need < (unsigned long long)PMAX ? np_need : PMAX);
             // fast layer-1 path: every valid row has its prefix slot (or s = 2: none needed);
             // with R <= kStageR its inner-digit tables come from shared memory
             const bool fast_t = !gather && ((ni == 2 && s > 2 && np_need <= (unsigned long long)PMAX) || s == 2);
             const bool stage_t = fast_t && R <= kStageR;
+            // layer-1 tables (compacted: column j' holds neuron perm_1[j']) and the
+            // number of columns the dense layer 2 reads
+            const float* __restrict__ tabq = cmp ? Q.tabc : Q.tab;
+            const int W1cols = 64 * S.kch[2];
+            if (stage_t && S.kch[2] <= kStageAll) {
+                // the two inner digits' tables of every chunk, copied while the rows decode
+                const int per = 2 * R * 16;  // 16-byte units per chunk
+                for (int e = wtid; e < S.kch[2] * per; e += NWT) {
+                    const int c = e / per, rem0 = e - c * per;
+                    const int tt = rem0 / (R * 16), rem = rem0 - tt * (R * 16), dgt = rem >> 4, u = rem & 15;
+                    cp_async16(&S.tstage[c][tt][dgt][4 * u],
+                               tabq + ((size_t)(s - 2 + tt) * R + dgt) * H1 + 64 * c + 4 * u);
+                }
+                cp_async_commit();
+            }
             if (wtid < MROWS) {
                 const int r = wtid;
                 unsigned long long t = 0;
@@ -466,11 +487,24 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 }
             } else if (wtid >= MROWS + 64 && wtid - (MROWS + 64) < s) {
                 S.pixs[wtid - (MROWS + 64)] = Q.pix[wtid - (MROWS + 64)];  // validated by the prologue
-            } else if (wtid - MROWS < np) {  // digits of outer prefix slot k
-                const int k = wtid - MROWS;
-                int dd[kMaxS];
-                decode_digits(p0 + (unsigned long long)k, s - ni, R, dd);
-                for (int p = 0; p < s - ni; ++p) S.pdig[k][p] = (unsigned char)dd[p];
+            }
+            if (pre && wtid >= kPfx0) {
+                // outer-prefix partial sums of layer 1, while the rows decode: slot k is
+                // the prefix p0 + k (digits by carry from those of p0), summed over the
+                // outer pixels in order
+                int pd[kMaxS];
+                decode_digits(p0, s - ni, R, pd);
+                for (int k = 0; k < np; ++k) {
+                    for (int j = wtid - kPfx0; j < W1cols; j += NWT - kPfx0) {
+                        float acc = 0.f;
+                        for (int p = 0; p < s - ni; ++p) acc += __ldg(&tabq[((size_t)p * R + pd[p]) * H1 + j]);
+                        S.souter[k][j] = acc;
+                    }
+                    for (int p = s - ni - 1; p >= 0; --p) {
+                        if (++pd[p] < R) break;
+                        pd[p] = 0;
+                    }
+                }
             }
             if (wtid == 0) {
                 S.npref = np;
@@ -484,21 +518,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     S.k1s[e] = make_float4(kB.y, kB.z, cr ? kA.x : 0.f, cr ? kB.x : 0.f);
                 }
             }
-            tc::named_bar_sync(1, NWT);
-            // layer-1 tables (compacted: column j' holds neuron perm_1[j']) and the
-            // number of columns the dense layer 2 reads
-            const float* __restrict__ tabq = cmp ? Q.tabc : Q.tab;
-            const int W1cols = 64 * S.kch[2];
-
-            // outer-prefix partial sums of layer 1
-            for (int k = 0; k < S.npref; ++k) {
-                for (int j = wtid; j < W1cols; j += NWT) {
-                    float acc = 0.f;
-                    for (int p = 0; p < s - ni; ++p)
-                        acc += __ldg(&tabq[((size_t)p * R + S.pdig[k][p]) * H1 + j]);
-                    S.souter[k][j] = acc;
-                }
-            }
+            cp_async_wait_all();  // this thread's table copies (staged at once) have landed
             tc::named_bar_sync(1, NWT);
 
             // ---- W1: layer-1 deltas -> operand of layer 2 (rows wid*RPW .. +RPW-1,
@@ -523,13 +543,15 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     }
                     cp_async_commit();
                 };
-                if (stage) stage_chunk(0, 0);
+                // all chunks' tables were staged during the decode, or chunk by chunk here
+                const bool stage_all = stage && kch <= kStageAll;
+                if (stage && !stage_all) stage_chunk(0, 0);
                 for (int c = 0; c < kch; ++c) {
                     const int a0 = ait % NA, a1 = (ait + 1) % NA;
                     tc::mbar_wait(bar(AEMPTY(a0)), ((ait / NA) & 1) ^ 1, abortp);
                     if (SPLIT) tc::mbar_wait(bar(AEMPTY(a1)), (((ait + 1) / NA) & 1) ^ 1, abortp);
-                    const int sbuf = c & 1;
-                    if (stage) {
+                    const int sbuf = stage_all ? c : (c & 1);
+                    if (stage && !stage_all) {
                         cp_async_wait_all();            // this thread's copies of chunk c
                         tc::named_bar_sync(1, NWT);     // everyone's; and chunk c-1's buffer is no longer read
                         if (c + 1 < kch) stage_chunk(c + 1, sbuf ^ 1);
