@@ -86,7 +86,9 @@ struct TcSmem {
     // column constants of the layer in work, staged once per tile and layer from
     // the query's kcol arrays; thr' > 0 marks the class "cross" (ub', thr' are 0
     // for the other classes, whose signs are certain)
-    float4 k1s[512];       // layer 1: (c1, c2, ub', thr')
+    float4 k1p[256];       // layer 1, per column pair (2i, 2i+1): (c1, c2, c1, c2)
+    float4 k1u[256];       //   and (ub', thr', ub', thr') (read only where a column is "cross")
+    uint2 k1cm[8];         //   per 64-column chunk: the "cross" columns 2 lane (x), 2 lane + 1 (y)
     float4 kd4[512];       // drained layer: (ub', ||Wq_i||, ||W_i - Wq_i (- Wlo_i)||, thr')
     float2 kd2[512];       //   and (c1, c2)
     union {
@@ -510,12 +512,17 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 S.npref = np;
                 S.fast = fast_t;
             }
-            {   // the query's layer-1 column constants, for the build below
+            {   // the query's layer-1 column constants, for the build below: warp c of the
+                // loop takes chunk c (its lanes the column pairs), whole warps only
                 const float4* __restrict__ kcl = cmp ? Q.kcolc : Q.kcol;
-                for (int e = wtid; e < 64 * S.kch[2]; e += NWT) {
-                    const float4 kA = kcl[2 * e], kB = kcl[2 * e + 1];
-                    const bool cr = kB.w == 2.f;
-                    S.k1s[e] = make_float4(kB.y, kB.z, cr ? kA.x : 0.f, cr ? kB.x : 0.f);
+                for (int e = wtid; e < 32 * S.kch[2]; e += NWT) {
+                    const float4 kA0 = kcl[4 * e], kB0 = kcl[4 * e + 1];
+                    const float4 kA1 = kcl[4 * e + 2], kB1 = kcl[4 * e + 3];
+                    const bool cr0 = kB0.w == 2.f, cr1 = kB1.w == 2.f;
+                    S.k1p[e] = make_float4(kB0.y, kB0.z, kB1.y, kB1.z);
+                    S.k1u[e] = make_float4(cr0 ? kA0.x : 0.f, cr0 ? kB0.x : 0.f, cr1 ? kA1.x : 0.f, cr1 ? kB1.x : 0.f);
+                    const unsigned m0 = __ballot_sync(0xffffffffu, cr0), m1 = __ballot_sync(0xffffffffu, cr1);
+                    if ((e & 31) == 0) S.k1cm[e >> 5] = make_uint2(m0, m1);
                 }
             }
             cp_async_wait_all();  // this thread's table copies (staged at once) have landed
@@ -559,11 +566,19 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     const int j = 64 * c + 2 * lane;  // column (compacted: position) of this lane
                     // the columns' constants (staged for the tile, class folded in);
                     // dh = max(du + c1, c2) covers all classes: pos (0, -inf), neg (-inf, 0)
-                    const float4 k0 = S.k1s[j], k1 = S.k1s[j + 1];
-                    const bool cr0 = k0.w > 0.f, cr1 = k1.w > 0.f;
-                    const float c10 = k0.x, c20 = k0.y, c11 = k1.x, c21 = k1.y;
-                    const float ub0 = k0.z, ub1 = k1.z, th0 = k0.w, th1 = k1.w;
-                    const bool anyc = __any_sync(0xffffffffu, cr0 || cr1);
+                    const float4 kp = S.k1p[32 * c + lane];
+                    const uint2 cm = S.k1cm[c];
+                    const bool cr0 = (cm.x >> lane) & 1u, cr1 = (cm.y >> lane) & 1u;
+                    const bool anyc = (cm.x | cm.y) != 0u;  // warp-uniform
+                    const float c10 = kp.x, c20 = kp.y, c11 = kp.z, c21 = kp.w;
+                    float ub0 = 0.f, th0 = 0.f, ub1 = 0.f, th1 = 0.f;
+                    if (anyc) {
+                        const float4 ku = S.k1u[32 * c + lane];
+                        ub0 = ku.x;
+                        th0 = ku.y;
+                        ub1 = ku.z;
+                        th1 = ku.w;
+                    }
                     const uint32_t lanepart = (lane & 3) * 4;
                     constexpr int RB = SPLIT ? (RPW < 4 ? RPW : 4) : (RPW < 8 ? RPW : 8);  // rows per batch
 #pragma unroll
