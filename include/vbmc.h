@@ -150,6 +150,21 @@ typedef struct {
                          * count (shortest job first) and runs them in up to
                          * 8 waves of about equal work, each a full chain of
                          * passes: a query is final when its wave ends   */
+    double time_budget_ms; /* one query (verify_query / _device), BF16/FP16
+                         * fused screen or FP32 path: device-time budget from
+                         * the call's prologue, 0 for none. The first pass
+                         * takes its tiles of [lo, hi) in index order and
+                         * takes none after the budget; every tile taken is
+                         * finished, rechecks included, so the result is exact
+                         * for the checked prefix [lo, checked_hi) of the
+                         * summary, and the call returns VBMC_ERR_TIMEOUT when
+                         * that prefix is shorter than [lo, hi); the result
+                         * handle then holds that prefix's result (summary and
+                         * get_* calls read it). A timed-out check resumes
+                         * with lo = checked_hi (results of ranges merge:
+                         * sums, min, bitwise or). Other paths
+                         * (FP64, FP8, wide layers, small nets, batches)
+                         * check the whole range.                         */
 } vbmc_options;
 
 /* Capacities fixed when a result handle is created. */
@@ -189,6 +204,8 @@ typedef struct {
                                 * FP32 pass, double-float pass, FP64 pass
                                 * (batch: first wave; wide-layer path: all
                                 * in ms_screen, its chunks interleave)     */
+    uint64_t checked_hi;       /* end of the checked prefix [lo, checked_hi)
+                                * (hi unless the time budget ran out)      */
 } vbmc_summary;
 
 typedef struct vbmc_net vbmc_net;

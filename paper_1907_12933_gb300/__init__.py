@@ -28,6 +28,15 @@ class VbmcError(RuntimeError):
         self.status = status
 
 
+class VbmcTimeout(VbmcError):
+    """VBMC_ERR_TIMEOUT: the time budget ran out; `summary` is the result of the
+    checked prefix [lo, summary["checked_hi"])."""
+
+    def __init__(self, status: int, msg: str, summary: dict):
+        super().__init__(status, msg)
+        self.summary = summary
+
+
 class _MlpDesc(C.Structure):
     _fields_ = [("n_layers", C.c_int32), ("dims", C.POINTER(C.c_int32)),
                 ("W", C.POINTER(C.POINTER(C.c_float))), ("b", C.POINTER(C.POINTER(C.c_float))),
@@ -60,7 +69,7 @@ def l2_max_of(radius: float) -> int:
 
 class _Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("coverage", C.c_int32), ("bitmap", C.c_int32),
-                ("graph", C.c_int32), ("schedule", C.c_int32)]
+                ("graph", C.c_int32), ("schedule", C.c_int32), ("time_budget_ms", C.c_double)]
 
 
 SCHEDULES = {"given": 0, "small_first": 1}
@@ -78,7 +87,7 @@ class _Summary(C.Structure):
                 ("n_recheck", C.c_uint64 * 4), ("ms_device", C.c_double),
                 ("ms_prologue", C.c_double), ("ms_screen", C.c_double),
                 ("ms_recheck", C.c_double), ("ms_to_verdict", C.c_double),
-                ("ms_pass", C.c_double * 4)]
+                ("ms_pass", C.c_double * 4), ("checked_hi", C.c_uint64)]
 
 
 class _SearchOut(C.Structure):
@@ -283,10 +292,11 @@ def result_create_batch(net: Net, nq: int, max_points: int = 0, max_s: int = MAX
     return out
 
 
-def _options(precision, coverage, bitmap, graph=False, schedule="given"):
+def _options(precision, coverage, bitmap, graph=False, schedule="given", time_budget_ms=0.0):
     p = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     sc = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
-    return _Options(p, int(bool(coverage)), int(bool(bitmap)), int(bool(graph)), sc)
+    return _Options(p, int(bool(coverage)), int(bool(bitmap)), int(bool(graph)), sc,
+                    float(time_budget_ms))
 
 
 def _summary_dict(s: _Summary) -> dict:
@@ -295,22 +305,27 @@ def _summary_dict(s: _Summary) -> dict:
             "first_witness": None if s.first_witness == NO_WITNESS else int(s.first_witness),
             "n_ties": s.n_ties, "n_recheck": list(s.n_recheck), "ms_device": s.ms_device,
             "ms_prologue": s.ms_prologue, "ms_screen": s.ms_screen, "ms_recheck": s.ms_recheck,
-            "ms_to_verdict": s.ms_to_verdict, "ms_pass": list(s.ms_pass)}
+            "ms_to_verdict": s.ms_to_verdict, "ms_pass": list(s.ms_pass),
+            "checked_hi": int(s.checked_hi)}
 
 
 def verify_query(net: Net, res: Result, image, pixels, k: int, lo: int = 0, hi: int = 0,
                  precision="fp32", coverage: bool = True, bitmap: bool = True,
                  filter: int = 0, l2_max: int = 0, threshold: float | None = None,
-                 stream: int | None = None, wait: bool = True) -> dict | None:
+                 stream: int | None = None, wait: bool = True,
+                 time_budget_ms: float = 0.0) -> dict | None:
     """vbmc_verify_query: host inputs; with wait (default) blocks until the result
     is final and returns its summary, else returns once the work is enqueued.
     filter: FILTER_L2 (with l2_max) and/or FILTER_SHELL; threshold V: check Eq. 11."""
     img = np.ascontiguousarray(image, dtype=np.uint8)
     pix = np.ascontiguousarray(pixels, dtype=np.int32)
     q = _query(img, pix, k, lo, hi, filter, l2_max, threshold)
-    opt = _options(precision, coverage, bitmap)
+    opt = _options(precision, coverage, bitmap, time_budget_ms=time_budget_ms)
     st = current_stream() if stream is None else stream
-    _check(lib().vbmc_verify_query(net.h, C.byref(q), C.byref(opt), res.h, C.c_void_p(st)))
+    rc = lib().vbmc_verify_query(net.h, C.byref(q), C.byref(opt), res.h, C.c_void_p(st))
+    if rc == -4:  # VBMC_ERR_TIMEOUT: the result holds the checked prefix
+        raise VbmcTimeout(rc, lib().vbmc_last_error().decode(), result_summary_partial(res))
+    _check(rc)
     return result_summary(res) if wait else None
 
 
@@ -346,6 +361,13 @@ def verify_batch(net: Net, results: list, queries: list, precision="fp32",
     st = current_stream() if stream is None else stream
     _check(lib().vbmc_verify_batch(net.h, qs, len(queries), C.byref(opt), hs, C.c_void_p(st)))
     return [result_summary(r) for r in results]
+
+
+def result_summary_partial(res: Result) -> dict:
+    """vbmc_result_summary of a call that timed out (the summary of its prefix)."""
+    s = _Summary()
+    lib().vbmc_result_summary(res.h, C.byref(s))
+    return _summary_dict(s)
 
 
 def result_summary(res: Result) -> dict:

@@ -89,12 +89,18 @@ struct BatchArena {
     uint8_t* d_stage = nullptr;
     size_t stage_stride = 0;
     unsigned long long* d_qcount = nullptr;
+    unsigned long long* d_claim = nullptr;  // tile claims of each wave's first pass
     QEntry* d_queue[4] = {nullptr, nullptr, nullptr, nullptr};
     uint64_t queue_cap = 0;
     cudaEvent_t ev[7] = {};  // start, prologue, screen, end, split, FP32, double-float
     cudaEvent_t evw = nullptr;       // marks between waves (not read)
     cudaStream_t gstream = nullptr;  // graph capture needs a capturable (non-legacy) stream
     cudaEvent_t gev = nullptr;
+    // the pass chain of the last graph call, instantiated, and the shapes it was
+    // captured for (kernel arguments depend only on them; the queries' data and
+    // tile prefixes are copied in before each launch)
+    cudaGraphExec_t gexec = nullptr;
+    std::string gsig;
     std::vector<void*> owned;
 };
 
@@ -118,6 +124,10 @@ struct vbmc_result {
     unsigned long long* d_tiles = nullptr;  // VBMC_MAX_TILES counters of vbmc_tile_counts
     TcQueryWork tw{};  // compacted operands of the fused tensor screen (single-query calls)
     bool have_tw = false;
+    unsigned long long* d_claim = nullptr;  // tile claim counter of the first pass
+    unsigned long long* h_claim = nullptr;  // pinned copy after the call
+    unsigned long long ntiles = 0;          // first-pass tiles of the last call
+    int tile_pts = 0;                       // points per first-pass tile (0: no claim counter)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_pro = nullptr, ev_scr = nullptr;
     cudaEvent_t ev_split = nullptr, ev_f32 = nullptr, ev_df = nullptr;  // after each recheck pass
     cudaStream_t last_stream = nullptr;
@@ -345,6 +355,7 @@ vbmc_status create_result(const vbmc_net* net, const vbmc_caps* caps, BatchArena
     r->caps.queue_cap = qc;
     for (int i = 0; i < 4; ++i) A(&r->d_queue[i], (size_t)qc);
     A(&r->d_tiles, (size_t)VBMC_MAX_TILES);
+    A(&r->d_claim, 1);
     // compacted columns of the fused tensor screen (calls with one query)
     const bool tcnet = tc_supported(v, VBMC_PREC_BF16) || tc_supported(v, VBMC_PREC_FP16);
     const bool fused = !arena && tcnet;
@@ -358,6 +369,7 @@ vbmc_status create_result(const vbmc_net* net, const vbmc_caps* caps, BatchArena
         for (int l = 2; l <= v.L; ++l) A(&q.wtc[l], (size_t)v.dims[l - 1] * v.dims[l]);
     }
     if (e == cudaSuccess) e = cudaMallocHost((void**)&r->h_cnt, sizeof(Counters));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&r->h_claim, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaEventCreate(&r->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&r->ev1);
     if (e == cudaSuccess) e = cudaEventCreate(&r->ev_pro);
@@ -406,6 +418,7 @@ void arena_release(BatchArena* a) {
         if (ev) cudaEventDestroy(ev);
     if (a->evw) cudaEventDestroy(a->evw);
     if (a->gev) cudaEventDestroy(a->gev);
+    if (a->gexec) cudaGraphExecDestroy(a->gexec);
     if (a->gstream) cudaStreamDestroy(a->gstream);
     delete a;
 }
@@ -434,6 +447,7 @@ extern "C" vbmc_status vbmc_result_create_batch(const vbmc_net* net, const vbmc_
     A(&ar->d_tp, 2 * (size_t)nq + 2);  // one tile prefix per wave, back to back
     A(&ar->d_stage, ar->stage_stride * (size_t)nq);
     A(&ar->d_qcount, 4);
+    A(&ar->d_claim, 1);
     ar->queue_cap = std::max<uint64_t>(1, caps->queue_cap);
     for (int i = 0; i < 4; ++i) A(&ar->d_queue[i], (size_t)ar->queue_cap);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&ar->h_cnt, sizeof(Counters) * (size_t)nq);
@@ -465,6 +479,7 @@ extern "C" vbmc_status vbmc_result_free(vbmc_result* r) {
     tc_query_work_free(r->tw);
     arena_release(r->arena);
     if (r->h_cnt) cudaFreeHost(r->h_cnt);
+    if (r->h_claim) cudaFreeHost(r->h_claim);
     if (r->ev0) cudaEventDestroy(r->ev0);
     if (r->ev1) cudaEventDestroy(r->ev1);
     if (r->ev_pro) cudaEventDestroy(r->ev_pro);
@@ -529,7 +544,8 @@ vbmc_status enqueue_passes(vbmc_net* net, QueryView* d_qs, const QueryView* hq, 
                            unsigned long long* d_qcount, QEntry* const* d_queue,
                            unsigned long long cap, const cudaEvent_t* ev, const vbmc_options& opt,
                            cudaStream_t st, bool capturing = false, int stages = STAGE_ALL,
-                           WideWork* ww = nullptr, TcQueryWork* tw = nullptr) {
+                           WideWork* ww = nullptr, TcQueryWork* tw = nullptr,
+                           unsigned long long* d_claim = nullptr) {
     if (nq != 1) tw = nullptr;  // compacted columns are per query: single-query calls only
     const NetView& v = net->v;
     // inside a stream capture an event record must be an explicit graph node
@@ -599,14 +615,15 @@ vbmc_status enqueue_passes(vbmc_net* net, QueryView* d_qs, const QueryView* hq, 
     } else if (any) {
         if (opt.precision == VBMC_PREC_FP32) {
             if (simt_tile_points(v) == 0) return fail(VBMC_ERR_UNSUPPORTED, "layer width above 1024");
-            launch_screen_simt(v, d_qs, nq, d_tp, ntiles, nullptr, nullptr, 0, qdf, 2, net->n_sm, st);
+            launch_screen_simt(v, d_qs, nq, d_tp, ntiles, nullptr, nullptr, 0, qdf, 2, net->n_sm, st,
+                               (nq == 1 && small_supported(v)) ? nullptr : d_claim);
             VB_CUDA(record(ev[2]));
             VB_CUDA(record(ev[4]));
             VB_CUDA(record(ev[5]));
         } else {
             // one query: screen -> split tensor pass -> FP32; many: screen -> FP32 directly
             vbmc_status sst = tc_launch_screen(net->tc, v, d_qs, nq, d_tp, ntiles, opt.precision,
-                                   nq == 1 ? qsplit : q32, nq == 1 ? 0 : 1, net->n_sm, st, tw);
+                                   nq == 1 ? qsplit : q32, nq == 1 ? 0 : 1, net->n_sm, st, tw, d_claim);
             if (sst != VBMC_OK)
                 return fail(sst, std::string("tensor-core screen launch failed: ") + cudaGetErrorString(cudaGetLastError()));
             VB_CUDA(record(ev[2]));
@@ -684,15 +701,25 @@ vbmc_status enqueue(vbmc_net* net, vbmc_result* r, const uint8_t* d_image, const
                     int k, uint64_t lo, uint64_t hi, uint64_t n, const vbmc_options& opt,
                     cudaStream_t st, const QueryExtra& x = QueryExtra()) {
     QueryView q = make_view(r, d_image, d_pix, s, k, lo, hi, n, opt, 0, x);
+    q.budget_ns = opt.time_budget_ms > 0.0 ? (unsigned long long)(opt.time_budget_ms * 1e6) : 0ull;
     std::vector<unsigned long long> tp = tile_prefix(net->v, opt.precision, &q, 1);
+    // the first pass takes its tiles from the claim counter on the fused tensor
+    // screen and the FP32 path (not on small nets): the checked prefix follows
+    const bool tensor16 = opt.precision == VBMC_PREC_BF16 || opt.precision == VBMC_PREC_FP16;
+    const bool claims = (tensor16 && tc_supported(net->v, opt.precision)) ||
+                        (opt.precision == VBMC_PREC_FP32 && !small_supported(net->v));
+    r->ntiles = tp[1];
+    r->tile_pts = claims ? (tensor16 ? tc_tile_points() : simt_tile_points(net->v)) : 0;
     VB_CUDA(cudaMemcpyAsync(r->d_q, &q, sizeof(QueryView), cudaMemcpyHostToDevice, st));
     VB_CUDA(cudaMemcpyAsync(r->d_tp, tp.data(), sizeof(unsigned long long) * 2, cudaMemcpyHostToDevice, st));
     const cudaEvent_t ev[7] = {r->ev0, r->ev_pro, r->ev_scr, r->ev1, r->ev_split, r->ev_f32, r->ev_df};
     vbmc_status sst = enqueue_passes(net, r->d_q, &q, 1, r->d_tp, tp[1], r->d_qcount, r->d_queue,
                                      std::max<uint64_t>(1, r->caps.queue_cap), ev, opt, st, false, STAGE_ALL,
-                                     &r->ww, r->have_tw ? &r->tw : nullptr);
+                                     &r->ww, r->have_tw ? &r->tw : nullptr, claims ? r->d_claim : nullptr);
     if (sst != VBMC_OK) return sst;
     VB_CUDA(cudaMemcpyAsync(r->h_cnt, r->d_cnt, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+    if (claims)
+        VB_CUDA(cudaMemcpyAsync(r->h_claim, r->d_claim, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     r->last_stream = st;
     r->pending = true;
     r->have_result = true;
@@ -722,11 +749,24 @@ void fill_summary(vbmc_result* r, const Counters& c, float ms, float ms_p, float
     s.ms_recheck = ms - ms_p - ms_s;
     for (int i = 0; i < 4; ++i) s.ms_pass[i] = ms_pass ? ms_pass[i] : 0.0;
     s.ms_to_verdict = c.t_final > c.t0 ? (double)(c.t_final - c.t0) * 1e-6 : 0.0;
-    if (r->lo != 0 || r->hi != r->n_space) s.verdict = VBMC_PARTIAL;
+    // the checked prefix: tiles [0, claims) of the first pass (all of them unless
+    // the time budget stopped the claims)
+    s.checked_hi = r->hi;
+    if (r->tile_pts > 0 && *r->h_claim < r->ntiles) {
+        const uint64_t end = (r->lo & ~31ull) + *r->h_claim * (uint64_t)r->tile_pts;
+        s.checked_hi = std::max<uint64_t>(r->lo, std::min<uint64_t>(r->hi, end));
+        if (!(r->opt.time_budget_ms > 0.0)) s.checked_hi = r->hi;  // no budget: every tile was taken
+        else if (s.n_points == r->hi - r->lo) s.n_points = s.checked_hi - r->lo;  // no filter: count the prefix
+    }
+    if (r->lo != 0 || s.checked_hi != r->n_space) s.verdict = VBMC_PARTIAL;
     else if (c.n_adv) s.verdict = VBMC_UNSAFE;
     else if (c.n_ties) s.verdict = VBMC_TIES_ONLY;
     else s.verdict = VBMC_SAFE;
 }
+
+// A result that timed out holds the exact result of its checked prefix: the
+// getters read it and a new call may reuse the handle.
+bool usable(vbmc_status st) { return st == VBMC_OK || st == VBMC_ERR_TIMEOUT; }
 
 vbmc_status counters_status(const Counters& c) {
     if (c.err & DERR_PIXELS) return fail(VBMC_ERR_ARG, "pixel list not distinct or out of range");
@@ -752,6 +792,8 @@ vbmc_status finish(vbmc_result* r) {
         (void)cudaGetLastError();  // timing is informative only
         fill_summary(r, *r->h_cnt, ms, ms_p, ms_s, mp);
         r->last_status = counters_status(*r->h_cnt);
+        if (r->last_status == VBMC_OK && r->sum.checked_hi < r->hi)
+            r->last_status = fail(VBMC_ERR_TIMEOUT, "time budget ran out: the summary covers [lo, checked_hi)");
     }
     return r->last_status;
 }
@@ -767,7 +809,7 @@ extern "C" vbmc_status vbmc_verify_query_device(vbmc_net* net, const uint8_t* d_
     if (res->net != net) return fail(VBMC_ERR_ARG, "result belongs to another net");
     if (res->pending) {
         vbmc_status st = finish(res);
-        if (st != VBMC_OK) return st;
+        if (!usable(st)) return st;
     }
     uint64_t n, h;
     vbmc_status st = check_query_shape(res, s, k, lo, hi, opt, &n, &h);
@@ -784,7 +826,7 @@ extern "C" vbmc_status vbmc_verify_query(vbmc_net* net, const vbmc_query* q, con
     if (res->net != net) return fail(VBMC_ERR_ARG, "result belongs to another net");
     if (res->pending) {
         vbmc_status st = finish(res);
-        if (st != VBMC_OK) return st;
+        if (!usable(st)) return st;
     }
     uint64_t n, h;
     vbmc_status st = check_query_shape(res, q->s, q->k, q->lo, q->hi, opt, &n, &h);
@@ -821,7 +863,7 @@ extern "C" vbmc_status vbmc_get_witness(vbmc_result* res, uint64_t* index, int32
                                         uint8_t* image, double* margin) {
     if (!res) return fail(VBMC_ERR_ARG, "null argument");
     vbmc_status st = finish(res);
-    if (st != VBMC_OK) return st;
+    if (!usable(st)) return st;
     const uint64_t t = res->sum.first_witness;
     if (index) *index = t;
     if (t == VBMC_NO_WITNESS) return VBMC_OK;
@@ -867,7 +909,7 @@ extern "C" vbmc_status vbmc_get_coverage(vbmc_result* res, uint32_t* flip, size_
                                          uint32_t* ss_tie, double* covered_fraction) {
     if (!res) return fail(VBMC_ERR_ARG, "null argument");
     vbmc_status st = finish(res);
-    if (st != VBMC_OK) return st;
+    if (!usable(st)) return st;
     if (!res->opt.coverage) return fail(VBMC_ERR_STATE, "coverage was off for the last call");
     const NetView& v = res->net->v;
     if ((flip || flip_tie) && flip_words < (size_t)v.flip_words)
@@ -909,7 +951,7 @@ extern "C" vbmc_status vbmc_get_coverage(vbmc_result* res, uint32_t* flip, size_
 extern "C" vbmc_status vbmc_get_verdict_bitmap(vbmc_result* res, uint32_t* words, size_t n_words) {
     if (!res || !words) return fail(VBMC_ERR_ARG, "null argument");
     vbmc_status st = finish(res);
-    if (st != VBMC_OK) return st;
+    if (!usable(st)) return st;
     if (!res->opt.bitmap) return fail(VBMC_ERR_STATE, "bitmap was off for the last call");
     const size_t need = (size_t)((res->hi + 31) / 32);
     if (n_words < need) return fail(VBMC_ERR_ARG, "bitmap buffer too small");
@@ -920,7 +962,7 @@ extern "C" vbmc_status vbmc_get_verdict_bitmap(vbmc_result* res, uint32_t* words
 extern "C" vbmc_status vbmc_get_ties(vbmc_result* res, uint64_t* idx, size_t cap, uint64_t* n_ties) {
     if (!res) return fail(VBMC_ERR_ARG, "null argument");
     vbmc_status st = finish(res);
-    if (st != VBMC_OK) return st;
+    if (!usable(st)) return st;
     const uint64_t n = res->sum.n_ties;
     if (n_ties) *n_ties = n;
     const size_t kept = (size_t)std::min<uint64_t>(n, res->caps.ties_cap);
@@ -971,7 +1013,7 @@ extern "C" vbmc_status vbmc_verify_batch(vbmc_net* net, const vbmc_query* querie
         vbmc_result* r = results[i];
         if (r->pending) {
             vbmc_status fs = finish(r);
-            if (fs != VBMC_OK) return fs;
+            if (!usable(fs)) return fs;
         }
         if (!q.image || (!q.pixels && q.s > 0)) return fail(VBMC_ERR_ARG, "null query buffer");
         uint64_t n, h;
@@ -1051,29 +1093,48 @@ extern "C" vbmc_status vbmc_verify_batch(vbmc_net* net, const vbmc_query* querie
                                         w == 0 ? ar->ev[6] : ar->evw};
             vbmc_status ws = enqueue_passes(net, ar->d_qs_run + j0, hrun.data() + j0, j1 - j0,
                                             ar->d_tp + tp_at[w], wave_tiles[w], ar->d_qcount, ar->d_queue,
-                                            ar->queue_cap, evs, *opt, st, capturing);
+                                            ar->queue_cap, evs, *opt, st, capturing, STAGE_ALL, nullptr, nullptr,
+                                            ar->d_claim);
             if (ws != VBMC_OK) return ws;
         }
         return VBMC_OK;
     };
     vbmc_status sst;
     if (opt->graph) {
-        // the passes as one CUDA graph (the host-to-device copies above stay outside)
-        cudaGraph_t g = nullptr;
-        cudaGraphExec_t ge = nullptr;
-        VB_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        sst = run_waves(true);
-        cudaError_t ce = cudaStreamEndCapture(st, &g);
-        if (sst != VBMC_OK) {
-            if (g) cudaGraphDestroy(g);
-            return sst;
+        // the passes as one CUDA graph (the host-to-device copies above stay
+        // outside); captured and instantiated once per batch shape, then relaunched
+        std::string sig = std::to_string(nq) + ":" + std::to_string(opt->precision) + ":" +
+                          std::to_string(opt->coverage) + ":" + std::to_string(opt->bitmap) + ":" +
+                          std::to_string(opt->schedule);
+        for (int j = 0; j < nq; ++j) {
+            const QueryView& h = hrun[j];
+            sig += "|" + std::to_string(h.s) + "," + std::to_string(h.k) + "," + std::to_string(h.lo) + "," +
+                   std::to_string(h.hi) + "," + std::to_string(h.filter) + "," + std::to_string(h.l2max) + "," +
+                   std::to_string(h.prop) + "," + std::to_string(perm[j]);
         }
-        if (ce != cudaSuccess) return fail(VBMC_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
-        ce = cudaGraphInstantiate(&ge, g, 0);
-        if (ce == cudaSuccess) ce = cudaGraphLaunch(ge, st);
-        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
-        if (ge) cudaGraphExecDestroy(ge);
-        cudaGraphDestroy(g);
+        if (!ar->gexec || ar->gsig != sig) {
+            if (ar->gexec) cudaGraphExecDestroy(ar->gexec);
+            ar->gexec = nullptr;
+            ar->gsig.clear();
+            cudaGraph_t g = nullptr;
+            VB_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            sst = run_waves(true);
+            cudaError_t ce = cudaStreamEndCapture(st, &g);
+            if (sst != VBMC_OK) {
+                if (g) cudaGraphDestroy(g);
+                return sst;
+            }
+            if (ce != cudaSuccess) return fail(VBMC_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(ce));
+            ce = cudaGraphInstantiate(&ar->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (ce != cudaSuccess) {
+                ar->gexec = nullptr;
+                return fail(VBMC_ERR_CUDA, std::string("graph: ") + cudaGetErrorString(ce));
+            }
+            ar->gsig = sig;
+        }
+        // the thresholds of Eq. 11 live in the views (copied above), not in the graph
+        cudaError_t ce = cudaGraphLaunch(ar->gexec, st);
         if (ce != cudaSuccess) return fail(VBMC_ERR_CUDA, std::string("graph: ") + cudaGetErrorString(ce));
     } else {
         sst = run_waves(false);
@@ -1109,6 +1170,7 @@ extern "C" vbmc_status vbmc_verify_batch(vbmc_net* net, const vbmc_query* querie
         r->image.assign(q.image, q.image + H0);
         r->pixels.assign(q.pixels, q.pixels + q.s);
         r->hq.image = hq[i].image;
+        r->tile_pts = 0;  // batches check every tile (no budget)
         fill_summary(r, ar->h_cnt[i], ms, ms_p, ms_s, mp);
         r->last_status = counters_status(ar->h_cnt[i]);
         if (r->last_status != VBMC_OK && result == VBMC_OK) result = r->last_status;
@@ -1129,7 +1191,7 @@ extern "C" vbmc_status vbmc_enum_coverage(vbmc_net* net, const vbmc_query* q, co
     if (res->net != net) return fail(VBMC_ERR_ARG, "result belongs to another net");
     if (res->pending) {
         vbmc_status st = finish(res);
-        if (st != VBMC_OK) return st;
+        if (!usable(st)) return st;
     }
     uint64_t n, h;
     vbmc_status st = check_query_shape(res, q->s, q->k, q->lo, q->hi, nullptr, &n, &h);
@@ -1211,7 +1273,7 @@ extern "C" vbmc_status vbmc_search_query(vbmc_net* net, const vbmc_query* q, int
     if (n_tiles < 1) return fail(VBMC_ERR_ARG, "n_tiles must be positive");
     if (res->pending) {
         vbmc_status st = finish(res);
-        if (st != VBMC_OK) return st;
+        if (!usable(st)) return st;
     }
     uint64_t n, h;
     vbmc_status st = check_query_shape(res, q->s, q->k, 0, 0, opt, &n, &h);
@@ -1299,6 +1361,7 @@ extern "C" vbmc_status vbmc_search_query(vbmc_net* net, const vbmc_query* q, int
     res->opt = *opt;
     res->image.assign(q->image, q->image + H0);
     res->pixels.assign(q->pixels, q->pixels + q->s);
+    res->tile_pts = 0;  // the tile search checks whole tiles (no budget)
     fill_summary(res, *res->h_cnt, ms, ms_p, 0.f);
     res->sum.n_points = so.points_checked;
     res->sum.ms_to_verdict = ms;
@@ -1313,7 +1376,7 @@ extern "C" vbmc_status vbmc_tile_counts(vbmc_result* res, int32_t n_tiles, uint6
     if (!res || !counts) return fail(VBMC_ERR_ARG, "null argument");
     if (n_tiles < 1) return fail(VBMC_ERR_ARG, "n_tiles must be positive");
     vbmc_status st = finish(res);
-    if (st != VBMC_OK) return st;
+    if (!usable(st)) return st;
     if (!res->opt.bitmap) return fail(VBMC_ERR_STATE, "bitmap was off for the last call");
     if (res->lo != 0 || res->hi != res->n_space)
         return fail(VBMC_ERR_STATE, "the last call did not cover the whole space");

@@ -89,6 +89,8 @@ struct QueryView {
     double V;               // PROP_THRESHOLD: the reference value V
     unsigned long long n_points, lo, hi;  // space size and checked range
     unsigned long long ntiles;            // screen tiles of this query (time-to-verdict)
+    unsigned long long budget_ns;         // time budget of the call from the query's prologue
+                                          // (0: none); see claim_tile
     const uint8_t* image;   // H_0 grey levels (device)
     const int* pix_in;      // s pixel indices as given (device)
     int* pix;               // validated copy
@@ -223,6 +225,25 @@ __device__ __forceinline__ void record_adversarial(const QueryView& Q, unsigned 
     atomicAdd(&Q.cnt->n_adv, 1ull);
     atomicMin(&Q.cnt->first, t);
     if (Q.bitmap && t < Q.bitmap_bits) set_bit_atomic(Q.bitmap, t);
+}
+
+// Tile claims of the persistent first passes. With a claim counter the tiles
+// are handed out in increasing order, one atomicAdd each, so the tiles a launch
+// has taken always form a prefix [0, min(counter, ntiles)) of its tile list;
+// a claim checks the time budget (deadline in %globaltimer ns, 0: none)
+// before it takes a tile, so none is taken past the deadline and every tile
+// taken is finished. Without a counter the tiles are statically strided.
+constexpr unsigned long long kNoTile = ~0ull;
+
+__device__ __forceinline__ unsigned long long claim_tile(unsigned long long* ctr, unsigned long long i,
+                                                         unsigned long long ntiles, unsigned long long deadline) {
+    if (!ctr) {
+        const unsigned long long g = (unsigned long long)blockIdx.x + i * (unsigned long long)gridDim.x;
+        return g < ntiles ? g : kNoTile;
+    }
+    if (deadline && globaltimer_ns() > deadline) return kNoTile;
+    const unsigned long long g = atomicAdd(ctr, 1ull);
+    return g < ntiles ? g : kNoTile;
 }
 
 // Mixed-radix decode: first pixel most significant.

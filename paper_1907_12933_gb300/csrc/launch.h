@@ -14,14 +14,15 @@ void launch_prologue(const NetView& net, QueryView* d_qs, int nq, int max_sr, cu
 int simt_variant(const NetView& net);
 
 // FP32 SIMT screen. Range mode (gather == nullptr): tiles of each query are
-// numbered tile_prefix[q] .. tile_prefix[q+1]-1, n_tiles in total. Gather
-// mode: the points are gather[0 .. *gather_count). Points the FP32 bound
-// cannot decide go to `out`.
+// numbered tile_prefix[q] .. tile_prefix[q+1]-1, n_tiles in total, taken from
+// the claim counter when one is given (zeroed here; in order, under the time
+// budget: see claim_tile). Gather mode: the points are gather[0 ..
+// *gather_count). Points the FP32 bound cannot decide go to `out`.
 void launch_screen_simt(const NetView& net, const QueryView* d_qs, int nq,
                         const unsigned long long* d_tile_prefix, unsigned long long n_tiles,
                         const QEntry* gather, const unsigned long long* gather_count,
                         unsigned long long gather_cap, Queue out, int out_level, int n_sm,
-                        cudaStream_t st);
+                        cudaStream_t st, unsigned long long* claim = nullptr);
 
 // Points per tile of the SIMT screen for this net (its range-pass variant).
 int simt_tile_points(const NetView& net);

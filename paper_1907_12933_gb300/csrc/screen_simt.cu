@@ -6,7 +6,7 @@ namespace vbmc {
 #define VB_SIMT_DECL(i)                                                                            \
     void launch_simt_v##i(const NetView&, const QueryView*, int, const unsigned long long*,      \
                           unsigned long long, const QEntry*, const unsigned long long*,          \
-                          unsigned long long, Queue, int, int, cudaStream_t);
+                          unsigned long long, Queue, int, int, cudaStream_t, unsigned long long*);
 VB_SIMT_DECL(1)
 VB_SIMT_DECL(2)
 VB_SIMT_DECL(3)
@@ -72,23 +72,24 @@ void launch_screen_simt(const NetView& net, const QueryView* d_qs, int nq,
                         const unsigned long long* tp, unsigned long long n_tiles,
                         const QEntry* gather, const unsigned long long* gc,
                         unsigned long long gcap, Queue out, int level, int n_sm,
-                        cudaStream_t st) {
+                        cudaStream_t st, unsigned long long* claim) {
     if (nq == 1 && small_supported(net)) {  // one thread per point
         launch_small(net, d_qs, tp, n_tiles, gather, gc, gcap, out, level, n_sm, st);
         return;
     }
+    if (claim && !gather && cudaMemsetAsync(claim, 0, sizeof(unsigned long long), st) != cudaSuccess) return;
     int var = simt_variant(net);
     if (gather) {
         const int t = net.simt_var_gather;
         var = (t >= 1 && t <= kSimtVariants && net.hmax <= simt_variant_width(t)) ? t : simt_variant_default(net);
     }
     switch (var) {
-        case 1: launch_simt_v1(net, d_qs, nq, tp, n_tiles, gather, gc, gcap, out, level, n_sm, st); break;
-        case 2: launch_simt_v2(net, d_qs, nq, tp, n_tiles, gather, gc, gcap, out, level, n_sm, st); break;
-        case 3: launch_simt_v3(net, d_qs, nq, tp, n_tiles, gather, gc, gcap, out, level, n_sm, st); break;
-        case 4: launch_simt_v4(net, d_qs, nq, tp, n_tiles, gather, gc, gcap, out, level, n_sm, st); break;
-        case 5: launch_simt_v5(net, d_qs, nq, tp, n_tiles, gather, gc, gcap, out, level, n_sm, st); break;
-        case 6: launch_simt_v6(net, d_qs, nq, tp, n_tiles, gather, gc, gcap, out, level, n_sm, st); break;
+        case 1: launch_simt_v1(net, d_qs, nq, tp, n_tiles, gather, gc, gcap, out, level, n_sm, st, claim); break;
+        case 2: launch_simt_v2(net, d_qs, nq, tp, n_tiles, gather, gc, gcap, out, level, n_sm, st, claim); break;
+        case 3: launch_simt_v3(net, d_qs, nq, tp, n_tiles, gather, gc, gcap, out, level, n_sm, st, claim); break;
+        case 4: launch_simt_v4(net, d_qs, nq, tp, n_tiles, gather, gc, gcap, out, level, n_sm, st, claim); break;
+        case 5: launch_simt_v5(net, d_qs, nq, tp, n_tiles, gather, gc, gcap, out, level, n_sm, st, claim); break;
+        case 6: launch_simt_v6(net, d_qs, nq, tp, n_tiles, gather, gc, gcap, out, level, n_sm, st, claim); break;
         default: break;
     }
 }

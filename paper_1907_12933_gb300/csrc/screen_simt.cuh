@@ -53,6 +53,7 @@ struct SimtSmem {
     int fcnt[MT][kMaxL + 1];
     short flist[MT][kMaxL + 1][FCAP];
     unsigned char dig[MT][kMaxS];
+    unsigned long long g;  // the CTA's current tile
     float cpx[MT][kMaxS];  // per point and pixel: fl(dv_p / 255), the pixel's input change
 };
 
@@ -340,7 +341,7 @@ __global__ void __launch_bounds__(THREADS, PPW * NQ <= 64 ? 2 : 1)
 k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
               const unsigned long long* __restrict__ tile_prefix, unsigned long long n_tiles,
               const QEntry* __restrict__ gather, const unsigned long long* __restrict__ gather_count,
-              unsigned long long gather_cap, Queue out, int out_level) {
+              unsigned long long gather_cap, Queue out, int out_level, unsigned long long* claim) {
     using Sm = SimtSmem<PPW, NQ>;
     constexpr int MT = Sm::MT;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -358,7 +359,16 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
         tiles = (gcount + MT - 1) / MT;
     }
 
-    for (unsigned long long g = blockIdx.x; g < tiles; g += gridDim.x) {
+    // range mode with a claim counter: tiles in order under the time budget
+    unsigned long long* const ctr = gather ? nullptr : claim;
+    const unsigned long long deadline =
+        (!gather && qs[0].budget_ns) ? qs[0].cnt->t0 + qs[0].budget_ns : 0ull;
+    for (unsigned long long ti = 0;; ++ti) {
+        if (threadIdx.x == 0) S.g = claim_tile(ctr, ti, tiles, deadline);
+        __syncthreads();
+        const unsigned long long g = S.g;
+        __syncthreads();  // every thread has read S.g before the next claim overwrites it
+        if (g == kNoTile) break;
         // ---- S1: decode
         if (lane < PPW) {
             const int m = warp * PPW + lane;
@@ -597,7 +607,8 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
 template <int PPW, int NQ>
 void launch_variant(const NetView& net, const QueryView* d_qs, int nq, const unsigned long long* tp,
                     unsigned long long n_tiles, const QEntry* gather, const unsigned long long* gc,
-                    unsigned long long gcap, Queue out, int level, int n_sm, cudaStream_t st) {
+                    unsigned long long gcap, Queue out, int level, int n_sm, cudaStream_t st,
+                    unsigned long long* claim = nullptr) {
     const size_t smem = sizeof(SimtSmem<PPW, NQ>);
     auto kern = k_screen_simt<PPW, NQ>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -607,7 +618,7 @@ void launch_variant(const NetView& net, const QueryView* d_qs, int nq, const uns
     unsigned long long grid = (unsigned long long)n_sm * per_sm;
     if (!gather && n_tiles < grid) grid = n_tiles ? n_tiles : 1;
     kern<<<(unsigned)grid, THREADS, smem, st>>>(net, d_qs, nq, tp, n_tiles, gather, gc, gcap, out,
-                                                level);
+                                                level, claim);
 }
 
 }  // namespace simt

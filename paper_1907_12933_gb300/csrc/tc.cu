@@ -99,11 +99,12 @@ struct TcSmem {
     };
     int curq;
     int npref;
+    unsigned long long claim[2];  // tile i of this CTA in claim[i & 1] (kNoTile: none left)
     int kch[kTcMaxL + 1];  // layer l: K chunks of 64 (compacted: the query's width of layer l-1)
     int nsl[kTcMaxL + 1];  //   N slices per K chunk
     int np[kTcMaxL + 1];   //   N computed (compacted: the query's width of layer l)
     int uniform_base;
-    unsigned long long bars[2 * NB + 2 * NA + 5];
+    unsigned long long bars[2 * NB + 2 * NA + 7];
     uint32_t tmem_slot;
     int abort_flag;
 };
@@ -126,6 +127,7 @@ constexpr int DFULL = 2 * NB + 2 * NA;
 constexpr int TFREE = DFULL + 1;
 constexpr int DRAINED = DFULL + 2;
 constexpr int FIN = DFULL + 3;
+__device__ __forceinline__ int CLAIMB(int i) { return DFULL + 4 + i; }  // claim[i] written
 
 __device__ __forceinline__ float norm_up(float s) { return __fsqrt_ru(__fmul_ru(s, 1.0002f)); }
 
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restrict__ qs, int nq,
      const unsigned long long* __restrict__ tile_prefix, const QEntry* __restrict__ gather,
      const unsigned long long* __restrict__ gcount, unsigned long long gcap, Queue out,
-     int out_level) {
+     int out_level, unsigned long long* claim_ctr) {
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte aligned by pointer arithmetic on the shared array, so the compiler
     // keeps every access in the shared address space
@@ -182,6 +184,11 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
     } else {
         ntiles = tile_prefix[nq];
     }
+    // range mode: tiles from the claim counter (in order, under the time budget);
+    // gather mode: statically strided
+    unsigned long long* const ctr = gather ? nullptr : claim_ctr;
+    const unsigned long long deadline =
+        (!gather && qs[0].budget_ns) ? qs[0].cnt->t0 + qs[0].budget_ns : 0ull;
 
     auto bar = [&](int i) { return tc::smem_u32(&S.bars[i]); };
 
@@ -198,8 +205,11 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
         tc::mbar_init(bar(TFREE), NW);
         tc::mbar_init(bar(DRAINED), NW);
         tc::mbar_init(bar(FIN), 1);
+        tc::mbar_init(bar(CLAIMB(0)), 1);
+        tc::mbar_init(bar(CLAIMB(1)), 1);
         S.abort_flag = 0;
         S.curq = -1;
+        S.claim[0] = claim_tile(ctr, 0, ntiles, deadline);  // this CTA's first tile
         // loop sizes per layer; compacted: the widths of the (single) query's
         // non-"neg" columns, rounded up to 64, from its set-up
         for (int l = 2; l <= L; ++l) {
@@ -226,13 +236,16 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = S.tmem_slot;
+    if (threadIdx.x == 0) tc::mbar_arrive(bar(CLAIMB(0)));  // claim[0] holds tile 0
 
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
-            for (unsigned long long g = blockIdx.x; g < ntiles && ok; g += gridDim.x)
+            for (uint32_t ti = 0; ok; ++ti) {
+                if (!tc::mbar_wait(bar(CLAIMB(ti & 1)), (ti >> 1) & 1, abortp)) { ok = false; break; }
+                if (S.claim[ti & 1] == kNoTile) break;
                 for (int l = 2; l <= L && ok; ++l) {
                     const TcLayer& ly = P.ly[l];
                     for (int kc = 0; kc < S.kch[l] && ok; ++kc)
@@ -249,6 +262,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                                 ++it;
                             }
                 }
+            }
             if (!ok) {  // let the copies already issued land before the CTA leaves
                 const uint64_t t0 = tc::global_ns();
                 for (uint32_t i = it > (uint32_t)NB ? it - NB : 0; i < it; ++i)
@@ -262,7 +276,9 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
         if (lane == 0) {
             uint32_t ait = 0, bit = 0, tile_i = 0, drit = 0;
             bool ok = true;
-            for (unsigned long long g = blockIdx.x; g < ntiles && ok; g += gridDim.x, ++tile_i) {
+            for (;; ++tile_i) {
+                if (!tc::mbar_wait(bar(CLAIMB(tile_i & 1)), (tile_i >> 1) & 1, abortp)) { ok = false; break; }
+                if (S.claim[tile_i & 1] == kNoTile) break;
                 if (!tc::mbar_wait(bar(TFREE), (tile_i & 1) ^ 1, abortp)) { ok = false; break; }
                 tc::tc_fence_after();
                 for (int l = 2; l <= L && ok; ++l) {
@@ -331,8 +347,14 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
         const float uacc_base = P.acc_unit * (SPLIT ? 3.f : 1.f);  // measured by tc_f16_selftest
         (void)H0;
         const bool cmp = P.compact != 0;  // compacted columns (one query): positions -> neurons by perm
-        for (unsigned long long g = blockIdx.x; g < ntiles; g += gridDim.x) {
+        for (uint32_t ti = 0;; ++ti) {
             if (*abortp) break;
+            const unsigned long long g = S.claim[ti & 1];  // written before a barrier the workers passed
+            if (g == kNoTile) break;
+            if (wtid == 0) {  // claim the next tile now: the producer prefetches its weights
+                S.claim[(ti + 1) & 1] = claim_tile(ctr, ti + 1, ntiles, deadline);
+                tc::mbar_arrive(bar(CLAIMB((ti + 1) & 1)));
+            }
             int q = 0;
             if (!gather) {
                 int a = 0, b = nq - 1;
@@ -1796,25 +1818,26 @@ template <bool SPLIT, bool BF>
 static void launch_k(const TcParams& P, const NetView& v, const QueryView* d_q, int nq,
                      const unsigned long long* tp, unsigned long long ntiles, const QEntry* g,
                      const unsigned long long* gc, unsigned long long cap, Queue out, int level,
-                     int n_sm, cudaStream_t st) {
+                     int n_sm, cudaStream_t st, unsigned long long* claim) {
     const size_t smem = sizeof(TcSmem) + 1024;
     auto kern = k_tc<SPLIT, BF>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     unsigned grid = (unsigned)n_sm;
     if (!g && ntiles < grid) grid = (unsigned)(ntiles ? ntiles : 1);
-    kern<<<grid, TC_THREADS, smem, st>>>(P, v, d_q, nq, tp, g, gc, cap, out, level);
+    kern<<<grid, TC_THREADS, smem, st>>>(P, v, d_q, nq, tp, g, gc, cap, out, level, claim);
 }
 
 vbmc_status tc_launch_screen(TcNet& tc, const NetView& v, const QueryView* d_q, int nq,
                              const unsigned long long* d_tile_prefix, unsigned long long ntiles,
                              int precision, Queue out, int out_level, int n_sm, cudaStream_t st,
-                             TcQueryWork* qw) {
+                             TcQueryWork* qw, unsigned long long* d_claim) {
     const bool bf = precision == VBMC_PREC_BF16;
     TcParams Pc;
     if (qw && nq == 1 && !compact_params(tc.prec[bf ? 0 : 1].p, v, *qw, bf ? 0 : 1, Pc)) return VBMC_ERR_CUDA;
     const TcParams& P = (qw && nq == 1) ? Pc : tc.prec[bf ? 0 : 1].p;
-    if (bf) launch_k<false, true>(P, v, d_q, nq, d_tile_prefix, ntiles, nullptr, nullptr, 0, out, out_level, n_sm, st);
-    else launch_k<false, false>(P, v, d_q, nq, d_tile_prefix, ntiles, nullptr, nullptr, 0, out, out_level, n_sm, st);
+    if (d_claim && cudaMemsetAsync(d_claim, 0, sizeof(unsigned long long), st) != cudaSuccess) return VBMC_ERR_CUDA;
+    if (bf) launch_k<false, true>(P, v, d_q, nq, d_tile_prefix, ntiles, nullptr, nullptr, 0, out, out_level, n_sm, st, d_claim);
+    else launch_k<false, false>(P, v, d_q, nq, d_tile_prefix, ntiles, nullptr, nullptr, 0, out, out_level, n_sm, st, d_claim);
     return cudaPeekAtLastError() == cudaSuccess ? VBMC_OK : VBMC_ERR_CUDA;  // the caller reports the error
 }
 
@@ -1825,8 +1848,8 @@ vbmc_status tc_launch_gather(TcNet& tc, const NetView& v, const QueryView* d_q, 
     TcParams Pc;
     if (qw && !compact_params(tc.prec[bf ? 0 : 1].p, v, *qw, bf ? 0 : 1, Pc)) return VBMC_ERR_CUDA;
     const TcParams& P = qw ? Pc : tc.prec[bf ? 0 : 1].p;
-    if (bf) launch_k<true, true>(P, v, d_q, 1, nullptr, 0, in, in_count, cap, out, 1, n_sm, st);
-    else launch_k<true, false>(P, v, d_q, 1, nullptr, 0, in, in_count, cap, out, 1, n_sm, st);
+    if (bf) launch_k<true, true>(P, v, d_q, 1, nullptr, 0, in, in_count, cap, out, 1, n_sm, st, nullptr);
+    else launch_k<true, false>(P, v, d_q, 1, nullptr, 0, in, in_count, cap, out, 1, n_sm, st, nullptr);
     return cudaPeekAtLastError() == cudaSuccess ? VBMC_OK : VBMC_ERR_CUDA;  // the caller reports the error
 }
 

@@ -77,10 +77,12 @@ void tc_launch_query_setup(TcNet& tc, const NetView& v, QueryView* d_q, int nq, 
 // Screen over nq queries: tiles of query q are d_tile_prefix[q] .. d_tile_prefix[q+1]-1
 // (ntiles in total), each tc_tile_points() consecutive indices from (lo & ~31).
 // qw: the compacted operands of the (single) query, prepared by the set-up.
+// d_claim: the launch's tile claim counter (zeroed here; tiles are then taken in
+// order under the queries' time budget, see claim_tile), or null for static tiles.
 vbmc_status tc_launch_screen(TcNet& tc, const NetView& v, const QueryView* d_q, int nq,
                              const unsigned long long* d_tile_prefix, unsigned long long ntiles,
                              int precision, Queue out, int out_level, int n_sm, cudaStream_t st,
-                             TcQueryWork* qw = nullptr);
+                             TcQueryWork* qw = nullptr, unsigned long long* d_claim = nullptr);
 int tc_tile_points();
 vbmc_status tc_launch_gather(TcNet& tc, const NetView& v, const QueryView* d_q, const QEntry* in,
                              const unsigned long long* in_count, unsigned long long cap,

@@ -124,6 +124,42 @@ def test_config4_net_batch(vb, prec, graph, schedule):
         r.free()
 
 
+def batch_check(vb, net, qs, results, sums):
+    for q, r, s in zip(qs, results, sums):
+        o = oracle.verify(net, q)
+        g = {"summary": s, "n": oracle.space_size(len(q["pixels"]), q["k"])}
+        g.update(vb.get_coverage(r))
+        g["bitmap"] = vb.get_verdict_bitmap(r, g["n"])
+        g["ties"] = np.sort(vb.get_ties(r))
+        g["witness"] = vb.get_witness(r, len(q["pixels"]), 784)
+        compare(g, o, net, q)
+
+
+def test_config4_wide_queries_and_graph_reuse(vb):
+    """Queries of the batch workload with s = 4..6 pixels (small k), in one batch
+    arena: the graph captured by the first call is relaunched by the second (same
+    shapes) and captured again for a batch of other shapes; every result against
+    the oracle each time."""
+    w = synth.workload("mlp784x256x256_relu_batch4096", nq=20, s_range=(4, 6), k_range=(1, 2))
+    net = w["net"]
+    vnet = vb.Net(net)
+    qs = w["queries"]
+    assert {len(q["pixels"]) for q in qs} == {4, 5, 6}
+    other = synth.workload("mlp784x256x256_relu_batch4096", nq=20, s_range=(3, 6), k_range=(1, 3),
+                           seed=2004)["queries"]
+    nmax = max(oracle.space_size(len(q["pixels"]), q["k"]) for q in qs + other)
+    results = vb.result_create_batch(vnet, len(qs), max_points=nmax, max_s=6, max_k=3, queue_cap=1 << 20)
+    for _ in range(2):
+        sums = vb.verify_batch(vnet, results, qs, precision="bf16", coverage=True, bitmap=True,
+                               graph=True, schedule="small_first")
+        batch_check(vb, net, qs, results, sums)
+    sums = vb.verify_batch(vnet, results, other, precision="bf16", coverage=True, bitmap=True,
+                           graph=True, schedule="small_first")
+    batch_check(vb, net, other, results, sums)
+    for r in results:
+        r.free()
+
+
 @pytest.mark.parametrize("prec", PLAIN)
 def test_edge_cases(vb, prec):
     net, q = small_relu_case(k=4)
