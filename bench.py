@@ -216,15 +216,15 @@ class Clocks:
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of each pass
 # of the timed step, from one ncu capture of this configuration on a GB300
-# (profiles/traffic_mlp784x512x512_s6k7_bf16.md; ncu replays each kernel from a
-# cold L2, so queue entries that a normal step keeps in L2 count as DRAM reads).
+# (profiles/traffic_mlp784x512x512_s6k7_bf16.md, one kernel per capture; ncu replays
+# each kernel from a cold L2, so queue entries a normal step keeps in L2 count as reads).
 # Keyed by (workload, precision, coverage, s, k); other configurations report null.
 PROFILED_TRAFFIC = {
     ("mlp784x512x512_relu_s6k7", "bf16", True, 6, 7): {
-        "screen (first pass over every point)": 2261760 + 302848,
-        "split tensor pass": 51234304 + 26368,
-        "FP32 pass": 23104000 + 5632,
-        "double-float pass": 2907648 + 103680,
+        "screen (first pass over every point)": 1197568 + 1070080,
+        "split tensor pass": 50189312 + 126976,
+        "FP32 pass": 22082304 + 46848,
+        "double-float pass": 2501376 + 129792,
     },
 }
 
