@@ -639,7 +639,7 @@ vbmc_status enqueue_passes(vbmc_net* net, QueryView* d_qs, const QueryView* hq, 
                                net->n_sm, st);
             VB_CUDA(record(ev[5]));
         }
-        launch_df(v, d_qs, d_queue[2], d_qcount + 2, cap, q64, 3, net->n_sm, st);
+        launch_df(v, d_qs, nq, d_queue[2], d_qcount + 2, cap, q64, 3, net->n_sm, st);
         VB_CUDA(record(ev[6]));
         launch_fp64(v, d_qs, nq, d_queue[3], d_qcount + 3, cap, 0, 0, net->n_sm, st);
     } else {
@@ -1597,7 +1597,7 @@ extern "C" vbmc_status vbmc_autotune(vbmc_net* net, const char* cache_path, vbmc
     for (int per = 2; per <= 16; per *= 2) {
         net->v.df_ctas = per;
         const float md = time_it([&] {
-            launch_df(net->v, r->d_q, r->d_queue[1], r->d_qcount + 1, cap, q64, 3, net->n_sm, sq);
+            launch_df(net->v, r->d_q, 1, r->d_queue[1], r->d_qcount + 1, cap, q64, 3, net->n_sm, sq);
         });
         if (md < best_d) {
             best_d = md;

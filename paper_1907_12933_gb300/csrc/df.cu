@@ -28,23 +28,35 @@ __device__ __forceinline__ double act64(int act, double u) {
     return u;
 }
 
-__device__ __forceinline__ double block_sum64(double v, double* red) {
+// M block-wide sums at once (one barrier pair for all of them); every thread
+// gets the totals in v. red holds (blockDim.x / 32) x M doubles.
+template <int M>
+__device__ __forceinline__ void block_sums64(double (&v)[M], double* red) {
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int i = 0; i < M; ++i) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    }
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int i = 0; i < M; ++i) red[w * M + i] = v[i];
+    }
     __syncthreads();
-    double t = 0.0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
-    __syncthreads();
-    return t;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+        double t = 0.0;
+        for (int k = 0; k < nw; ++k) t += red[k * M + i];
+        v[i] = t;
+    }
 }
 
 // PB points per CTA (one weight load serves all of them). Per point b: its
 // potentials u[b], delta pair dh[b], certain sign changes fl[b].
 template <int PB>
 __global__ void __launch_bounds__(TDF)
-k_df(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__ gather,
+k_df(NetView net, const QueryView* __restrict__ qs, int nq, const QEntry* __restrict__ gather,
      const unsigned long long* __restrict__ gcount, unsigned long long gcap, Queue out,
      int out_level) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -52,7 +64,7 @@ k_df(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__ g
     double* u = reinterpret_cast<double*>(smem_raw);                       // [PB][total]
     float2* dh = reinterpret_cast<float2*>(u + (size_t)PB * total);        // [PB][hmax]
     unsigned char* fl = reinterpret_cast<unsigned char*>(dh + (size_t)PB * hmax);  // [PB][total]
-    __shared__ double red[32];
+    __shared__ double redm[(TDF / 32) * 2 * PB];
     __shared__ int nflip[PB][kMaxL + 2], only[PB][kMaxL + 2];
     __shared__ double dvs[PB][kMaxS];  // the point's input changes dv_p / 255 (FP64), once per pixel
     __shared__ int undecided[PB], valid[PB];
@@ -64,6 +76,9 @@ k_df(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__ g
     const int L = net.L;
     const double c46 = 0x1p-46, u52 = 0x1p-52;
     const double lam = net.act == ACT_SIGMOID ? 0.25 : 1.0;
+    // compacted columns: one query whose set-up kept the non-"neg" neurons (their
+    // change is 0 at every point of the box: dropped from the dense layers)
+    const bool cmp = nq == 1 && qs[0].compact;
     for (unsigned long long e0 = (unsigned long long)blockIdx.x * PB; e0 < n;
          e0 += (unsigned long long)gridDim.x * PB) {
         if (threadIdx.x < PB) {
@@ -81,6 +96,7 @@ k_df(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__ g
                 for (int p = 0; p < Q.s; ++p) dvs[b][p] = (double)Q.dv[p * Q.R + d[p]] / 255.0;
             }
         }
+        for (int e = threadIdx.x; e < PB * total; e += TDF) fl[e] = 0;  // neurons not computed: no change
         if (threadIdx.x < PB * (kMaxL + 2)) {
             nflip[threadIdx.x / (kMaxL + 2)][threadIdx.x % (kMaxL + 2)] = 0;
             only[threadIdx.x / (kMaxL + 2)][threadIdx.x % (kMaxL + 2)] = -1;
@@ -89,16 +105,25 @@ k_df(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__ g
         double N[PB], E[PB];
         // ---- layer 1 in FP64; its signs are decided here
         const int H1 = net.dims[1];
+        const int W1 = cmp ? qs[0].kc[1] : H1, cnt1 = cmp ? qs[0].kc[kMaxL + 2] : H1;
+        double sq1[2 * PB];  // per point: ||dh_1||^2, ||err(dh_1)||^2 (this thread's terms)
         for (int b = 0; b < PB; ++b) {
             double nsq = 0.0, esq = 0.0;
             if (valid[b]) {
                 const QueryView& Q = qs[qpt[b]];
-                for (int j = threadIdx.x; j < H1; j += TDF) {
+                for (int jp = threadIdx.x; jp < W1; jp += TDF) {  // position jp holds neuron j
+                    if (jp >= cnt1) {
+                        dh[(size_t)b * hmax + jp] = make_float2(0.f, 0.f);
+                        continue;
+                    }
+                    const int j = cmp ? Q.perm[jp] : jp;
                     const double ub = Q.ub[j];
                     double a = ub, mag = fabs(ub);
                     for (int p = 0; p < Q.s; ++p) {
-                        // W_1[j][pix] from the transposed copy: threads over j read contiguously
-                        const double term = (double)net.WT[1][(size_t)Q.pix[p] * H1 + j] * dvs[b][p];
+                        // W_1[j][pix] from the transposed copy (compacted: the query's own rows
+                        // by position): threads over j read contiguously
+                        const float w = cmp ? Q.w1c[(size_t)p * H1 + jp] : net.WT[1][(size_t)Q.pix[p] * H1 + j];
+                        const double term = (double)w * dvs[b][p];
                         a += term;
                         mag += fabs(term);
                     }
@@ -110,26 +135,37 @@ k_df(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__ g
                     fl[(size_t)b * total + j] = certain && ((a >= 0.0) != (ub >= 0.0));
                     const double d = (L > 1 ? act64(net.act, a) : a) - Q.hb[j];
                     const float hi = (float)d;
-                    dh[(size_t)b * hmax + j] = make_float2(hi, (float)(d - (double)hi));
+                    dh[(size_t)b * hmax + jp] = make_float2(hi, (float)(d - (double)hi));
                     nsq += d * d;
                     const double ej = 2.0 * err + u52 * (fabs(a) + fabs(Q.hb[j])) * 4.0 + 0x1p-47 * fabs(d);
                     esq += ej * ej;
                 }
             }
-            N[b] = sqrt(block_sum64(nsq, red)) * (1.0 + 1e-12);
-            E[b] = sqrt(block_sum64(esq, red)) * (1.0 + 1e-12);
+            sq1[2 * b] = nsq;
+            sq1[2 * b + 1] = esq;
+        }
+        block_sums64<2 * PB>(sq1, redm);
+#pragma unroll
+        for (int b = 0; b < PB; ++b) {
+            N[b] = sqrt(sq1[2 * b]) * (1.0 + 1e-12);
+            E[b] = sqrt(sq1[2 * b + 1]) * (1.0 + 1e-12);
         }
         // ---- layers 2..L in double-float, PB points per weight load
         for (int l = 2; l <= L; ++l) {
             bool any = false;
             for (int b = 0; b < PB; ++b) any = any || (valid[b] && !undecided[b]);
             if (!any) break;
-            const int K = net.dims[l - 1], Nn = net.dims[l], off = net.noff[l];
-            const float* WT = net.WT[l];
+            const int NS = net.dims[l], off = net.noff[l];  // row stride of W_l^T
+            const int K = cmp ? qs[0].kc[l - 1] : net.dims[l - 1];
+            const int Nn = (cmp && l < L) ? qs[0].kc[l] : NS;
+            const int cntN = (cmp && l < L) ? qs[0].kc[kMaxL + 1 + l] : NS;
+            const float* WT = cmp ? qs[0].wtc[l] : net.WT[l];
             const double cK = (K + 2) * c46;
             double nsq2[PB], esq2[PB];
             for (int b = 0; b < PB; ++b) nsq2[b] = esq2[b] = 0.0;
-            for (int i = threadIdx.x; i < Nn; i += TDF) {
+            for (int i = threadIdx.x; i < Nn; i += TDF) {  // position i holds neuron io
+                if (i >= cntN) continue;  // padding: change 0
+                const int io = (cmp && l < L) ? qs[0].perm[off + i] : i;
                 float S[PB], sl[PB];
 #pragma unroll
                 for (int b = 0; b < PB; ++b) S[b] = sl[b] = 0.f;
@@ -137,7 +173,7 @@ k_df(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__ g
                 // point's sum still runs in order of j)
 #pragma unroll 4
                 for (int j = 0; j < K; ++j) {
-                    const float w = WT[(size_t)j * Nn + i];
+                    const float w = WT[(size_t)j * NS + i];
 #pragma unroll
                     for (int b = 0; b < PB; ++b) {
                         const float2 h = dh[(size_t)b * hmax + j];
@@ -155,19 +191,19 @@ k_df(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__ g
                 for (int b = 0; b < PB; ++b) {
                     if (!valid[b] || undecided[b]) continue;
                     const QueryView& Q = qs[qpt[b]];
-                    const double ub = Q.ub[off + i];
+                    const double ub = Q.ub[off + io];
                     const double ui = ub + ((double)S[b] + (double)sl[b]);
-                    u[(size_t)b * total + off + i] = ui;
-                    const double err = (double)net.rownorm[l][i] * (cK * N[b] + E[b]) + Q.eub[off + i] +
+                    u[(size_t)b * total + off + io] = ui;
+                    const double err = (double)net.rownorm[l][io] * (cK * N[b] + E[b]) + Q.eub[off + io] +
                                        u52 * (fabs(ui) + fabs(ub));
                     const bool certain = fabs(ui) > err + 2.0 * kTau && fabs(ub) >= kTau;
                     if (!certain && Q.flip) undecided[b] = 1;  // signs matter only for coverage
-                    fl[(size_t)b * total + off + i] = certain && ((ui >= 0.0) != (ub >= 0.0));
+                    fl[(size_t)b * total + off + io] = certain && ((ui >= 0.0) != (ub >= 0.0));
                     if (l < L) {
-                        const double d = act64(net.act, ui) - Q.hb[off + i];
+                        const double d = act64(net.act, ui) - Q.hb[off + io];
                         nsq2[b] += d * d;
-                        const double ej = lam * (Q.eub[off + i] + u52 * (fabs(ui) + fabs(ub))) +
-                                          Q.eub[off + i] + u52 * (fabs(ui) + fabs(Q.hb[off + i])) * 4.0 +
+                        const double ej = lam * (Q.eub[off + io] + u52 * (fabs(ui) + fabs(ub))) +
+                                          Q.eub[off + io] + u52 * (fabs(ui) + fabs(Q.hb[off + io])) * 4.0 +
                                           0x1p-47 * fabs(d);
                         esq2[b] += ej * ej;
                     }
@@ -175,19 +211,31 @@ k_df(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__ g
             }
             __syncthreads();  // dh of layer l-1 fully consumed
             if (l < L) {
+                double sq2[2 * PB];
                 for (int b = 0; b < PB; ++b) {
                     if (valid[b]) {
                         const QueryView& Q = qs[qpt[b]];
                         for (int i = threadIdx.x; i < Nn; i += TDF) {
-                            const double d = act64(net.act, u[(size_t)b * total + off + i]) - Q.hb[off + i];
+                            if (i >= cntN) {  // padding position
+                                dh[(size_t)b * hmax + i] = make_float2(0.f, 0.f);
+                                continue;
+                            }
+                            const int io = cmp ? Q.perm[off + i] : i;
+                            const double d = act64(net.act, u[(size_t)b * total + off + io]) - Q.hb[off + io];
                             const float hi = (float)d;
                             dh[(size_t)b * hmax + i] = make_float2(hi, (float)(d - (double)hi));
                         }
                     }
+                    sq2[2 * b] = nsq2[b];
+                    sq2[2 * b + 1] = esq2[b];
+                }
+                block_sums64<2 * PB>(sq2, redm);
+#pragma unroll
+                for (int b = 0; b < PB; ++b) {
                     // ||err(dh_l)|| <= lambda (sigma_l E + (K+2) 2^-46 ||W_l||_F N) + per-element rounding
                     const double En = lam * ((double)net.sig[l] * E[b] + cK * (double)net.frob[l] * N[b]);
-                    N[b] = sqrt(block_sum64(nsq2[b], red)) * (1.0 + 1e-12);
-                    E[b] = (En + sqrt(block_sum64(esq2[b], red))) * (1.0 + 1e-12);
+                    N[b] = sqrt(sq2[2 * b]) * (1.0 + 1e-12);
+                    E[b] = (En + sqrt(sq2[2 * b + 1])) * (1.0 + 1e-12);
                 }
             }
             __syncthreads();
@@ -266,15 +314,15 @@ k_df(NetView net, const QueryView* __restrict__ qs, const QEntry* __restrict__ g
 
 }  // namespace
 
-void launch_df(const NetView& net, const QueryView* d_qs, const QEntry* gather,
+void launch_df(const NetView& net, const QueryView* d_qs, int nq, const QEntry* gather,
                const unsigned long long* gather_count, unsigned long long gather_cap, Queue out,
                int out_level, int n_sm, cudaStream_t st) {
     constexpr int PB = 4;
     const size_t smem = PB * (sizeof(double) * net.total + sizeof(float2) * net.hmax + (size_t)net.total);
     cudaFuncSetAttribute(k_df<PB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int per_sm = (net.df_ctas >= 1 && net.df_ctas <= 32) ? net.df_ctas : 4;
-    k_df<PB><<<(unsigned)(n_sm * per_sm), TDF, smem, st>>>(net, d_qs, gather, gather_count, gather_cap, out,
-                                                          out_level);
+    k_df<PB><<<(unsigned)(n_sm * per_sm), TDF, smem, st>>>(net, d_qs, nq, gather, gather_count, gather_cap,
+                                                          out, out_level);
 }
 
 }  // namespace vbmc

@@ -66,7 +66,7 @@ double spectral_bound(const std::vector<double>& A, int m, int n);
 
 // Double-float pass (FP32 pairs on CUDA cores) over a queue; points it cannot
 // decide go to `out`.
-void launch_df(const NetView& net, const QueryView* d_qs, const QEntry* gather,
+void launch_df(const NetView& net, const QueryView* d_qs, int nq, const QEntry* gather,
                const unsigned long long* gather_count, unsigned long long gather_cap, Queue out,
                int out_level, int n_sm, cudaStream_t st);
 

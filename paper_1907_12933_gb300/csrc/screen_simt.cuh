@@ -493,8 +493,19 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
 
         // ---- S4: dense layers on the deltas
         for (int l = 2; l <= L; ++l) {
-            if (net.dims[l] > 32) dense_layer<PPW, NQ, NQ>(S, net, qs, l, warp, lane, cmp);
-            else dense_layer<PPW, NQ, 1>(S, net, qs, l, warp, lane, cmp);
+            if (net.dims[l] <= 32) {
+                dense_layer<PPW, NQ, 1>(S, net, qs, l, warp, lane, cmp);
+                continue;
+            }
+            // a compacted hidden layer narrower than the variant's width runs with
+            // fewer slots per lane (whole 128-column groups: the paired slot layout)
+            const int ng = (cmp && l < L) ? (qs[0].kc[l] + 127) / 128 : NQ;
+            if (NQ % 8 == 0 && NQ >= 8 && 8 * ng <= NQ)
+                dense_layer<PPW, NQ, (NQ % 8 == 0 && NQ >= 8 ? NQ / 2 : NQ)>(S, net, qs, l, warp, lane, cmp);
+            else if (NQ % 16 == 0 && 16 * ng <= 3 * NQ)
+                dense_layer<PPW, NQ, (NQ % 16 == 0 ? 3 * NQ / 4 : NQ)>(S, net, qs, l, warp, lane, cmp);
+            else
+                dense_layer<PPW, NQ, NQ>(S, net, qs, l, warp, lane, cmp);
         }
 
         // ---- S5: verdict (layer L values are in A[m][0..H_L))

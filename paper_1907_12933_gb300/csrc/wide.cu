@@ -1058,7 +1058,7 @@ vbmc_status wide_run(const WideNet& wn, int type, WideWork& w, const NetView& v,
         else launch_chunk<WIDE_FP16>(P, type, w, dv, v, d_q, c0, count, err, q32, n_sm, st, tr);
         // this chunk's undecided points: FP32, double-float, FP64 passes
         launch_screen_simt(v, d_q, 1, nullptr, 0, d_queue[1], d_qcount + 1, cap, qdf, 2, n_sm, st);
-        launch_df(v, d_q, d_queue[2], d_qcount + 2, cap, q64, 3, n_sm, st);
+        launch_df(v, d_q, 1, d_queue[2], d_qcount + 2, cap, q64, 3, n_sm, st);
         launch_fp64(v, d_q, 1, d_queue[3], d_qcount + 3, cap, 0, 0, n_sm, st);
     }
     k_wide_work_done<<<1, 1, 0, st>>>(d_q);
