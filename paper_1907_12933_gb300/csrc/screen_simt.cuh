@@ -123,7 +123,7 @@ constexpr float kUseg = 0x1.00002p-24f * (float)(CKC * KC);  // u' CKL, rounded 
 template <int PPW, int NQ, int NQA>
 __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView& net,
                                             const QueryView* __restrict__ qs, int l, int warp,
-                                            int lane, bool cmp) {
+                                            int lane, bool cmp, bool oneq) {
     constexpr int HS = SimtSmem<PPW, NQ>::HS;
     constexpr int HW = 32 * NQA;  // columns of the weight chunk in use
     constexpr bool PER_NEURON = NQA == 1;
@@ -254,6 +254,62 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
     const float lf = net.lamfrob[l], gl = net.gam[l];
     const float lam = net.act == ACT_SIGMOID ? 0.25f : 1.0f;
     const float G = (float)((nchunks * KCL + CKC * KC - 1) / (CKC * KC));  // checkpoint segments
+    // One query for the warp's points (and a layer wider than a warp): slots
+    // outside, points inside, so that each column constant is loaded once for
+    // the PPW points; the same operations per point as the loop below.
+    const bool one = oneq && !PER_NEURON;
+    float nsumA[PPW], usumA[PPW];
+    uint32_t uncbA[PPW], flipbA[PPW];
+    if (one) {
+        const QueryView& Q = qs[0];
+        unsigned vmask = 0u;
+        float X[PPW];
+#pragma unroll
+        for (int r = 0; r < PPW; ++r) {
+            const int m = warp * PPW + r;
+            vmask |= (unsigned)(S.valid[m] != 0) << r;
+            X[r] = __fmaf_ru(gl, S.N[m], S.E[m]);
+            nsumA[r] = usumA[r] = 0.f;
+            uncbA[r] = flipbA[r] = 0u;
+        }
+#pragma unroll
+        for (int qq = 0; qq < NQ; ++qq) {
+            const int n = qq < NQA ? slot_neuron<NQA>(lane, qq) : lane + 32 * qq;  // position
+            const int no = (cmp && l < L) ? (n < cntN ? Q.perm[off + n] : -1) : n;
+            if (qq < NQA && n < N && no >= 0) {
+                const int gi = off + no;
+                const float ub = __ldg(&Q.ub32[gi]), rnn = __ldg(&rn[no]), th = __ldg(&Q.thr[gi]);
+                float c1 = 0.f, c2 = 0.f;
+                if (l < L) {
+                    c1 = __ldg(&Q.c1[gi]);
+                    c2 = __ldg(&Q.c2[gi]);
+                }
+#pragma unroll
+                for (int r = 0; r < PPW; ++r) {
+                    if (!((vmask >> r) & 1u)) continue;
+                    const int m = warp * PPW + r;
+                    const float du = accv(r, qq < NQA ? qq : 0);
+                    const float u = ub + du;
+                    const float bound = __fadd_ru(__fmul_ru(rnn, X[r]), th);
+                    const bool cert = __fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound;
+                    uncbA[r] |= (uint32_t)!cert << qq;
+                    flipbA[r] |= (uint32_t)(cert && ((u >= 0.f) != (ub >= 0.f))) << qq;
+                    if (l < L) {
+                        const float dh = act_delta(net.act, du, u, c1, c2);
+                        nsumA[r] = fmaf(dh, dh, nsumA[r]);
+                        usumA[r] = fmaf(u, u, usumA[r]);
+                        S.A[m][n] = dh;
+                    } else {
+                        S.A[m][n] = u;
+                    }
+                }
+            } else if ((qq < NQA && n < N) || (l < L && n < HS)) {
+#pragma unroll
+                for (int r = 0; r < PPW; ++r)
+                    if ((vmask >> r) & 1u) S.A[warp * PPW + r][n] = 0.f;
+            }
+        }
+    }
 #pragma unroll
     for (int r = 0; r < PPW; ++r) {
         const int m = warp * PPW + r;
@@ -263,40 +319,48 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
         const float X = __fmaf_ru(gl, Nin, Ein);
         float nsum = 0.f, usum = 0.f;
         uint32_t uncb = 0u, flipb = 0u;  // per slot: uncertain sign, certain change (handled after)
+        if (one) {
+            nsum = nsumA[r];
+            usum = usumA[r];
+            uncb = uncbA[r];
+            flipb = flipbA[r];
+        }
+        if (!one) {
 #pragma unroll
-        for (int qq = 0; qq < NQ; ++qq) {
-            const int n = qq < NQA ? slot_neuron<NQA>(lane, qq) : lane + 32 * qq;  // position
-            // neuron at position n; -1: a padding position (output change 0)
-            const int no = (cmp && l < L) ? (n < cntN ? Q.perm[off + n] : -1) : n;
-            if (qq < NQA && n < N && no < 0) {
-                S.A[m][n] = 0.f;
-            } else if (qq < NQA && n < N) {
-                const int gi = off + no;
-                const float du = accv(r, qq < NQA ? qq : 0);
-                const float ub = __ldg(&Q.ub32[gi]);
-                const float u = ub + du;
-                const float rnn = __ldg(&rn[no]);
-                // |du - exact|: rounding (a priori, or a posteriori with one neuron per lane) + propagated
-                float bnd = __fmul_ru(rnn, X);
-                if (PER_NEURON) {
-                    const float rho = __fmul_ru(kUseg, __fmaf_ru(rnn, Nin, chk[r]));
-                    bnd = fminf(bnd, __fmaf_ru(rnn, Ein, rho));
-                    if (l == L && no < 32) S.rho[m][no] = fminf(__fmul_ru(rnn, __fmul_ru(gl, Nin)), rho);
+            for (int qq = 0; qq < NQ; ++qq) {
+                const int n = qq < NQA ? slot_neuron<NQA>(lane, qq) : lane + 32 * qq;  // position
+                // neuron at position n; -1: a padding position (output change 0)
+                const int no = (cmp && l < L) ? (n < cntN ? Q.perm[off + n] : -1) : n;
+                if (qq < NQA && n < N && no < 0) {
+                    S.A[m][n] = 0.f;
+                } else if (qq < NQA && n < N) {
+                    const int gi = off + no;
+                    const float du = accv(r, qq < NQA ? qq : 0);
+                    const float ub = __ldg(&Q.ub32[gi]);
+                    const float u = ub + du;
+                    const float rnn = __ldg(&rn[no]);
+                    // |du - exact|: rounding (a priori, or a posteriori with one neuron per lane) + propagated
+                    float bnd = __fmul_ru(rnn, X);
+                    if (PER_NEURON) {
+                        const float rho = __fmul_ru(kUseg, __fmaf_ru(rnn, Nin, chk[r]));
+                        bnd = fminf(bnd, __fmaf_ru(rnn, Ein, rho));
+                        if (l == L && no < 32) S.rho[m][no] = fminf(__fmul_ru(rnn, __fmul_ru(gl, Nin)), rho);
+                    }
+                    const float bound = __fadd_ru(bnd, __ldg(&Q.thr[gi]));
+                    const bool cert = __fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound;
+                    uncb |= (uint32_t)!cert << qq;
+                    flipb |= (uint32_t)(cert && ((u >= 0.f) != (ub >= 0.f))) << qq;
+                    if (l < L) {
+                        const float dh = act_delta(net.act, du, u, __ldg(&Q.c1[gi]), __ldg(&Q.c2[gi]));
+                        nsum = fmaf(dh, dh, nsum);
+                        usum = fmaf(u, u, usum);
+                        S.A[m][n] = dh;
+                    } else {
+                        S.A[m][n] = u;
+                    }
+                } else if (l < L && n < HS) {
+                    S.A[m][n] = 0.f;
                 }
-                const float bound = __fadd_ru(bnd, __ldg(&Q.thr[gi]));
-                const bool cert = __fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound;
-                uncb |= (uint32_t)!cert << qq;
-                flipb |= (uint32_t)(cert && ((u >= 0.f) != (ub >= 0.f))) << qq;
-                if (l < L) {
-                    const float dh = act_delta(net.act, du, u, __ldg(&Q.c1[gi]), __ldg(&Q.c2[gi]));
-                    nsum = fmaf(dh, dh, nsum);
-                    usum = fmaf(u, u, usum);
-                    S.A[m][n] = dh;
-                } else {
-                    S.A[m][n] = u;
-                }
-            } else if (l < L && n < HS) {
-                S.A[m][n] = 0.f;
             }
         }
         if (uncb && Q.flip) S.unc[m] = 1;  // signs matter only for coverage
@@ -333,6 +397,93 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
         }
     }
     __syncwarp();
+}
+
+// Layer 1 of a warp's PPW points when they all belong to one query: the same
+// arithmetic as the per-point loop of the kernel (per point, the sum over p in
+// order of fl(W_1[j][pix_p] * fl(dv_p / 255))), with each weight and column
+// constant loaded once for the PPW points instead of once per point.
+template <int PPW, int NQ>
+__device__ __forceinline__ void layer1_one_query(SimtSmem<PPW, NQ>& S, const NetView& net,
+                                                 const QueryView& Q, int warp, int lane, bool cmp) {
+    const int L = net.L, H1 = net.dims[1];
+    const int W1 = cmp ? Q.kc[1] : H1;            // positions computed
+    const int cnt1 = cmp ? Q.kc[kMaxL + 2] : H1;  // kept neurons
+    const int s = Q.s;
+    unsigned vmask = 0u;  // valid points of the warp
+#pragma unroll
+    for (int r = 0; r < PPW; ++r) vmask |= (unsigned)(S.valid[warp * PPW + r] != 0) << r;
+    float dus[PPW][NQ];
+#pragma unroll
+    for (int r = 0; r < PPW; ++r)
+#pragma unroll
+        for (int qq = 0; qq < NQ; ++qq) dus[r][qq] = 0.f;
+    const float* __restrict__ W1T = net.WT[1];  // [H_0][H_1]
+    for (int p = 0; p < s; ++p) {
+        const float* wr = cmp ? Q.w1c + (size_t)p * H1 : W1T + (size_t)Q.pix[p] * H1;
+        float c[PPW];
+#pragma unroll
+        for (int r = 0; r < PPW; ++r) c[r] = ((vmask >> r) & 1u) ? S.cpx[warp * PPW + r][p] : 0.f;
+#pragma unroll
+        for (int qq = 0; qq < NQ; ++qq) {
+            const int j = lane + 32 * qq;
+            if (j < W1) {
+                const float w = __ldg(&wr[j]);
+#pragma unroll
+                for (int r = 0; r < PPW; ++r) dus[r][qq] += __fmul_rn(w, c[r]);
+            }
+        }
+    }
+    float nsum[PPW];
+    uint32_t uncb[PPW], flipb[PPW];
+#pragma unroll
+    for (int r = 0; r < PPW; ++r) {
+        nsum[r] = 0.f;
+        uncb[r] = flipb[r] = 0u;
+    }
+#pragma unroll
+    for (int qq = 0; qq < NQ; ++qq) {
+        const int j = lane + 32 * qq;                          // position
+        const int jo = cmp ? (j < cnt1 ? Q.perm[j] : -1) : j;  // neuron (-1: padding)
+        if (j < W1 && jo >= 0) {
+            const float ub = __ldg(&Q.ub32[jo]), th = __ldg(&Q.thr[jo]);
+            const float c1 = __ldg(&Q.c1[jo]), c2 = __ldg(&Q.c2[jo]);
+#pragma unroll
+            for (int r = 0; r < PPW; ++r) {
+                const float du = dus[r][qq];
+                const float u = ub + du;
+                const bool cert = __fmul_rd(fabsf(u), 1.f - 0x1p-22f) > th;
+                uncb[r] |= (uint32_t)!cert << qq;
+                flipb[r] |= (uint32_t)(cert && ((u >= 0.f) != (ub >= 0.f))) << qq;
+                const float dh = L > 1 ? act_delta(net.act, du, u, c1, c2) : u;
+                nsum[r] = fmaf(dh, dh, nsum[r]);
+                S.A[warp * PPW + r][j] = dh;
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < PPW; ++r) S.A[warp * PPW + r][j] = 0.f;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < PPW; ++r) {
+        if (!((vmask >> r) & 1u)) continue;
+        const int m = warp * PPW + r;
+        if (uncb[r] && Q.flip) S.unc[m] = 1;  // signs matter only for coverage
+        while (flipb[r]) {
+            const int jp = lane + 32 * (__ffs(flipb[r]) - 1);
+            const int j = cmp ? Q.perm[jp] : jp;
+            flipb[r] &= flipb[r] - 1u;
+            const int idx = atomicAdd(&S.fcnt[m][1], 1);
+            if (idx < FCAP) S.flist[m][1][idx] = (short)j;
+            if (Q.flip) set_bit_once(Q.flip, j);
+        }
+        const float ns = warp_sum(nsum[r]);
+        if (lane == 0) {
+            const float N = norm_up(ns);
+            S.N[m] = N;
+            S.E[m] = __fmaf_ru(0x1p-24f, N, Q.kvec[1]);
+        }
+    }
 }
 
 // Tiles of at most 64 accumulators per thread are built for two CTAs per SM.
@@ -423,7 +574,10 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
         }
 
         // ---- S2/S3: layer 1 from the delta tables
-        {
+        if (nq == 1) {
+            layer1_one_query<PPW, NQ>(S, net, qs[0], warp, lane, cmp);
+            __syncwarp();
+        } else {
             const int H1 = net.dims[1];
             const int W1 = cmp ? qs[0].kc[1] : H1;               // positions computed
             const int cnt1 = cmp ? qs[0].kc[kMaxL + 2] : H1;     // kept neurons
@@ -494,18 +648,18 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
         // ---- S4: dense layers on the deltas
         for (int l = 2; l <= L; ++l) {
             if (net.dims[l] <= 32) {
-                dense_layer<PPW, NQ, 1>(S, net, qs, l, warp, lane, cmp);
+                dense_layer<PPW, NQ, 1>(S, net, qs, l, warp, lane, cmp, nq == 1);
                 continue;
             }
             // a compacted hidden layer narrower than the variant's width runs with
             // fewer slots per lane (whole 128-column groups: the paired slot layout)
             const int ng = (cmp && l < L) ? (qs[0].kc[l] + 127) / 128 : NQ;
             if (NQ % 8 == 0 && NQ >= 8 && 8 * ng <= NQ)
-                dense_layer<PPW, NQ, (NQ % 8 == 0 && NQ >= 8 ? NQ / 2 : NQ)>(S, net, qs, l, warp, lane, cmp);
+                dense_layer<PPW, NQ, (NQ % 8 == 0 && NQ >= 8 ? NQ / 2 : NQ)>(S, net, qs, l, warp, lane, cmp, nq == 1);
             else if (NQ % 16 == 0 && 16 * ng <= 3 * NQ)
-                dense_layer<PPW, NQ, (NQ % 16 == 0 ? 3 * NQ / 4 : NQ)>(S, net, qs, l, warp, lane, cmp);
+                dense_layer<PPW, NQ, (NQ % 16 == 0 ? 3 * NQ / 4 : NQ)>(S, net, qs, l, warp, lane, cmp, nq == 1);
             else
-                dense_layer<PPW, NQ, NQ>(S, net, qs, l, warp, lane, cmp);
+                dense_layer<PPW, NQ, NQ>(S, net, qs, l, warp, lane, cmp, nq == 1);
         }
 
         // ---- S5: verdict (layer L values are in A[m][0..H_L))
