@@ -40,7 +40,7 @@ struct SimtSmem {
     static constexpr int MT = 8 * PPW;
     static constexpr int HS = 32 * NQ;
     static constexpr int WS = HS + 4;
-    float A[MT][HS];
+    float A[MT][HS + 4];  // rows padded by 16 bytes: float4 reads of 4 consecutive rows hit distinct banks
     float Wsm[2][KC][WS];
     unsigned long long t[MT];
     int q[MT];
@@ -120,10 +120,251 @@ __device__ __forceinline__ float warp_sum_ru(float v) {
 constexpr int CKC = 2;                       // chunks per checkpoint segment
 constexpr float kUseg = 0x1.00002p-24f * (float)(CKC * KC);  // u' CKL, rounded up
 
+// Register-blocked dense layer for a tile of one query (paired slot widths):
+// lane = (point group pg of 4, column group ng of 8); each lane accumulates 4
+// points x QL columns, warps split the tile into blocks of 16 points x CBW
+// columns. A weight float4 is read by 8 distinct lanes (one 128-byte
+// wavefront, broadcast to the 4 point groups) and an operand float4 by 4
+// (padded rows: one wavefront), so the FMAs, not the shared-memory reads, set
+// the pace. Per point and column the operations are those of dense_layer:
+// the same FMA sequence over k, checkpoints, sign tests and delta activation;
+// the per-point sums of squares are combined across lanes and warps in
+// another order (bounds that hold for any order).
+template <int PPW, int NQ, int NQA>
+__device__ __forceinline__ void dense_blocked(SimtSmem<PPW, NQ>& S, const NetView& net,
+                                              const QueryView& Q, int l, int warp, int lane, bool cmp) {
+    constexpr int HS = SimtSmem<PPW, NQ>::HS;
+    constexpr int MT = SimtSmem<PPW, NQ>::MT;
+    constexpr int HW = 32 * NQA;
+    constexpr int WSL = HW + 4;
+    constexpr int KCL = KC;
+    constexpr int NPB = PPW / 2;     // blocks of 16 points
+    constexpr int NCB = 16 / PPW;    // column blocks per point block
+    constexpr int CBW = HW / NCB;    // columns per block
+    constexpr int QL = CBW / 8;      // columns per lane
+    constexpr int QT = QL / 4;       // float4 groups per lane
+    static_assert(NPB * NCB == 8 && QL % 4 == 0 && QL <= 32 && 3 * NCB <= 32, "blocked layout");
+    const int L = net.L;
+    const int NS = net.dims[l];
+    const int K = cmp ? Q.kc[l - 1] : net.dims[l - 1];
+    const int N = (cmp && l < L) ? Q.kc[l] : NS;
+    const int cntN = (cmp && l < L) ? Q.kc[kMaxL + 1 + l] : NS;
+    const float* __restrict__ WT = cmp ? Q.wtc[l] : net.WT[l];  // [K][NS]
+    const int nchunks = (K + KCL - 1) / KCL;
+    float* const Wb = &S.Wsm[0][0][0];
+    const int pbk = warp % NPB, cb = warp / NPB;
+    const int pg = lane >> 3, ng = lane & 7;
+    const int colb = cb * CBW + 4 * ng;  // the lane's columns: colb + 32 t + e
+    int mrow[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) mrow[i] = pbk * 16 + 4 * i + pg;
+    float2 acc[4][QT][2];
+    float chk[4];  // sum_g ||s_g||^2 over this lane's columns, per point
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        chk[i] = 0.f;
+#pragma unroll
+        for (int t = 0; t < QT; ++t) acc[i][t][0] = acc[i][t][1] = make_float2(0.f, 0.f);
+    }
+    const bool vec = (N % 4) == 0 && (NS % 4) == 0;
+    auto load_chunk = [&](int c, int buf) {
+        float* const dst = Wb + buf * (KCL * WSL);
+        if (vec) {
+            for (int e = threadIdx.x; e < KCL * (HW / 4); e += THREADS) {
+                const int kk = e / (HW / 4), n = (e % (HW / 4)) * 4, k = c * KCL + kk;
+                const bool ok = k < K && n < N;
+                cp_async16(dst + kk * WSL + n, ok ? (const void*)&WT[(size_t)k * NS + n] : (const void*)WT, ok);
+            }
+        } else {
+            for (int e = threadIdx.x; e < KCL * HW; e += THREADS) {
+                const int kk = e / HW, n = e % HW, k = c * KCL + kk;
+                const bool ok = k < K && n < N;
+                cp_async4(dst + kk * WSL + n, ok ? (const void*)&WT[(size_t)k * NS + n] : (const void*)WT, ok);
+            }
+        }
+        cp_async_commit();
+    };
+    __syncthreads();  // previous users of Wsm are done
+    load_chunk(0, 0);
+    for (int c = 0; c < nchunks; ++c) {
+        const int buf = c & 1;
+        cp_async_wait0();
+        __syncthreads();  // chunk c visible to all; chunk c-1's buffer free
+        if (c + 1 < nchunks) load_chunk(c + 1, buf ^ 1);
+        const float* const wc = Wb + buf * (KCL * WSL);
+#pragma unroll
+        for (int kk = 0; kk < KCL; kk += 4) {
+            const int k0 = c * KCL + kk;
+            if (k0 > 0 && k0 % (CKC * KC) == 0) {  // checkpoint: the partial sums at k = k0
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int t = 0; t < QT; ++t)
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            chk[i] = __fmaf_ru(acc[i][t][h].x, acc[i][t][h].x, chk[i]);
+                            chk[i] = __fmaf_ru(acc[i][t][h].y, acc[i][t][h].y, chk[i]);
+                        }
+            }
+            float4 a4[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a4[i] = *reinterpret_cast<const float4*>(&S.A[mrow[i]][k0]);
+#pragma unroll
+            for (int k4 = 0; k4 < 4; ++k4) {
+#pragma unroll
+                for (int t = 0; t < QT; ++t) {
+                    const float4 w4 = *reinterpret_cast<const float4*>(wc + (kk + k4) * WSL + colb + 32 * t);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float av = k4 == 0 ? a4[i].x : k4 == 1 ? a4[i].y : k4 == 2 ? a4[i].z : a4[i].w;
+                        const float2 aa = make_float2(av, av);
+                        acc[i][t][0] = __ffma2_rn(aa, make_float2(w4.x, w4.y), acc[i][t][0]);
+                        acc[i][t][1] = __ffma2_rn(aa, make_float2(w4.z, w4.w), acc[i][t][1]);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();  // every warp has read this layer's operand rows: they are overwritten below
+    // epilogue: the sign tests and delta activation of each (point, column)
+    const float* rn = net.rownorm[l];
+    const int off = net.noff[l];
+    const float lf = net.lamfrob[l], gl = net.gam[l];
+    const float lam = net.act == ACT_SIGMOID ? 0.25f : 1.0f;
+    const float G = (float)((nchunks * KCL + CKC * KC - 1) / (CKC * KC));  // checkpoint segments
+    unsigned vmask = 0u;
+    float X[4], nsum[4], usum[4];
+    uint32_t uncb[4], flipb[4];  // per slot: uncertain sign, certain change
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        vmask |= (unsigned)(S.valid[mrow[i]] != 0) << i;
+        X[i] = __fmaf_ru(gl, S.N[mrow[i]], S.E[mrow[i]]);
+        nsum[i] = usum[i] = 0.f;
+        uncb[i] = flipb[i] = 0u;
+    }
+#pragma unroll
+    for (int t = 0; t < QT; ++t) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int n = colb + 32 * t + e;  // position
+            const int slot = 4 * t + e;
+            // neuron at position n; -1: a padding position (output change 0)
+            const int no = (cmp && l < L) ? (n < cntN ? Q.perm[off + n] : -1) : n;
+            if (n < N && no >= 0) {
+                const int gi = off + no;
+                const float ub = __ldg(&Q.ub32[gi]), rnn = __ldg(&rn[no]), th = __ldg(&Q.thr[gi]);
+                float c1 = 0.f, c2 = 0.f;
+                if (l < L) {
+                    c1 = __ldg(&Q.c1[gi]);
+                    c2 = __ldg(&Q.c2[gi]);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    if (!((vmask >> i) & 1u)) continue;
+                    const float du = (e & 1) ? acc[i][t][e >> 1].y : acc[i][t][e >> 1].x;
+                    const float u = ub + du;
+                    // |du - exact| <= ||W_i|| (gamma N + E) (a priori), plus the column's threshold
+                    const float bound = __fadd_ru(__fmul_ru(rnn, X[i]), th);
+                    const bool cert = __fmul_rd(fabsf(u), 1.f - 0x1p-22f) > bound;
+                    uncb[i] |= (uint32_t)!cert << slot;
+                    flipb[i] |= (uint32_t)(cert && ((u >= 0.f) != (ub >= 0.f))) << slot;
+                    if (l < L) {
+                        const float dh = act_delta(net.act, du, u, c1, c2);
+                        nsum[i] = fmaf(dh, dh, nsum[i]);
+                        usum[i] = fmaf(u, u, usum[i]);
+                        S.A[mrow[i]][n] = dh;
+                    } else {
+                        S.A[mrow[i]][n] = u;
+                    }
+                }
+            } else if (n < N || l < L) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if ((vmask >> i) & 1u) S.A[mrow[i]][n] = 0.f;
+            }
+        }
+    }
+    if (l < L && HS > HW)  // operand columns past this layer's width: no change
+        for (int e = threadIdx.x; e < MT * (HS - HW); e += THREADS)
+            S.A[e / (HS - HW)][HW + e % (HS - HW)] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        if (!((vmask >> i) & 1u)) continue;
+        const int m = mrow[i];
+        if (uncb[i] && Q.flip) S.unc[m] = 1;  // signs matter only for coverage
+        while (flipb[i]) {
+            const int slot = __ffs(flipb[i]) - 1;
+            flipb[i] &= flipb[i] - 1u;
+            const int np = colb + 32 * (slot >> 2) + (slot & 3);
+            const int n = (cmp && l < L) ? Q.perm[off + np] : np;  // neuron
+            const int idx = atomicAdd(&S.fcnt[m][l], 1);
+            if (idx < FCAP) S.flist[m][l][idx] = (short)n;
+            if (Q.flip) set_bit_once(Q.flip, off + n);
+        }
+    }
+    // per point: sums over the 8 lanes of its group, then over the NCB column blocks
+    // (partials parked in rho, which only an output layer of width <= 32 uses)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float a = nsum[i], b = usum[i], v = chk[i];
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+            v = __fadd_ru(v, __shfl_xor_sync(0xffffffffu, v, o));
+        }
+        if (ng == 0 && ((vmask >> i) & 1u)) {
+            float* pp = &S.rho[mrow[i]][3 * cb];
+            pp[0] = a;
+            pp[1] = b;
+            pp[2] = v;
+        }
+    }
+    __syncthreads();  // partials written; every read of the layer's input N, E done
+    for (int m = threadIdx.x; m < MT; m += THREADS) {
+        if (!S.valid[m]) continue;
+        float ns = 0.f, us = 0.f, vc = 0.f;
+#pragma unroll
+        for (int c = 0; c < NCB; ++c) {
+            ns += S.rho[m][3 * c];
+            us += S.rho[m][3 * c + 1];
+            vc = __fadd_ru(vc, S.rho[m][3 * c + 2]);
+        }
+        const float Nin = S.N[m], Ein = S.E[m];
+        const float vv = __fmul_ru(G, vc);  // ||V||_2^2 bound of the checkpoint sums
+        // rounding error vector of the layer, l2: min(a priori, a posteriori)
+        const float rpri = __fmul_ru(__fmul_ru(lf, gl), Nin);
+        const float rpost = __fmul_ru(lam, __fmul_ru(kUseg, __fmaf_ru(net.frob[l], Nin, __fsqrt_ru(vv))));
+        const float rl = fminf(rpri, rpost);
+        if (l < L) {
+            const float Nl = norm_up(ns);
+            // lambda (rounding) + lambda sigma_l E_{l-1} + kvec_l + u N_l
+            float El = __fadd_ru(rl, Q.kvec[l]);
+            El = __fmaf_ru(net.lamsig[l], Ein, El);
+            El = __fmaf_ru(0x1p-24f, Nl, El);
+            if (net.act == ACT_SIGMOID) El = __fmaf_ru(0x1p-26f, norm_up(us), El);
+            S.N[m] = Nl;
+            S.E[m] = El;
+        } else {
+            S.N[m] = __fmul_ru(gl, Nin);  // gamma N_{L-1}: a priori dot-product rounding
+        }
+    }
+    __syncthreads();  // N, E and the rows of this layer are final
+}
+
 template <int PPW, int NQ, int NQA>
 __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView& net,
                                             const QueryView* __restrict__ qs, int l, int warp,
                                             int lane, bool cmp, bool oneq) {
+    // one query and a paired slot width that the blocked layout tiles
+    constexpr bool BLK = NQA % 4 == 0 && PPW % 2 == 0 && PPW <= 16 && (NQA * PPW) % 16 == 0 &&
+                         NQA * PPW <= 128;
+    if constexpr (BLK) {
+        if (oneq) {
+            dense_blocked<PPW, NQ, (BLK ? NQA : 4)>(S, net, qs[0], l, warp, lane, cmp);
+            return;
+        }
+    }
     constexpr int HS = SimtSmem<PPW, NQ>::HS;
     constexpr int HW = 32 * NQA;  // columns of the weight chunk in use
     constexpr bool PER_NEURON = NQA == 1;
