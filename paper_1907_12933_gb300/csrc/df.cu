@@ -368,6 +368,14 @@ __device__ __forceinline__ void block_sums_ru(float (&v)[M], float* red) {
     }
 }
 
+// Threads per position of a layer of Nn positions with K inputs: a narrow
+// layer (at most half a block) splits its dot products into chunks of k.
+__device__ __forceinline__ int df_split(int Nn, int K) {
+    if (2 * Nn > TDF || K < 64) return 1;
+    const int ks = TDF / Nn;
+    return ks < 32 ? ks : 32;
+}
+
 __device__ __forceinline__ float abs_up(float2 a) { return __fmul_ru(fabsf(a.x), 1.f + 0x1p-22f); }
 
 template <int PB>
@@ -383,6 +391,7 @@ k_df32(NetView net, const QueryView* __restrict__ qs, int nq, const QEntry* __re
     float2* dh = u + (size_t)PB * total;                                    // [PB][hmax]
     unsigned char* fl = reinterpret_cast<unsigned char*>(dh + (size_t)PB * hmax);  // [PB][total]
     __shared__ float redm[(TDF / 32) * 2 * PB];
+    __shared__ float2 part[PB][TDF];  // narrow layers: the chunk sums of each position
     __shared__ int nflip[PB][kMaxL + 2], only[PB][kMaxL + 2];
     __shared__ float2 dvs[PB][kMaxS];  // dv_p / 255 as a pair (|error| <= 2^-48 of it)
     __shared__ float dvm[PB][kMaxS];   // an upper bound of |dv_p / 255|
@@ -508,23 +517,20 @@ k_df32(NetView net, const QueryView* __restrict__ qs, int nq, const QEntry* __re
             const int Nn = (cmp && l < L) ? qs[0].kc[l] : NS;
             const int cntN = (cmp && l < L) ? qs[0].kc[kMaxL + 1 + l] : NS;
             const float* WT = cmp ? qs[0].wtc[l] : net.WT[l];
-            const float cK = (float)(K + 2) * 0x1p-45f;
+            const int KS = df_split(Nn, K);  // threads per neuron (narrow layers)
+            const float cK = (float)(K + 2 + (KS > 1 ? KS : 0)) * 0x1p-45f;
             float X[PB];  // cK N + E: with ||W_i||, the propagated and summation error of u_i
 #pragma unroll
             for (int b = 0; b < PB; ++b) X[b] = __fmaf_ru(cK, N[b], E[b]);
             float sq[2 * PB];
 #pragma unroll
             for (int i = 0; i < 2 * PB; ++i) sq[i] = 0.f;
-            for (int i = threadIdx.x; i < Nn; i += TDF) {  // position i holds neuron io
-                if (i >= cntN) continue;  // padding: change 0
-                const int io = (cmp && l < L) ? qs[0].perm[off + i] : i;
-                float S[PB], sl[PB];
+            // S + sl over k in [j0, j1) for position i, in order of k (loads of several k in flight)
+            auto dot = [&](int i, int j0, int j1, float (&S)[PB], float (&sl)[PB]) {
 #pragma unroll
                 for (int b = 0; b < PB; ++b) S[b] = sl[b] = 0.f;
-                // unrolled so that the weight loads of several j are in flight (each
-                // point's sum still runs in order of j)
 #pragma unroll 4
-                for (int j = 0; j < K; ++j) {
+                for (int j = j0; j < j1; ++j) {
                     const float w = WT[(size_t)j * NS + i];
 #pragma unroll
                     for (int b = 0; b < PB; ++b) {
@@ -539,6 +545,9 @@ k_df32(NetView net, const QueryView* __restrict__ qs, int nq, const QEntry* __re
                         sl[b] = __fadd_rn(sl[b], __fadd_rn(er, ep));
                     }
                 }
+            };
+            // the sign tests and the next delta of position i (neuron io) from its sums
+            auto finish = [&](int io, const float (&S)[PB], const float (&sl)[PB]) {
                 const float rn = net.rownorm[l][io];
                 unsigned cq = ~0u;
                 float2 ubd = make_float2(0.f, 0.f), nhb = make_float2(0.f, 0.f);
@@ -578,6 +587,40 @@ k_df32(NetView net, const QueryView* __restrict__ qs, int nq, const QEntry* __re
                         u[(size_t)b * total + off + io] = a;  // output potentials for the verdict
                     }
                 }
+            };
+            if (KS == 1) {
+                for (int i = threadIdx.x; i < Nn; i += TDF) {  // position i holds neuron io
+                    if (i >= cntN) continue;  // padding: change 0
+                    float S[PB], sl[PB];
+                    dot(i, 0, K, S, sl);
+                    finish((cmp && l < L) ? qs[0].perm[off + i] : i, S, sl);
+                }
+            } else {
+                // KS threads per position, each a contiguous chunk of k; the chunks' pairs
+                // are then added in chunk order (each addition within the bound's KS term)
+                const int Kc = (K + KS - 1) / KS;
+                {
+                    const int i = threadIdx.x / KS, c = threadIdx.x % KS;
+                    if (i < Nn && i < cntN) {
+                        float S[PB], sl[PB];
+                        dot(i, min(K, c * Kc), min(K, (c + 1) * Kc), S, sl);
+#pragma unroll
+                        for (int b = 0; b < PB; ++b) part[b][threadIdx.x] = make_float2(S[b], sl[b]);
+                    }
+                }
+                __syncthreads();
+                const int i = threadIdx.x;
+                if (i < Nn && i < cntN) {
+                    float S[PB], sl[PB];
+#pragma unroll
+                    for (int b = 0; b < PB; ++b) {
+                        float2 acc = make_float2(0.f, 0.f);
+                        for (int c = 0; c < KS; ++c) acc = df_add(acc, part[b][i * KS + c]);
+                        S[b] = acc.x;
+                        sl[b] = acc.y;
+                    }
+                    finish((cmp && l < L) ? qs[0].perm[off + i] : i, S, sl);
+                }
             }
             __syncthreads();  // dh of layer l-1 fully consumed
             if (l < L) {
@@ -610,7 +653,8 @@ k_df32(NetView net, const QueryView* __restrict__ qs, int nq, const QEntry* __re
             const int HL = net.dims[L], offL = net.noff[L];
             const float2* y = u + (size_t)b * total + offL;
             const int D = Q.cnt->D;
-            const float cKL = (float)(net.dims[L - 1] + 2) * 0x1p-45f;
+            // the output layer's summation term (a split layer adds at most 32 to K + 2)
+            const float cKL = (float)(net.dims[L - 1] + 2 + 32) * 0x1p-45f;
             const float cN = __fmul_ru(cKL, N[b]);
             bool unsafe = false, safe = true;
             if (Q.prop == PROP_THRESHOLD) {  // Eq. 11: per output ||W_o|| (cK N + E) + eub_o
