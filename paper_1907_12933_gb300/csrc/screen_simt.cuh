@@ -728,7 +728,9 @@ __device__ __forceinline__ void layer1_one_query(SimtSmem<PPW, NQ>& S, const Net
 }
 
 // Tiles of at most 64 accumulators per thread are built for two CTAs per SM.
-template <int PPW, int NQ>
+// ONEQ: every tile belongs to query 0 (nq == 1); the instantiation keeps only
+// the paths of that case (the other one's code would crowd the instruction cache).
+template <int PPW, int NQ, bool ONEQ>
 __global__ void __launch_bounds__(THREADS, PPW * NQ <= 64 ? 2 : 1)
 k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
               const unsigned long long* __restrict__ tile_prefix, unsigned long long n_tiles,
@@ -741,8 +743,9 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int L = net.L;
 
+    if (ONEQ) nq = 1;
     // compacted columns: one query whose set-up built them (tensor-screen calls)
-    const bool cmp = nq == 1 && qs[0].compact;
+    const bool cmp = ONEQ && qs[0].compact;
     unsigned long long tiles = n_tiles;
     unsigned long long gcount = 0;
     if (gather) {
@@ -815,7 +818,7 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
         }
 
         // ---- S2/S3: layer 1 from the delta tables
-        if (nq == 1) {
+        if (ONEQ) {
             layer1_one_query<PPW, NQ>(S, net, qs[0], warp, lane, cmp);
             __syncwarp();
         } else {
@@ -889,18 +892,18 @@ k_screen_simt(NetView net, const QueryView* __restrict__ qs, int nq,
         // ---- S4: dense layers on the deltas
         for (int l = 2; l <= L; ++l) {
             if (net.dims[l] <= 32) {
-                dense_layer<PPW, NQ, 1>(S, net, qs, l, warp, lane, cmp, nq == 1);
+                dense_layer<PPW, NQ, 1>(S, net, qs, l, warp, lane, cmp, ONEQ);
                 continue;
             }
             // a compacted hidden layer narrower than the variant's width runs with
             // fewer slots per lane (whole 128-column groups: the paired slot layout)
             const int ng = (cmp && l < L) ? (qs[0].kc[l] + 127) / 128 : NQ;
             if (NQ % 8 == 0 && NQ >= 8 && 8 * ng <= NQ)
-                dense_layer<PPW, NQ, (NQ % 8 == 0 && NQ >= 8 ? NQ / 2 : NQ)>(S, net, qs, l, warp, lane, cmp, nq == 1);
+                dense_layer<PPW, NQ, (NQ % 8 == 0 && NQ >= 8 ? NQ / 2 : NQ)>(S, net, qs, l, warp, lane, cmp, ONEQ);
             else if (NQ % 16 == 0 && 16 * ng <= 3 * NQ)
-                dense_layer<PPW, NQ, (NQ % 16 == 0 ? 3 * NQ / 4 : NQ)>(S, net, qs, l, warp, lane, cmp, nq == 1);
+                dense_layer<PPW, NQ, (NQ % 16 == 0 ? 3 * NQ / 4 : NQ)>(S, net, qs, l, warp, lane, cmp, ONEQ);
             else
-                dense_layer<PPW, NQ, NQ>(S, net, qs, l, warp, lane, cmp, nq == 1);
+                dense_layer<PPW, NQ, NQ>(S, net, qs, l, warp, lane, cmp, ONEQ);
         }
 
         // ---- S5: verdict (layer L values are in A[m][0..H_L))
@@ -1016,7 +1019,7 @@ void launch_variant(const NetView& net, const QueryView* d_qs, int nq, const uns
                     unsigned long long gcap, Queue out, int level, int n_sm, cudaStream_t st,
                     unsigned long long* claim = nullptr) {
     const size_t smem = sizeof(SimtSmem<PPW, NQ>);
-    auto kern = k_screen_simt<PPW, NQ>;
+    auto kern = nq == 1 ? k_screen_simt<PPW, NQ, true> : k_screen_simt<PPW, NQ, false>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = smem < 60000 ? 2 : 1;
     const int tuned = gather ? net.simt_ctas_gather : net.simt_ctas_range;
