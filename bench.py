@@ -221,10 +221,10 @@ class Clocks:
 # Keyed by (workload, precision, coverage, s, k); other configurations report null.
 PROFILED_TRAFFIC = {
     ("mlp784x512x512_relu_s6k7", "bf16", True, 6, 7): {
-        "screen (first pass over every point)": 1197568 + 1070080,
-        "split tensor pass": 50189312 + 126976,
-        "FP32 pass": 22082304 + 46848,
-        "double-float pass": 2501376 + 129792,
+        "screen (first pass over every point)": 1344256 + 1194752,
+        "split tensor pass": 50234368 + 161536,
+        "FP32 pass": 22650624 + 97536,
+        "double-float pass": 1776896 + 1280,
     },
 }
 
