@@ -421,74 +421,132 @@ __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView&
         }
         cp_async_commit();
     };
-    __syncthreads();  // previous users of Wsm are done
-    load_chunk(0, 0);
-    for (int c = 0; c < nchunks; ++c) {
-        const int buf = c & 1;
-        cp_async_wait0();
-        __syncthreads();  // chunk c visible to all; chunk c-1's buffer free
-        if (c + 1 < nchunks) load_chunk(c + 1, buf ^ 1);
-        const float* const wc = Wb + buf * (KCL * WSL);
-#pragma unroll KUNROLL
-        for (int kk = 0; kk < KCL; kk += AK) {
-            const int k0 = c * KCL + kk;
-            if (k0 > 0 && k0 % (CKC * KC) == 0) {  // checkpoint: the partial sums at k = k0
+    // A narrow output layer (one neuron per lane, at most 16 outputs): GS lane
+    // groups share each output, group g taking the blocks of 4 k whose index is
+    // g mod GS; each group sum keeps its own checkpoints (segments of 16 of its
+    // terms), and the groups are added after the loop with |each addition's
+    // result| added to V (its rounding is at most u times that), so the a
+    // posteriori bound u' 16 (V + ||W_i|| ||x||) and the a priori one still hold.
+    const int GS = (PER_NEURON && l == L && N >= 1 && N <= 16) ? min(32 / N, 8) : 1;
+    const int gq = lane / (N >= 1 ? N : 1), nq = lane - gq * (N >= 1 ? N : 1);
+    if (PER_NEURON && GS > 1) {
+        // its weights (K x N floats, read by every tile) are loaded straight from
+        // global memory and stay in L1: no chunk barriers. The operand rows are
+        // this warp's own points (written before the layer's call).
+        __syncwarp();
+        if (gq < GS) {
+            int own = 0;  // this lane's terms so far
+            // unrolled so that the loads of several blocks are in flight (each
+            // group's sum still runs in order of its k)
+#pragma unroll 4
+            for (int kb = 4 * gq; kb < K; kb += 4 * GS) {
+                if (own > 0 && (own & 15) == 0) {  // checkpoint: this group's partial sums
 #pragma unroll
-                for (int r = 0; r < PPW; ++r) {
-                    if (PER_NEURON) {
-                        chk[r] = __fadd_ru(chk[r], fabsf(acc[r][0].x));
-                    } else {
-#pragma unroll
-                        for (int qq = 0; qq < NQA; ++qq) chk[r] = __fmaf_ru(accv(r, qq), accv(r, qq), chk[r]);
-                    }
+                    for (int r = 0; r < PPW; ++r) chk[r] = __fadd_ru(chk[r], fabsf(acc[r][0].x));
                 }
-            }
-            float av[PPW][AK];
+                float4 a4[PPW];
 #pragma unroll
-            for (int r = 0; r < PPW; ++r) {
-                if (AK == 4) {
-                    const float4 t = *reinterpret_cast<const float4*>(&S.A[warp * PPW + r][k0]);
-                    av[r][0] = t.x;
-                    av[r][1] = t.y;
-                    av[r][AK > 2 ? 2 : 0] = t.z;
-                    av[r][AK > 3 ? 3 : 0] = t.w;
-                } else {
-                    const float2 t = *reinterpret_cast<const float2*>(&S.A[warp * PPW + r][k0]);
-                    av[r][0] = t.x;
-                    av[r][1] = t.y;
-                }
-            }
+                for (int r = 0; r < PPW; ++r) a4[r] = *reinterpret_cast<const float4*>(&S.A[warp * PPW + r][kb]);
 #pragma unroll
-            for (int k4 = 0; k4 < AK; ++k4) {
-                if (PAIRED) {
-                    // paired FMA (each half rounds to nearest like fmaf, half the
-                    // instructions), one float4 of weights at a time
-                    float2 aa[PPW];
-#pragma unroll
-                    for (int r = 0; r < PPW; ++r) aa[r] = make_float2(av[r][k4], av[r][k4]);
-#pragma unroll
-                    for (int g = 0; g < NQA / 4; ++g) {
-                        const float4 w4 = *reinterpret_cast<const float4*>(wc + (kk + k4) * WSL + 128 * g + 4 * lane);
-#pragma unroll
-                        for (int r = 0; r < PPW; ++r) {
-                            acc[r][2 * g] = __ffma2_rn(aa[r], make_float2(w4.x, w4.y), acc[r][2 * g]);
-                            acc[r][2 * g + 1] = __ffma2_rn(aa[r], make_float2(w4.z, w4.w), acc[r][2 * g + 1]);
-                        }
-                    }
-                } else {
-                    float wv[NQA];
-#pragma unroll
-                    for (int qq = 0; qq < NQA; ++qq) wv[qq] = wc[(kk + k4) * WSL + lane + 32 * qq];
+                for (int e = 0; e < 4; ++e) {
+                    const int k = kb + e;
+                    const float w = k < K ? __ldg(&WT[(size_t)k * NS + nq]) : 0.f;
 #pragma unroll
                     for (int r = 0; r < PPW; ++r) {
+                        const float av = e == 0 ? a4[r].x : e == 1 ? a4[r].y : e == 2 ? a4[r].z : a4[r].w;
+                        acc[r][0].x = fmaf(av, w, acc[r][0].x);
+                    }
+                }
+                own += 4;
+            }
+        }
+    } else {
+        __syncthreads();  // previous users of Wsm are done
+        load_chunk(0, 0);
+        for (int c = 0; c < nchunks; ++c) {
+            const int buf = c & 1;
+            cp_async_wait0();
+            __syncthreads();  // chunk c visible to all; chunk c-1's buffer free
+            if (c + 1 < nchunks) load_chunk(c + 1, buf ^ 1);
+            const float* const wc = Wb + buf * (KCL * WSL);
+#pragma unroll KUNROLL
+            for (int kk = 0; kk < KCL; kk += AK) {
+                const int k0 = c * KCL + kk;
+                if (k0 > 0 && k0 % (CKC * KC) == 0) {  // checkpoint: the partial sums at k = k0
 #pragma unroll
-                        for (int qq = 0; qq < NQA; ++qq) accv(r, qq) = fmaf(av[r][k4], wv[qq], accv(r, qq));
+                    for (int r = 0; r < PPW; ++r) {
+                        if (PER_NEURON) {
+                            chk[r] = __fadd_ru(chk[r], fabsf(acc[r][0].x));
+                        } else {
+#pragma unroll
+                            for (int qq = 0; qq < NQA; ++qq) chk[r] = __fmaf_ru(accv(r, qq), accv(r, qq), chk[r]);
+                        }
+                    }
+                }
+                float av[PPW][AK];
+#pragma unroll
+                for (int r = 0; r < PPW; ++r) {
+                    if (AK == 4) {
+                        const float4 t = *reinterpret_cast<const float4*>(&S.A[warp * PPW + r][k0]);
+                        av[r][0] = t.x;
+                        av[r][1] = t.y;
+                        av[r][AK > 2 ? 2 : 0] = t.z;
+                        av[r][AK > 3 ? 3 : 0] = t.w;
+                    } else {
+                        const float2 t = *reinterpret_cast<const float2*>(&S.A[warp * PPW + r][k0]);
+                        av[r][0] = t.x;
+                        av[r][1] = t.y;
+                    }
+                }
+#pragma unroll
+                for (int k4 = 0; k4 < AK; ++k4) {
+                    if (PAIRED) {
+                        // paired FMA (each half rounds to nearest like fmaf, half the
+                        // instructions), one float4 of weights at a time
+                        float2 aa[PPW];
+#pragma unroll
+                        for (int r = 0; r < PPW; ++r) aa[r] = make_float2(av[r][k4], av[r][k4]);
+#pragma unroll
+                        for (int g = 0; g < NQA / 4; ++g) {
+                            const float4 w4 = *reinterpret_cast<const float4*>(wc + (kk + k4) * WSL + 128 * g + 4 * lane);
+#pragma unroll
+                            for (int r = 0; r < PPW; ++r) {
+                                acc[r][2 * g] = __ffma2_rn(aa[r], make_float2(w4.x, w4.y), acc[r][2 * g]);
+                                acc[r][2 * g + 1] = __ffma2_rn(aa[r], make_float2(w4.z, w4.w), acc[r][2 * g + 1]);
+                            }
+                        }
+                    } else {
+                        float wv[NQA];
+#pragma unroll
+                        for (int qq = 0; qq < NQA; ++qq) wv[qq] = wc[(kk + k4) * WSL + lane + 32 * qq];
+#pragma unroll
+                        for (int r = 0; r < PPW; ++r) {
+#pragma unroll
+                            for (int qq = 0; qq < NQA; ++qq) accv(r, qq) = fmaf(av[r][k4], wv[qq], accv(r, qq));
+                        }
                     }
                 }
             }
         }
     }
 
+    if (PER_NEURON && GS > 1) {  // add the groups' sums into the lanes of group 0
+#pragma unroll
+        for (int r = 0; r < PPW; ++r) {
+            const float v = acc[r][0].x, vc = chk[r];
+            float tot = v, vs = vc;
+            for (int g = 1; g < GS; ++g) {
+                const float o = __shfl_sync(0xffffffffu, v, (lane + g * N) & 31);
+                const float oc = __shfl_sync(0xffffffffu, vc, (lane + g * N) & 31);
+                tot = __fadd_rn(tot, o);
+                vs = __fadd_ru(vs, __fadd_ru(oc, fabsf(tot)));
+            }
+            if (gq == 0) {
+                acc[r][0].x = tot;
+                chk[r] = vs;
+            }
+        }
+    }
     // epilogue of layer l
     const float* rn = net.rownorm[l];
     const int off = net.noff[l];
