@@ -61,6 +61,8 @@ constexpr int SLOTB = 16384;             // weight slot: 128 rows (one N slice) 
 constexpr int FCAP = 4;
 constexpr int PMAX = 4;
 constexpr int MROWS = 128;
+// floats of the layer-1 staging union past the per-row input changes
+constexpr int kWgen = kStageAll * 2 * kStageR * 64 - MROWS * kMaxS;
 
 struct TcSmem {
     uint8_t A[NA][SLOT];
@@ -96,6 +98,9 @@ struct TcSmem {
         float tstage[kStageAll][2][kStageR][64];
         // other tiles: per row and pixel fl(dv_p / 255), the pixel's input change
         float cpx[MROWS][kMaxS];
+        // the same tiles: past cpx (from float MROWS * kMaxS on), the s weight rows
+        // W_1[.][pix_p] of the layer-1 columns, when they fit
+        float wgen[kStageAll * 2 * kStageR * 64];
     };
     int curq;
     int npref;
@@ -534,6 +539,15 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 S.npref = np;
                 S.fast = fast_t;
             }
+            if (!fast_t) {  // general layer-1 path: the query's s weight rows, once per tile
+                const int Wc = 64 * S.kch[2];
+                if (s * Wc <= kWgen)
+                    for (int e = wtid; e < s * Wc; e += NWT) {
+                        const int p = e / Wc, jj = e - p * Wc;
+                        S.wgen[MROWS * kMaxS + e] =
+                            jj >= H1 ? 0.f : (cmp ? Q.w1c[(size_t)p * H1 + jj] : net.WT[1][(size_t)Q.pix[p] * H1 + jj]);
+                    }
+            }
             {   // the query's layer-1 column constants, for the build below: warp c of the
                 // loop takes chunk c (its lanes the column pairs), whole warps only
                 const float4* __restrict__ kcl = cmp ? Q.kcolc : Q.kcol;
@@ -677,9 +691,12 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                                                         : make_float2(0.f, 0.f);
                             pfrom[ii] = !ri.w ? s : (pi >= 0 ? s - ni : 0);
                         }
+                        const int Wc = 64 * kch;
+                        const bool wsh = s * Wc <= kWgen;  // the weight rows were staged (tile-uniform)
                         for (int p = 0; p < s; ++p) {
-                            const float2 w2 = __ldg(reinterpret_cast<const float2*>(
-                                cmp ? &Q.w1c[(size_t)p * H1 + j] : &net.WT[1][(size_t)S.pixs[p] * H1 + j]));
+                            const float2 w2 = wsh ? *reinterpret_cast<const float2*>(&S.wgen[MROWS * kMaxS + p * Wc + j])
+                                                  : __ldg(reinterpret_cast<const float2*>(
+                                                        cmp ? &Q.w1c[(size_t)p * H1 + j] : &net.WT[1][(size_t)S.pixs[p] * H1 + j]));
 #pragma unroll
                             for (int ii = 0; ii < RB; ++ii) {
                                 if (p < pfrom[ii]) continue;
