@@ -676,10 +676,12 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         }
                     } else {
                         // general path: a row's outer-prefix sum when it has a slot, then
-                        // W_1[j][pix_p] * fl(dv_p / 255) for its remaining pixels in order.
+                        // W_1[j][pix_p] * fl(dv_p / 255) for its remaining pixels in order,
+                        // each term fused into the sum (paired FMA over the lane's two
+                        // columns: one rounding per term, against two in a table entry
+                        // plus the sum, so inside the prologue's table-sum bound e1).
                         // The weight pair of pixel p is the same for every row: one load
-                        // per pixel serves the batch. Per term at most 2u |t_p| from the
-                        // exact product: inside the prologue's table-sum bound e1.
+                        // per pixel serves the batch.
                         int pfrom[RB];
 #pragma unroll
                         for (int ii = 0; ii < RB; ++ii) {
@@ -701,8 +703,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                             for (int ii = 0; ii < RB; ++ii) {
                                 if (p < pfrom[ii]) continue;
                                 const float c = S.cpx[wid * RPW + i0 + ii][p];
-                                dus[ii].x += __fmul_rn(w2.x, c);
-                                dus[ii].y += __fmul_rn(w2.y, c);
+                                dus[ii] = __ffma2_rn(w2, make_float2(c, c), dus[ii]);
                             }
                         }
                     }
