@@ -221,10 +221,10 @@ class Clocks:
 # Keyed by (workload, precision, coverage, s, k); other configurations report null.
 PROFILED_TRAFFIC = {
     ("mlp784x512x512_relu_s6k7", "bf16", True, 6, 7): {
-        "screen (first pass over every point)": 1344256 + 1194752,
-        "split tensor pass": 50234368 + 161536,
-        "FP32 pass": 22650624 + 97536,
-        "double-float pass": 1776896 + 1280,
+        "screen (first pass over every point)": 1238016 + 1092352,
+        "split tensor pass": 50250496 + 98560,
+        "FP32 pass": 22883328 + 101888,
+        "double-float pass": 1807104 + 1536,
     },
 }
 
