@@ -517,8 +517,11 @@ k_df32(NetView net, const QueryView* __restrict__ qs, int nq, const QEntry* __re
             const int Nn = (cmp && l < L) ? qs[0].kc[l] : NS;
             const int cntN = (cmp && l < L) ? qs[0].kc[kMaxL + 1 + l] : NS;
             const float* WT = cmp ? qs[0].wtc[l] : net.WT[l];
-            const int KS = df_split(Nn, K);  // threads per neuron (narrow layers)
-            const float cK = (float)(K + 2 + (KS > 1 ? KS : 0)) * 0x1p-45f;
+            // positions run in rounds of TDF; a round of at most half a block (the
+            // last one) splits each dot product over KS <= 32 threads
+            const int remL = Nn % TDF;
+            const bool anysplit = remL != 0 && df_split(remL, K) > 1;
+            const float cK = (float)(K + 2 + (anysplit ? 32 : 0)) * 0x1p-45f;
             float X[PB];  // cK N + E: with ||W_i||, the propagated and summation error of u_i
 #pragma unroll
             for (int b = 0; b < PB; ++b) X[b] = __fmaf_ru(cK, N[b], E[b]);
@@ -588,38 +591,42 @@ k_df32(NetView net, const QueryView* __restrict__ qs, int nq, const QEntry* __re
                     }
                 }
             };
-            if (KS == 1) {
-                for (int i = threadIdx.x; i < Nn; i += TDF) {  // position i holds neuron io
-                    if (i >= cntN) continue;  // padding: change 0
-                    float S[PB], sl[PB];
-                    dot(i, 0, K, S, sl);
-                    finish((cmp && l < L) ? qs[0].perm[off + i] : i, S, sl);
-                }
-            } else {
-                // KS threads per position, each a contiguous chunk of k; the chunks' pairs
-                // are then added in chunk order (each addition within the bound's KS term)
-                const int Kc = (K + KS - 1) / KS;
-                {
-                    const int i = threadIdx.x / KS, c = threadIdx.x % KS;
-                    if (i < Nn && i < cntN) {
+            for (int i0 = 0; i0 < Nn; i0 += TDF) {
+                const int rem = min(TDF, Nn - i0);
+                const int KS = df_split(rem, K);  // threads per position in this round
+                if (KS == 1) {
+                    const int i = i0 + threadIdx.x;  // position i holds neuron io
+                    if (i < Nn && i < cntN) {        // padding positions: change 0
                         float S[PB], sl[PB];
-                        dot(i, min(K, c * Kc), min(K, (c + 1) * Kc), S, sl);
-#pragma unroll
-                        for (int b = 0; b < PB; ++b) part[b][threadIdx.x] = make_float2(S[b], sl[b]);
+                        dot(i, 0, K, S, sl);
+                        finish((cmp && l < L) ? qs[0].perm[off + i] : i, S, sl);
                     }
-                }
-                __syncthreads();
-                const int i = threadIdx.x;
-                if (i < Nn && i < cntN) {
-                    float S[PB], sl[PB];
+                } else {
+                    // KS threads per position, each a contiguous chunk of k; the chunks'
+                    // pairs are then added in chunk order (within the bound's split term)
+                    const int Kc = (K + KS - 1) / KS;
+                    {
+                        const int i = i0 + threadIdx.x / KS, c = threadIdx.x % KS;
+                        if (i < Nn && i < cntN && threadIdx.x / KS < rem) {
+                            float S[PB], sl[PB];
+                            dot(i, min(K, c * Kc), min(K, (c + 1) * Kc), S, sl);
 #pragma unroll
-                    for (int b = 0; b < PB; ++b) {
-                        float2 acc = make_float2(0.f, 0.f);
-                        for (int c = 0; c < KS; ++c) acc = df_add(acc, part[b][i * KS + c]);
-                        S[b] = acc.x;
-                        sl[b] = acc.y;
+                            for (int b = 0; b < PB; ++b) part[b][threadIdx.x] = make_float2(S[b], sl[b]);
+                        }
                     }
-                    finish((cmp && l < L) ? qs[0].perm[off + i] : i, S, sl);
+                    __syncthreads();
+                    const int i = i0 + threadIdx.x;
+                    if (threadIdx.x < rem && i < cntN) {
+                        float S[PB], sl[PB];
+#pragma unroll
+                        for (int b = 0; b < PB; ++b) {
+                            float2 acc = make_float2(0.f, 0.f);
+                            for (int c = 0; c < KS; ++c) acc = df_add(acc, part[b][threadIdx.x * KS + c]);
+                            S[b] = acc.x;
+                            sl[b] = acc.y;
+                        }
+                        finish((cmp && l < L) ? qs[0].perm[off + i] : i, S, sl);
+                    }
                 }
             }
             __syncthreads();  // dh of layer l-1 fully consumed
