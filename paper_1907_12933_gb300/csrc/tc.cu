@@ -168,9 +168,13 @@ __device__ __forceinline__ uint32_t sw_off(int r, int u) {
 template <bool SPLIT, bool BF>
 __global__ void __launch_bounds__(TC_THREADS, 1)
 k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restrict__ qs, int nq,
-     const unsigned long long* __restrict__ tile_prefix, const QEntry* __restrict__ gather,
+     const unsigned long long* __restrict__ tile_prefix, const QEntry* __restrict__ gather_in,
      const unsigned long long* __restrict__ gcount, unsigned long long gcap, Queue out,
      int out_level, unsigned long long* claim_ctr) {
+    // the split pass always reads a queue (gather mode), the screen always ranges
+    // (launch_k): the mode is known at compile time, and each instantiation keeps
+    // only its own mode's code
+    const QEntry* __restrict__ const gather = SPLIT ? gather_in : nullptr;
     extern __shared__ uint8_t smem_raw[];
     // 1024-byte aligned by pointer arithmetic on the shared array, so the compiler
     // keeps every access in the shared address space
@@ -182,7 +186,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
     // range mode: tiles of query q are tile_prefix[q] .. tile_prefix[q+1]-1, each
     // tile 128 consecutive indices from (lo & ~31); gather mode: 128 queue entries
     unsigned long long ntiles, gn = 0;
-    if (gather) {
+    if (SPLIT) {
         gn = *gcount;
         if (gn > gcap) gn = gcap;
         ntiles = (gn + MROWS - 1) / MROWS;
@@ -191,9 +195,9 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
     }
     // range mode: tiles from the claim counter (in order, under the time budget);
     // gather mode: statically strided
-    unsigned long long* const ctr = gather ? nullptr : claim_ctr;
+    unsigned long long* const ctr = SPLIT ? nullptr : claim_ctr;
     const unsigned long long deadline =
-        (!gather && qs[0].budget_ns) ? qs[0].cnt->t0 + qs[0].budget_ns : 0ull;
+        (!SPLIT && qs[0].budget_ns) ? qs[0].cnt->t0 + qs[0].budget_ns : 0ull;
 
     auto bar = [&](int i) { return tc::smem_u32(&S.bars[i]); };
 
@@ -361,7 +365,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 tc::mbar_arrive(bar(CLAIMB((ti + 1) & 1)));
             }
             int q = 0;
-            if (!gather) {
+            if (!SPLIT) {
                 int a = 0, b = nq - 1;
                 while (a < b) {
                     const int mid = (a + b + 1) >> 1;
@@ -375,7 +379,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
             unsigned long long Rni = 1;
             for (int i = 0; i < ni; ++i) Rni *= (unsigned long long)R;
             const unsigned long long base = Q.lo & ~31ull;
-            const unsigned long long gq = gather ? 0 : g - tile_prefix[q];
+            const unsigned long long gq = SPLIT ? 0 : g - tile_prefix[q];
             if (q != S.curq) {  // this CTA's sign changes belong to the previous query
                 const int cq = S.curq;
                 if (cq >= 0)
@@ -397,7 +401,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
             // consecutive, so their outer prefixes t / R^ni (the digits above the ni
             // inner ones) are consecutive integers from p0, that of the tile's first
             // index in [lo, hi): row r uses prefix slot t / R^ni - p0 when below PMAX.
-            const bool pre = !gather && s > ni;
+            const bool pre = !SPLIT && s > ni;
             unsigned long long p0 = 0, np_need = 0;
             if (pre) {
                 const unsigned long long t0 = base + gq * MROWS;
@@ -414,7 +418,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
             const int np = (int)(np_need < (unsigned long long)PMAX ? np_need : PMAX);
             // fast layer-1 path: every valid row has its prefix slot (or s = 2: none needed);
             // with R <= kStageR its inner-digit tables come from shared memory
-            const bool fast_t = !gather && ((ni == 2 && s > 2 && np_need <= (unsigned long long)PMAX) || s == 2);
+            const bool fast_t = !SPLIT && ((ni == 2 && s > 2 && np_need <= (unsigned long long)PMAX) || s == 2);
             const bool stage_t = fast_t && R <= kStageR;
             // layer-1 tables (compacted: column j' holds neuron perm_1[j']) and the
             // number of columns the dense layer 2 reads
@@ -435,7 +439,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 const int r = wtid;
                 unsigned long long t = 0;
                 bool ok;
-                if (gather) {
+                if (SPLIT) {
                     const unsigned long long idx = g * MROWS + r;
                     ok = idx < gn;
                     if (ok) t = gather[idx].t;
@@ -462,8 +466,8 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 } else {
                     decode_digits(ok ? t : 0, s, R, d);
                 }
-                if (ok && !gather && Q.filter) ok = in_filter(Q, d);  // L2 ball / shell
-                if (!gather && Q.filter) {  // points that pass the filter are counted here
+                if (ok && !SPLIT && Q.filter) ok = in_filter(Q, d);  // L2 ball / shell
+                if (!SPLIT && Q.filter) {  // points that pass the filter are counted here
                     const unsigned vm = __ballot_sync(0xffffffffu, ok);
                     if ((wtid & 31) == 0 && vm) atomicAdd(&Q.cnt->n_points, (unsigned long long)__popc(vm));
                 }
@@ -1047,7 +1051,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     const bool adv = rv && !bad && vv == 1;
                     if (hf == 0) {
                         queue_push_warp(out, bad, t, (unsigned)q, Q.cnt, out_level);
-                    } else if (hf == 1 && !gather) {
+                    } else if (hf == 1 && !SPLIT) {
                         const unsigned m = __ballot_sync(0xffffffffu, adv);
                         if (m && lane == 0) {
                             atomicAdd(&Q.cnt->n_adv, (unsigned long long)__popc(m));
@@ -1070,7 +1074,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 }
                 tc::named_bar_sync(1, NWT);
                 // time to verdict: a screen tile done, or this tile's queued points resolved
-                if (wtid == 0) work_done(Q.cnt, gather ? (g * MROWS + MROWS <= gn ? MROWS : gn - g * MROWS) : 1);
+                if (wtid == 0) work_done(Q.cnt, SPLIT ? (g * MROWS + MROWS <= gn ? MROWS : gn - g * MROWS) : 1);
             }
         }
     }
