@@ -356,13 +356,23 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
         const float uacc_base = P.acc_unit * (SPLIT ? 3.f : 1.f);  // measured by tc_f16_selftest
         (void)H0;
         const bool cmp = P.compact != 0;  // compacted columns (one query): positions -> neurons by perm
+        // The next tile's claim and the previous tile's count of finished work (time to
+        // verdict) are global atomics: a worker thread without a row, a prefix sum or a
+        // pixel in the decode issues them at the tile's start and publishes the claim at
+        // the decode's end, so their latency overlaps the decode.
+        constexpr int kAtomT = MROWS;
+        static_assert(kAtomT < kPfx0 && kAtomT < MROWS + 64, "the atomics' thread has no decode row");
+        Counters* pend_c = nullptr;    // thread kAtomT: the previous tile's finished units
+        unsigned long long pend_n = 0;
         for (uint32_t ti = 0;; ++ti) {
             if (*abortp) break;
             const unsigned long long g = S.claim[ti & 1];  // written before a barrier the workers passed
             if (g == kNoTile) break;
-            if (wtid == 0) {  // claim the next tile now: the producer prefetches its weights
-                S.claim[(ti + 1) & 1] = claim_tile(ctr, ti + 1, ntiles, deadline);
-                tc::mbar_arrive(bar(CLAIMB((ti + 1) & 1)));
+            unsigned long long nxt = kNoTile;
+            if (wtid == kAtomT) {
+                nxt = claim_tile(ctr, ti + 1, ntiles, deadline);
+                if (pend_n) work_done(pend_c, pend_n);  // after the barrier that followed its pushes
+                pend_n = 0;
             }
             int q = 0;
             if (!SPLIT) {
@@ -564,6 +574,10 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     const unsigned m0 = __ballot_sync(0xffffffffu, cr0), m1 = __ballot_sync(0xffffffffu, cr1);
                     if ((e & 31) == 0) S.k1cm[e >> 5] = make_uint2(m0, m1);
                 }
+            }
+            if (wtid == kAtomT) {  // the producer and MMA warps learn the next tile
+                S.claim[(ti + 1) & 1] = nxt;
+                tc::mbar_arrive(bar(CLAIMB((ti + 1) & 1)));
             }
             cp_async_wait_all();  // this thread's table copies (staged at once) have landed
             tc::named_bar_sync(1, NWT);
@@ -1074,9 +1088,13 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 }
                 tc::named_bar_sync(1, NWT);
                 // time to verdict: a screen tile done, or this tile's queued points resolved
-                if (wtid == 0) work_done(Q.cnt, SPLIT ? (g * MROWS + MROWS <= gn ? MROWS : gn - g * MROWS) : 1);
+                if (wtid == kAtomT) {  // counted at the next tile's start (or below)
+                    pend_c = Q.cnt;
+                    pend_n = SPLIT ? (g * MROWS + MROWS <= gn ? MROWS : gn - g * MROWS) : 1;
+                }
             }
         }
+        if (wtid == kAtomT && pend_n) work_done(pend_c, pend_n);
     }
     // ---- teardown: wait for outstanding tensor-core work, release TMEM
     tc::tc_fence_before();
