@@ -731,9 +731,32 @@ k_df32(NetView net, const QueryView* __restrict__ qs, int nq, const QEntry* __re
                 }
             }
             __syncthreads();
-            if (threadIdx.x == 0) work_done(Q.cnt, 1);  // time to verdict: this point is resolved
+        }
+        // time to verdict: the iteration's points are resolved (the queued ones stay
+        // counted through their push), one count per query; a thread that decodes no
+        // point reads them before the barrier and adds them after it, while the next
+        // iteration decodes
+        constexpr int kCntT = TDF - 1;
+        static_assert(kCntT >= PB, "the counting thread decodes no point");
+        unsigned cq[PB];
+        unsigned long long cn[PB];
+        int ncq = 0;
+        if (threadIdx.x == kCntT) {
+#pragma unroll
+            for (int b = 0; b < PB; ++b) {
+                if (!valid[b]) continue;
+                int k = 0;
+                while (k < ncq && cq[k] != qpt[b]) ++k;
+                if (k == ncq) {
+                    cq[ncq] = qpt[b];
+                    cn[ncq++] = 0;
+                }
+                ++cn[k];
+            }
         }
         __syncthreads();
+        if (threadIdx.x == kCntT)
+            for (int k = 0; k < ncq; ++k) work_done(qs[cq[k]].cnt, cn[k]);
     }
 }
 
