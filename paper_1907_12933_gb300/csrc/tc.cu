@@ -364,6 +364,9 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
         static_assert(kAtomT < kPfx0 && kAtomT < MROWS + 64, "the atomics' thread has no decode row");
         Counters* pend_c = nullptr;    // thread kAtomT: the previous tile's finished units
         unsigned long long pend_n = 0;
+        // the query whose staged column constants (layer 1; the drain of the one hidden
+        // layer of a two-hidden-layer net) are in shared memory: restaged on a change
+        int kq1 = -1, kqd = -1;
         for (uint32_t ti = 0;; ++ti) {
             if (*abortp) break;
             const unsigned long long g = S.claim[ti & 1];  // written before a barrier the workers passed
@@ -553,7 +556,9 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 S.npref = np;
                 S.fast = fast_t;
             }
-            if (!fast_t) {  // general layer-1 path: the query's s weight rows, once per tile
+            // general layer-1 path: the query's s weight rows, once per tile; the split
+            // pass (one query, every tile on this path, nothing else in the region) once
+            if (!fast_t && (!SPLIT || ti == 0)) {
                 const int Wc = 64 * S.kch[2];
                 if (s * Wc <= kWgen)
                     for (int e = wtid; e < s * Wc; e += NWT) {
@@ -562,8 +567,8 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                             jj >= H1 ? 0.f : (cmp ? Q.w1c[(size_t)p * H1 + jj] : net.WT[1][(size_t)Q.pix[p] * H1 + jj]);
                     }
             }
-            {   // the query's layer-1 column constants, for the build below: warp c of the
-                // loop takes chunk c (its lanes the column pairs), whole warps only
+            if (q != kq1) {  // the query's layer-1 column constants, for the build below: warp c
+                // of the loop takes chunk c (its lanes the column pairs), whole warps only
                 const float4* __restrict__ kcl = cmp ? Q.kcolc : Q.kcol;
                 for (int e = wtid; e < 32 * S.kch[2]; e += NWT) {
                     const float4 kA0 = kcl[4 * e], kB0 = kcl[4 * e + 1];
@@ -575,6 +580,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                     if ((e & 31) == 0) S.k1cm[e >> 5] = make_uint2(m0, m1);
                 }
             }
+            kq1 = q;
             if (wtid == kAtomT) {  // the producer and MMA warps learn the next tile
                 S.claim[(ti + 1) & 1] = nxt;
                 tc::mbar_arrive(bar(CLAIMB((ti + 1) & 1)));
@@ -817,8 +823,8 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
             const int r = 32 * qd + lane;
             for (int l = 2; l < L; ++l) {
                 const TcLayer& ly = P.ly[l];
-                {   // this layer's column constants (the previous readers passed a barrier);
-                    // their loads overlap the wait for the layer's MMAs
+                if (L > 3 || q != kqd) {  // this layer's column constants (the previous readers
+                    // passed a barrier); their loads overlap the wait for the layer's MMAs
                     const float4* __restrict__ kcl = (cmp ? Q.kcolc : Q.kcol) + 2 * net.noff[l];
                     for (int e = wtid; e < S.np[l]; e += NWT) {
                         const float4 kA = kcl[2 * e], kB = kcl[2 * e + 1];
@@ -828,6 +834,7 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                         S.kd2[e] = make_float2(kB.y, kB.z);
                     }
                 }
+                kqd = q;
                 tc::mbar_wait(bar(DFULL), dit & 1, abortp);
                 ++dit;
                 tc::tc_fence_after();
