@@ -120,7 +120,8 @@ __device__ __forceinline__ float warp_sum_ru(float v) {
 constexpr int CKC = 2;                       // chunks per checkpoint segment
 constexpr float kUseg = 0x1.00002p-24f * (float)(CKC * KC);  // u' CKL, rounded up
 
-// Register-blocked dense layer for a tile of one query (paired slot widths):
+// Register-blocked dense layer (paired slot widths; the epilogue loads each
+// column's constants once for a tile of one query, per point otherwise):
 // lane = (point group pg of 4, column group ng of 8); each lane accumulates 4
 // points x QL columns, warps split the tile into blocks of 16 points x CBW
 // columns. A weight float4 is read by 8 distinct lanes (one 128-byte
@@ -132,7 +133,9 @@ constexpr float kUseg = 0x1.00002p-24f * (float)(CKC * KC);  // u' CKL, rounded 
 // another order (bounds that hold for any order).
 template <int PPW, int NQ, int NQA>
 __device__ __forceinline__ void dense_blocked(SimtSmem<PPW, NQ>& S, const NetView& net,
-                                              const QueryView& Q, int l, int warp, int lane, bool cmp) {
+                                              const QueryView* __restrict__ qs, int l, int warp, int lane,
+                                              bool cmp, bool oneq) {
+    const QueryView& Q = qs[0];  // compacted columns: one query (cmp implies oneq)
     constexpr int HS = SimtSmem<PPW, NQ>::HS;
     constexpr int MT = SimtSmem<PPW, NQ>::MT;
     constexpr int HW = 32 * NQA;
@@ -235,8 +238,10 @@ __device__ __forceinline__ void dense_blocked(SimtSmem<PPW, NQ>& S, const NetVie
     unsigned vmask = 0u;
     float X[4], nsum[4], usum[4];
     uint32_t uncb[4], flipb[4];  // per slot: uncertain sign, certain change
+    int qi[4];                   // each point's query
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
+        qi[i] = oneq ? 0 : S.q[mrow[i]];
         vmask |= (unsigned)(S.valid[mrow[i]] != 0) << i;
         X[i] = __fmaf_ru(gl, S.N[mrow[i]], S.E[mrow[i]]);
         nsum[i] = usum[i] = 0.f;
@@ -252,15 +257,29 @@ __device__ __forceinline__ void dense_blocked(SimtSmem<PPW, NQ>& S, const NetVie
             const int no = (cmp && l < L) ? (n < cntN ? Q.perm[off + n] : -1) : n;
             if (n < N && no >= 0) {
                 const int gi = off + no;
-                const float ub = __ldg(&Q.ub32[gi]), rnn = __ldg(&rn[no]), th = __ldg(&Q.thr[gi]);
-                float c1 = 0.f, c2 = 0.f;
-                if (l < L) {
-                    c1 = __ldg(&Q.c1[gi]);
-                    c2 = __ldg(&Q.c2[gi]);
+                const float rnn = __ldg(&rn[no]);
+                // the column's constants: once for the warp's points of one query, else per point
+                float ub = 0.f, th = 0.f, c1 = 0.f, c2 = 0.f;
+                if (oneq) {
+                    ub = __ldg(&Q.ub32[gi]);
+                    th = __ldg(&Q.thr[gi]);
+                    if (l < L) {
+                        c1 = __ldg(&Q.c1[gi]);
+                        c2 = __ldg(&Q.c2[gi]);
+                    }
                 }
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
                     if (!((vmask >> i) & 1u)) continue;
+                    if (!oneq) {
+                        const QueryView& Qi = qs[qi[i]];
+                        ub = __ldg(&Qi.ub32[gi]);
+                        th = __ldg(&Qi.thr[gi]);
+                        if (l < L) {
+                            c1 = __ldg(&Qi.c1[gi]);
+                            c2 = __ldg(&Qi.c2[gi]);
+                        }
+                    }
                     const float du = (e & 1) ? acc[i][t][e >> 1].y : acc[i][t][e >> 1].x;
                     const float u = ub + du;
                     // |du - exact| <= ||W_i|| (gamma N + E) (a priori), plus the column's threshold
@@ -291,7 +310,8 @@ __device__ __forceinline__ void dense_blocked(SimtSmem<PPW, NQ>& S, const NetVie
     for (int i = 0; i < 4; ++i) {
         if (!((vmask >> i) & 1u)) continue;
         const int m = mrow[i];
-        if (uncb[i] && Q.flip) S.unc[m] = 1;  // signs matter only for coverage
+        const QueryView& Qi = qs[qi[i]];
+        if (uncb[i] && Qi.flip) S.unc[m] = 1;  // signs matter only for coverage
         while (flipb[i]) {
             const int slot = __ffs(flipb[i]) - 1;
             flipb[i] &= flipb[i] - 1u;
@@ -299,7 +319,7 @@ __device__ __forceinline__ void dense_blocked(SimtSmem<PPW, NQ>& S, const NetVie
             const int n = (cmp && l < L) ? Q.perm[off + np] : np;  // neuron
             const int idx = atomicAdd(&S.fcnt[m][l], 1);
             if (idx < FCAP) S.flist[m][l][idx] = (short)n;
-            if (Q.flip) set_bit_once(Q.flip, off + n);
+            if (Qi.flip) set_bit_once(Qi.flip, off + n);
         }
     }
     // per point: sums over the 8 lanes of its group, then over the NCB column blocks
@@ -339,7 +359,7 @@ __device__ __forceinline__ void dense_blocked(SimtSmem<PPW, NQ>& S, const NetVie
         if (l < L) {
             const float Nl = norm_up(ns);
             // lambda (rounding) + lambda sigma_l E_{l-1} + kvec_l + u N_l
-            float El = __fadd_ru(rl, Q.kvec[l]);
+            float El = __fadd_ru(rl, qs[oneq ? 0 : S.q[m]].kvec[l]);
             El = __fmaf_ru(net.lamsig[l], Ein, El);
             El = __fmaf_ru(0x1p-24f, Nl, El);
             if (net.act == ACT_SIGMOID) El = __fmaf_ru(0x1p-26f, norm_up(us), El);
@@ -356,14 +376,12 @@ template <int PPW, int NQ, int NQA>
 __device__ __forceinline__ void dense_layer(SimtSmem<PPW, NQ>& S, const NetView& net,
                                             const QueryView* __restrict__ qs, int l, int warp,
                                             int lane, bool cmp, bool oneq) {
-    // one query and a paired slot width that the blocked layout tiles
+    // a paired slot width that the blocked layout tiles
     constexpr bool BLK = NQA % 4 == 0 && PPW % 2 == 0 && PPW <= 16 && (NQA * PPW) % 16 == 0 &&
                          NQA * PPW <= 128;
     if constexpr (BLK) {
-        if (oneq) {
-            dense_blocked<PPW, NQ, (BLK ? NQA : 4)>(S, net, qs[0], l, warp, lane, cmp);
-            return;
-        }
+        dense_blocked<PPW, NQ, (BLK ? NQA : 4)>(S, net, qs, l, warp, lane, cmp, oneq);
+        return;
     }
     constexpr int HS = SimtSmem<PPW, NQ>::HS;
     constexpr int HW = 32 * NQA;  // columns of the weight chunk in use
