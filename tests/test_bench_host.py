@@ -116,3 +116,18 @@ def test_reference_arm_times_each_step_on_its_own_sample(monkeypatch):
     assert 1 <= m <= n and cores >= 1
     assert rate == pytest.approx(m / (ms_step / 1e3), rel=1e-9)
     assert sample.startswith(f"3 steps of {m} contiguous points")
+
+
+def test_passes_without_their_own_time_are_left_out():
+    """The wide-layer path rechecks each chunk's points inside the first pass's
+    timed region: those passes carry no separate time (a few microseconds of
+    event markers) and get no roofline of their own; they are named instead."""
+    dims, s, n = [784, 1024, 1024, 1024, 10], 5, 28_629_151
+    pk = {"bf16_tflops": 2000.0, "sm_max_mhz": 2000.0}
+    sums = _sums(5000.0, [0.002, 0.002, 0.002, 0.006], [0, 27_989_462, 619_518, 1316])
+    r = bench.pass_rooflines("bf16", dims, s, n, sums, pk, "measured")
+    names = [p["kernel"] for p in r["passes"]]
+    assert "FP32 pass" not in names and "double-float pass" not in names and "FP64 pass" not in names
+    assert r["passes_timed_in_screen"] == ["FP32 pass", "double-float pass", "FP64 pass"]
+    assert r["kernel"] == "screen (first pass over every point)"
+    assert r["frac"] < 1.0
