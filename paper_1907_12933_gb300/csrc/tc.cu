@@ -542,7 +542,10 @@ k_tc(const __grid_constant__ TcParams P, NetView net, const QueryView* __restric
                 decode_digits(p0, s - ni, R, pd);
                 for (int k = 0; k < np; ++k) {
                     for (int j = wtid - kPfx0; j < W1cols; j += NWT - kPfx0) {
+                        // unrolled so that the table loads are in flight together
+                        // (the sum still runs over p in order)
                         float acc = 0.f;
+#pragma unroll 4
                         for (int p = 0; p < s - ni; ++p) acc += __ldg(&tabq[((size_t)p * R + pd[p]) * H1 + j]);
                         S.souter[k][j] = acc;
                     }
