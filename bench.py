@@ -221,10 +221,10 @@ class Clocks:
 # Keyed by (workload, precision, coverage, s, k); other configurations report null.
 PROFILED_TRAFFIC = {
     ("mlp784x512x512_relu_s6k7", "bf16", True, 6, 7): {
-        "screen (first pass over every point)": 1193728 + 1054464,
-        "split tensor pass": 50305792 + 94208,
-        "FP32 pass": 22736384 + 102144,
-        "double-float pass": 2300160 + 2816,
+        "screen (first pass over every point)": 1509632 + 1111808,
+        "split tensor pass": 50135040 + 103168,
+        "FP32 pass": 22624000 + 96000,
+        "double-float pass": 2200576 + 1536,
     },
 }
 
