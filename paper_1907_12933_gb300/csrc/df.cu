@@ -368,8 +368,9 @@ __device__ __forceinline__ void block_sums_ru(float (&v)[M], float* red) {
     }
 }
 
-// Threads per position of a layer of Nn positions with K inputs: a narrow
-// layer (at most half a block) splits its dot products into chunks of k.
+// Threads per position of a round of Nn positions with K inputs: a round of at
+// most half a block (a narrow layer, or a layer's last round) splits its dot
+// products into chunks of k.
 __device__ __forceinline__ int df_split(int Nn, int K) {
     if (2 * Nn > TDF || K < 64) return 1;
     const int ks = TDF / Nn;
